@@ -1,0 +1,185 @@
+/*
+ * pitn.h -- C ABI of the parallel-in-time Newton ODE solver (arXiv 2511.01465)
+ * for NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 2.1, eq. 2.1):  dx/dt = f(x), x(t0) = x0, discretised by the
+ * explicit Euler one-step map phi(x) = x + h f(x) (eq. 2.2) on N steps.
+ * The solver finds xi = [x_1 .. x_N] with h(xi) = 0, where
+ *     h_n = x_n - phi(x_{n-1}),  n = 1..N                       (eq. 3.8)
+ * by Newton's method (eqs. 3.10-3.11).  Each Newton step solves the affine
+ * recursion  dx_1 = -h_1,  dx_n = J_{n-1} dx_{n-1} - h_n  (eq. 3.13), with
+ * J = dphi/dx, as a parallel prefix scan over the affine elements
+ * (J_n, -h_{n+1}) combined by (A2,b2) o (A1,b1) = (A2 A1, A2 b1 + b2)
+ * (eq. 3.3; element 1 is the earlier one).  The solve stops when
+ * ||h(xi)||_inf <= tol (Sec. 4), when a residual entry is not finite, or
+ * after max_iter Newton updates.
+ *
+ * Conventions shared by every entry point
+ *   - Arrays are FP64 (int64/int32 where stated), contiguous, row-major.
+ *     A pointer may be device memory of the current CUDA device or host
+ *     memory (pageable or pinned); the library detects which with
+ *     cudaPointerGetAttributes and stages host arrays through device memory.
+ *     All array arguments of one call should live on the same side.
+ *   - Ownership: the caller owns every array.  The library never frees or
+ *     keeps a pointer after the call returns.  Scratch memory comes from a
+ *     per-device cache that grows on demand; pitn_release_workspace frees it.
+ *   - Streams: work runs on opt->stream (pitn_solve_ex etc.) or on the
+ *     legacy default stream.  Every call blocks until its results are
+ *     available on the host (it must read the device status word).
+ *   - Errors: every call returns a pitn_status.  Argument errors are detected
+ *     on the host before any device work and leave all outputs untouched.
+ *     Nothing is thrown across the ABI.
+ *   - Counting: `iters` is the number of Newton updates applied; the paper's
+ *     K (number of residual evaluations) is iters + 1.
+ */
+#ifndef PITN_H
+#define PITN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes.  Non-negative codes describe a completed solve. */
+typedef enum {
+    PITN_OK = 0,              /* ||h||_inf <= tol reached */
+    PITN_NOT_CONVERGED = 1,   /* max_iter updates applied, tolerance not met */
+    PITN_NONFINITE = 2,       /* a residual entry, or (plain Newton) a Newton
+                                 correction, was NaN/Inf; the trajectory holds
+                                 the last iterate whose residual was finite */
+    PITN_EINVAL = -1,         /* bad argument (nothing was written) */
+    PITN_ENOMEM = -2,         /* device or host allocation failed */
+    PITN_ECUDA = -3,          /* a CUDA runtime call failed */
+    PITN_ETIMEOUT = -4,       /* an in-kernel wait exceeded its time limit */
+    PITN_EUNSUPPORTED = -5    /* valid request this build does not implement */
+} pitn_status;
+
+/* ODE systems (right-hand sides f; parameters in this order). */
+enum {
+    PITN_LORENZ63 = 1,   /* d = 3; params {sigma, rho, beta}:
+                            f = (sigma(y-x), x(rho-z)-y, xy-beta z) */
+    PITN_VDP = 2,        /* d = 2; params {mu}; state (x, dx/dt):
+                            f = (v, mu(1-x^2)v - x)  (Sec. 4.1, van der Pol) */
+    PITN_LINEAR_OSC = 3, /* d = 2; params {omega, zeta}; state (x, dx/dt):
+                            f = (v, -omega^2 x - 2 zeta omega v) (affine) */
+    PITN_FKPP = 4        /* d >= 3 interior nodes of [0,1], spacing 1/(d+1),
+                            zero Dirichlet ends; params {D}:
+                            f_i = D (u_{i-1} - 2u_i + u_{i+1})/dx^2 + u_i(1-u_i) */
+};
+
+/* Arithmetic of the Newton step (the residual and the update are always FP64). */
+enum {
+    PITN_PREC_FP64 = 0,        /* every operation in FP64 */
+    PITN_PREC_MIXED_BF16 = 1   /* d >= 64 only: dense composes of the scan on
+                                  tensor cores (BF16 operands, FP32
+                                  accumulation) in the delta form A = J - I;
+                                  an inexact Newton step */
+};
+
+/* Per-solve outcome. */
+typedef struct {
+    int32_t iters;        /* Newton updates applied (paper K - 1) */
+    int32_t status;       /* PITN_OK / PITN_NOT_CONVERGED / PITN_NONFINITE */
+    double final_res;     /* ||h(xi)||_inf of the returned trajectory */
+    int64_t guard_index;  /* guard cut q of the last update, N if none */
+} pitn_result;
+
+/* Options for the _ex entry points; a zero-initialised struct (or NULL)
+ * selects the defaults shown. */
+typedef struct {
+    int32_t precision;      /* PITN_PREC_*; default FP64 */
+    int32_t tile_elems;     /* elements per thread of the scan; 0 = autotuned */
+    double guard_B;         /* <= 0: the paper's plain Newton (default).
+                               > 0: divergence guard (not in the paper): after
+                               each Newton step, q = first step index whose
+                               correction has an entry that is not finite or
+                               exceeds guard_B in magnitude; steps before q
+                               are updated, steps from q on are set to the
+                               last updated state (x0 if q = 0). */
+    const double* guess;    /* NULL: constant guess x_n = x0; else [N][d] */
+    void* stream;           /* cudaStream_t; NULL = legacy default stream */
+    double* res_history;    /* NULL or host array of max_iter + 1 doubles:
+                               ||h||_inf at every residual evaluation */
+} pitn_options;
+
+/*
+ * Solve one IVP by the paper's plain Newton method in FP64.
+ *   system_id  PITN_LORENZ63 / PITN_VDP / PITN_LINEAR_OSC / PITN_FKPP
+ *   params     system parameters (see the enum), host or device
+ *   x0         initial value x_0, [d]
+ *   h          step size (finite, > 0)
+ *   N          number of steps (>= 1); the trajectory has N states x_1..x_N
+ *   d          state dimension; must match the system
+ *   tol        stop when ||h(xi)||_inf <= tol (finite, >= 0)
+ *   max_iter   maximum Newton updates (>= 0; 0 evaluates the residual only)
+ *   traj_out   [N][d] output x_1..x_N
+ * Returns the solve status (PITN_OK / PITN_NOT_CONVERGED / PITN_NONFINITE)
+ * or a negative error code.
+ */
+int pitn_solve(int system_id, const double* params, const double* x0, double h, int64_t N, int d,
+               double tol, int max_iter, double* traj_out);
+
+/* pitn_solve with options (NULL = defaults) and an optional result record. */
+int pitn_solve_ex(int system_id, const double* params, const double* x0, double h, int64_t N,
+                  int d, double tol, int max_iter, double* traj_out, const pitn_options* opt,
+                  pitn_result* result);
+
+/*
+ * Solve B independent IVPs of one system and uneven lengths N[b] in one
+ * segmented scan per Newton iteration (not in the paper: its experiments run
+ * one IVP at a time).  Each IVP runs its own Newton iteration with its own
+ * stopping test; an IVP that has stopped is frozen (neither its trajectory
+ * nor its count changes), and the launch sequence ends when every IVP has
+ * stopped or max_iter is reached.
+ *   params     [B][P], x0 [B][d], h [B], N [B] (each >= 1)
+ *   traj_out   [sum N][d]: IVP b occupies rows offsets[b] .. offsets[b+1]-1
+ *   offsets_out [B+1]: exclusive prefix sum of N (int64)
+ *   iters_out, status_out [B] (int32); res_out [B] (nullable) final norms
+ *   opt        guard_B, stream and tile_elems are honoured; precision must be
+ *              FP64; guess and res_history must be NULL.
+ * Returns PITN_OK when every IVP converged, PITN_NOT_CONVERGED when one did
+ * not (see status_out), or a negative error code.
+ */
+int pitn_solve_batch(int system_id, int64_t B, const double* params, const double* x0,
+                     const double* h, const int64_t* N, int d, double tol, int max_iter,
+                     double* traj_out, int64_t* offsets_out, int32_t* iters_out,
+                     int32_t* status_out, double* res_out, const pitn_options* opt);
+
+/*
+ * Gradients of a loss L(x_1..x_N) of converged trajectories with respect to
+ * x0 and the parameters, for B IVPs laid out as in pitn_solve_batch (not in
+ * the paper; the transposed, reverse-time form of the recursion of eq. 3.13):
+ *   lambda_N = G_N,  lambda_n = J_n^T lambda_{n+1} + G_n,
+ *   dL/dx0 = J_0^T lambda_1,  dL/dp = sum_n (dphi/dp(x_n))^T lambda_{n+1},
+ * with G_n = grad_traj row n-1 (nullable) plus grad_xN on G_N (nullable).
+ * The reverse recursion runs as an affine scan over (J^T, G); the scan keeps
+ * one checkpoint (block product and block offset) per ckpt_every steps
+ * (0 = 1024) and recomputes J_n from traj.
+ *   traj       [sum N][d] forward trajectories (x_1..x_N per IVP)
+ *   grad_x0_out [B][d], grad_params_out [B][P]
+ */
+int pitn_backward(int system_id, int64_t B, const double* params, const double* x0,
+                  const double* h, const int64_t* N, int d, const double* traj,
+                  const double* grad_traj, const double* grad_xN, int ckpt_every,
+                  double* grad_x0_out, double* grad_params_out, const pitn_options* opt);
+
+/* Number of parameters of a system, or -1 for an unknown id. */
+int pitn_num_params(int system_id);
+
+/* Static description of a code. */
+const char* pitn_status_string(int code);
+
+/* Frees the cached scratch memory of the current device.  Not to be called
+ * while a solve is running on another host thread. */
+int pitn_release_workspace(void);
+
+/* Number of kernel launches the library issued since the process started
+ * (all devices, all entry points). */
+int64_t pitn_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PITN_H */

@@ -1,0 +1,96 @@
+// common.cuh -- device helpers shared by the solver's kernels: memory-order
+// primitives for inter-CTA signalling, bounded waits, a grid barrier for
+// cooperative launches, and the workspace / launch bookkeeping of the host side.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <float.h>
+
+#include "pitn.h"
+
+namespace pitn {
+
+// ---------------------------------------------------------------------------
+// Memory-order primitives (gpu scope).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// L2-coherent load (bypasses L1, which other SMs' writes do not invalidate).
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+
+// Every spin-wait in the library gives up after this long and raises
+// PITN_ETIMEOUT instead of hanging the device.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
+
+// Error word written by kernels (0 = fine).
+__device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Grid-wide barrier for cooperative launches (all CTAs co-resident).
+// count/gen live in device memory zeroed before the launch.  Returns false
+// (and sets *err) when the wait times out or another CTA already failed.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
+                                             int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g = ld_acquire_u32(gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            st_release_u32(gen, g + 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_u32(gen) == g) {
+                if (*(volatile int*)err != 0) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                    raise_error(err, PITN_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        if (*(volatile int*)err != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    __threadfence();
+    return s_ok != 0;
+}
+
+// atomicMax on non-negative doubles (and NaN, which orders above +inf) via
+// their IEEE bit patterns.
+__device__ __forceinline__ void atomic_max_abs_bits(unsigned long long* p, double a) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(fabs(a)));
+}
+
+}  // namespace pitn
+
+// ---------------------------------------------------------------------------
+// Host-side helpers (implemented in api.cu).
+// ---------------------------------------------------------------------------
+namespace pitn_host {
+
+// Scratch memory cache of the current device; returns nullptr on failure.
+void* workspace(size_t bytes, int slot = 0);
+// Counts kernel launches issued by the library.
+void count_launch(int64_t n = 1);
+// Device properties of the current device (cached).
+const cudaDeviceProp& props();
+
+}  // namespace pitn_host

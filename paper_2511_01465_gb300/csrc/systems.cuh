@@ -1,0 +1,144 @@
+// systems.cuh -- small-state ODE systems for the fused Newton kernels.
+//
+// Each system describes the explicit Euler step map phi(x) = x + h f(x)
+// (eq. 2.2) through
+//   eval(xp, xc, r, jv):  r  = xc - phi(xp)            (one entry of h(xi), eq. 3.8)
+//                         jv = the entries of J = dphi/dx(xp) = I + h df/dx(xp)
+//                              that depend on xp (a compact Jacobian)
+//   jmul(jv, M, out):     out = J M   (M, out: D x D row-major)
+//   jvec(jv, v, out):     out = J v
+//   jtvec(jv, v, out):    out = J^T v           (adjoint)
+//   vjp_param(xp, v, g):  g += (dphi/dp(xp))^T v  (adjoint, g has P entries)
+// The compact form stores only the state-dependent entries of J, so an
+// element of the scan costs D + JN registers instead of D + D*D.
+#pragma once
+
+namespace pitn {
+
+// Lorenz-63: f = (s(y-x), x(r-z)-y, xy-b z).
+//   J = [[1-hs, hs, 0], [h(r-z), 1-h, -hx], [hy, hx, 1-hb]]
+struct Lorenz63 {
+    static constexpr int D = 3, JN = 3, P = 3;
+    double s, r, b, h;
+    double j00, j01, j11, j22;
+    __host__ __device__ void init(const double* p, double hh) {
+        s = p[0]; r = p[1]; b = p[2]; h = hh;
+        j00 = 1.0 - h * s; j01 = h * s; j11 = 1.0 - h; j22 = 1.0 - h * b;
+    }
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
+                                         double* jv) const {
+        double f0 = s * (xp[1] - xp[0]);
+        double f1 = xp[0] * (r - xp[2]) - xp[1];
+        double f2 = xp[0] * xp[1] - b * xp[2];
+        res[0] = xc[0] - (xp[0] + h * f0);
+        res[1] = xc[1] - (xp[1] + h * f1);
+        res[2] = xc[2] - (xp[2] + h * f2);
+        jv[0] = h * (r - xp[2]);
+        jv[1] = h * xp[0];
+        jv[2] = h * xp[1];
+    }
+    __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double m0 = M[j], m1 = M[3 + j], m2 = M[6 + j];
+            o[j] = j00 * m0 + j01 * m1;
+            o[3 + j] = jv[0] * m0 + j11 * m1 - jv[1] * m2;
+            o[6 + j] = jv[2] * m0 + jv[1] * m1 + j22 * m2;
+        }
+    }
+    __device__ __forceinline__ void jvec(const double* jv, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1], v2 = v[2];
+        o[0] = j00 * v0 + j01 * v1;
+        o[1] = jv[0] * v0 + j11 * v1 - jv[1] * v2;
+        o[2] = jv[2] * v0 + jv[1] * v1 + j22 * v2;
+    }
+    __device__ __forceinline__ void jtvec(const double* jv, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1], v2 = v[2];
+        o[0] = j00 * v0 + jv[0] * v1 + jv[2] * v2;
+        o[1] = j01 * v0 + j11 * v1 + jv[1] * v2;
+        o[2] = -jv[1] * v1 + j22 * v2;
+    }
+    __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
+        g[0] += h * (xp[1] - xp[0]) * v[0];
+        g[1] += h * xp[0] * v[1];
+        g[2] += -h * xp[2] * v[2];
+    }
+};
+
+// Van der Pol, state (x, v): f = (v, mu(1-x^2)v - x).
+//   J = [[1, h], [h(-2 mu x v - 1), 1 + h mu (1-x^2)]]
+struct VanDerPol {
+    static constexpr int D = 2, JN = 2, P = 1;
+    double mu, h;
+    __host__ __device__ void init(const double* p, double hh) { mu = p[0]; h = hh; }
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
+                                         double* jv) const {
+        double x = xp[0], v = xp[1];
+        double w = 1.0 - x * x;
+        double f1 = mu * w * v - x;
+        res[0] = xc[0] - (x + h * v);
+        res[1] = xc[1] - (v + h * f1);
+        jv[0] = h * (-2.0 * mu * x * v - 1.0);
+        jv[1] = 1.0 + h * mu * w;
+    }
+    __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
+        double m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
+        o[0] = m00 + h * m10;
+        o[1] = m01 + h * m11;
+        o[2] = jv[0] * m00 + jv[1] * m10;
+        o[3] = jv[0] * m01 + jv[1] * m11;
+    }
+    __device__ __forceinline__ void jvec(const double* jv, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1];
+        o[0] = v0 + h * v1;
+        o[1] = jv[0] * v0 + jv[1] * v1;
+    }
+    __device__ __forceinline__ void jtvec(const double* jv, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1];
+        o[0] = v0 + jv[0] * v1;
+        o[1] = h * v0 + jv[1] * v1;
+    }
+    __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
+        g[0] += h * (1.0 - xp[0] * xp[0]) * xp[1] * v[1];
+    }
+};
+
+// Damped linear oscillator, state (x, v): f = (v, -w^2 x - 2 z w v); J is constant.
+struct LinearOsc {
+    static constexpr int D = 2, JN = 1, P = 2;  // JN = 1 keeps arrays non-empty
+    double w, z, h, j10, j11;
+    __host__ __device__ void init(const double* p, double hh) {
+        w = p[0]; z = p[1]; h = hh;
+        j10 = -h * w * w; j11 = 1.0 - 2.0 * h * z * w;
+    }
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
+                                         double* jv) const {
+        double f1 = -w * w * xp[0] - 2.0 * z * w * xp[1];
+        res[0] = xc[0] - (xp[0] + h * xp[1]);
+        res[1] = xc[1] - (xp[1] + h * f1);
+        jv[0] = 0.0;
+    }
+    __device__ __forceinline__ void jmul(const double*, const double* M, double* o) const {
+        double m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
+        o[0] = m00 + h * m10;
+        o[1] = m01 + h * m11;
+        o[2] = j10 * m00 + j11 * m10;
+        o[3] = j10 * m01 + j11 * m11;
+    }
+    __device__ __forceinline__ void jvec(const double*, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1];
+        o[0] = v0 + h * v1;
+        o[1] = j10 * v0 + j11 * v1;
+    }
+    __device__ __forceinline__ void jtvec(const double*, const double* v, double* o) const {
+        double v0 = v[0], v1 = v[1];
+        o[0] = v0 + j10 * v1;
+        o[1] = h * v0 + j11 * v1;
+    }
+    __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
+        g[0] += h * (-2.0 * w * xp[0] - 2.0 * z * xp[1]) * v[1];
+        g[1] += h * (-2.0 * w * xp[1]) * v[1];
+    }
+};
+
+}  // namespace pitn

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every function include/pitn.h
+declares; argument checks that happen on the host before any device work
+return their codes without a GPU."""
+import ctypes
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pitn.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(pitn_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2511_01465_gb300 import build, pitn
+    if not os.path.exists(pitn.LIB_PATH) or not build.up_to_date():
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build libpitn.so")
+        build.build()
+    return pitn.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ("pitn_solve", "pitn_solve_ex", "pitn_solve_batch", "pitn_backward",
+              "pitn_status_string", "pitn_release_workspace", "pitn_num_params", "pitn_launch_count"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_params(lib):
+    from paper_2511_01465_gb300 import pitn as P
+    assert P.pitn_num_params(P.PITN_LORENZ63) == 3
+    assert P.pitn_num_params(P.PITN_VDP) == 1
+    assert P.pitn_num_params(P.PITN_LINEAR_OSC) == 2
+    assert P.pitn_num_params(P.PITN_FKPP) == 1
+    assert P.pitn_num_params(99) == -1
+    for code in (0, 1, 2, -1, -2, -3, -4, -5):
+        assert P.pitn_status_string(code)
+
+
+def test_argument_errors_are_detected_on_the_host(lib):
+    from paper_2511_01465_gb300 import pitn as P
+    p = np.array([10.0, 28.0, 8 / 3])
+    x0 = np.ones(3)
+    out = np.zeros((10, 3))
+    E = P.PITN_EINVAL
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 0, 3, 1e-10, 5, out) == E        # N = 0
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 10, 2, 1e-10, 5, out) == E       # d mismatch
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, -1e-3, 10, 3, 1e-10, 5, out) == E      # h < 0
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, float("nan"), 10, 3, 1e-10, 5, out) == E
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, -1.0, 5, out) == E        # tol < 0
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, -1, out) == E      # max_iter < 0
+    assert P.pitn_solve(77, p, x0, 1e-3, 10, 3, 1e-10, 5, out) == E                    # system
+    assert P.pitn_solve(P.PITN_LORENZ63, None, x0, 1e-3, 10, 3, 1e-10, 5, out) == E    # null
+    assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, None) == E
+    assert P.pitn_solve(P.PITN_FKPP, np.ones(1), np.ones(200), 1e-3, 10, 200, 1e-10, 5,
+                        np.zeros((10, 200))) == E                                        # d > 128
+    opt = P.make_options(precision=P.PITN_PREC_MIXED_BF16)
+    rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+    assert rc == E                                                                       # mixed needs d >= 64
+    assert not out.any()  # nothing written on an argument error
