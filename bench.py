@@ -41,14 +41,22 @@ def load_peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-# FP64 peak of a GB300 (nominal 1.25 TFLOP/s dense FP64, FMA = 2 flops).
+# ALU peaks of a GB300 from unit counts and clocks: 152 SMs at 2.07 GHz;
+# FP64: nominal 1.25 TFLOP/s dense (FMA = 2 flops);
+# FP32: 128 FP32 lanes per SM -> 152 * 128 * 2 * 2.07e9 = 80.5 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# FP64 flops per step per Newton pass executed by the fused small-state
-# kernel (residual + compact Jacobian + thread fold + replay + update; FMA
-# counted as 2), counted from the kernel source.  The warp/block scan and the
-# look-back add a per-thread overhead amortised over C steps, not counted.
-FLOPS_PER_STEP = {"vdp": 44.0, "osc": 38.0, "lorenz": 104.0}
+# FP64 flops per step executed by the small-state kernel, counted from its
+# source (FMA = 2): phase 1 (residual, compact Jacobian, thread fold) runs on
+# every residual evaluation, phase 3 (replay, update) once per Newton update.
+SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0)}
+# Fisher-KPP (d padded to 128): per step, fold of the dense column block
+# (4 flops per entry in the working precision) + FP64 residual/diagonal and
+# vector fold; per compose 2*128^3.
+FK_FOLD_REAL_FLOPS = 128 * 128 * 4
+FK_FOLD_F64_FLOPS = 128 * (15 + 5)
+FK_COMPOSE_FLOPS = 2 * 128 ** 3
 
 
 # ---------------------------------------------------------------------------
@@ -65,6 +73,13 @@ def workload(name):
     if name == "lorenz":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0,
                     desc="lorenz63 sigma=10 rho=28 beta=8/3 x0=(1,1,1) h=1e-3 N=8192, guarded Newton B=100")
+    if name == "fkpp":
+        return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=0,
+                    desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, FP64 scan")
+    if name == "fkpp_mixed":
+        return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=1,
+                    desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, BF16 tensor-core "
+                         "composes (FP32 accumulate), FP64 residual and update")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -145,7 +160,8 @@ def run_ours(args, rank, world, local_rank):
     x0 = torch.tensor(wl.x0, dtype=torch.float64, device=dev)
     traj = torch.empty((wl.N, wl.d), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
-    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+    prec = spec.get("precision", 0)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec)
 
     def solve_once():
         rc, res = P.pitn_solve_ex(wl.system, params, x0, wl.h, wl.N, wl.d, spec["tol"],
@@ -165,6 +181,8 @@ def run_ours(args, rank, world, local_rank):
         gpu_id = str(local_rank)
     clocks = ClockSampler(gpu_id)
     clocks.start()
+    P.pitn_timing_reset()
+    P.pitn_timing_enable(True)
     launches0 = pk.pitn_launch_count()
     times = []
     for _ in range(args.steps):
@@ -179,6 +197,10 @@ def run_ours(args, rank, world, local_rank):
         times.append(e0.elapsed_time(e1))
     launches = pk.pitn_launch_count() - launches0
     torch.cuda.synchronize(dev)
+    P.pitn_timing_enable(False)
+    ktimes = {k: P.pitn_timing_get(k) for k in
+              ("newton_small", "fkpp_fold", "fkpp_compose", "fkpp_down", "fkpp_replay")}
+    ktimes = {k: v for k, v in ktimes.items() if v[1] > 0}
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
@@ -188,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    converged = res.status == P.PITN_OK and res.final_res <= 1e-8
+    converged = res.status == P.PITN_OK and res.final_res <= spec["tol"]
     steps_solved = wl.N if converged else 0
     value = world * steps_solved / (ms_per_step / 1e3)
 
@@ -199,7 +221,7 @@ def run_ours(args, rank, world, local_rank):
         h_x0 = torch.tensor(wl.x0, dtype=torch.float64).pin_memory()
         h_traj = torch.empty((wl.N, wl.d), dtype=torch.float64).pin_memory()
         hp, hx, ht = h_params.numpy(), h_x0.numpy(), h_traj.numpy()
-        opt_h = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+        opt_h = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec)
         P.pitn_solve_ex(wl.system, hp, hx, wl.h, wl.N, wl.d, spec["tol"], spec["max_iter"], ht, opt_h)
         et = []
         for _ in range(max(1, min(args.steps, 5))):
@@ -210,19 +232,12 @@ def run_ours(args, rank, world, local_rank):
                                       spec["max_iter"], ht, opt_h)
             et.append(time.perf_counter() - t0)
         e2e_s = statistics.median(et)
-        e2e_ok = r2.status == P.PITN_OK and r2.final_res <= 1e-8
+        e2e_ok = r2.status == P.PITN_OK and r2.final_res <= spec["tol"]
         e2e = {"value": (world * wl.N / e2e_s) if e2e_ok else 0.0, "unit": UNIT,
                "h2d_bytes_per_step": int((wl.d + len(wl.params)) * 8),
                "d2h_bytes_per_step": int(wl.N * wl.d * 8), "ms_per_step": e2e_s * 1e3}
 
-    passes = res.iters + 1
-    flops = FLOPS_PER_STEP[args.workload] * wl.N * passes
-    achieved_tflops = flops / (ms_per_step / 1e3) / 1e12
-    hbm, _, _, src = load_peaks()
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "newton_small_kernel", "peak_source": "nominal GB300 FP64",
-                "hbm_frac_of_" + src: (2 * wl.N * wl.d * 8 * passes) / (ms_per_step / 1e3) / 1e9 / hbm}
+    roofline = roofline_for(args.workload, spec, wl, res, ktimes, args.steps)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -230,9 +245,52 @@ def run_ours(args, rank, world, local_rank):
                        "max_iter": spec["max_iter"], "newton_updates": res.iters,
                        "status": P.pitn_status_string(res.status), "final_res": res.final_res,
                        "l2": "flushed (512 MiB write) between timed steps",
+                       "step_ms": [round(t, 3) for t in times],
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}
     return line
+
+
+def roofline_for(name, spec, wl, res, ktimes, steps):
+    """Roofline of the kernel family with the largest device time."""
+    kern = max(ktimes, key=lambda k: ktimes[k][0])
+    ms, launches = ktimes[kern]
+    passes = res.iters + 1
+    per_step_s = ms / 1e3 / steps
+    if kern == "newton_small":
+        p1, p3 = SMALL_FLOPS[name]
+        flops = wl.N * (p1 * passes + p3 * res.iters)
+        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
+        note = "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"
+    elif kern == "fkpp_fold":
+        mixed = spec.get("precision", 0) == 1
+        flops = wl.N * passes * FK_FOLD_REAL_FLOPS
+        peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+        bound, unit = "alu", "TFLOP/s"
+        note = ("dense fold flops in " + ("FP32" if mixed else "FP64") +
+                "; peak from unit counts and clocks")
+    elif kern == "fkpp_compose":
+        mixed = spec.get("precision", 0) == 1
+        T = (wl.N - 1 + 63) // 64
+        flops = (T - 1) * FK_COMPOSE_FLOPS * passes
+        if mixed:
+            _, bf16, _, src = load_peaks()
+            peak, bound, unit = bf16, "tensor", "TFLOP/s"
+            note = f"BF16 tensor-core composes; peak = {src} cuBLAS bf16 burst"
+        else:
+            peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
+            note = "FP64 CUDA-core composes; peak = nominal GB300 FP64"
+    else:
+        hbm, _, _, src = load_peaks()
+        flops = None
+        peak, bound, unit = hbm, "hbm", "GB/s"
+        note = "memory-bound helper"
+    achieved = (flops / per_step_s / 1e12) if flops is not None else 0.0
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": None, "kernel": kern,
+            "kernel_launches_per_step": launches / steps,
+            "kernel_ms_per_launch": ms / max(launches, 1), "note": note}
 
 
 # ---------------------------------------------------------------------------
@@ -251,6 +309,20 @@ def oracle_sample(spec, sample_iters):
     return dt / evals, r
 
 
+def oracle_passes(name, fallback):
+    """Residual evaluations the oracle's own full solve needs (stored by
+    tests/golden/make_oracle_golden.py, which runs only the oracle)."""
+    key = {"vdp": "vdp_2^22_guard100_tol1e-12_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
+           "lorenz": "lorenz_8192_guard100_tol1e-12_it100",
+           "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50"}
+    p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
+    try:
+        with open(p) as f:
+            return json.load(f)[key[name]]["iters"] + 1
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
 def cpu_baseline(spec, full_passes, sample_iters):
     per_eval, r = oracle_sample(spec, sample_iters)
     wl = spec["wl"]
@@ -261,13 +333,17 @@ def cpu_baseline(spec, full_passes, sample_iters):
                       f"{full_passes} evaluations of the full solve"}
 
 
+# Newton iterations of the oracle timed per baseline sample (bounded CPU time)
+SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3}
+
+
 def run_reference(args):
     spec = workload(args.workload)
     wl = spec["wl"]
     import oracle as O
-    # number of residual evaluations of the full solve (oracle iteration count)
-    full_passes = {"vdp": 157, "osc": 2, "lorenz": 63}.get(args.workload)
-    sample_iters = {"vdp": 6, "osc": 1, "lorenz": 62}.get(args.workload, 5)
+    # number of residual evaluations of the oracle's full solve
+    full_passes = oracle_passes(args.workload, 2)
+    sample_iters = SAMPLE_ITERS.get(args.workload, 5)
     for _ in range(args.warmup):
         oracle_sample(spec, 0)
     vals = []
@@ -313,9 +389,9 @@ def main():
     ge.build_library_only()
     line = run_ours(args, rank, world, local_rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        full_passes = line["config"]["newton_updates"] + 1
-        sample_iters = {"vdp": 6, "osc": 1, "lorenz": 62}.get(args.workload, 5)
-        line["cpu_baseline"] = cpu_baseline(workload(args.workload), full_passes, sample_iters)
+        full_passes = oracle_passes(args.workload, line["config"]["newton_updates"] + 1)
+        line["cpu_baseline"] = cpu_baseline(workload(args.workload), full_passes,
+                                            SAMPLE_ITERS.get(args.workload, 5))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -178,6 +178,16 @@ int pitn_release_workspace(void);
  * (all devices, all entry points). */
 int64_t pitn_launch_count(void);
 
+/* Per-kernel timing (tracing).  While enabled, every kernel launch of the
+ * library is bracketed by CUDA events on its stream; pitn_timing_get returns
+ * the summed device time and launch count of one kernel family since the
+ * last reset (names: "newton_small", "fkpp_fold", "fkpp_compose",
+ * "fkpp_down", "fkpp_replay", "batch", "adjoint").  Timing adds two event
+ * records per launch; it is off by default. */
+int pitn_timing_enable(int on);
+int pitn_timing_reset(void);
+int pitn_timing_get(const char* kernel, double* total_ms, int64_t* launches);
+
 #ifdef __cplusplus
 }
 #endif

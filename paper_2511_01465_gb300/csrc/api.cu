@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -24,7 +25,55 @@ struct DevCache {
 };
 std::map<int, DevCache> g_cache;
 std::map<int, cudaDeviceProp> g_props;
+
+// kernel timing
+std::atomic<int> g_timing{0};
+struct Pending {
+    cudaEvent_t e0, e1;
+    std::string name;
+};
+std::vector<Pending> g_pending;
+std::map<std::string, std::pair<double, int64_t>> g_times;
+std::mutex g_tmu;
 }  // namespace
+
+TimedToken timed_begin(const char* name, cudaStream_t st) {
+    TimedToken t;
+    if (!g_timing.load()) return t;
+    cudaEvent_t e0;
+    if (cudaEventCreate(&e0) != cudaSuccess) return t;
+    cudaEventRecord(e0, st);
+    t.e0 = (void*)e0;
+    t.name = name;
+    return t;
+}
+
+void timed_end(const TimedToken& t, cudaStream_t st) {
+    if (!t.e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy((cudaEvent_t)t.e0);
+        return;
+    }
+    cudaEventRecord(e1, st);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_pending.push_back(Pending{(cudaEvent_t)t.e0, e1, t.name});
+}
+
+static void resolve_timing() {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (auto& p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.e1) == cudaSuccess && cudaEventElapsedTime(&ms, p.e0, p.e1) == cudaSuccess) {
+            auto& v = g_times[p.name];
+            v.first += ms;
+            v.second += 1;
+        }
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    g_pending.clear();
+}
 
 void* workspace(size_t bytes, int slot) {
     int dev = 0;
@@ -205,6 +254,34 @@ int pitn_release_workspace(void) {
 }
 
 int64_t pitn_launch_count(void) { return g_launches.load(); }
+
+int pitn_timing_enable(int on) {
+    resolve_timing();
+    g_timing.store(on ? 1 : 0);
+    return PITN_OK;
+}
+
+int pitn_timing_reset(void) {
+    resolve_timing();
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_times.clear();
+    return PITN_OK;
+}
+
+int pitn_timing_get(const char* kernel, double* total_ms, int64_t* launches) {
+    if (!kernel || !total_ms || !launches) return PITN_EINVAL;
+    resolve_timing();
+    std::lock_guard<std::mutex> lk(g_tmu);
+    auto it = g_times.find(kernel);
+    if (it == g_times.end()) {
+        *total_ms = 0.0;
+        *launches = 0;
+    } else {
+        *total_ms = it->second.first;
+        *launches = it->second.second;
+    }
+    return PITN_OK;
+}
 
 int pitn_solve(int system_id, const double* params, const double* x0, double h, int64_t N, int d,
                double tol, int max_iter, double* traj_out) {

@@ -38,15 +38,6 @@
 
 namespace pitn {
 
-// Published state of one tile for the look-back.
-template <int D>
-struct __align__(16) TileSlot {
-    unsigned flag;          // (epoch << 2) | 1 (aggregate) or | 2 (inclusive)
-    unsigned pad;
-    double agg[D * D + D];  // tile aggregate (P row-major, then c)
-    double incl[D];         // inclusive prefix vector (state after the tile)
-};
-
 struct SolveRecord {
     int iters;
     int status;
@@ -59,21 +50,25 @@ struct SmallArgs {
     double* X0;         // trajectory buffer 0 [N][D]
     double* X1;         // trajectory buffer 1 [N][D]
     double* out;        // destination of the final iterate
+    double* scratch;    // [N][JN + D]: compact Jacobian and residual of every step
+    double* agg;        // [gridDim][D*D + D]: CTA aggregates
     long long N;
-    double h, tol, cap;
+    long long chunk;    // consecutive steps per thread
+    double h, tol;
+    unsigned long long cap_bits;  // |dx| bits above this are cut (guard bound or DBL_MAX)
     int guarded;
     int max_iter;
     long long q_init;   // 0: constant guess x0 (buffer contents ignored); N: buffer 0 holds the guess
     double params[4];
-    void* tiles;
-    long long num_tiles;
     unsigned long long* res_bits;  // [max_iter + 1]  ||r||_inf bits per iteration
-    int* nonfinite;                // [max_iter + 1]
     unsigned long long* qenc;      // [max_iter + 1]  max of ~q (0 = no cut)
     unsigned* bar;                 // [2] grid barrier
     int* err;
     SolveRecord* rec;
 };
+
+constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
 template <int D>
 __device__ __forceinline__ void mat_identity(double* P) {
@@ -81,7 +76,7 @@ __device__ __forceinline__ void mat_identity(double* P) {
     for (int i = 0; i < D * D; ++i) P[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
 }
 
-// (P, c) <- (P2, c2) o (P1, c1) = (P2 P1, P2 c1 + c2)
+// (P, c) <- (P2, c2) o (P1, c1) = (P2 P1, P2 c1 + c2)   (eq. 3.3, 2 = later)
 template <int D>
 __device__ __forceinline__ void compose(const double* P2, const double* c2, const double* P1,
                                         const double* c1, double* P, double* c) {
@@ -90,9 +85,9 @@ __device__ __forceinline__ void compose(const double* P2, const double* c2, cons
     for (int i = 0; i < D; ++i) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            double s = 0.0;
+            double s = P2[i * D] * P1[j];
 #pragma unroll
-            for (int l = 0; l < D; ++l) s = fma(P2[i * D + l], P1[l * D + j], s);
+            for (int l = 1; l < D; ++l) s = fma(P2[i * D + l], P1[l * D + j], s);
             tP[i * D + j] = s;
         }
         double s = c2[i];
@@ -121,7 +116,7 @@ __device__ __forceinline__ void apply(const double* P, const double* c, const do
     for (int i = 0; i < D; ++i) o[i] = t[i];
 }
 
-// x_k of the current iterate with the guard's lazy fill.
+// x_k of the current iterate with the guard's lazy fill (L2-coherent loads).
 template <int D>
 __device__ __forceinline__ void load_state(const double* __restrict__ X, const double* __restrict__ x0,
                                            long long k, long long q, double* o) {
@@ -136,286 +131,291 @@ __device__ __forceinline__ void load_state(const double* __restrict__ X, const d
 
 constexpr int kMaxWarps = 8;  // BLOCK <= 256
 
-template <class Sys, int C>
+// Inclusive Kogge-Stone scan of (P, c) across the warp (later lanes on the left).
+template <int D>
+__device__ __forceinline__ void warp_scan(double* P, double* c, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        double uP[D * D], uc[D];
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, P[j], off);
+#pragma unroll
+        for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, c[j], off);
+        if (lane >= off) compose<D>(P, c, uP, uc, P, c);
+    }
+}
+
+// Exclusive block scan of per-thread elements.  On return (eP, ec) is the
+// lane-exclusive prefix within the warp, s_wex[warp] the warp-exclusive
+// prefix, and s_tot the block total.  All in a fixed order.
+template <int D>
+__device__ __forceinline__ void block_scan(double* P, double* c, double* eP, double* ec,
+                                           double (*s_wex)[D * D + D], double* s_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    warp_scan<D>(P, c, lane);
+#pragma unroll
+    for (int j = 0; j < D * D; ++j) eP[j] = __shfl_up_sync(0xffffffffu, P[j], 1);
+#pragma unroll
+    for (int j = 0; j < D; ++j) ec[j] = __shfl_up_sync(0xffffffffu, c[j], 1);
+    if (lane == 0) {
+        mat_identity<D>(eP);
+#pragma unroll
+        for (int j = 0; j < D; ++j) ec[j] = 0.0;
+    }
+    __syncthreads();  // s_wex may still be read from a previous use
+    if (lane == 31) {
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) s_wex[warp][j] = P[j];
+#pragma unroll
+        for (int j = 0; j < D; ++j) s_wex[warp][D * D + j] = c[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double wP[D * D], wc[D];
+        if (lane < nwarps) {
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) wP[j] = s_wex[lane][j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) wc[j] = s_wex[lane][D * D + j];
+        } else {
+            mat_identity<D>(wP);
+#pragma unroll
+            for (int j = 0; j < D; ++j) wc[j] = 0.0;
+        }
+#pragma unroll
+        for (int off = 1; off < kMaxWarps; off <<= 1) {
+            double uP[D * D], uc[D];
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, wP[j], off);
+#pragma unroll
+            for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, wc[j], off);
+            if (lane >= off) compose<D>(wP, wc, uP, uc, wP, wc);
+        }
+        double xP[D * D], xc[D];
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) xP[j] = __shfl_up_sync(0xffffffffu, wP[j], 1);
+#pragma unroll
+        for (int j = 0; j < D; ++j) xc[j] = __shfl_up_sync(0xffffffffu, wc[j], 1);
+        __syncwarp();
+        if (lane < nwarps) {
+            if (lane == 0) {
+                mat_identity<D>(xP);
+#pragma unroll
+                for (int j = 0; j < D; ++j) xc[j] = 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) s_wex[lane][j] = xP[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_wex[lane][D * D + j] = xc[j];
+        }
+        if (lane == nwarps - 1) {
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) s_tot[j] = wP[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_tot[D * D + j] = wc[j];
+        }
+    }
+    __syncthreads();
+}
+
+// Deterministic three-phase Newton kernel (persistent, cooperative launch).
+// Thread g owns steps [g*chunk, (g+1)*chunk).  Per Newton iteration:
+//   phase 1: residuals + compact Jacobians (stored to scratch), thread fold,
+//            block scan, CTA aggregate to global;   grid barrier;
+//   decision on ||r||_inf (identical in every CTA);
+//   scan of the CTA aggregates in a fixed order (every CTA derives its own
+//   incoming prefix the same way), replay of the thread's steps from its
+//   incoming vector, update into the other buffer, first guard cut;
+//   grid barrier.
+template <class Sys>
 __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
-    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
     Sys sys;
     sys.init(a.params, a.h);
 
-    __shared__ double s_wagg[kMaxWarps][E];   // warp totals -> warp-exclusive prefixes
-    __shared__ double s_tile[E];              // tile aggregate
-    __shared__ double s_zin[D];               // incoming prefix vector of the tile
+    __shared__ double s_wex[kMaxWarps][E];
+    __shared__ double s_tot[E];
+    __shared__ double s_g[kMaxWarps][E];
+    __shared__ double s_gtot[E];
+    __shared__ double s_zin[D];
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31;
     const long long N = a.N;
-    const long long TILE = (long long)blockDim.x * C;
-    TileSlot<D>* slots = reinterpret_cast<TileSlot<D>*>(a.tiles);
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k0 = gt * a.chunk;
+    const long long k1 = min(N, k0 + a.chunk);
+    const unsigned G = gridDim.x;
+    double* __restrict__ scr = a.scratch;
 
     int cur = 0;
-    long long q = a.q_init;       // lazy-fill index of the current iterate
+    long long q = a.q_init;
     long long last_cut = N;
     int it = 0, status = PITN_NOT_CONVERGED;
     double final_res = 0.0;
-    bool failed = false;
 
     for (;;) {
         const double* __restrict__ Xc = cur ? a.X1 : a.X0;
         double* __restrict__ Xn = cur ? a.X0 : a.X1;
-        const unsigned epoch = (unsigned)it + 1u;
-        unsigned long long my_res = 0ull, my_q = 0ull;
-        bool my_nf = false;
-
-        for (long long t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
-            const long long base = t * TILE + (long long)threadIdx.x * C;
-            // ---- 1. states, residuals, Jacobians ------------------------------
-            double xs[C + 1][D];
-            double r[C][D], jv[C][JN];
-            load_state<D>(Xc, a.x0, base - 1, q, xs[0]);
+        // ---- phase 1: residual, Jacobian, fold -------------------------------
+        unsigned long long my_res = 0ull;
+        double P[D * D], c[D];
+        mat_identity<D>(P);
 #pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const long long k = base + i;
-                if (k < N) {
-                    load_state<D>(Xc, a.x0, k, q, xs[i + 1]);
-                    sys.eval(xs[i], xs[i + 1], r[i], jv[i]);
+        for (int j = 0; j < D; ++j) c[j] = 0.0;
+        double xp[D];
+        if (k0 < k1) load_state<D>(Xc, a.x0, k0 - 1, q, xp);
+        for (long long k = k0; k < k1; ++k) {
+            double x[D], r[D], jv[JN];
+            load_state<D>(Xc, a.x0, k, q, x);
+            sys.eval(xp, x, r, jv);
 #pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        unsigned long long b = (unsigned long long)__double_as_longlong(fabs(r[i][j]));
-                        my_res = b > my_res ? b : my_res;
-                        my_nf |= !isfinite(r[i][j]);
-                    }
-                } else {
+            for (int j = 0; j < JN; ++j) scr[k * W + j] = jv[j];
 #pragma unroll
-                    for (int j = 0; j < D; ++j) { xs[i + 1][j] = 0.0; r[i][j] = 0.0; }
-#pragma unroll
-                    for (int j = 0; j < JN; ++j) jv[i][j] = 0.0;
-                }
+            for (int j = 0; j < D; ++j) {
+                scr[k * W + JN + j] = r[j];
+                const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
+                my_res = b > my_res ? b : my_res;
             }
-            // ---- 2. thread aggregate ---------------------------------------
-            double P[D * D], c[D];
-            mat_identity<D>(P);
+            if (k == 0) {  // a_0 = (0, -r_0), eq. 3.4
 #pragma unroll
-            for (int j = 0; j < D; ++j) c[j] = 0.0;
+                for (int j = 0; j < D * D; ++j) P[j] = 0.0;
 #pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const long long k = base + i;
-                if (k >= N) continue;               // identity element
-                if (k == 0) {                       // a_0 = (0, -r_0), eq. 3.4
+                for (int j = 0; j < D; ++j) c[j] = -r[j];
+            } else {
+                double tP[D * D], tc[D];
+                sys.jmul(jv, P, tP);
+                sys.jvec(jv, c, tc);
 #pragma unroll
-                    for (int j = 0; j < D * D; ++j) P[j] = 0.0;
+                for (int j = 0; j < D * D; ++j) P[j] = tP[j];
 #pragma unroll
-                    for (int j = 0; j < D; ++j) c[j] = -r[i][j];
-                } else {
-                    double tP[D * D], tc[D];
-                    sys.jmul(jv[i], P, tP);
-                    sys.jvec(jv[i], c, tc);
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) P[j] = tP[j];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) c[j] = tc[j] - r[i][j];
-                }
+                for (int j = 0; j < D; ++j) c[j] = tc[j] - r[j];
             }
-            // ---- 3. warp scan (inclusive), then lane-exclusive ----------------
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                double uP[D * D], uc[D];
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, P[j], off);
-#pragma unroll
-                for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, c[j], off);
-                if (lane >= off) compose<D>(P, c, uP, uc, P, c);
-            }
-            double eP[D * D], ec[D];
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) eP[j] = __shfl_up_sync(0xffffffffu, P[j], 1);
-#pragma unroll
-            for (int j = 0; j < D; ++j) ec[j] = __shfl_up_sync(0xffffffffu, c[j], 1);
-            if (lane == 0) {
-                mat_identity<D>(eP);
-#pragma unroll
-                for (int j = 0; j < D; ++j) ec[j] = 0.0;
-            }
-            if (lane == 31) {
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) s_wagg[warp][j] = P[j];
-#pragma unroll
-                for (int j = 0; j < D; ++j) s_wagg[warp][D * D + j] = c[j];
-            }
-            __syncthreads();
-            // ---- block level: warp 0 scans the warp totals --------------------
-            if (warp == 0) {
-                double wP[D * D], wc[D];
-                if (lane < nwarps) {
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) wP[j] = s_wagg[lane][j];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) wc[j] = s_wagg[lane][D * D + j];
-                } else {
-                    mat_identity<D>(wP);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) wc[j] = 0.0;
-                }
-#pragma unroll
-                for (int off = 1; off < kMaxWarps; off <<= 1) {
-                    double uP[D * D], uc[D];
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, wP[j], off);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, wc[j], off);
-                    if (lane >= off) compose<D>(wP, wc, uP, uc, wP, wc);
-                }
-                double xP[D * D], xc[D];
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) xP[j] = __shfl_up_sync(0xffffffffu, wP[j], 1);
-#pragma unroll
-                for (int j = 0; j < D; ++j) xc[j] = __shfl_up_sync(0xffffffffu, wc[j], 1);
-                __syncwarp();
-                if (lane < nwarps) {
-                    if (lane == 0) {
-                        mat_identity<D>(xP);
-#pragma unroll
-                        for (int j = 0; j < D; ++j) xc[j] = 0.0;
-                    }
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) s_wagg[lane][j] = xP[j];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) s_wagg[lane][D * D + j] = xc[j];
-                }
-                if (lane == nwarps - 1) {
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) s_tile[j] = wP[j];
-#pragma unroll
-                    for (int j = 0; j < D; ++j) s_tile[D * D + j] = wc[j];
-                }
-            }
-            __syncthreads();
-            // ---- 4. publish + decoupled look-back (thread 0) ------------------
-            if (threadIdx.x == 0) {
-                TileSlot<D>* me = slots + t;
-                double zin[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) zin[j] = 0.0;
-                if (t == 0) {
-                    // contains element 0, so its aggregate is already inclusive
-#pragma unroll
-                    for (int j = 0; j < D; ++j) me->incl[j] = s_tile[D * D + j];
-                    st_release_u32(&me->flag, (epoch << 2) | 2u);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < E; ++j) me->agg[j] = s_tile[j];
-                    st_release_u32(&me->flag, (epoch << 2) | 1u);
-                    double Q[D * D], e[D];
-                    mat_identity<D>(Q);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) e[j] = 0.0;
-                    long long jt = t - 1;
-                    uint64_t t0 = 0;
-                    for (;;) {
-                        TileSlot<D>* s = slots + jt;
-                        unsigned f = ld_acquire_u32(&s->flag);
-                        if ((f >> 2) != epoch) {
-                            if (t0 == 0) t0 = globaltimer_ns();
-                            else if (globaltimer_ns() - t0 > kWaitLimitNs || *(volatile int*)a.err) {
-                                raise_error(a.err, PITN_ETIMEOUT);
-                                break;
-                            }
-                            continue;
-                        }
-                        t0 = 0;
-                        if ((f & 3u) == 2u) {
-                            double z[D];
-#pragma unroll
-                            for (int j = 0; j < D; ++j) z[j] = ldcg(&s->incl[j]);
-                            apply<D>(Q, e, z, zin);
-                            break;
-                        }
-                        double sP[D * D], sc[D];
-#pragma unroll
-                        for (int j = 0; j < D * D; ++j) sP[j] = ldcg(&s->agg[j]);
-#pragma unroll
-                        for (int j = 0; j < D; ++j) sc[j] = ldcg(&s->agg[D * D + j]);
-                        compose<D>(Q, e, sP, sc, Q, e);
-                        --jt;
-                    }
-                    double zo[D];
-                    apply<D>(s_tile, s_tile + D * D, zin, zo);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) me->incl[j] = zo[j];
-                    st_release_u32(&me->flag, (epoch << 2) | 2u);
-                }
-#pragma unroll
-                for (int j = 0; j < D; ++j) s_zin[j] = zin[j];
-            }
-            __syncthreads();
-            // ---- 5. replay + update ------------------------------------------
-            double z[D], zw[D];
-            apply<D>(s_wagg[warp], s_wagg[warp] + D * D, s_zin, zw);
-            apply<D>(eP, ec, zw, z);
-#pragma unroll
-            for (int i = 0; i < C; ++i) {
-                const long long k = base + i;
-                if (k >= N) break;
-                if (k == 0) {
-#pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = -r[i][j];
-                } else {
-                    double tz[D];
-                    sys.jvec(jv[i], z, tz);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = tz[j] - r[i][j];
-                }
-                bool bad = false;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    bad |= !(fabs(z[j]) <= a.cap);
-                    Xn[k * D + j] = xs[i + 1][j] + z[j];
-                }
-                if (bad) {
-                    unsigned long long e = ~(unsigned long long)k;
-                    my_q = e > my_q ? e : my_q;
-                }
-            }
-            __syncthreads();  // shared scratch is reused by the next tile
+            for (int j = 0; j < D; ++j) xp[j] = x[j];
         }
-
-        // ---- iteration reductions -------------------------------------------
+        double eP[D * D], ec[D];
+        block_scan<D>(P, c, eP, ec, s_wex, s_tot);
+        if (threadIdx.x < E) a.agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            unsigned long long o = __shfl_xor_sync(0xffffffffu, my_res, off);
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_res, off);
             my_res = o > my_res ? o : my_res;
-            o = __shfl_xor_sync(0xffffffffu, my_q, off);
-            my_q = o > my_q ? o : my_q;
         }
-        bool any_nf = __any_sync(0xffffffffu, my_nf);
-        if (lane == 0) {
-            atomicMax(a.res_bits + it, my_res);
-            if (my_q) atomicMax(a.qenc + it, my_q);
-            if (any_nf) atomicOr(a.nonfinite + it, 1);
-        }
-        if (!grid_barrier(a.bar, a.bar + 1, gridDim.x, a.err)) { failed = true; break; }
+        if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
 
-        // ---- decision (identical in every CTA) ------------------------------
-        const double res = __longlong_as_double((long long)__ldcg(a.res_bits + it));
-        const int nf = *(volatile int*)(a.nonfinite + it);
-        const unsigned long long qe = __ldcg(a.qenc + it);
-        const long long cut = qe ? (long long)(~qe) : N;
+        // ---- decision --------------------------------------------------------
+        const unsigned long long rb = __ldcg(a.res_bits + it);
+        const double res = __longlong_as_double((long long)rb);
         final_res = res;
-        if (nf) { status = PITN_NONFINITE; break; }
+        if (rb >= kInfBits) { status = PITN_NONFINITE; break; }
         if (res <= a.tol) { status = PITN_OK; break; }
         if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
+
+        // ---- incoming prefix of this CTA: fixed-order scan of the aggregates ----
+        {
+            const unsigned m = (G + blockDim.x - 1) / blockDim.x;   // aggregates per thread
+            double gP[D * D], gc[D];
+            mat_identity<D>(gP);
+#pragma unroll
+            for (int j = 0; j < D; ++j) gc[j] = 0.0;
+            for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
+                double sP[D * D], sc[D];
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(a.agg + (size_t)i * E + j);
+#pragma unroll
+                for (int j = 0; j < D; ++j) sc[j] = __ldcg(a.agg + (size_t)i * E + D * D + j);
+                compose<D>(sP, sc, gP, gc, gP, gc);
+            }
+            double xP[D * D], xc[D];
+            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot);
+            // CTA b needs the prefix through aggregate b-1, held by thread (b-1)/m:
+            // its exclusive prefix (warp part, then lane part) applied to the zero
+            // vector -- every prefix from aggregate 0 has matrix 0 -- then the
+            // aggregates it owns up to b-1, in order.
+            if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
+                double v[D], t[D], zero[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) zero[j] = 0.0;
+                apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
+                apply<D>(xP, xc, t, v);
+                for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
+                    double sP[D * D], sc[D];
+#pragma unroll
+                    for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(a.agg + (size_t)i * E + j);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(a.agg + (size_t)i * E + D * D + j);
+                    apply<D>(sP, sc, v, t);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) v[j] = t[j];
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = v[j];
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = 0.0;
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 3: replay + update ------------------------------------------
+        unsigned long long my_q = 0ull;
+        {
+            double zw[D], z[D];
+            apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
+            apply<D>(eP, ec, zw, z);
+            bool found = false;
+            for (long long k = k0; k < k1; ++k) {
+                double jv[JN], r[D], x[D];
+#pragma unroll
+                for (int j = 0; j < JN; ++j) jv[j] = scr[k * W + j];
+#pragma unroll
+                for (int j = 0; j < D; ++j) r[j] = scr[k * W + JN + j];
+                load_state<D>(Xc, a.x0, k, q, x);
+                if (k == 0) {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) z[j] = -r[j];
+                } else {
+                    double tz[D];
+                    sys.jvec(jv, z, tz);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) z[j] = tz[j] - r[j];
+                }
+                unsigned long long zb = 0ull;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    Xn[k * D + j] = x[j] + z[j];
+                    const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
+                    zb = b > zb ? b : zb;
+                }
+                if (!found && zb > a.cap_bits) {
+                    found = true;
+                    my_q = ~(unsigned long long)k;
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+            my_q = o > my_q ? o : my_q;
+        }
+        if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        const unsigned long long qe = __ldcg(a.qenc + it);
+        const long long cut = qe ? (long long)(~qe) : N;
         if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }
         cur ^= 1;
         q = a.guarded ? cut : N;
         last_cut = cut;
         ++it;
     }
-    if (failed) return;
 
     // ---- write the final iterate (with its fill) to the destination ---------
     const double* Xc = cur ? a.X1 : a.X0;
     const bool same = (Xc == a.out);
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += stride) {
+    for (long long k = gt; k < N; k += stride) {
         if (same && k < q) continue;
         double v[D];
         load_state<D>(Xc, a.x0, k, q, v);
@@ -430,77 +430,73 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Host launcher
-// ---------------------------------------------------------------------------
-struct SmallConfig {
-    int block;
-    int C;
-};
-
-template <class Sys, int C>
-static cudaError_t launch_one(SmallArgs& a, int block, cudaStream_t st, int* grid_out) {
-    auto kern = newton_small_kernel<Sys, C>;
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long cap = (long long)per_sm * pitn_host::props().multiProcessorCount;
-    int grid = (int)std::min<long long>(a.num_tiles, cap);
+template <class Sys>
+static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
     void* args[] = {(void*)&a};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(block), args, 0, st);
-    pitn_host::count_launch();
-    if (grid_out) *grid_out = grid;
+    auto tok = pitn_host::timed_begin("newton_small", st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)newton_small_kernel<Sys>, dim3(grid),
+                                                dim3(block), args, 0, st);
+    pitn_host::timed_end(tok, st);
+    pitn_host::count_launch(1);
     return e;
 }
 
 template <class Sys>
-static cudaError_t dispatch_c(SmallArgs& a, SmallConfig cfg, cudaStream_t st) {
-    switch (cfg.C) {
-    case 2: return launch_one<Sys, 2>(a, cfg.block, st, nullptr);
-    case 4: return launch_one<Sys, 4>(a, cfg.block, st, nullptr);
-    case 8: return launch_one<Sys, 8>(a, cfg.block, st, nullptr);
-    default: return cudaErrorInvalidValue;
-    }
+static int max_blocks_per_sm(int block) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Sys>, block, 0) !=
+        cudaSuccess)
+        return 0;
+    return per_sm;
 }
 
 }  // namespace pitn
 
 namespace pitn_host {
 
-static size_t tile_slot_bytes(int d) {
-    return d == 3 ? sizeof(pitn::TileSlot<3>) : sizeof(pitn::TileSlot<2>);
-}
-
-// Default tiling: the largest block that still leaves about two tiles per SM.
+// Launch shape: about `cmin` steps per thread at least, as many CTAs as the
+// device holds at once (cooperative launch), blocks of 32..256 threads.
 void small_default_config(int d, long long N, int* block, int* C) {
-    int c = (d == 3) ? 4 : 8;
-    int sms = props().multiProcessorCount;
-    int b = 256;
-    while (b > 32 && (N + (long long)b * c - 1) / ((long long)b * c) < 2LL * sms) b >>= 1;
-    *block = b;
-    *C = c;
+    (void)d;
+    const int sms = props().multiProcessorCount;
+    const long long cmin = 4;
+    long long threads = (N + cmin - 1) / cmin;
+    long long b = (threads + sms - 1) / sms;
+    b = ((b + 31) / 32) * 32;
+    b = std::max(32LL, std::min(256LL, b));
+    *block = (int)b;
+    *C = (int)cmin;
 }
 
 int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
                      int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out) {
     using namespace pitn;
-    int block = 0, C = 0;
-    small_default_config(d, N, &block, &C);
-    if (o.tile_elems > 0) {
-        if (o.tile_elems != 2 && o.tile_elems != 4 && o.tile_elems != 8) return PITN_EINVAL;
-        C = o.tile_elems;
+    int block = 0, cmin = 0;
+    small_default_config(d, N, &block, &cmin);
+    if (o.tile_elems > 0) cmin = o.tile_elems;
+    int per_sm = 0;
+    switch (system_id) {
+    case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63>(block); break;
+    case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol>(block); break;
+    case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc>(block); break;
+    default: return PITN_EINVAL;
     }
-    const long long tile = (long long)block * C;
-    const long long num_tiles = (N + tile - 1) / tile;
+    if (per_sm < 1) return PITN_ECUDA;
+    per_sm = std::min(per_sm, 2);
+    const long long max_grid = (long long)per_sm * props().multiProcessorCount;
+    const long long want = (N + (long long)block * cmin - 1) / ((long long)block * cmin);
+    const int grid = (int)std::max(1LL, std::min(max_grid, want));
+    const long long chunk = (N + (long long)grid * block - 1) / ((long long)grid * block);
+    const int W = (d == 3) ? (Lorenz63::JN + 3) : (system_id == PITN_VDP ? VanDerPol::JN + 2 : LinearOsc::JN + 2);
+    const int E = d * d + d;
 
     double* X1 = (double*)workspace((size_t)N * d * sizeof(double), kSlotX1);
-    // control block: tiles | res_bits | qenc | nonfinite | bar | err | record
-    size_t off_tiles = 0;
-    size_t off_res = off_tiles + (size_t)num_tiles * tile_slot_bytes(d);
+    double* scratch = (double*)workspace((size_t)N * W * sizeof(double), kSlotAux);
+    // control block: agg | res_bits | qenc | bar | err | record
+    size_t off_agg = 0;
+    size_t off_res = off_agg + (size_t)grid * E * sizeof(double);
     size_t off_q = off_res + sizeof(unsigned long long) * (size_t)(max_iter + 1);
-    size_t off_nf = off_q + sizeof(unsigned long long) * (size_t)(max_iter + 1);
-    size_t off_bar = (off_nf + sizeof(int) * (size_t)(max_iter + 1) + 15) & ~(size_t)15;
+    size_t off_bar = (off_q + sizeof(unsigned long long) * (size_t)(max_iter + 1) + 15) & ~(size_t)15;
     size_t off_err = off_bar + 16;
     size_t off_rec = off_err + 16;
     size_t total = off_rec + sizeof(SolveRecord);
@@ -508,38 +504,39 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
     // host mirror: err | record | history
     size_t hbytes = 16 + sizeof(SolveRecord) + sizeof(double) * (size_t)(max_iter + 1);
     char* hbuf = (char*)pinned(hbytes);
-    if (!X1 || !ctrl || !hbuf) return PITN_ENOMEM;
+    if (!X1 || !scratch || !ctrl || !hbuf) return PITN_ENOMEM;
 
     SmallArgs a{};
     a.x0 = io.x0_dev;
     a.X0 = io.traj_dev;
     a.X1 = X1;
     a.out = io.traj_dev;
+    a.scratch = scratch;
+    a.agg = (double*)(ctrl + off_agg);
     a.N = N;
+    a.chunk = chunk;
     a.h = h;
     a.tol = tol;
     a.guarded = (o.guard_B > 0.0 && std::isfinite(o.guard_B)) ? 1 : 0;
-    a.cap = a.guarded ? o.guard_B : DBL_MAX;
+    {
+        const double cap = a.guarded ? o.guard_B : DBL_MAX;
+        std::memcpy(&a.cap_bits, &cap, sizeof(cap));
+    }
     a.max_iter = max_iter;
     a.q_init = io.have_guess ? N : 0;
     for (int i = 0; i < 4; ++i) a.params[i] = io.params[i];
-    a.tiles = ctrl + off_tiles;
-    a.num_tiles = num_tiles;
     a.res_bits = (unsigned long long*)(ctrl + off_res);
     a.qenc = (unsigned long long*)(ctrl + off_q);
-    a.nonfinite = (int*)(ctrl + off_nf);
     a.bar = (unsigned*)(ctrl + off_bar);
     a.err = (int*)(ctrl + off_err);
     a.rec = (SolveRecord*)(ctrl + off_rec);
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
-    SmallConfig cfg{block, C};
     cudaError_t e;
     switch (system_id) {
-    case PITN_LORENZ63: e = dispatch_c<Lorenz63>(a, cfg, st); break;
-    case PITN_VDP: e = dispatch_c<VanDerPol>(a, cfg, st); break;
-    case PITN_LINEAR_OSC: e = dispatch_c<LinearOsc>(a, cfg, st); break;
-    default: return PITN_EINVAL;
+    case PITN_LORENZ63: e = launch_small<Lorenz63>(a, grid, block, st); break;
+    case PITN_VDP: e = launch_small<VanDerPol>(a, grid, block, st); break;
+    default: e = launch_small<LinearOsc>(a, grid, block, st); break;
     }
     if (e != cudaSuccess) { cudaGetLastError(); return PITN_ECUDA; }
     int* h_err = (int*)hbuf;

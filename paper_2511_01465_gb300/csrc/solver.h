@@ -38,6 +38,16 @@ int num_params(int sys);
 int fetch_to_host(const double* src, size_t n, double* dst);
 std::recursive_mutex& api_mutex();
 
+// Optional per-kernel timing (CUDA events on the launching stream).
+// timed_begin returns a token to pass to timed_end; both are no-ops while
+// timing is disabled.
+struct TimedToken {
+    void* e0 = nullptr;
+    const char* name = nullptr;
+};
+TimedToken timed_begin(const char* name, cudaStream_t st);
+void timed_end(const TimedToken& t, cudaStream_t st);
+
 // Inputs of one single-IVP solve, resident on the device.
 struct SolveIO {
     double params[kMaxParams];  // host copy of the parameters

@@ -74,6 +74,12 @@ def lib():
         L.pitn_release_workspace.restype = c_int
         L.pitn_launch_count.argtypes = []
         L.pitn_launch_count.restype = i64
+        L.pitn_timing_enable.argtypes = [c_int]
+        L.pitn_timing_enable.restype = c_int
+        L.pitn_timing_reset.argtypes = []
+        L.pitn_timing_reset.restype = c_int
+        L.pitn_timing_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.pitn_timing_get.restype = c_int
         _lib = L
         return L
 
@@ -165,6 +171,23 @@ def pitn_release_workspace():
 
 def pitn_launch_count():
     return lib().pitn_launch_count()
+
+
+def pitn_timing_enable(on=True):
+    return lib().pitn_timing_enable(1 if on else 0)
+
+
+def pitn_timing_reset():
+    return lib().pitn_timing_reset()
+
+
+def pitn_timing_get(kernel):
+    """(total device ms, launches) of one kernel family since the last reset."""
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    rc = lib().pitn_timing_get(kernel.encode(), ctypes.byref(ms), ctypes.byref(n))
+    if rc != 0:
+        raise ValueError(rc)
+    return ms.value, n.value
 
 
 class PitnError(RuntimeError):

@@ -22,9 +22,9 @@ CASES = {
     # name: (workload, tol, max_iter, guard_B)
     "lorenz_8192_plain_tol1e-10_it50": (W.lorenz(), 1e-10, 50, 0.0),
     "lorenz_8192_guard100_tol1e-10_it50": (W.lorenz(), 1e-10, 50, 100.0),
-    "lorenz_8192_guard100_tol1e-10_it100": (W.lorenz(), 1e-10, 100, 100.0),
+    "lorenz_8192_guard100_tol1e-12_it100": (W.lorenz(), 1e-12, 100, 100.0),
     "vdp_2^22_plain_tol1e-8_it200": (W.vdp(), 1e-8, 200, 0.0),
-    "vdp_2^22_guard100_tol1e-8_it200": (W.vdp(), 1e-8, 200, 100.0),
+    "vdp_2^22_guard100_tol1e-12_it400": (W.vdp(), 1e-12, 400, 100.0),
     "osc_2^22_plain_tol1e-8_it10": (W.damped_oscillator(), 1e-8, 10, 0.0),
     "fkpp_d128_2^15_plain_tol1e-8_it50": (W.fkpp(), 1e-8, 50, 0.0),
 }

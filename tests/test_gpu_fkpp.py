@@ -1,0 +1,86 @@
+"""GPU parity of the Fisher-KPP (method-of-lines, d up to 128) Newton path.
+
+FP64: integer outcomes equal the oracle's, trajectories within 1e-10 (max
+relative error normalised by the largest entry).  Mixed precision (BF16
+tensor-core composes, FP32 accumulation, FP64 residual and update): the
+solve must reach the same FP64 residual tolerance and stay within 1e-6 of
+the FP64 oracle; its Newton count is reported, not required to match (it is
+an inexact Newton by design).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_01465_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01465_gb300 as pk
+    return pk
+
+
+def relerr(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def gpu(pk, wl, tol, max_iter, precision=0, guard_B=0.0):
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, tol, max_iter,
+                          precision=precision, guard_B=guard_B, history=True)
+    return traj.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("d", [3, 16, 100, 128])
+@pytest.mark.parametrize("N", [1, 2, 64, 65, 66, 130, 1000, 2049])
+def test_fp64_ragged_against_oracle(pk, d, N):
+    wl = W.fkpp(d=d, N=N)
+    g, gi = gpu(pk, wl, 1e-12, 30)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-12, 30)
+    assert (gi["iters"], gi["status"], gi["guard_index"]) == (o["iters"], o["status"], o["guard_index"])
+    assert relerr(g, o["traj"]) <= 1e-10
+    np.testing.assert_allclose(gi["res_history"], o["res_hist"], rtol=1e-6, atol=1e-15)
+
+
+def test_fp64_full_size(pk):
+    wl = W.fkpp()
+    g, gi = gpu(pk, wl, 1e-8, 50)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 50)
+    assert (gi["iters"], gi["status"]) == (o["iters"], o["status"]) == (3, O.OK)
+    assert relerr(g, o["traj"]) <= 1e-10
+    np.testing.assert_allclose(gi["res_history"], o["res_hist"], rtol=1e-6, atol=1e-15)
+
+
+def test_fp64_max_iter_and_guess(pk):
+    wl = W.fkpp(d=128, N=3000)
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
+    guess = seq * 1.01
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 1, guess=guess, history=True)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 1, guess=guess)
+    assert info["iters"] == o["iters"] == 1 and info["status"] == o["status"]
+    assert relerr(traj.cpu().numpy(), o["traj"]) <= 1e-10
+
+
+@pytest.mark.parametrize("N", [1, 65, 4097, 1 << 15])
+def test_mixed_precision_within_1e6(pk, N):
+    wl = W.fkpp(N=N)
+    g, gi = gpu(pk, wl, 1e-8, 50, precision=pk.PITN_PREC_MIXED_BF16)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-12, 50)
+    assert gi["status"] == O.OK
+    assert gi["final_res"] <= 1e-8
+    err = relerr(g, o["traj"])
+    assert err <= 1e-6, err
+    # the FP64 residual of the returned trajectory, recomputed by the oracle
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, g)
+    assert not nf and res <= 1e-8 * (1 + 1e-6)
+
+
+def test_mixed_requires_large_d(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    wl = W.fkpp(d=16, N=100)
+    with pytest.raises(P.PitnError):
+        gpu(pk, wl, 1e-8, 10, precision=P.PITN_PREC_MIXED_BF16)
