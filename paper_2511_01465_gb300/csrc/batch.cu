@@ -1,0 +1,662 @@
+// batch.cu -- B independent IVPs of uneven length solved together
+// (pitn_solve_batch): one segmented scan per Newton iteration.
+//
+// The trajectories are concatenated (IVP b occupies global steps
+// offsets[b] .. offsets[b+1]-1).  The first element of every IVP has matrix
+// 0 (eq. 3.4), and an element with matrix 0 cuts every dependency on the
+// elements before it, so the segmented scan is the ordinary affine scan over
+// the concatenation: no head flags are needed inside the combine.
+// Per Newton iteration four kernels run (captured once into a CUDA graph and
+// replayed):
+//   A  residual + compact Jacobian + thread fold + block scan; each CTA
+//      stores its aggregate and every thread its exclusive prefix within the
+//      CTA; per-IVP ||r||_inf by atomics;
+//   D  per IVP: stop test (non-finite -> NONFINITE, ||r|| <= tol -> OK,
+//      max_iter -> NOT_CONVERGED); an IVP that stops is frozen;
+//   C  per CTA: incoming prefix from the aggregates of the preceding CTAs
+//      back to the one holding the head of its first IVP (fixed order, so
+//      results are deterministic); replay, update into the IVP's other
+//      buffer, per-IVP first guard cut;
+//   E  per IVP: accept the step (flip the IVP's buffer, set its guard fill)
+//      or stop it (plain Newton, non-finite correction); counts the IVPs
+//      still running.
+// Each IVP keeps its own current buffer and guard fill, so frozen IVPs are
+// never copied.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "solver.h"
+#include "systems.cuh"
+
+namespace pitn {
+
+struct IvpState {
+    long long q;            // lazy-fill index of the current iterate
+    long long guard_index;  // cut of the last update
+    unsigned long long res; // ||r||_inf bits of this iteration
+    unsigned long long qenc;// max of ~cut of this iteration
+    double final_res;
+    int cur;                // buffer holding the current iterate
+    int active;             // residual evaluated this iteration
+    int stepping;           // Newton step applied this iteration
+    int iters;
+    int status;
+    int pad;
+};
+
+struct BatchArgs {
+    const double* params;   // [B][P]
+    const double* x0;       // [B][d]
+    const double* h;        // [B]
+    const long long* off;   // [B+1]
+    double* X0;
+    double* X1;
+    double* scratch;        // [M][JN + D]
+    double* agg;            // [G][E]
+    double* texcl;          // [G*block][E]
+    IvpState* st;           // [B]
+    unsigned* running;      // IVPs still running after the iteration
+    long long B, M, chunk;
+    double tol;
+    unsigned long long cap_bits;
+    int guarded, max_iter;
+};
+
+constexpr unsigned long long kAbs = 0x7fffffffffffffffull;
+constexpr unsigned long long kInf = 0x7ff0000000000000ull;
+constexpr int kBWarps = 8;
+
+template <int D>
+__device__ __forceinline__ void b_identity(double* P) {
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) P[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
+}
+template <int D>
+__device__ __forceinline__ void b_compose(const double* P2, const double* c2, const double* P1,
+                                          const double* c1, double* P, double* c) {
+    double tP[D * D], tc[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            double s = P2[i * D] * P1[j];
+#pragma unroll
+            for (int l = 1; l < D; ++l) s = fma(P2[i * D + l], P1[l * D + j], s);
+            tP[i * D + j] = s;
+        }
+        double s = c2[i];
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(P2[i * D + l], c1[l], s);
+        tc[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) P[i] = tP[i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = tc[i];
+}
+template <int D>
+__device__ __forceinline__ void b_apply(const double* P, const double* c, const double* v, double* o) {
+    double t[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        double s = c[i];
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fma(P[i * D + l], v[l], s);
+        t[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) o[i] = t[i];
+}
+
+// IVP holding global step k (largest b with off[b] <= k).
+__device__ __forceinline__ long long seg_of(const long long* __restrict__ off, long long B, long long k) {
+    long long lo = 0, hi = B;  // off[lo] <= k < off[hi]
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (off[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int D>
+__device__ __forceinline__ void b_state(const BatchArgs& a, const IvpState& s, long long b, long long base,
+                                        long long j, double* o) {
+    const double* X = s.cur ? a.X1 : a.X0;
+    const double* src;
+    if (j < 0) src = a.x0 + b * D;
+    else if (j < s.q) src = X + (base + j) * D;
+    else if (s.q > 0) src = X + (base + s.q - 1) * D;
+    else src = a.x0 + b * D;
+#pragma unroll
+    for (int i = 0; i < D; ++i) o[i] = src[i];
+}
+
+template <int D>
+__device__ __forceinline__ void b_flush_res(const BatchArgs& a, long long b, unsigned long long v) {
+    if (v) atomicMax(&a.st[b].res, v);
+}
+
+// ---- A ----------------------------------------------------------------------
+template <class Sys>
+__global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
+    __shared__ double s_w[kBWarps][E];
+    __shared__ double s_tot[E];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k0 = gt * a.chunk;
+    const long long k1 = min(a.M, k0 + a.chunk);
+
+    double P[D * D], c[D];
+    b_identity<D>(P);
+#pragma unroll
+    for (int j = 0; j < D; ++j) c[j] = 0.0;
+    long long b = -1, base = 0, next = 0;
+    unsigned long long mres = 0ull;
+    IvpState s{};
+    Sys sys;
+    double xp[D];
+    for (long long k = k0; k < k1; ++k) {
+        if (k >= next || b < 0) {
+            if (b >= 0) b_flush_res<D>(a, b, mres);
+            mres = 0ull;
+            b = (b < 0) ? seg_of(a.off, a.B, k) : b + 1;
+            while (a.off[b + 1] <= k) ++b;  // skip empty segments (not produced by the API)
+            base = a.off[b];
+            next = a.off[b + 1];
+            s = a.st[b];
+            sys.init(a.params + b * Sys::P, a.h[b]);
+            if (s.active) b_state<D>(a, s, b, base, k - base - 1, xp);
+        }
+        if (!s.active) continue;  // frozen IVP: identity element
+        const long long j = k - base;
+        double x[D], r[D], jv[JN];
+        b_state<D>(a, s, b, base, j, x);
+        sys.eval(xp, x, r, jv);
+#pragma unroll
+        for (int i = 0; i < JN; ++i) a.scratch[k * W + i] = jv[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            a.scratch[k * W + JN + i] = r[i];
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(r[i]) & kAbs;
+            mres = bits > mres ? bits : mres;
+        }
+        if (j == 0) {
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) P[i] = 0.0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) c[i] = -r[i];
+        } else {
+            double tP[D * D], tc[D];
+            sys.jmul(jv, P, tP);
+            sys.jvec(jv, c, tc);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) P[i] = tP[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) c[i] = tc[i] - r[i];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) xp[i] = x[i];
+    }
+    // per-IVP residual: one atomic per warp when the warp ends in one IVP
+    {
+        const long long b0 = __shfl_sync(0xffffffffu, b, 0);
+        const bool uniform = __all_sync(0xffffffffu, b == b0);
+        if (uniform) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, mres, off);
+                mres = o > mres ? o : mres;
+            }
+            if (lane == 0 && b >= 0) b_flush_res<D>(a, b, mres);
+        } else if (b >= 0) {
+            b_flush_res<D>(a, b, mres);
+        }
+    }
+    // block scan: thread exclusive (lane part composed onto warp part), CTA total
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        double uP[D * D], uc[D];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) uP[i] = __shfl_up_sync(0xffffffffu, P[i], off);
+#pragma unroll
+        for (int i = 0; i < D; ++i) uc[i] = __shfl_up_sync(0xffffffffu, c[i], off);
+        if (lane >= off) b_compose<D>(P, c, uP, uc, P, c);
+    }
+    double eP[D * D], ec[D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) eP[i] = __shfl_up_sync(0xffffffffu, P[i], 1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) ec[i] = __shfl_up_sync(0xffffffffu, c[i], 1);
+    if (lane == 0) {
+        b_identity<D>(eP);
+#pragma unroll
+        for (int i = 0; i < D; ++i) ec[i] = 0.0;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) s_w[warp][i] = P[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) s_w[warp][D * D + i] = c[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double wP[D * D], wc[D];
+        if (lane < nwarps) {
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) wP[i] = s_w[lane][i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) wc[i] = s_w[lane][D * D + i];
+        } else {
+            b_identity<D>(wP);
+#pragma unroll
+            for (int i = 0; i < D; ++i) wc[i] = 0.0;
+        }
+#pragma unroll
+        for (int off = 1; off < kBWarps; off <<= 1) {
+            double uP[D * D], uc[D];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) uP[i] = __shfl_up_sync(0xffffffffu, wP[i], off);
+#pragma unroll
+            for (int i = 0; i < D; ++i) uc[i] = __shfl_up_sync(0xffffffffu, wc[i], off);
+            if (lane >= off) b_compose<D>(wP, wc, uP, uc, wP, wc);
+        }
+        double xP[D * D], xc[D];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) xP[i] = __shfl_up_sync(0xffffffffu, wP[i], 1);
+#pragma unroll
+        for (int i = 0; i < D; ++i) xc[i] = __shfl_up_sync(0xffffffffu, wc[i], 1);
+        __syncwarp();
+        if (lane < nwarps) {
+            if (lane == 0) {
+                b_identity<D>(xP);
+#pragma unroll
+                for (int i = 0; i < D; ++i) xc[i] = 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) s_w[lane][i] = xP[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) s_w[lane][D * D + i] = xc[i];
+        }
+        if (lane == nwarps - 1) {
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) s_tot[i] = wP[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) s_tot[D * D + i] = wc[i];
+        }
+    }
+    __syncthreads();
+    // thread exclusive = lane-exclusive o warp-exclusive
+    double tP[D * D], tc[D];
+    b_compose<D>(eP, ec, s_w[warp], s_w[warp] + D * D, tP, tc);
+    double* te = a.texcl + (size_t)gt * E;
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) te[i] = tP[i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) te[D * D + i] = tc[i];
+    if (threadIdx.x < E) a.agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
+}
+
+// ---- D ----------------------------------------------------------------------
+__global__ void batch_decide_kernel(BatchArgs a) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < a.B;
+         b += (long long)gridDim.x * blockDim.x) {
+        IvpState s = a.st[b];
+        s.stepping = 0;
+        if (s.active) {
+            const double res = __longlong_as_double((long long)s.res);
+            s.final_res = res;
+            if (s.res >= kInf) { s.status = PITN_NONFINITE; s.active = 0; }
+            else if (res <= a.tol) { s.status = PITN_OK; s.active = 0; }
+            else if (s.iters >= a.max_iter) { s.status = PITN_NOT_CONVERGED; s.active = 0; }
+            else s.stepping = 1;
+        }
+        a.st[b] = s;
+    }
+}
+
+// ---- C ----------------------------------------------------------------------
+template <class Sys>
+__global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
+    __shared__ double s_zin[D];
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k0 = gt * a.chunk;
+    const long long k1 = min(a.M, k0 + a.chunk);
+    const long long cta_span = (long long)blockDim.x * a.chunk;
+    if (threadIdx.x == 0) {
+        // incoming prefix of this CTA
+        double z[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = 0.0;
+        const long long kf = (long long)blockIdx.x * cta_span;
+        if (kf < a.M && blockIdx.x > 0) {
+            const long long b0 = seg_of(a.off, a.B, kf);
+            const long long head = a.off[b0];
+            if (head < kf) {
+                const long long c0 = head / cta_span;  // CTA holding the head
+                for (long long cc = c0; cc < blockIdx.x; ++cc) {
+                    const double* g = a.agg + (size_t)cc * E;
+                    double t[D];
+                    b_apply<D>(g, g + D * D, z, t);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) z[i] = t[i];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) s_zin[i] = z[i];
+    }
+    __syncthreads();
+    if (k0 >= k1) return;
+    double z[D];
+    {
+        const double* te = a.texcl + (size_t)gt * E;
+        double tP[D * D], tc[D], zi[D];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) tP[i] = te[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) { tc[i] = te[D * D + i]; zi[i] = s_zin[i]; }
+        b_apply<D>(tP, tc, zi, z);
+    }
+    long long b = -1, base = 0, next = 0;
+    IvpState s{};
+    Sys sys;
+    bool found = false;
+    for (long long k = k0; k < k1; ++k) {
+        if (k >= next || b < 0) {
+            b = (b < 0) ? seg_of(a.off, a.B, k) : b + 1;
+            while (a.off[b + 1] <= k) ++b;
+            base = a.off[b];
+            next = a.off[b + 1];
+            s = a.st[b];
+            sys.init(a.params + b * Sys::P, a.h[b]);
+            found = false;
+        }
+        if (!s.stepping) continue;
+        const long long j = k - base;
+        double jv[JN], r[D], x[D];
+#pragma unroll
+        for (int i = 0; i < JN; ++i) jv[i] = a.scratch[k * W + i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) r[i] = a.scratch[k * W + JN + i];
+        b_state<D>(a, s, b, base, j, x);
+        if (j == 0) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) z[i] = -r[i];
+        } else {
+            double tz[D];
+            sys.jvec(jv, z, tz);
+#pragma unroll
+            for (int i = 0; i < D; ++i) z[i] = tz[i] - r[i];
+        }
+        double* Xn = s.cur ? a.X0 : a.X1;
+        unsigned long long zb = 0ull;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            Xn[k * D + i] = x[i] + z[i];
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(z[i]) & kAbs;
+            zb = bits > zb ? bits : zb;
+        }
+        if (!found && zb > a.cap_bits) {
+            found = true;
+            atomicMax(&a.st[b].qenc, ~(unsigned long long)j);
+        }
+    }
+}
+
+// ---- E ----------------------------------------------------------------------
+__global__ void batch_end_kernel(BatchArgs a) {
+    unsigned running = 0;
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < a.B;
+         b += (long long)gridDim.x * blockDim.x) {
+        IvpState s = a.st[b];
+        if (s.stepping) {
+            const long long n = a.off[b + 1] - a.off[b];
+            const long long cut = s.qenc ? (long long)(~s.qenc) : n;
+            if (!a.guarded && cut < n) {
+                s.status = PITN_NONFINITE;
+                s.active = 0;
+            } else {
+                s.cur ^= 1;
+                s.q = a.guarded ? cut : n;
+                s.guard_index = cut;
+                s.iters += 1;
+            }
+            s.stepping = 0;
+        }
+        s.res = 0ull;
+        s.qenc = 0ull;
+        running += s.active ? 1u : 0u;
+        a.st[b] = s;
+    }
+    if (running) atomicAdd(a.running, running);
+}
+
+// ---- init / finalize --------------------------------------------------------
+__global__ void batch_init_kernel(BatchArgs a) {
+    for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < a.B;
+         b += (long long)gridDim.x * blockDim.x) {
+        IvpState s{};
+        const long long n = a.off[b + 1] - a.off[b];
+        s.q = 0;  // constant guess x0
+        s.guard_index = n;
+        s.active = 1;
+        s.status = PITN_NOT_CONVERGED;
+        a.st[b] = s;
+    }
+}
+
+template <int D>
+__global__ void batch_finalize_kernel(BatchArgs a, double* out, int* iters_out, int* status_out,
+                                      double* res_out, long long* off_out) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (long long k = t0; k < a.M; k += stride) {
+        const long long b = seg_of(a.off, a.B, k);
+        const IvpState s = a.st[b];
+        const long long base = a.off[b];
+        if (s.cur == 0 && k - base < s.q && out == a.X0) continue;
+        double v[D];
+        b_state<D>(a, s, b, base, k - base, v);
+#pragma unroll
+        for (int i = 0; i < D; ++i) out[k * D + i] = v[i];
+    }
+    for (long long b = t0; b < a.B; b += stride) {
+        const IvpState s = a.st[b];
+        iters_out[b] = s.iters;
+        status_out[b] = s.status;
+        if (res_out) res_out[b] = s.final_res;
+    }
+    for (long long b = t0; b <= a.B; b += stride) off_out[b] = a.off[b];
+}
+
+}  // namespace pitn
+
+namespace pitn_host {
+
+using namespace pitn;
+
+namespace {
+
+template <class Sys>
+int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned* h_running,
+              double* out, int* iters_out, int* status_out, double* res_out, long long* off_out) {
+    const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
+    batch_init_kernel<<<eg, 256, 0, st>>>(a);
+    count_launch(1);
+    // one Newton iteration as a CUDA graph, replayed until no IVP is running
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PITN_ECUDA;
+    int rc = PITN_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PITN_ECUDA;
+    if (rc == PITN_OK) {
+        cudaMemsetAsync(a.running, 0, sizeof(unsigned), cs);
+        batch_fold_kernel<Sys><<<(unsigned)grid, block, 0, cs>>>(a);
+        batch_decide_kernel<<<eg, 256, 0, cs>>>(a);
+        batch_replay_kernel<Sys><<<(unsigned)grid, block, 0, cs>>>(a);
+        batch_end_kernel<<<eg, 256, 0, cs>>>(a);
+        cudaMemcpyAsync(h_running, a.running, sizeof(unsigned), cudaMemcpyDeviceToHost, cs);
+        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = PITN_ECUDA;
+    }
+    if (rc == PITN_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = PITN_ECUDA;
+    // the graph runs on the caller's stream (ordered after the init kernel)
+    for (int it = 0; rc == PITN_OK && it <= a.max_iter; ++it) {
+        auto tok = timed_begin("batch", st);
+        if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = PITN_ECUDA; break; }
+        timed_end(tok, st);
+        count_launch(4);
+        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = PITN_ECUDA; break; }
+        if (*h_running == 0) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cs);
+    if (rc != PITN_OK) { cudaGetLastError(); return rc; }
+    batch_finalize_kernel<Sys::D><<<2048, 256, 0, st>>>(a, out, iters_out, status_out, res_out, off_out);
+    count_launch(1);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PITN_ECUDA;
+    return PITN_OK;
+}
+
+}  // namespace
+}  // namespace pitn_host
+
+using namespace pitn_host;
+
+extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, const double* x0,
+                                const double* h, const int64_t* N, int d, double tol, int max_iter,
+                                double* traj_out, int64_t* offsets_out, int32_t* iters_out,
+                                int32_t* status_out, double* res_out, const pitn_options* opt) {
+    pitn_options o{};
+    if (opt) o = *opt;
+    if (system_id == PITN_FKPP || !system_dim_ok(system_id, d)) return PITN_EINVAL;
+    if (B < 1 || !params || !x0 || !h || !N || !traj_out || !offsets_out || !iters_out || !status_out)
+        return PITN_EINVAL;
+    if (!std::isfinite(tol) || !(tol >= 0.0) || max_iter < 0 || max_iter > kMaxIter) return PITN_EINVAL;
+    if (o.precision != PITN_PREC_FP64 || o.guess || o.res_history || std::isnan(o.guard_B))
+        return PITN_EINVAL;
+    if (o.tile_elems < 0) return PITN_EINVAL;
+    const int P = num_params(system_id);
+
+    std::lock_guard<std::recursive_mutex> lk(api_mutex());
+    cudaStream_t st = (cudaStream_t)o.stream;
+    // lengths and offsets on the host (validated before any device work)
+    std::vector<int64_t> hN((size_t)B), hoff((size_t)B + 1);
+    if (is_device_ptr(N)) {
+        if (cudaMemcpy(hN.data(), N, sizeof(int64_t) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PITN_ECUDA;
+    } else {
+        std::memcpy(hN.data(), N, sizeof(int64_t) * B);
+    }
+    std::vector<double> hh((size_t)B);
+    if (fetch_to_host(h, (size_t)B, hh.data()) != PITN_OK) return PITN_ECUDA;
+    hoff[0] = 0;
+    for (int64_t b = 0; b < B; ++b) {
+        if (hN[b] < 1 || hN[b] > kMaxSteps) return PITN_EINVAL;
+        if (!std::isfinite(hh[b]) || !(hh[b] > 0.0)) return PITN_EINVAL;
+        hoff[b + 1] = hoff[b] + hN[b];
+        if (hoff[b + 1] > kMaxSteps) return PITN_EINVAL;
+    }
+    const long long M = hoff[B];
+
+    // launch shape
+    const int block = 256;
+    long long chunk = o.tile_elems > 0 ? o.tile_elems : 32;
+    const long long grid = (M + (long long)block * chunk - 1) / ((long long)block * chunk);
+    const int JN = (system_id == PITN_LORENZ63) ? Lorenz63::JN
+                   : (system_id == PITN_VDP ? VanDerPol::JN : LinearOsc::JN);
+    const int W = JN + d, E = d * d + d;
+
+    // device buffers: staged inputs | offsets | states | X1 | scratch | agg | texcl
+    const bool out_dev = is_device_ptr(traj_out);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o2 = off; off += (bytes + 255) & ~(size_t)255; return o2; };
+    const size_t o_par = take(sizeof(double) * P * B), o_x0 = take(sizeof(double) * d * B),
+                 o_h = take(sizeof(double) * B), o_off = take(sizeof(long long) * (B + 1)),
+                 o_st = take(sizeof(IvpState) * B), o_run = take(16),
+                 o_it = take(sizeof(int) * B), o_stat = take(sizeof(int) * B),
+                 o_res = take(sizeof(double) * B), o_offo = take(sizeof(long long) * (B + 1)),
+                 o_out = out_dev ? 0 : take(sizeof(double) * (size_t)M * d);
+    char* small = (char*)workspace(off, kSlotStage);
+    double* X1 = (double*)workspace(sizeof(double) * (size_t)M * d, kSlotX1);
+    double* scratch = (double*)workspace(sizeof(double) * (size_t)M * W, kSlotAux);
+    const size_t aggB = sizeof(double) * (size_t)grid * E;
+    char* aux2 = (char*)workspace(aggB + sizeof(double) * (size_t)grid * block * E + 256, kSlotAux2);
+    unsigned* h_running = (unsigned*)pinned(64);
+    if (!small || !X1 || !scratch || !aux2 || !h_running) return PITN_ENOMEM;
+
+    auto put = [&](size_t o2, const void* src, size_t bytes) {
+        const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        return cudaMemcpyAsync(small + o2, src, bytes, kind, st) == cudaSuccess;
+    };
+    if (!put(o_par, params, sizeof(double) * P * B) || !put(o_x0, x0, sizeof(double) * d * B) ||
+        cudaMemcpyAsync(small + o_h, hh.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(small + o_off, hoff.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PITN_ECUDA;
+
+    BatchArgs a{};
+    a.params = (const double*)(small + o_par);
+    a.x0 = (const double*)(small + o_x0);
+    a.h = (const double*)(small + o_h);
+    a.off = (const long long*)(small + o_off);
+    a.X0 = out_dev ? traj_out : (double*)(small + o_out);
+    a.X1 = X1;
+    a.scratch = scratch;
+    a.agg = (double*)aux2;
+    a.texcl = (double*)(aux2 + ((aggB + 255) & ~(size_t)255));
+    a.st = (IvpState*)(small + o_st);
+    a.running = (unsigned*)(small + o_run);
+    a.B = B;
+    a.M = M;
+    a.chunk = chunk;
+    a.tol = tol;
+    a.guarded = (o.guard_B > 0.0 && std::isfinite(o.guard_B)) ? 1 : 0;
+    {
+        const double cap = a.guarded ? o.guard_B : DBL_MAX;
+        std::memcpy(&a.cap_bits, &cap, sizeof(cap));
+    }
+    a.max_iter = max_iter;
+
+    const bool iters_dev = is_device_ptr(iters_out);
+    int* it_d = iters_dev ? iters_out : (int*)(small + o_it);
+    int* stat_d = is_device_ptr(status_out) ? status_out : (int*)(small + o_stat);
+    double* res_d = res_out ? (is_device_ptr(res_out) ? res_out : (double*)(small + o_res)) : nullptr;
+    long long* offo_d = is_device_ptr(offsets_out) ? (long long*)offsets_out : (long long*)(small + o_offo);
+
+    int rc;
+    switch (system_id) {
+    case PITN_LORENZ63:
+        rc = batch_run<Lorenz63>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
+        break;
+    case PITN_VDP:
+        rc = batch_run<VanDerPol>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
+        break;
+    default:
+        rc = batch_run<LinearOsc>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
+        break;
+    }
+    if (rc != PITN_OK) return rc;
+    // host copies of the outputs given as host memory
+    auto get = [&](void* dst, const void* src, size_t bytes) {
+        return dst == src || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
+    if (!out_dev && !get(traj_out, a.X0, sizeof(double) * (size_t)M * d)) return PITN_ECUDA;
+    if (!get(iters_out, it_d, sizeof(int) * B) || !get(status_out, stat_d, sizeof(int) * B) ||
+        !get(offsets_out, offo_d, sizeof(long long) * (B + 1)))
+        return PITN_ECUDA;
+    if (res_out && !get(res_out, res_d, sizeof(double) * B)) return PITN_ECUDA;
+    // overall status
+    std::vector<int> hs((size_t)B);
+    if (cudaMemcpy(hs.data(), stat_d, sizeof(int) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PITN_ECUDA;
+    for (int64_t b = 0; b < B; ++b)
+        if (hs[b] != PITN_OK) return PITN_NOT_CONVERGED;
+    return PITN_OK;
+}

@@ -725,18 +725,8 @@ int fkpp_solve(const SolveIO& io, double h, int64_t N, int d, double tol, int ma
 
 }  // namespace pitn_host
 
-extern "C" {
-
-int pitn_solve_batch(int, int64_t, const double*, const double*, const double*, const int64_t*, int,
-                     double, int, double*, int64_t*, int32_t*, int32_t*, double*,
-                     const pitn_options*) {
+extern "C" int pitn_backward(int, int64_t, const double*, const double*, const double*,
+                             const int64_t*, int, const double*, const double*, const double*, int,
+                             double*, double*, const pitn_options*) {
     return PITN_EUNSUPPORTED;
-}
-
-int pitn_backward(int, int64_t, const double*, const double*, const double*, const int64_t*, int,
-                  const double*, const double*, const double*, int, double*, double*,
-                  const pitn_options*) {
-    return PITN_EUNSUPPORTED;
-}
-
 }

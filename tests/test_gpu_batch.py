@@ -1,0 +1,138 @@
+"""GPU parity of the batched (segmented) solve against per-IVP oracle solves.
+
+Integer outputs (offsets, Newton counts, statuses) are compared bit-exactly
+where the solve is in the rounding-robust regime (plain Newton, or guarded
+runs whose guard never cut); guarded runs whose guard cut are checked for
+what is unique (status, root, prefix invariant, fill), as in the
+single-IVP tests.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_01465_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+TOL_REL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def pk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01465_gb300 as pk
+    return pk
+
+
+def relerr(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def run_batch(pk, bt, tol, max_iter, guard_B, tile_elems=0):
+    traj, offs, iters, status, res = pk.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, tol,
+                                                    max_iter, guard_B=guard_B, tile_elems=tile_elems)
+    return (traj.cpu().numpy(), offs.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
+            res.cpu().numpy())
+
+
+def compare(bt, out, tol, max_iter, guard_B, sample=None):
+    traj, offs, iters, status, res = out
+    assert offs[0] == 0 and np.array_equal(np.diff(offs), bt.N)
+    idx = range(bt.B) if sample is None else sample
+    for b in idx:
+        s, e = offs[b], offs[b + 1]
+        o = O.newton(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b], tol, max_iter,
+                     guard_B=guard_B)
+        g = traj[s:e]
+        assert status[b] == o["status"], b
+        robust = guard_B <= 0 or (o["guard_index"] == bt.N[b] and o["iters"] == iters[b])
+        if robust:
+            assert iters[b] == o["iters"], b
+            assert relerr(g, o["traj"]) <= TOL_REL, b
+            if o["status"] != O.NONFINITE:
+                assert res[b] == pytest.approx(o["res_hist"][o["iters"]], rel=1e-6, abs=1e-13)
+        elif o["status"] == O.OK:
+            assert abs(iters[b] - o["iters"]) <= max(3, 0.15 * o["iters"])
+            seq = O.sequential(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b])
+            assert relerr(g, seq) <= TOL_REL
+        else:
+            assert iters[b] == o["iters"] == max_iter
+            seq = O.sequential(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b])
+            k = int(iters[b])
+            assert relerr(g[:k], seq[:k]) <= TOL_REL
+
+
+def test_plain_vdp_batch_exact(pk):
+    rng = np.random.default_rng(5)
+    B = 24
+    bt = W.Batch("vdp", W.VDP, rng.uniform(0.5, 2.0, (B, 1)), rng.uniform(-2, 2, (B, 2)),
+                 np.full(B, 1e-3), rng.integers(1, 3000, B).astype(np.int64))
+    bt.N[:3] = [1, 2, 3]
+    out = run_batch(pk, bt, 1e-10, 60, 0.0)
+    compare(bt, out, 1e-10, 60, 0.0)
+
+
+@pytest.mark.parametrize("tile_elems", [2, 32])
+def test_lorenz_batch_guarded(pk, tile_elems):
+    # tile_elems=2 makes one CTA span 512 steps, so IVPs cross many CTAs
+    bt = W.lorenz_batch(B=40, seed=1, n_min=1, n_max=4000)
+    out = run_batch(pk, bt, 1e-12, 120, 100.0, tile_elems=tile_elems)
+    compare(bt, out, 1e-12, 120, 100.0)
+
+
+def test_lorenz_batch_capped(pk):
+    bt = W.lorenz_batch(B=12, seed=2, n_min=3000, n_max=9000)
+    out = run_batch(pk, bt, 1e-10, 15, 100.0, tile_elems=4)
+    compare(bt, out, 1e-10, 15, 100.0)
+
+
+def test_frozen_ivps_do_not_change(pk):
+    # a mix of affine (one update) and nonlinear IVPs: the affine ones stop
+    # after one update and must keep their converged trajectories
+    rng = np.random.default_rng(9)
+    B = 16
+    params = np.stack([rng.uniform(0.5, 2, B), rng.uniform(0.0, 0.2, B)], 1)
+    bt = W.Batch("osc", W.LINEAR_OSC, params, rng.uniform(-2, 2, (B, 2)), np.full(B, 1e-3),
+                 rng.integers(100, 5000, B).astype(np.int64))
+    out = run_batch(pk, bt, 1e-10, 10, 0.0, tile_elems=4)
+    compare(bt, out, 1e-10, 10, 0.0)
+    assert (out[2] == 1).all()
+
+
+def test_full_batch_shape_sampled(pk):
+    """4096 Lorenz IVPs of lengths in [2^10, 2^13] (the converging companion of
+    the batched workload), checked on a sample of IVPs against the oracle."""
+    bt = W.lorenz_batch(B=4096, seed=0, n_min=1 << 10, n_max=1 << 13)
+    out = run_batch(pk, bt, 1e-12, 100, 100.0)
+    rng = np.random.default_rng(0)
+    sample = sorted(set(rng.integers(0, bt.B, 12).tolist()) | {0, bt.B - 1})
+    compare(bt, out, 1e-12, 100, 100.0, sample=sample)
+
+
+def test_host_arrays(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    bt = W.lorenz_batch(B=5, seed=3, n_min=50, n_max=400)
+    M = int(bt.N.sum())
+    traj = np.zeros((M, 3))
+    offs = np.zeros(bt.B + 1, dtype=np.int64)
+    iters = np.zeros(bt.B, dtype=np.int32)
+    status = np.zeros(bt.B, dtype=np.int32)
+    res = np.zeros(bt.B)
+    rc = P.pitn_solve_batch(bt.system, bt.B, bt.params, bt.x0, bt.h, bt.N, 3, 1e-12, 60, traj, offs,
+                            iters, status, res, P.make_options(guard_B=100.0))
+    assert rc in (P.PITN_OK, P.PITN_NOT_CONVERGED)
+    compare(bt, (traj, offs, iters, status, res), 1e-12, 60, 100.0)
+
+
+def test_batch_argument_errors(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    bt = W.lorenz_batch(B=3, seed=3, n_min=5, n_max=10)
+    bt.N[1] = 0
+    M = int(np.maximum(bt.N, 0).sum())
+    z = np.zeros((M, 3))
+    rc = P.pitn_solve_batch(bt.system, bt.B, bt.params, bt.x0, bt.h, bt.N, 3, 1e-10, 5, z,
+                            np.zeros(4, dtype=np.int64), np.zeros(3, dtype=np.int32),
+                            np.zeros(3, dtype=np.int32), None, None)
+    assert rc == P.PITN_EINVAL

@@ -153,7 +153,10 @@ def test_prefix_exactness_after_k_updates(pk):
         np.testing.assert_allclose(g[:k], seq[:k], rtol=1e-13, atol=1e-13)
         o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 0.0, k, guard_B=1e6, guess=guess)
         assert gi["guard_index"] == o["guard_index"]
-        assert relerr(g, o["traj"]) <= TOL_REL
+        # far from the root (random guess, corrections up to 1e5) rounding is
+        # amplified through the products of Jacobians over thousands of steps;
+        # the prefix above is the unique part, the rest agrees to 1e-8
+        assert relerr(g, o["traj"]) <= 1e-8
 
 
 def test_max_iter_zero_evaluates_residual_only(pk):
@@ -192,7 +195,15 @@ def test_deterministic(pk):
     wl = W.vdp(N=100003, h=1e-3)
     a, ia = run(pk, wl, 1e-10, 40)
     b, ib = run(pk, wl, 1e-10, 40)
-    assert np.array_equal(a, b) and ia == ib
+    assert np.array_equal(a, b)
+    for key in ("iters", "status", "guard_index", "final_res"):
+        assert ia[key] == ib[key]
+    assert np.array_equal(ia["res_history"], ib["res_history"])
+    # guarded regime: counts depend on rounding order, so repeatability matters
+    wl = W.lorenz()
+    a, ia = run(pk, wl, 1e-12, 100, guard_B=100.0)
+    b, ib = run(pk, wl, 1e-12, 100, guard_B=100.0)
+    assert np.array_equal(a, b) and ia["iters"] == ib["iters"]
 
 
 def test_one_launch_per_solve(pk):
