@@ -178,6 +178,36 @@ int pitn_release_workspace(void);
  * (all devices, all entry points). */
 int64_t pitn_launch_count(void);
 
+/*
+ * Allocation-free solve for the small-state systems (PITN_LORENZ63, PITN_VDP,
+ * PITN_LINEAR_OSC).  The paper has no counterpart: this is a deployment aid.
+ *
+ * Some callers cannot call cudaMalloc once they are running: a real-time
+ * control loop whose time budget cannot absorb cudaMalloc's implicit device
+ * synchronisation, or a host application whose own allocator has reserved
+ * the device memory.  This entry point allocates nothing.  Its scratch is one
+ * fixed file-scope __device__ array (about 4.8 MB, held on every GPU that
+ * loads the library until the process exits), sized for at most
+ * PITN_NOALLOC_MAX_STEPS steps and PITN_NOALLOC_MAX_ITER Newton updates;
+ * larger requests return PITN_EINVAL.
+ *   traj_out  [N][d] DEVICE memory (nothing can be staged for a host array);
+ *   params, x0 host or device memory; guard_B as in pitn_options (<= 0 plain);
+ *   result    nullable; runs on the legacy default stream and blocks until
+ *             the result is on the host.
+ * The first call on a device looks up the array's device address (a
+ * one-time set-up per device); make that first call before any stream
+ * capture on the device.  Every call shares the array and finds it holding
+ * the previous call's contents; each call clears what must start at zero.
+ * Calls that overlapped on the GPU would race on the array, so the entry
+ * point holds a process-wide lock until its results are back on the host.
+ * Results equal pitn_solve_ex's for the same arguments.
+ */
+#define PITN_NOALLOC_MAX_STEPS 65536
+#define PITN_NOALLOC_MAX_ITER 1024
+int pitn_solve_noalloc(int system_id, const double* params, const double* x0, double h, int64_t N,
+                       int d, double tol, int max_iter, double guard_B, double* traj_out,
+                       pitn_result* result);
+
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream; pitn_timing_get returns
  * the summed device time and launch count of one kernel family since the

@@ -564,3 +564,157 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
 }
 
 }  // namespace pitn_host
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the small-state solve.
+//
+// Some callers must not allocate device memory once they are running: a
+// real-time control loop (the optimal-control use the method targets) whose
+// time budget cannot absorb cudaMalloc's implicit device synchronisation, or
+// a host application whose own allocator has reserved the device memory, so
+// that a cudaMalloc from this library would fail or fragment its pool.  This
+// entry point keeps all of its scratch in one file-scope __device__ array of
+// fixed size instead of the library's growing workspace cache.  Every GPU that
+// loads the library holds that array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long long kNaMaxSteps = 1LL << 16;  // N limit
+constexpr int kNaMaxIter = 1024;              // max_iter limit
+constexpr int kNaMaxCtas = 1024;              // CTA aggregates
+constexpr size_t kNaX1 = 0;                                            // [N][3]
+constexpr size_t kNaScratch = kNaX1 + (size_t)kNaMaxSteps * 3;         // [N][6]
+constexpr size_t kNaAgg = kNaScratch + (size_t)kNaMaxSteps * 6;        // [CTAs][12]
+constexpr size_t kNaRes = kNaAgg + (size_t)kNaMaxCtas * 12;            // [iter+1] bits
+constexpr size_t kNaQ = kNaRes + (size_t)(kNaMaxIter + 1);             // [iter+1] bits
+constexpr size_t kNaCtl = kNaQ + (size_t)(kNaMaxIter + 1);             // bar, err, record, x0
+constexpr size_t kNaDoubles = kNaCtl + 32;
+
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNaDoubles];
+
+namespace {
+std::mutex g_na_mu;
+double* g_na_addr[256] = {};  // device address of the array, per device ordinal
+}  // namespace
+
+extern "C" int pitn_solve_noalloc(int system_id, const double* params, const double* x0, double h,
+                                  int64_t N, int d, double tol, int max_iter, double guard_B,
+                                  double* traj_out, pitn_result* result) {
+    using namespace pitn;
+    using namespace pitn_host;
+    if (system_id != PITN_LORENZ63 && system_id != PITN_VDP && system_id != PITN_LINEAR_OSC)
+        return PITN_EINVAL;
+    if (!system_dim_ok(system_id, d) || !params || !x0 || !traj_out) return PITN_EINVAL;
+    if (N < 1 || N > kNaMaxSteps || max_iter < 0 || max_iter > kNaMaxIter) return PITN_EINVAL;
+    if (!std::isfinite(h) || !(h > 0.0) || !std::isfinite(tol) || !(tol >= 0.0) || std::isnan(guard_B))
+        return PITN_EINVAL;
+    if (!is_device_ptr(traj_out)) return PITN_EINVAL;  // nowhere to stage a host trajectory
+
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return PITN_ECUDA;
+    if (!g_na_addr[dev]) {
+        // one-time set-up on this device: the host-side name of the array is
+        // not a device address, so ask the runtime for the real one
+        double* ptr = nullptr;
+        if (cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+            cudaGetLastError();
+            return PITN_ECUDA;
+        }
+        g_na_addr[dev] = ptr;
+    }
+    double* base = g_na_addr[dev];
+
+    double hp[4] = {0.0, 0.0, 0.0, 0.0};
+    const int P = num_params(system_id);
+    if (is_device_ptr(params)) {
+        if (cudaMemcpy(hp, params, sizeof(double) * P, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return PITN_ECUDA;
+    } else {
+        for (int i = 0; i < P; ++i) hp[i] = params[i];
+    }
+
+    // launch shape: the same rule as the workspace-backed solve, capped by
+    // the number of CTA aggregates the array holds
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PITN_ECUDA;
+    const long long cmin = 4;
+    long long b = ((N + cmin - 1) / cmin + sms - 1) / sms;
+    b = std::max(32LL, std::min(256LL, ((b + 31) / 32) * 32));
+    const int block = (int)b;
+    int per_sm = 0;
+    cudaError_t e = cudaSuccess;
+    switch (system_id) {
+    case PITN_LORENZ63:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Lorenz63>, block, 0);
+        break;
+    case PITN_VDP:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<VanDerPol>, block, 0);
+        break;
+    default:
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<LinearOsc>, block, 0);
+        break;
+    }
+    if (e != cudaSuccess || per_sm < 1) return PITN_ECUDA;
+    per_sm = std::min(per_sm, 2);
+    const long long want = (N + (long long)block * cmin - 1) / ((long long)block * cmin);
+    const int grid = (int)std::max(1LL, std::min<long long>({(long long)per_sm * sms, want, (long long)kNaMaxCtas}));
+    const long long chunk = (N + (long long)grid * block - 1) / ((long long)grid * block);
+
+    cudaStream_t st = 0;
+    char* ctl = (char*)(base + kNaCtl);
+    SmallArgs a{};
+    double* x0_dev = (double*)(ctl + 128);
+    const cudaMemcpyKind k0 = is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(x0_dev, x0, sizeof(double) * d, k0, st) != cudaSuccess) return PITN_ECUDA;
+    // everything that must start at zero: per-iteration reductions, barrier, error, record
+    if (cudaMemsetAsync(base + kNaRes, 0, sizeof(double) * (kNaCtl - kNaRes) + 128, st) != cudaSuccess)
+        return PITN_ECUDA;
+    a.x0 = x0_dev;
+    a.X0 = traj_out;
+    a.X1 = base + kNaX1;
+    a.out = traj_out;
+    a.scratch = base + kNaScratch;
+    a.agg = base + kNaAgg;
+    a.N = N;
+    a.chunk = chunk;
+    a.h = h;
+    a.tol = tol;
+    a.guarded = (guard_B > 0.0 && std::isfinite(guard_B)) ? 1 : 0;
+    {
+        const double cap = a.guarded ? guard_B : DBL_MAX;
+        std::memcpy(&a.cap_bits, &cap, sizeof(cap));
+    }
+    a.max_iter = max_iter;
+    a.q_init = 0;
+    for (int i = 0; i < 4; ++i) a.params[i] = hp[i];
+    a.res_bits = (unsigned long long*)(base + kNaRes);
+    a.qenc = (unsigned long long*)(base + kNaQ);
+    a.bar = (unsigned*)ctl;
+    a.err = (int*)(ctl + 16);
+    a.rec = (SolveRecord*)(ctl + 32);
+    void* args[] = {(void*)&a};
+    const void* kern = (system_id == PITN_LORENZ63) ? (const void*)newton_small_kernel<Lorenz63>
+                       : (system_id == PITN_VDP)    ? (const void*)newton_small_kernel<VanDerPol>
+                                                    : (const void*)newton_small_kernel<LinearOsc>;
+    if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st) != cudaSuccess) {
+        cudaGetLastError();
+        return PITN_ECUDA;
+    }
+    count_launch(1);
+    SolveRecord rec{};
+    int err = 0;
+    if (cudaMemcpy(&err, ctl + 16, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&rec, ctl + 32, sizeof(SolveRecord), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PITN_ECUDA;
+    if (err != 0) return err;
+    if (result) {
+        result->iters = rec.iters;
+        result->status = rec.status;
+        result->final_res = rec.final_res;
+        result->guard_index = rec.guard_index;
+    }
+    return rec.status;
+}

@@ -74,6 +74,9 @@ def lib():
         L.pitn_release_workspace.restype = c_int
         L.pitn_launch_count.argtypes = []
         L.pitn_launch_count.restype = i64
+        L.pitn_solve_noalloc.argtypes = [c_int, vp, vp, d, i64, c_int, d, c_int, d, vp,
+                                          ctypes.POINTER(pitn_result)]
+        L.pitn_solve_noalloc.restype = c_int
         L.pitn_timing_enable.argtypes = [c_int]
         L.pitn_timing_enable.restype = c_int
         L.pitn_timing_reset.argtypes = []
@@ -155,6 +158,16 @@ def pitn_backward(system_id, B, params, x0, h, N, d, traj, grad_traj, grad_xN, c
                                _ptr(N, np.int64), int(d), _ptr(traj), _ptr(grad_traj),
                                _ptr(grad_xN), int(ckpt_every), _ptr(grad_x0_out),
                                _ptr(grad_params_out), optp)
+
+
+def pitn_solve_noalloc(system_id, params, x0, h, N, d, tol, max_iter, guard_B, traj_out):
+    """Allocation-free solve (small-state systems; traj_out must be device memory).
+    Returns (code, pitn_result)."""
+    res = pitn_result()
+    rc = lib().pitn_solve_noalloc(int(system_id), _ptr(params), _ptr(x0), float(h), int(N), int(d),
+                                  float(tol), int(max_iter), float(guard_B), _ptr(traj_out),
+                                  ctypes.byref(res))
+    return rc, res
 
 
 def pitn_num_params(system_id):
