@@ -80,6 +80,14 @@ def workload(name):
         return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=1,
                     desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, BF16 tensor-core "
                          "composes (FP32 accumulate), FP64 residual and update")
+    if name == "batch":
+        return dict(kind="batch", bt=W.lorenz_batch(), tol=1e-8, max_iter=50, guard_B=100.0,
+                    desc="4096 lorenz63 IVPs (seed 0; sigma~U[8,12], rho~U[20,35], beta~U[2,3], "
+                         "x0~N(0,25I)), h=1e-3, N_i~U{2^10..2^16}, guarded Newton B=100, max_iter 50")
+    if name == "batch_small":
+        return dict(kind="batch", bt=W.lorenz_batch(n_max=1 << 13), tol=1e-8, max_iter=100, guard_B=100.0,
+                    desc="4096 lorenz63 IVPs (seed 0), h=1e-3, N_i~U{2^10..2^13}, guarded Newton B=100, "
+                         "max_iter 100")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -146,6 +154,95 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def run_ours_batch(args, rank, world, local_rank, spec):
+    import torch
+    import paper_2511_01465_gb300 as pk
+    from paper_2511_01465_gb300 import pitn as P
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    bt = spec["bt"]
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device=dev)
+    params, x0, h, N = t(bt.params), t(bt.x0), t(bt.h), t(bt.N, torch.int64)
+    M, d = int(bt.N.sum()), bt.d
+    traj = torch.empty((M, d), dtype=torch.float64, device=dev)
+    offs = torch.empty(bt.B + 1, dtype=torch.int64, device=dev)
+    iters = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    status = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    res = torch.empty(bt.B, dtype=torch.float64, device=dev)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+
+    def solve_once():
+        rc = P.pitn_solve_batch(bt.system, bt.B, params, x0, h, N, d, spec["tol"], spec["max_iter"],
+                                traj, offs, iters, status, res, opt)
+        P.check(rc, "pitn_solve_batch")
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    P.pitn_timing_reset()
+    P.pitn_timing_enable(True)
+    launches0 = pk.pitn_launch_count()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = pk.pitn_launch_count() - launches0
+    P.pitn_timing_enable(False)
+    kms, kl = P.pitn_timing_get("batch")
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    st_h, it_h, res_h = status.cpu().numpy(), iters.cpu().numpy(), res.cpu().numpy()
+    ok = (st_h == P.PITN_OK) & (res_h <= spec["tol"])
+    solved = int(bt.N[ok].sum())
+    value = world * solved / (ms_per_step / 1e3)
+    # FP64 flops of the iterations actually run, counted from the kernel source
+    p1, p3 = SMALL_FLOPS["lorenz"]
+    flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
+    achieved = flops / (kms / 1e3 / args.steps) / 1e12 if kms > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "batch iteration graph (fold, decide, replay, end)",
+                "kernel_launches_per_step": kl / args.steps, "kernel_ms_per_launch": kms / max(kl, 1),
+                "note": "FP64 flops of the executed iterations counted from the kernel source; "
+                        "peak = nominal GB300 FP64"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "B": bt.B, "sum_N": M, "d": d, "tol": spec["tol"],
+                       "max_iter": spec["max_iter"], "converged_ivps": int(ok.sum()),
+                       "converged_steps": solved, "not_converged_ivps": int((st_h == 1).sum()),
+                       "nonfinite_ivps": int((st_h == 2).sum()),
+                       "mean_newton_updates": float(it_h.mean()),
+                       "step_ms": [round(x, 3) for x in times],
+                       "l2": "inputs (>3 GB per trajectory buffer) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    return line
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_2511_01465_gb300 as pk
@@ -337,6 +434,23 @@ def cpu_baseline(spec, full_passes, sample_iters):
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3}
 
 
+def cpu_baseline_batch(spec, n_ivps=24):
+    """The oracle solving the first n_ivps IVPs of the batch one after another."""
+    import oracle as O
+    bt = spec["bt"]
+    t0 = time.perf_counter()
+    solved = 0
+    for b in range(n_ivps):
+        r = O.newton(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b], spec["tol"], spec["max_iter"],
+                     guard_B=spec["guard_B"])
+        if r["status"] == O.OK:
+            solved += int(bt.N[b])
+    dt = time.perf_counter() - t0
+    return {"value": solved / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle Newton on the first {n_ivps} IVPs of the batch, one after another "
+                      f"({dt:.1f} s)"}
+
+
 def run_reference(args):
     spec = workload(args.workload)
     wl = spec["wl"]
@@ -387,8 +501,14 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import __graft_entry__ as ge
     ge.build_library_only()
-    line = run_ours(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    spec0 = workload(args.workload)
+    if spec0["kind"] == "batch":
+        line = run_ours_batch(args, rank, world, local_rank, spec0)
+    else:
+        line = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and spec0["kind"] == "batch":
+        line["cpu_baseline"] = cpu_baseline_batch(spec0)
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         full_passes = oracle_passes(args.workload, line["config"]["newton_updates"] + 1)
         line["cpu_baseline"] = cpu_baseline(workload(args.workload), full_passes,
                                             SAMPLE_ITERS.get(args.workload, 5))

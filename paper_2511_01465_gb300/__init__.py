@@ -10,7 +10,7 @@ its Python binding.
 Modules:
   pitn       ctypes binding, same names as the C ABI
   api        torch helpers: solve, solve_batch, backward
-  autograd   torch.autograd.Function over solve_batch/backward
+  autograd   torch.autograd.Function over solve_batch/backward (import it explicitly)
   workloads  seeded synthetic inputs
   build      nvcc build of libpitn.so
 """

@@ -724,9 +724,3 @@ int fkpp_solve(const SolveIO& io, double h, int64_t N, int d, double tol, int ma
 }
 
 }  // namespace pitn_host
-
-extern "C" int pitn_backward(int, int64_t, const double*, const double*, const double*,
-                             const int64_t*, int, const double*, const double*, const double*, int,
-                             double*, double*, const pitn_options*) {
-    return PITN_EUNSUPPORTED;
-}

@@ -9,6 +9,8 @@
 //   jvec(jv, v, out):     out = J v
 //   jtvec(jv, v, out):    out = J^T v           (adjoint)
 //   vjp_param(xp, v, g):  g += (dphi/dp(xp))^T v  (adjoint, g has P entries)
+//   jac(xp, jv):          the compact Jacobian alone
+//   jfull(jv, J):         the dense D x D Jacobian from its compact form
 // The compact form stores only the state-dependent entries of J, so an
 // element of the scan costs D + JN registers instead of D + D*D.
 #pragma once
@@ -58,6 +60,16 @@ struct Lorenz63 {
         o[1] = j01 * v0 + j11 * v1 + jv[1] * v2;
         o[2] = -jv[1] * v1 + j22 * v2;
     }
+    __device__ __forceinline__ void jfull(const double* jv, double* J) const {
+        J[0] = j00;   J[1] = j01;   J[2] = 0.0;
+        J[3] = jv[0]; J[4] = j11;   J[5] = -jv[1];
+        J[6] = jv[2]; J[7] = jv[1]; J[8] = j22;
+    }
+    __device__ __forceinline__ void jac(const double* xp, double* jv) const {
+        jv[0] = h * (r - xp[2]);
+        jv[1] = h * xp[0];
+        jv[2] = h * xp[1];
+    }
     __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
         g[0] += h * (xp[1] - xp[0]) * v[0];
         g[1] += h * xp[0] * v[1];
@@ -98,6 +110,15 @@ struct VanDerPol {
         o[0] = v0 + jv[0] * v1;
         o[1] = h * v0 + jv[1] * v1;
     }
+    __device__ __forceinline__ void jfull(const double* jv, double* J) const {
+        J[0] = 1.0;   J[1] = h;
+        J[2] = jv[0]; J[3] = jv[1];
+    }
+    __device__ __forceinline__ void jac(const double* xp, double* jv) const {
+        const double x = xp[0], v = xp[1];
+        jv[0] = h * (-2.0 * mu * x * v - 1.0);
+        jv[1] = 1.0 + h * mu * (1.0 - x * x);
+    }
     __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
         g[0] += h * (1.0 - xp[0] * xp[0]) * xp[1] * v[1];
     }
@@ -135,6 +156,11 @@ struct LinearOsc {
         o[0] = v0 + j10 * v1;
         o[1] = h * v0 + j11 * v1;
     }
+    __device__ __forceinline__ void jfull(const double*, double* J) const {
+        J[0] = 1.0; J[1] = h;
+        J[2] = j10; J[3] = j11;
+    }
+    __device__ __forceinline__ void jac(const double*, double* jv) const { jv[0] = 0.0; }
     __device__ __forceinline__ void vjp_param(const double* xp, const double* v, double* g) const {
         g[0] += h * (-2.0 * w * xp[0] - 2.0 * z * xp[1]) * v[1];
         g[1] += h * (-2.0 * w * xp[1]) * v[1];
