@@ -88,6 +88,11 @@ def workload(name):
         return dict(kind="batch", bt=W.lorenz_batch(n_max=1 << 13), tol=1e-8, max_iter=100, guard_B=100.0,
                     desc="4096 lorenz63 IVPs (seed 0), h=1e-3, N_i~U{2^10..2^13}, guarded Newton B=100, "
                          "max_iter 100")
+    if name == "adjoint":
+        return dict(kind="adjoint", bt=W.vdp_adjoint_batch(), tol=1e-10, max_iter=200, guard_B=100.0,
+                    desc="256 van_der_pol IVPs (seed 0; mu~U[0.5,2], x0~U[-2,2]^2), h=1e-3, N=2^14: "
+                         "batched Newton forward (guarded B=100, tol 1e-10) + adjoint reverse scan "
+                         "(checkpoint every 1024 steps), loss sum ||x_N - (1,0)||^2")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -228,9 +233,30 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                 "kernel_launches_per_step": kl / args.steps, "kernel_ms_per_launch": kms / max(kl, 1),
                 "note": "FP64 flops of the executed iterations counted from the kernel source; "
                         "peak = nominal GB300 FP64"}
+    # the same IVPs solved one at a time by the single-IVP GPU solver (a sample)
+    single = None
+    if rank == 0:
+        n_s = min(64, bt.B)
+        so = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+        tr1 = torch.empty((int(bt.N[:n_s].max()), d), dtype=torch.float64, device=dev)
+        ps = [t(bt.params[b]) for b in range(n_s)]
+        xs = [t(bt.x0[b]) for b in range(n_s)]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        solved1 = 0
+        for b in range(n_s):
+            rc1, r1 = P.pitn_solve_ex(bt.system, ps[b], xs[b], float(bt.h[b]), int(bt.N[b]), d, spec["tol"],
+                                      spec["max_iter"], tr1, so)
+            if r1.status == P.PITN_OK and r1.final_res <= spec["tol"]:
+                solved1 += int(bt.N[b])
+        torch.cuda.synchronize(dev)
+        dt1 = time.perf_counter() - t0
+        single = {"value": solved1 / dt1, "unit": UNIT,
+                  "sample": f"first {n_s} IVPs, one pitn_solve_ex call each ({dt1 * 1e3:.1f} ms)"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "single_ivp_gpu_solver": single,
             "config": {"workload": spec["desc"], "B": bt.B, "sum_N": M, "d": d, "tol": spec["tol"],
                        "max_iter": spec["max_iter"], "converged_ivps": int(ok.sum()),
                        "converged_steps": solved, "not_converged_ivps": int((st_h == 1).sum()),
@@ -241,6 +267,80 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
     return line
+
+
+def run_ours_adjoint(args, rank, world, local_rank, spec):
+    import torch
+    import paper_2511_01465_gb300 as pk
+    from paper_2511_01465_gb300 import pitn as P
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    bt = spec["bt"]
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device=dev)
+    params, x0, h, N = t(bt.params), t(bt.x0), t(bt.h), t(bt.N, torch.int64)
+    M, d = int(bt.N.sum()), bt.d
+    traj = torch.empty((M, d), dtype=torch.float64, device=dev)
+    offs = torch.empty(bt.B + 1, dtype=torch.int64, device=dev)
+    iters = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    status = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    res = torch.empty(bt.B, dtype=torch.float64, device=dev)
+    gx0 = torch.empty((bt.B, d), dtype=torch.float64, device=dev)
+    gp = torch.empty((bt.B, bt.params.shape[1]), dtype=torch.float64, device=dev)
+    target = t([1.0, 0.0])
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+
+    def step():
+        rc = P.pitn_solve_batch(bt.system, bt.B, params, x0, h, N, d, spec["tol"], spec["max_iter"],
+                                traj, offs, iters, status, res, opt)
+        P.check(rc, "pitn_solve_batch")
+        last = offs[1:] - 1
+        gN = (2.0 * (traj[last] - target)).contiguous()
+        P.check(P.pitn_backward(bt.system, bt.B, params, x0, h, N, d, traj, None, gN, 1024, gx0, gp, opt),
+                "pitn_backward")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    P.pitn_timing_reset()
+    P.pitn_timing_enable(True)
+    launches0 = pk.pitn_launch_count()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = pk.pitn_launch_count() - launches0
+    P.pitn_timing_enable(False)
+    fwd_ms, fwd_n = P.pitn_timing_get("batch")
+    adj_ms, adj_n = P.pitn_timing_get("adjoint")
+    ms_per_step = float(sum(times)) / args.steps
+    st_h, it_h = status.cpu().numpy(), iters.cpu().numpy()
+    ok = st_h == P.PITN_OK
+    value = float(bt.N[ok].sum()) / (ms_per_step / 1e3)
+    p1, p3 = SMALL_FLOPS["vdp"]
+    flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
+    ach = flops / (fwd_ms / 1e3 / args.steps) / 1e12 if fwd_ms > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "batch iteration graph (forward solve)",
+                "kernel_launches_per_step": fwd_n / args.steps, "kernel_ms_per_launch": fwd_ms / max(fwd_n, 1),
+                "note": "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"}
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": spec["desc"], "B": bt.B, "sum_N": M, "d": d, "tol": spec["tol"],
+                       "converged_ivps": int(ok.sum()), "mean_newton_updates": float(it_h.mean()),
+                       "forward_ms_per_step": fwd_ms / args.steps,
+                       "adjoint_ms_per_step": adj_ms / args.steps,
+                       "step_ms": [round(x, 3) for x in times], "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": None, "gpu_launches": int(launches), "clocks": None}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -443,16 +543,32 @@ def cpu_baseline_batch(spec, n_ivps=24):
     for b in range(n_ivps):
         r = O.newton(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b], spec["tol"], spec["max_iter"],
                      guard_B=spec["guard_B"])
+        if spec["kind"] == "adjoint":
+            O.adjoint(bt.system, bt.params[b], bt.x0[b], bt.h[b], r["traj"],
+                      grad_xN=2.0 * (r["traj"][-1] - [1.0, 0.0]))
         if r["status"] == O.OK:
             solved += int(bt.N[b])
     dt = time.perf_counter() - t0
     return {"value": solved / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle Newton on the first {n_ivps} IVPs of the batch, one after another "
-                      f"({dt:.1f} s)"}
+            "sample": f"oracle Newton{' + adjoint' if spec['kind'] == 'adjoint' else ''} on the first "
+                      f"{n_ivps} IVPs of the batch, one after another ({dt:.1f} s)"}
 
 
 def run_reference(args):
     spec = workload(args.workload)
+    if spec["kind"] != "single":
+        vals = []
+        for _ in range(args.steps):
+            vals.append(cpu_baseline_batch(spec)["value"])
+        v = statistics.median(vals)
+        cb = cpu_baseline_batch(spec)
+        bt = spec["bt"]
+        return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": spec["desc"], "B": bt.B},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": cb["sample"]},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     wl = spec["wl"]
     import oracle as O
     # number of residual evaluations of the oracle's full solve
@@ -504,9 +620,11 @@ def main():
     spec0 = workload(args.workload)
     if spec0["kind"] == "batch":
         line = run_ours_batch(args, rank, world, local_rank, spec0)
+    elif spec0["kind"] == "adjoint":
+        line = run_ours_adjoint(args, rank, world, local_rank, spec0)
     else:
         line = run_ours(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and spec0["kind"] == "batch":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and spec0["kind"] in ("batch", "adjoint"):
         line["cpu_baseline"] = cpu_baseline_batch(spec0)
     elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         full_passes = oracle_passes(args.workload, line["config"]["newton_updates"] + 1)

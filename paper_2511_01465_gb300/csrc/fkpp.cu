@@ -68,7 +68,7 @@ __device__ __forceinline__ double fk_x(const FkParams& p, long long k, int i) {
 // different banks.
 template <typename Real> struct FoldTraits;
 template <> struct FoldTraits<float> {
-    static constexpr int R = 64, TPC = 2, PADR = 16, THREADS = FD * TPC;
+    static constexpr int R = 32, TPC = 4, PADR = 8, THREADS = FD * TPC;
 };
 template <> struct FoldTraits<double> {
     static constexpr int R = 32, TPC = 4, PADR = 2, THREADS = FD * TPC;
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
     constexpr int R = Tr::R, TPC = Tr::TPC;
     constexpr int FDP = fold_row_stride<Real>();
     extern __shared__ __align__(16) unsigned char smem[];
-    Real* a_s = reinterpret_cast<Real*>(smem);                                  // [TS][FDP]
-    double* r_s = reinterpret_cast<double*>(smem + ((sizeof(Real) * p.TS * FDP + 15) & ~(size_t)15));
+    Real* a_s = reinterpret_cast<Real*>(smem);            // [TS][FDP]  1 + e (leaf diagonal)
+    Real* r_s = a_s + (size_t)p.TS * FDP;                  // [TS][FDP]  residual (for the vector fold)
     const long long t = blockIdx.x;
     const long long k0 = 1 + t * p.TS;
     const long long k1 = min(p.N, k0 + p.TS);
@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
 
     unsigned long long my_res = 0ull;
     bool my_nf = false;
+    const Real hR = (Real)p.h, oR = (Real)p.o;
     for (int idx = threadIdx.x; idx < p.TS * FD; idx += blockDim.x) {
         const int s = idx / FD, i = idx - s * FD;
         Real a = (Real)1.0;
@@ -131,14 +132,16 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
             const double un = fk_x(p, k, i);
             const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
             rr = un - (u + p.h * f);
-            a = (Real)(1.0 + (p.h * (1.0 - 2.0 * u) - 2.0 * p.o));
+            // leaf diagonal in the working precision of the fold
+            const Real uR = (Real)u;
+            a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
             p.r[k * d + i] = rr;
             unsigned long long b = (unsigned long long)__double_as_longlong(fabs(rr));
             my_res = b > my_res ? b : my_res;
             my_nf |= !isfinite(rr);
         }
         a_s[s * FDP + pidx<Real>(i)] = a;
-        r_s[s * FDP + pidx<Real>(i)] = rr;
+        r_s[s * FDP + pidx<Real>(i)] = (Real)rr;
     }
     if (t == 0) {  // element 0: r_0 = x_1 - phi(x0)
         for (int i = threadIdx.x; i < d; i += blockDim.x) {
@@ -187,25 +190,26 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
         for (int i = 0; i < R; ++i) col[i] = s[i] - ((row0 + i == j) ? (Real)1.0 : (Real)0.0);
     }
     if (warp == 0) {
-        double b[4] = {0.0, 0.0, 0.0, 0.0};
+        // vector part of the aggregate, in the working precision
+        Real b[4] = {(Real)0.0, (Real)0.0, (Real)0.0, (Real)0.0};
         const int r0 = 4 * lane;
         for (int st = 0; st < len; ++st) {
             const Real* a = a_s + st * FDP;
-            const double* rr = r_s + st * FDP;
-            const double up = __shfl_up_sync(0xffffffffu, b[3], 1);
-            const double dn = __shfl_down_sync(0xffffffffu, b[0], 1);
-            double prev = (lane == 0) ? 0.0 : up;
+            const Real* rr = r_s + st * FDP;
+            const Real up = __shfl_up_sync(0xffffffffu, b[3], 1);
+            const Real dn = __shfl_down_sync(0xffffffffu, b[0], 1);
+            Real prev = (lane == 0) ? (Real)0.0 : up;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const double cur = b[i];
-                const double nxt = (i < 3) ? b[i + 1] : ((lane == 31) ? 0.0 : dn);
-                const double oi = (r0 + i < d) ? p.o : 0.0;
-                b[i] = (double)a[pidx<Real>(r0 + i)] * cur + oi * (prev + nxt) - rr[pidx<Real>(r0 + i)];
+                const Real cur = b[i];
+                const Real nxt = (i < 3) ? b[i + 1] : ((lane == 31) ? (Real)0.0 : dn);
+                const Real oi = (r0 + i < d) ? o : (Real)0.0;
+                b[i] = a[pidx<Real>(r0 + i)] * cur + oi * (prev + nxt) - rr[pidx<Real>(r0 + i)];
                 prev = cur;
             }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) b_out[(size_t)t * FD + r0 + i] = (Real)b[i];
+        for (int i = 0; i < 4; ++i) b_out[(size_t)t * FD + r0 + i] = b[i];
     }
 }
 
@@ -404,20 +408,21 @@ __global__ void __launch_bounds__(128) fk_down_kernel(const Real* __restrict__ S
                                                       const Real* __restrict__ z_parent,
                                                       Real* __restrict__ z_child, long long n_child,
                                                       const double* __restrict__ r0, int d) {
-    __shared__ double zs[FD];
+    __shared__ Real zs[FD];
     const long long m = blockIdx.x;
     const int i = threadIdx.x;
-    double zi;
-    if (r0) zi = (i < d) ? -r0[i] : 0.0;  // root: dx_1 = -h_1
-    else zi = (double)z_parent[m * FD + i];
+    Real zi;
+    if (r0) zi = (i < d) ? (Real)(-r0[i]) : (Real)0.0;  // root: dx_1 = -h_1
+    else zi = z_parent[m * FD + i];
     zs[i] = zi;
     __syncthreads();
-    z_child[(2 * m) * FD + i] = (Real)zi;
+    z_child[(2 * m) * FD + i] = zi;
     if (2 * m + 1 < n_child) {
         const Real* S = S_child + (size_t)(2 * m) * FD * FD;
-        double s = zi + (double)b_child[(2 * m) * FD + i];
-        for (int k = 0; k < FD; ++k) s = fma((double)S[(size_t)k * FD + i], zs[k], s);
-        z_child[(2 * m + 1) * FD + i] = (Real)s;
+        Real s = zi + b_child[(2 * m) * FD + i];
+#pragma unroll 8
+        for (int k = 0; k < FD; ++k) s = fma(S[(size_t)k * FD + i], zs[k], s);
+        z_child[(2 * m + 1) * FD + i] = s;
     }
 }
 
@@ -453,42 +458,56 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
             }
             if (bad) my_q = ~0ull;  // ~0 = index 0
         }
-        for (long long k = k0; k < k1; ++k) {
-            // neighbours of x_k (= xprev) for the diagonal; a_i = 1 + h(1 - 2u_i) - 2o
-            double xc[4], a[4], rk[4];
+        // steps in groups of G: the loads of a group are issued together so
+        // their latency overlaps; the recurrence itself is serial in k
+        constexpr int G = 4;
+        for (long long kg = k0; kg < k1; kg += G) {
+            double xc[G][4], rk[G][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int row = r0 + i;
-                xc[i] = (row < d) ? fk_x(p, k, row) : 0.0;
-                rk[i] = (row < d) ? p.r[k * d + row] : 0.0;
-                a[i] = 1.0 + (p.h * (1.0 - 2.0 * xprev[i]) - 2.0 * p.o);
-            }
-            const double up = __shfl_up_sync(0xffffffffu, z[3], 1);
-            const double dn = __shfl_down_sync(0xffffffffu, z[0], 1);
-            double prev = (lane == 0) ? 0.0 : up;
-            double nz[4];
+            for (int gq = 0; gq < G; ++gq) {
+                const long long k = kg + gq;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const double cur = z[i];
-                const double nxt = (i < 3) ? z[i + 1] : ((lane == 31) ? 0.0 : dn);
-                const double oi = (r0 + i < d) ? p.o : 0.0;
-                nz[i] = (r0 + i < d) ? (a[i] * cur + oi * (prev + nxt) - rk[i]) : 0.0;
-                prev = cur;
-            }
-            bool bad = false;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                z[i] = nz[i];
-                const int row = r0 + i;
-                if (row < d) {
-                    bad |= !(fabs(z[i]) <= p.cap);
-                    p.Xn[k * d + row] = xc[i] + z[i];
+                for (int i = 0; i < 4; ++i) {
+                    const int row = r0 + i;
+                    const bool live = (k < k1) && (row < d);
+                    xc[gq][i] = live ? fk_x(p, k, row) : 0.0;
+                    rk[gq][i] = live ? p.r[k * d + row] : 0.0;
                 }
-                xprev[i] = xc[i];
             }
-            if (bad) {
-                const unsigned long long e = ~(unsigned long long)k;
-                my_q = e > my_q ? e : my_q;
+#pragma unroll
+            for (int gq = 0; gq < G; ++gq) {
+                const long long k = kg + gq;
+                if (k >= k1) break;
+                double a[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = 1.0 + (p.h * (1.0 - 2.0 * xprev[i]) - 2.0 * p.o);
+                const double up = __shfl_up_sync(0xffffffffu, z[3], 1);
+                const double dn = __shfl_down_sync(0xffffffffu, z[0], 1);
+                double prev = (lane == 0) ? 0.0 : up;
+                double nz[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const double cur = z[i];
+                    const double nxt = (i < 3) ? z[i + 1] : ((lane == 31) ? 0.0 : dn);
+                    const double oi = (r0 + i < d) ? p.o : 0.0;
+                    nz[i] = (r0 + i < d) ? (a[i] * cur + oi * (prev + nxt) - rk[gq][i]) : 0.0;
+                    prev = cur;
+                }
+                bool bad = false;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    z[i] = nz[i];
+                    const int row = r0 + i;
+                    if (row < d) {
+                        bad |= !(fabs(z[i]) <= p.cap);
+                        p.Xn[k * d + row] = xc[gq][i] + z[i];
+                    }
+                    xprev[i] = xc[gq][i];
+                }
+                if (bad) {
+                    const unsigned long long e = ~(unsigned long long)k;
+                    my_q = e > my_q ? e : my_q;
+                }
             }
         }
     }
@@ -530,8 +549,7 @@ using namespace pitn;
 namespace {
 template <typename Real>
 size_t fold_smem_bytes(int TS) {
-    const size_t a = ((sizeof(Real) * TS * fold_row_stride<Real>()) + 15) & ~(size_t)15;
-    return a + sizeof(double) * TS * fold_row_stride<Real>();
+    return 2 * sizeof(Real) * (size_t)TS * fold_row_stride<Real>();
 }
 
 struct Tree {

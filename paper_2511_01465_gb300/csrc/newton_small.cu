@@ -257,14 +257,20 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         const double* __restrict__ Xc = cur ? a.X1 : a.X0;
         double* __restrict__ Xn = cur ? a.X0 : a.X1;
         // ---- phase 1: residual, Jacobian, fold -------------------------------
+        // Elements from sfill on lie in the guard's fill region: all their
+        // states equal x_{q-1}, so every one of them is the same element
+        // (J(x_{q-1}), -r_f); a thread folds its share of them by binary
+        // powering instead of one by one.
+        const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
+        const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
         unsigned long long my_res = 0ull;
         double P[D * D], c[D];
         mat_identity<D>(P);
 #pragma unroll
         for (int j = 0; j < D; ++j) c[j] = 0.0;
         double xp[D];
-        if (k0 < k1) load_state<D>(Xc, a.x0, k0 - 1, q, xp);
-        for (long long k = k0; k < k1; ++k) {
+        if (k0 < kreg) load_state<D>(Xc, a.x0, k0 - 1, q, xp);
+        for (long long k = k0; k < kreg; ++k) {
             double x[D], r[D], jv[JN];
             load_state<D>(Xc, a.x0, k, q, x);
             sys.eval(xp, x, r, jv);
@@ -292,6 +298,27 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             }
 #pragma unroll
             for (int j = 0; j < D; ++j) xp[j] = x[j];
+        }
+        if (kreg < k1) {
+            double xf[D], rf[D], jvf[JN], EP[D * D], Ec[D], RP[D * D], Rc[D];
+            load_state<D>(Xc, a.x0, q - 1, q, xf);
+            sys.eval(xf, xf, rf, jvf);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(rf[j]) & kAbsMask;
+                my_res = b > my_res ? b : my_res;
+                Ec[j] = -rf[j];
+                Rc[j] = 0.0;
+            }
+            sys.jfull(jvf, EP);
+            mat_identity<D>(RP);
+            for (long long e = k1 - kreg;;) {
+                if (e & 1) compose<D>(EP, Ec, RP, Rc, RP, Rc);
+                e >>= 1;
+                if (!e) break;
+                compose<D>(EP, Ec, EP, Ec, EP, Ec);
+            }
+            compose<D>(RP, Rc, P, c, P, c);
         }
         double eP[D * D], ec[D];
         block_scan<D>(P, c, eP, ec, s_wex, s_tot);
@@ -360,13 +387,15 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         }
 
         // ---- phase 3: replay + update ------------------------------------------
+        // A thread stops at its first cut index: every later state of its
+        // chunk lies beyond the iteration's cut and is never read again.
         unsigned long long my_q = 0ull;
         {
             double zw[D], z[D];
             apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
             apply<D>(eP, ec, zw, z);
             bool found = false;
-            for (long long k = k0; k < k1; ++k) {
+            for (long long k = k0; k < kreg && !found; ++k) {
                 double jv[JN], r[D], x[D];
 #pragma unroll
                 for (int j = 0; j < JN; ++j) jv[j] = scr[k * W + j];
@@ -389,9 +418,30 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
                     zb = b > zb ? b : zb;
                 }
-                if (!found && zb > a.cap_bits) {
+                if (zb > a.cap_bits) {
                     found = true;
                     my_q = ~(unsigned long long)k;
+                }
+            }
+            if (!found && kreg < k1) {
+                double xf[D], rf[D], jvf[JN];
+                load_state<D>(Xc, a.x0, q - 1, q, xf);
+                sys.eval(xf, xf, rf, jvf);
+                for (long long k = kreg; k < k1; ++k) {
+                    double tz[D];
+                    sys.jvec(jvf, z, tz);
+                    unsigned long long zb = 0ull;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        z[j] = tz[j] - rf[j];
+                        Xn[k * D + j] = xf[j] + z[j];
+                        const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
+                        zb = b > zb ? b : zb;
+                    }
+                    if (zb > a.cap_bits) {
+                        my_q = ~(unsigned long long)k;
+                        break;
+                    }
                 }
             }
         }

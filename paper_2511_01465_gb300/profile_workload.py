@@ -1,0 +1,65 @@
+"""Runs one workload a few times, for profiling under ncu.
+
+    python -m paper_2511_01465_gb300.profile_workload --workload vdp --N 1048576 --max-iter 10 --repeat 2
+    ncu --set full --clock-control none -k regex:newton_small -s 1 -c 1 \\
+        python -m paper_2511_01465_gb300.profile_workload --workload vdp --N 1048576 --max-iter 10
+
+Workloads: vdp, lorenz, osc (single IVP), fkpp, fkpp_mixed (d = 128),
+batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]), adjoint
+(Van der Pol batch forward + backward).  Sizes default to the small cases
+used for full captures; prints the outcome of the last repetition.
+"""
+from __future__ import annotations
+
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="vdp")
+    ap.add_argument("--N", type=int, default=1 << 20)
+    ap.add_argument("--max-iter", type=int, default=10)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--guard", type=float, default=100.0)
+    ap.add_argument("--repeat", type=int, default=2)
+    ap.add_argument("--B", type=int, default=512)
+    ap.add_argument("--nmin", type=int, default=1 << 10)
+    ap.add_argument("--nmax", type=int, default=1 << 13)
+    a = ap.parse_args()
+
+    import torch
+
+    from . import api, workloads as W
+    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16
+
+    out = None
+    for _ in range(a.repeat):
+        if a.workload in ("vdp", "lorenz", "osc"):
+            wl = {"vdp": W.vdp, "lorenz": W.lorenz, "osc": W.damped_oscillator}[a.workload](N=a.N)
+            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, guard_B=a.guard)[1]
+        elif a.workload in ("fkpp", "fkpp_mixed"):
+            wl = W.fkpp(N=a.N)
+            prec = PITN_PREC_MIXED_BF16 if a.workload == "fkpp_mixed" else PITN_PREC_FP64
+            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, precision=prec)[1]
+        elif a.workload == "batch":
+            bt = W.lorenz_batch(B=a.B, n_min=a.nmin, n_max=a.nmax)
+            r = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, a.tol, a.max_iter, guard_B=a.guard)
+            out = {"mean_iters": float(r[2].float().mean()), "converged": int((r[3] == 0).sum())}
+        elif a.workload == "adjoint":
+            bt = W.vdp_adjoint_batch(B=a.B, N=a.N)
+            traj, offs, it, st, res = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, 1e-12,
+                                                      a.max_iter, guard_B=a.guard)
+            last = offs[1:] - 1
+            gN = (2.0 * (traj[last] - torch.tensor([1.0, 0.0], dtype=torch.float64, device="cuda"))).contiguous()
+            gx0, gp = api.backward(bt.system, bt.params, bt.x0, bt.h, bt.N, traj, grad_xN=gN)
+            out = {"grad_norm": float(np.linalg.norm(gp.cpu().numpy()))}
+        else:
+            raise SystemExit(f"unknown workload {a.workload}")
+    torch.cuda.synchronize()
+    print(out)
+
+
+if __name__ == "__main__":
+    main()
