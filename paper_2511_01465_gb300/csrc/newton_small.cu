@@ -242,8 +242,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
     const int lane = threadIdx.x & 31;
     const long long N = a.N;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long k0 = gt * a.chunk;
-    const long long k1 = min(N, k0 + a.chunk);
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
     const unsigned G = gridDim.x;
     double* __restrict__ scr = a.scratch;
 
@@ -262,6 +261,21 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         // (J(x_{q-1}), -r_f); a thread folds its share of them by binary
         // powering instead of one by one.
         const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
+        // Work partition of this iteration: a regular element costs about four
+        // times a fill element (phase 1 + phase 3 against phase 3 only), so the
+        // steps are split over all threads by that weight; every thread derives
+        // its contiguous range [k0, k1) from (N, sfill) alone.
+        long long k0, k1;
+        {
+            const long long wreg = 4 * sfill;
+            const long long wtot = wreg + (N - sfill);
+            const long long per = (wtot + nthreads - 1) / nthreads;
+            const long long w0 = gt * per, w1 = w0 + per;
+            k0 = (w0 <= wreg) ? (w0 + 3) / 4 : sfill + (w0 - wreg);
+            k1 = (w1 <= wreg) ? (w1 + 3) / 4 : sfill + (w1 - wreg);
+            k0 = min(N, k0);
+            k1 = min(N, k1);
+        }
         const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
         unsigned long long my_res = 0ull;
         double P[D * D], c[D];
@@ -398,9 +412,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             for (long long k = k0; k < kreg && !found; ++k) {
                 double jv[JN], r[D], x[D];
 #pragma unroll
-                for (int j = 0; j < JN; ++j) jv[j] = scr[k * W + j];
+                for (int j = 0; j < JN; ++j) jv[j] = __ldcg(scr + k * W + j);
 #pragma unroll
-                for (int j = 0; j < D; ++j) r[j] = scr[k * W + JN + j];
+                for (int j = 0; j < D; ++j) r[j] = __ldcg(scr + k * W + JN + j);
                 load_state<D>(Xc, a.x0, k, q, x);
                 if (k == 0) {
 #pragma unroll
