@@ -395,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     P.pitn_timing_enable(False)
     ktimes = {k: P.pitn_timing_get(k) for k in
-              ("newton_small", "fkpp_fold", "fkpp_compose", "fkpp_down", "fkpp_replay")}
+              ("newton_small", "fkpp_residual", "fkpp_fold", "fkpp_compose", "fkpp_down", "fkpp_replay")}
     ktimes = {k: v for k, v in ktimes.items() if v[1] > 0}
     if world > 1:
         torch.distributed.barrier()
@@ -459,6 +459,10 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         flops = wl.N * (p1 * passes + p3 * res.iters)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
         note = "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"
+    elif kern == "fkpp_residual":
+        flops = wl.N * passes * 128 * 15
+        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
+        note = "FP64 residual flops (15 per entry); peak = nominal GB300 FP64"
     elif kern == "fkpp_fold":
         mixed = spec.get("precision", 0) == 1
         flops = wl.N * passes * FK_FOLD_REAL_FLOPS

@@ -164,6 +164,20 @@ int pitn_backward(int system_id, int64_t B, const double* params, const double* 
                   const double* grad_traj, const double* grad_xN, int ckpt_every,
                   double* grad_x0_out, double* grad_params_out, const pitn_options* opt);
 
+/*
+ * The combine of eq. 3.3 for dense elements in the delta form A = I + S, as
+ * used by the mixed-precision scan (Sec. 3.1; the delta form is not in the
+ * paper):
+ *   (I + S2, b2) o (I + S1, b1) = (I + S, b),  S = S2 + S1 + S2 S1,  b = b2 + b1 + S2 b1
+ * for n independent pairs of 128 x 128 FP32 matrices stored column-major
+ * (S[col][row]), element 2 the later one.  S2 S1 runs on the tensor cores
+ * with BF16 operands and FP32 accumulation; sums and b in FP32.  All pointers
+ * are device memory (matrices 16-byte aligned), n matrices / vectors each,
+ * packed; stream may be NULL.  Returns PITN_OK or a negative error code.
+ */
+int pitn_affine_combine_delta(int64_t n, const float* S2, const float* b2, const float* S1,
+                              const float* b1, float* S, float* b, void* stream);
+
 /* Number of parameters of a system, or -1 for an unknown id. */
 int pitn_num_params(int system_id);
 
@@ -211,7 +225,7 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream; pitn_timing_get returns
  * the summed device time and launch count of one kernel family since the
- * last reset (names: "newton_small", "fkpp_fold", "fkpp_compose",
+ * last reset (names: "newton_small", "fkpp_residual", "fkpp_fold", "fkpp_compose",
  * "fkpp_down", "fkpp_replay", "batch", "adjoint").  Timing adds two event
  * records per launch; it is off by default. */
 int pitn_timing_enable(int on);

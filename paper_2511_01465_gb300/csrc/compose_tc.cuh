@@ -1,0 +1,212 @@
+// compose_tc.cuh -- dense delta-form compose of two 128x128 affine elements
+// on the 5th-generation tensor cores (tcgen05, TMEM accumulator).
+//
+//   (I + S2, b2) o (I + S1, b1) = (I + S, b),
+//   S = S2 + S1 + S2 S1,   b = b2 + b1 + S2 b1                       (eq. 3.3)
+//
+// S2 S1 is one M = N = K = 128 product: BF16 operands staged in shared memory
+// in the canonical K-major core-matrix layout (8 rows x 16 bytes per core
+// matrix, no swizzle), eight tcgen05.mma (K = 16 each) issued by one thread
+// into a 128-lane x 128-column FP32 accumulator in TMEM, completion signalled
+// through an mbarrier, and read back with tcgen05.ld: TMEM lane m is row m of
+// the product, so thread m of the CTA owns row m in the epilogue, which adds
+// S2 + S1 in FP32 and stores column-major (coalesced across the warp).
+// The vector part uses the same BF16 rows of S2 with FP32 accumulation.
+// Matrices are column-major FP32 (S[col][row]), 128 x 128.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace pitn {
+namespace tc {
+
+constexpr int kDim = 128;
+constexpr uint32_t kCoreBytes = 128;             // 8 rows x 16 bytes
+constexpr uint32_t kGroupBytes = 16 * kCoreBytes;  // one 8-row group spans K = 128 (16 cores)
+constexpr uint32_t kTileBytes = 16 * kGroupBytes;  // 128 rows
+constexpr uint64_t kSpinLimit = 1ull << 26;       // bounded mbarrier wait
+
+// byte offset of element (row, k) in the K-major core-matrix layout
+__device__ __forceinline__ uint32_t core_off(int row, int k) {
+    return (uint32_t)((row >> 3) * kGroupBytes + (k >> 3) * kCoreBytes + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start address, leading byte offset (next
+// core matrix along K), stride byte offset (next 8-row group), version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kCoreBytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kGroupBytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::f16: D = F32, A = B = BF16, both K-major,
+// N = 128, M = 128
+__device__ __forceinline__ uint32_t make_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kDim >> 3) << 17) |
+           ((uint32_t)(kDim >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_addr(dst_smem)), "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_addr(mbar)) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    const uint32_t a = smem_addr(mbar);
+    for (uint64_t i = 0; i < kSpinLimit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared memory of one compose: A and B tiles, the mbarrier and the TMEM address.
+struct __align__(1024) ComposeSmem {
+    uint8_t A[kTileBytes];   // S2 (rows m, K-major)
+    uint8_t B[kTileBytes];   // S1 (rows n = columns of S1, K-major)
+    float b1[kDim];
+    uint64_t mbar;
+    uint32_t tmem;
+};
+
+// One compose by a CTA of exactly 128 threads.  Returns false (after
+// releasing the TMEM it holds) if the MMA completion wait timed out.
+__device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restrict__ S2,
+                                           const float* __restrict__ b2, const float* __restrict__ S1,
+                                           const float* __restrict__ b1, float* __restrict__ So,
+                                           float* __restrict__ bo, uint32_t phase) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // A(m, k) = S2[m][k] = S2 column-major [k][m]: thread gathers 8 consecutive
+    // k of one row m (coalesced across the warp) into one 16-byte core row
+    for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
+        const int m = idx % kDim, kc = (idx / kDim) * 8;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = S2[(size_t)(kc + j) * kDim + m];
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
+        uint4 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&h0);
+        pk.y = *reinterpret_cast<uint32_t*>(&h1);
+        pk.z = *reinterpret_cast<uint32_t*>(&h2);
+        pk.w = *reinterpret_cast<uint32_t*>(&h3);
+        *reinterpret_cast<uint4*>(sm.A + core_off(m, kc)) = pk;
+    }
+    // B(n, k) = S1[k][n] = S1 column-major [n][k]: 8 consecutive k are contiguous
+    for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
+        const int n = idx / (kDim / 8), kc = (idx % (kDim / 8)) * 8;
+        const float4 lo = *reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + kc);
+        const float4 hi = *reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + kc + 4);
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(lo.x, lo.y), h1 = __floats2bfloat162_rn(lo.z, lo.w);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(hi.x, hi.y), h3 = __floats2bfloat162_rn(hi.z, hi.w);
+        uint4 pk;
+        pk.x = *reinterpret_cast<uint32_t*>(&h0);
+        pk.y = *reinterpret_cast<uint32_t*>(&h1);
+        pk.z = *reinterpret_cast<uint32_t*>(&h2);
+        pk.w = *reinterpret_cast<uint32_t*>(&h3);
+        *reinterpret_cast<uint4*>(sm.B + core_off(n, kc)) = pk;
+    }
+    sm.b1[tid] = b1[tid];
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+        const uint32_t a0 = smem_addr(sm.A), b0 = smem_addr(sm.B), idesc = make_idesc();
+#pragma unroll
+        for (int s = 0; s < kDim / 16; ++s)
+            mma_bf16(sm.tmem, make_desc(a0 + s * 2 * kCoreBytes), make_desc(b0 + s * 2 * kCoreBytes), idesc,
+                     s > 0 ? 1u : 0u);
+        mma_commit(&sm.mbar);
+    }
+    const bool ok = mbar_wait(&sm.mbar, phase);
+    fence_after();
+    // epilogue: thread m owns row m (TMEM lane m)
+    const int m = tid;
+    const uint32_t trow = sm.tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < kDim; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const size_t off = (size_t)(c + j) * kDim + m;
+            So[off] = S2[off] + S1[off] + (ok ? v[j] : 0.0f);
+        }
+    }
+    {
+        // S2 b1 from the staged BF16 row of S2 (the same operand the product
+        // used), FP32 accumulation
+        float s = b2[m] + sm.b1[m];
+#pragma unroll 4
+        for (int kc = 0; kc < kDim; kc += 8) {
+            const uint4 pk = *reinterpret_cast<const uint4*>(sm.A + core_off(m, kc));
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h[j]);
+                s = fmaf(f.x, sm.b1[kc + 2 * j], s);
+                s = fmaf(f.y, sm.b1[kc + 2 * j + 1], s);
+            }
+        }
+        bo[m] = s;
+    }
+    fence_before();
+    __syncthreads();
+    return ok;
+}
+
+}  // namespace tc
+}  // namespace pitn

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "compose_tc.cuh"
 #include "solver.h"
 
 namespace pitn {
@@ -97,14 +98,51 @@ __device__ __forceinline__ void fk_reduce_res(unsigned long long my_res, bool my
 }
 
 // ---------------------------------------------------------------------------
-// A. residual + tile fold.  The threads own the 128 columns of P (TPC
+// A0. residual (FP64) and leaf diagonals (working precision), one thread per
+// entry, grid-stride: r_k = x_{k+1} - phi(x_k) (eq. 3.8) into p.r, the
+// diagonal 1 + e of J_k into a_out [N][128] (1 on padding rows), ||r||_inf.
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __restrict__ a_out) {
+    const int d = p.d;
+    const long long total = p.N * FD;
+    const Real hR = (Real)p.h, oR = (Real)p.o;
+    unsigned long long my_res = 0ull;
+    bool my_nf = false;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long k = idx / FD;
+        const int i = (int)(idx - k * FD);
+        Real a = (Real)1.0;
+        if (i < d) {
+            const double um = (i > 0) ? fk_x(p, k - 1, i - 1) : 0.0;
+            const double u = fk_x(p, k - 1, i);
+            const double up = (i < d - 1) ? fk_x(p, k - 1, i + 1) : 0.0;
+            const double un = fk_x(p, k, i);
+            const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
+            const double rr = un - (u + p.h * f);
+            const Real uR = (Real)u;
+            a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
+            p.r[k * d + i] = rr;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(rr));
+            my_res = b > my_res ? b : my_res;
+            my_nf |= !isfinite(rr);
+        }
+        a_out[idx] = a;
+    }
+    fk_reduce_res(my_res, my_nf, p);
+}
+
+// ---------------------------------------------------------------------------
+// A. tile fold.  The threads own the 128 columns of P (TPC
 // threads per column, R rows each, in registers); halo rows move by warp
 // shuffles, so the fold needs no block barrier per step.  Warp 0 then folds
 // the vector b (4 rows per lane).
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
-    fk_fold_kernel(FkParams p, Real* __restrict__ S_out, Real* __restrict__ b_out) {
+    fk_fold_kernel(FkParams p, const Real* __restrict__ a_in, Real* __restrict__ S_out,
+                   Real* __restrict__ b_out) {
     using Tr = FoldTraits<Real>;
     constexpr int R = Tr::R, TPC = Tr::TPC;
     constexpr int FDP = fold_row_stride<Real>();
@@ -117,47 +155,18 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
     const int len = (int)max(0LL, k1 - k0);
     const int d = p.d;
 
-    unsigned long long my_res = 0ull;
-    bool my_nf = false;
-    const Real hR = (Real)p.h, oR = (Real)p.o;
+    // leaf diagonals and residuals of this tile's elements, staged in shared memory
     for (int idx = threadIdx.x; idx < p.TS * FD; idx += blockDim.x) {
         const int s = idx / FD, i = idx - s * FD;
-        Real a = (Real)1.0;
-        double rr = 0.0;
-        if (s < len && i < d) {
+        Real a = (Real)1.0, rr = (Real)0.0;
+        if (s < len) {
             const long long k = k0 + s;
-            const double um = (i > 0) ? fk_x(p, k - 1, i - 1) : 0.0;
-            const double u = fk_x(p, k - 1, i);
-            const double up = (i < d - 1) ? fk_x(p, k - 1, i + 1) : 0.0;
-            const double un = fk_x(p, k, i);
-            const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
-            rr = un - (u + p.h * f);
-            // leaf diagonal in the working precision of the fold
-            const Real uR = (Real)u;
-            a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
-            p.r[k * d + i] = rr;
-            unsigned long long b = (unsigned long long)__double_as_longlong(fabs(rr));
-            my_res = b > my_res ? b : my_res;
-            my_nf |= !isfinite(rr);
+            a = a_in[k * FD + i];
+            if (i < d) rr = (Real)p.r[k * d + i];
         }
         a_s[s * FDP + pidx<Real>(i)] = a;
-        r_s[s * FDP + pidx<Real>(i)] = (Real)rr;
+        r_s[s * FDP + pidx<Real>(i)] = rr;
     }
-    if (t == 0) {  // element 0: r_0 = x_1 - phi(x0)
-        for (int i = threadIdx.x; i < d; i += blockDim.x) {
-            const double um = (i > 0) ? p.x0[i - 1] : 0.0;
-            const double u = p.x0[i];
-            const double up = (i < d - 1) ? p.x0[i + 1] : 0.0;
-            const double un = fk_x(p, 0, i);
-            const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
-            const double rr = un - (u + p.h * f);
-            p.r[i] = rr;
-            unsigned long long b = (unsigned long long)__double_as_longlong(fabs(rr));
-            my_res = b > my_res ? b : my_res;
-            my_nf |= !isfinite(rr);
-        }
-    }
-    fk_reduce_res(my_res, my_nf, p);
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -287,116 +296,47 @@ __global__ void __launch_bounds__(256) fk_compose_f64(LevelArgs a) {
     }
 }
 
-// Mixed: one CTA (8 warps) per node; S2 S1 on tensor cores with
-// mma.m16n8k16 BF16 -> FP32; S = S2 + S1 + S2 S1 and b in FP32.
-constexpr int BSTR = FD + 8;  // bf16 row stride in smem (bank-conflict-free ldmatrix)
+// Mixed, tensor cores of the 5th generation: one CTA of 128 threads per
+// compose (see compose_tc.cuh); a lone last child is copied.
+struct CombineArgs {
+    const float* S2; const float* b2;  // later elements (stride FD*FD / FD)
+    const float* S1; const float* b1;  // earlier elements
+    float* S; float* b;                // results
+    long long n;                       // composes
+    long long stride_in;               // element stride of the inputs in matrices (2 for tree levels)
+    long long n_lone;                  // index of a lone earlier element to copy (or -1)
+    int* err;
+};
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
+constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
 
-__global__ void __launch_bounds__(256) fk_compose_bf16(LevelArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(smem);  // [k][m]  (S2 column-major)
-    __nv_bfloat16* Bs = As + FD * BSTR;                           // [n][k]  (S1 column-major)
-    float* b1s = reinterpret_cast<float*>(Bs + FD * BSTR);        // [FD]
+__global__ void __launch_bounds__(128) fk_compose_tc_kernel(CombineArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    tc::ComposeSmem& sm =
+        *reinterpret_cast<tc::ComposeSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const long long m = blockIdx.x;
-    const float* Sin = (const float*)a.S_in;
-    const float* bin = (const float*)a.b_in;
-    float* Sout = (float*)a.S_out;
-    float* bout = (float*)a.b_out;
-    const long long ce = 2 * m, cl = 2 * m + 1;
-    const float* S1 = Sin + (size_t)ce * FD * FD;
-    float* So = Sout + (size_t)m * FD * FD;
-    if (cl >= a.n_in) {
-        for (int idx = threadIdx.x; idx < FD * FD / 4; idx += blockDim.x)
-            reinterpret_cast<float4*>(So)[idx] = reinterpret_cast<const float4*>(S1)[idx];
-        for (int i = threadIdx.x; i < FD; i += blockDim.x) bout[m * FD + i] = bin[ce * FD + i];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t MM = (size_t)FD * FD;
+    if (m == a.n_lone) {  // copy the lone earlier element
+        const float4* src = reinterpret_cast<const float4*>(a.S1 + (size_t)m * a.stride_in * MM);
+        float4* dst = reinterpret_cast<float4*>(a.S + (size_t)m * MM);
+        for (int i = tid; i < (int)(MM / 4); i += blockDim.x) dst[i] = src[i];
+        a.b[m * FD + tid] = a.b1[m * a.stride_in * FD + tid];
         return;
     }
-    const float* S2 = Sin + (size_t)cl * FD * FD;
-    for (int idx = threadIdx.x; idx < FD * FD / 4; idx += blockDim.x) {
-        const int c = idx / (FD / 4), r4 = (idx % (FD / 4)) * 4;
-        const float4 va = reinterpret_cast<const float4*>(S2)[idx];
-        const float4 vb = reinterpret_cast<const float4*>(S1)[idx];
-        __nv_bfloat16* pa = As + c * BSTR + r4;
-        __nv_bfloat16* pb = Bs + c * BSTR + r4;
-        pa[0] = __float2bfloat16_rn(va.x); pa[1] = __float2bfloat16_rn(va.y);
-        pa[2] = __float2bfloat16_rn(va.z); pa[3] = __float2bfloat16_rn(va.w);
-        pb[0] = __float2bfloat16_rn(vb.x); pb[1] = __float2bfloat16_rn(vb.y);
-        pb[2] = __float2bfloat16_rn(vb.z); pb[3] = __float2bfloat16_rn(vb.w);
+    if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
+    if (tid == 0) {
+        tc::mbar_init(&sm.mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < FD; i += blockDim.x) b1s[i] = bin[ce * FD + i];
+    tc::fence_before();
     __syncthreads();
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wm = (warp & 3) * 32;   // 4 warps along m
-    const int wn = (warp >> 2) * 64;  // 2 warps along n
-    float acc[2][8][4];
-#pragma unroll
-    for (int x = 0; x < 2; ++x)
-#pragma unroll
-        for (int y = 0; y < 8; ++y)
-#pragma unroll
-            for (int z = 0; z < 4; ++z) acc[x][y][z] = 0.f;
-    const int mat = lane >> 3, rr = lane & 7;
-#pragma unroll
-    for (int k0 = 0; k0 < FD; k0 += 16) {
-        unsigned af[2][4];
-#pragma unroll
-        for (int x = 0; x < 2; ++x) {
-            // A tile rows m = wm+16x.., k = k0..: stored As[k][m] -> ldmatrix.trans
-            const int kk = k0 + rr + ((mat & 2) ? 8 : 0);
-            const int mm = wm + 16 * x + ((mat & 1) ? 8 : 0);
-            const unsigned addr = smem_u32(As + kk * BSTR + mm);
-            asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(af[x][0]), "=r"(af[x][1]), "=r"(af[x][2]), "=r"(af[x][3])
-                         : "r"(addr));
-        }
-#pragma unroll
-        for (int y2 = 0; y2 < 4; ++y2) {
-            // two n-tiles (8 each) x two k halves: stored Bs[n][k] -> ldmatrix (no trans)
-            unsigned bf[4];
-            const int nn = wn + 16 * y2 + ((mat & 2) ? 8 : 0);
-            const int kk = k0 + ((mat & 1) ? 8 : 0);
-            const unsigned addr = smem_u32(Bs + (nn + rr) * BSTR + kk);
-            asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(bf[0]), "=r"(bf[1]), "=r"(bf[2]), "=r"(bf[3])
-                         : "r"(addr));
-#pragma unroll
-            for (int x = 0; x < 2; ++x) {
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    float* c = acc[x][2 * y2 + h2];
-                    asm volatile(
-                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-                        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                        : "r"(af[x][0]), "r"(af[x][1]), "r"(af[x][2]), "r"(af[x][3]),
-                          "r"(bf[2 * h2]), "r"(bf[2 * h2 + 1]));
-                }
-            }
-        }
-    }
-    // epilogue: S = S2 + S1 + acc, column-major
-    const int g = lane >> 2, tq = lane & 3;
-#pragma unroll
-    for (int x = 0; x < 2; ++x)
-#pragma unroll
-        for (int y = 0; y < 8; ++y)
-#pragma unroll
-            for (int z = 0; z < 4; ++z) {
-                const int mm = wm + 16 * x + g + ((z & 2) ? 8 : 0);
-                const int nn = wn + 8 * y + 2 * tq + (z & 1);
-                const size_t off = (size_t)nn * FD + mm;
-                So[off] = S2[off] + S1[off] + acc[x][y][z];
-            }
-    if (threadIdx.x < FD) {
-        const int i = threadIdx.x;
-        float s = bin[cl * FD + i] + b1s[i];
-        for (int k = 0; k < FD; ++k) s = fmaf(S2[(size_t)k * FD + i], b1s[k], s);
-        bout[m * FD + i] = s;
-    }
+    tc::fence_after();
+    const bool ok = tc::compose_tc(sm, a.S2 + (size_t)m * a.stride_in * MM, a.b2 + m * a.stride_in * FD,
+                                   a.S1 + (size_t)m * a.stride_in * MM, a.b1 + m * a.stride_in * FD,
+                                   a.S + (size_t)m * MM, a.b + m * FD, 0u);
+    if (!ok && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
+    if (warp == 0) tc::tmem_dealloc(sm.tmem, FD);
 }
 
 // ---------------------------------------------------------------------------
@@ -574,12 +514,20 @@ Tree make_tree(long long T) {
 }
 
 template <typename Real>
-int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, bool mixed,
-                  cudaStream_t st) {
+int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* abuf, bool mixed,
+                  int* err, cudaStream_t st) {
     const size_t smemA = fold_smem_bytes<Real>(p.TS);
     {
+        auto tok = timed_begin("fkpp_residual", st);
+        const long long total = p.N * FD;
+        const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+        fk_residual_kernel<Real><<<grid, 256, 0, st>>>(p, abuf);
+        timed_end(tok, st);
+        count_launch(1);
+    }
+    {
         auto tok = timed_begin("fkpp_fold", st);
-        fk_fold_kernel<Real><<<(unsigned)p.T, FoldTraits<Real>::THREADS, smemA, st>>>(p, S, b);
+        fk_fold_kernel<Real><<<(unsigned)p.T, FoldTraits<Real>::THREADS, smemA, st>>>(p, abuf, S, b);
         timed_end(tok, st);
         count_launch(1);
     }
@@ -593,8 +541,20 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, bool m
         la.n_in = tr.n[lv - 1];
         auto tok = timed_begin("fkpp_compose", st);
         if (mixed) {
-            const size_t sm = 2 * (size_t)FD * BSTR * sizeof(__nv_bfloat16) + FD * sizeof(float);
-            fk_compose_bf16<<<(unsigned)tr.n[lv], 256, sm, st>>>(la);
+            CombineArgs ca;
+            const float* Sin = (const float*)la.S_in;
+            const float* bin = (const float*)la.b_in;
+            ca.S1 = Sin;
+            ca.b1 = bin;
+            ca.S2 = Sin + (size_t)FD * FD;
+            ca.b2 = bin + FD;
+            ca.S = (float*)la.S_out;
+            ca.b = (float*)la.b_out;
+            ca.n = tr.n[lv];
+            ca.stride_in = 2;
+            ca.n_lone = (la.n_in & 1) ? la.n_in / 2 : -1;
+            ca.err = err;
+            fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 128, kTcSmem, st>>>(ca);
         } else {
             const size_t sm = (size_t)(FD * FD + 32 * FD) * sizeof(double);
             fk_compose_f64<<<dim3((unsigned)tr.n[lv], 4), 256, sm, st>>>(la);
@@ -643,7 +603,8 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     const size_t aggBytes = (size_t)tr.total * FD * FD * sizeof(Real) +
                             2 * (size_t)tr.total * FD * sizeof(Real);
     Real* S = (Real*)workspace(aggBytes, kSlotAux);
-    if (!S) return PITN_ENOMEM;
+    Real* abuf = (Real*)workspace((size_t)N * FD * sizeof(Real), kSlotAux2);
+    if (!S || !abuf) return PITN_ENOMEM;
     Real* b = S + (size_t)tr.total * FD * FD;
     Real* z = b + (size_t)tr.total * FD;
     const size_t ctrlBytes = (size_t)(max_iter + 1) * (8 + 8 + 4) + 64;
@@ -652,8 +613,9 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     unsigned long long* res_bits = (unsigned long long*)ctrl;
     unsigned long long* qenc = res_bits + (max_iter + 1);
     int* nonfinite = (int*)(qenc + (max_iter + 1));
+    int* err_d = (int*)(ctrl + ctrlBytes - 16);
     if (cudaMemsetAsync(ctrl, 0, ctrlBytes, st) != cudaSuccess) return PITN_ECUDA;
-    struct HostCtl { unsigned long long res, q; int nf; int pad; };
+    struct HostCtl { unsigned long long res, q; int nf; int err; };
     HostCtl* hc = (HostCtl*)pinned(sizeof(HostCtl));
     if (!hc) return PITN_ENOMEM;
 
@@ -662,8 +624,8 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         cudaFuncSetAttribute(fk_fold_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemA);
         cudaFuncSetAttribute(fk_compose_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((FD * FD + 32 * FD) * sizeof(double)));
-        cudaFuncSetAttribute(fk_compose_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * FD * BSTR * sizeof(__nv_bfloat16) + FD * sizeof(float)));
+        cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem);
     }
 
     const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
@@ -693,13 +655,15 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         p.res_bits = res_bits + it;
         p.qenc = qenc + it;
         p.nonfinite = nonfinite + it;
-        int rc = run_iteration<Real>(p, tr, S, b, z, mixed, st);
+        int rc = run_iteration<Real>(p, tr, S, b, z, abuf, mixed, err_d, st);
         if (rc != PITN_OK) return rc;
         if (cudaMemcpyAsync(&hc->res, res_bits + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&hc->q, qenc + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaMemcpyAsync(&hc->nf, nonfinite + it, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            cudaMemcpyAsync(&hc->nf, nonfinite + it, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&hc->err, err_d, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             return PITN_ECUDA;
         if (cudaStreamSynchronize(st) != cudaSuccess) return PITN_ECUDA;
+        if (hc->err) return hc->err;
         double res;
         std::memcpy(&res, &hc->res, sizeof(res));
         const long long cut = hc->q ? (long long)(~hc->q) : (long long)N;
@@ -742,3 +706,36 @@ int fkpp_solve(const SolveIO& io, double h, int64_t N, int d, double tol, int ma
 }
 
 }  // namespace pitn_host
+
+// ---------------------------------------------------------------------------
+// C-ABI primitive: n independent dense delta-form combines on tensor cores.
+// ---------------------------------------------------------------------------
+extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float* b2, const float* S1,
+                                         const float* b1, float* S, float* b, void* stream) {
+    using namespace pitn;
+    using namespace pitn_host;
+    if (n < 1 || !S2 || !b2 || !S1 || !b1 || !S || !b) return PITN_EINVAL;
+    if (!is_device_ptr(S2) || !is_device_ptr(b2) || !is_device_ptr(S1) || !is_device_ptr(b1) ||
+        !is_device_ptr(S) || !is_device_ptr(b))
+        return PITN_EINVAL;
+    if (((uintptr_t)S2 | (uintptr_t)S1 | (uintptr_t)S) & 15) return PITN_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(api_mutex());
+    cudaStream_t st = (cudaStream_t)stream;
+    int* err = (int*)workspace(64, kSlotCtrl);
+    if (!err) return PITN_ENOMEM;
+    if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return PITN_ECUDA;
+    cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    CombineArgs ca;
+    ca.S2 = S2; ca.b2 = b2; ca.S1 = S1; ca.b1 = b1; ca.S = S; ca.b = b;
+    ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err;
+    auto tok = timed_begin("fkpp_compose", st);
+    fk_compose_tc_kernel<<<(unsigned)n, 128, kTcSmem, st>>>(ca);
+    timed_end(tok, st);
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;
+    int h_err = 0;
+    if (cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return PITN_ECUDA;
+    return h_err ? h_err : PITN_OK;
+}

@@ -77,6 +77,8 @@ def lib():
         L.pitn_solve_noalloc.argtypes = [c_int, vp, vp, d, i64, c_int, d, c_int, d, vp,
                                           ctypes.POINTER(pitn_result)]
         L.pitn_solve_noalloc.restype = c_int
+        L.pitn_affine_combine_delta.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
+        L.pitn_affine_combine_delta.restype = c_int
         L.pitn_timing_enable.argtypes = [c_int]
         L.pitn_timing_enable.restype = c_int
         L.pitn_timing_reset.argtypes = []
@@ -168,6 +170,17 @@ def pitn_solve_noalloc(system_id, params, x0, h, N, d, tol, max_iter, guard_B, t
                                   float(tol), int(max_iter), float(guard_B), _ptr(traj_out),
                                   ctypes.byref(res))
     return rc, res
+
+
+def pitn_affine_combine_delta(n, S2, b2, S1, b1, S, b, stream=None):
+    """n dense delta-form combines (float32 CUDA tensors, matrices [n][128][128] column-major)."""
+    import torch
+    def fp(t):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError("float32 contiguous tensors expected")
+        return ctypes.c_void_p(t.data_ptr())
+    st = ctypes.c_void_p(int(stream)) if stream is not None else None
+    return lib().pitn_affine_combine_delta(int(n), fp(S2), fp(b2), fp(S1), fp(b1), fp(S), fp(b), st)
 
 
 def pitn_num_params(system_id):
