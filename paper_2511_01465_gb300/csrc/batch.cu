@@ -193,11 +193,11 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
         } else {
             double tP[D * D], tc[D];
             sys.jmul(jv, P, tP);
-            sys.jvec(jv, c, tc);
+            sys.jvec_sub(jv, c, r, tc);
 #pragma unroll
             for (int i = 0; i < D * D; ++i) P[i] = tP[i];
 #pragma unroll
-            for (int i = 0; i < D; ++i) c[i] = tc[i] - r[i];
+            for (int i = 0; i < D; ++i) c[i] = tc[i];
         }
 #pragma unroll
         for (int i = 0; i < D; ++i) xp[i] = x[i];
@@ -390,9 +390,9 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
             for (int i = 0; i < D; ++i) z[i] = -r[i];
         } else {
             double tz[D];
-            sys.jvec(jv, z, tz);
+            sys.jvec_sub(jv, z, r, tz);
 #pragma unroll
-            for (int i = 0; i < D; ++i) z[i] = tz[i] - r[i];
+            for (int i = 0; i < D; ++i) z[i] = tz[i];
         }
         double* Xn = s.cur ? a.X0 : a.X1;
         unsigned long long zb = 0ull;

@@ -277,14 +277,19 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             k1 = min(N, k1);
         }
         const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
+        // The regular part is folded as two interleaved halves A = [k0, km) and
+        // B = [km, kreg): two independent FP64 dependency chains per thread.
         unsigned long long my_res = 0ull;
-        double P[D * D], c[D];
-        mat_identity<D>(P);
+        const long long Lr = kreg - k0;
+        const long long LA = (Lr + 1) / 2, LB = Lr - LA, km = k0 + LA;
+        double PA[D * D], cA[D], PB[D * D], cB[D], xpA[D], xpB[D];
+        mat_identity<D>(PA);
+        mat_identity<D>(PB);
 #pragma unroll
-        for (int j = 0; j < D; ++j) c[j] = 0.0;
-        double xp[D];
-        if (k0 < kreg) load_state<D>(Xc, a.x0, k0 - 1, q, xp);
-        for (long long k = k0; k < kreg; ++k) {
+        for (int j = 0; j < D; ++j) { cA[j] = 0.0; cB[j] = 0.0; }
+        if (LA > 0) load_state<D>(Xc, a.x0, k0 - 1, q, xpA);
+        if (LB > 0) load_state<D>(Xc, a.x0, km - 1, q, xpB);
+        auto fold_step = [&](long long k, double* xp, double* P, double* c) {
             double x[D], r[D], jv[JN];
             load_state<D>(Xc, a.x0, k, q, x);
             sys.eval(xp, x, r, jv);
@@ -304,15 +309,21 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             } else {
                 double tP[D * D], tc[D];
                 sys.jmul(jv, P, tP);
-                sys.jvec(jv, c, tc);
+                sys.jvec_sub(jv, c, r, tc);
 #pragma unroll
                 for (int j = 0; j < D * D; ++j) P[j] = tP[j];
 #pragma unroll
-                for (int j = 0; j < D; ++j) c[j] = tc[j] - r[j];
+                for (int j = 0; j < D; ++j) c[j] = tc[j];
             }
 #pragma unroll
             for (int j = 0; j < D; ++j) xp[j] = x[j];
+        };
+        for (long long i = 0; i < LA; ++i) {
+            fold_step(k0 + i, xpA, PA, cA);
+            if (i < LB) fold_step(km + i, xpB, PB, cB);
         }
+        double P[D * D], c[D];
+        compose<D>(PB, cB, PA, cA, P, c);
         if (kreg < k1) {
             double xf[D], rf[D], jvf[JN], EP[D * D], Ec[D], RP[D * D], Rc[D];
             load_state<D>(Xc, a.x0, q - 1, q, xf);
@@ -405,11 +416,13 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         // chunk lies beyond the iteration's cut and is never read again.
         unsigned long long my_q = 0ull;
         {
-            double zw[D], z[D];
+            double zw[D], zA[D], zB[D];
             apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
-            apply<D>(eP, ec, zw, z);
-            bool found = false;
-            for (long long k = k0; k < kreg && !found; ++k) {
+            apply<D>(eP, ec, zw, zA);
+            apply<D>(PA, cA, zA, zB);  // state entering half B
+            bool foundA = false, foundB = false;
+            long long firstA = 0, firstB = 0;
+            auto replay_step = [&](long long k, double* z) -> bool {
                 double jv[JN], r[D], x[D];
 #pragma unroll
                 for (int j = 0; j < JN; ++j) jv[j] = __ldcg(scr + k * W + j);
@@ -421,9 +434,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     for (int j = 0; j < D; ++j) z[j] = -r[j];
                 } else {
                     double tz[D];
-                    sys.jvec(jv, z, tz);
+                    sys.jvec_sub(jv, z, r, tz);
 #pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = tz[j] - r[j];
+                    for (int j = 0; j < D; ++j) z[j] = tz[j];
                 }
                 unsigned long long zb = 0ull;
 #pragma unroll
@@ -432,22 +445,28 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
                     zb = b > zb ? b : zb;
                 }
-                if (zb > a.cap_bits) {
-                    found = true;
-                    my_q = ~(unsigned long long)k;
-                }
+                return zb > a.cap_bits;
+            };
+            for (long long i = 0; i < LA && !foundA; ++i) {
+                if (replay_step(k0 + i, zA)) { foundA = true; firstA = k0 + i; }
+                if (i < LB && !foundB && replay_step(km + i, zB)) { foundB = true; firstB = km + i; }
             }
+            bool found = foundA || foundB;
+            if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
+            double z[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) z[j] = (LB > 0) ? zB[j] : zA[j];
             if (!found && kreg < k1) {
                 double xf[D], rf[D], jvf[JN];
                 load_state<D>(Xc, a.x0, q - 1, q, xf);
                 sys.eval(xf, xf, rf, jvf);
                 for (long long k = kreg; k < k1; ++k) {
                     double tz[D];
-                    sys.jvec(jvf, z, tz);
+                    sys.jvec_sub(jvf, z, rf, tz);
                     unsigned long long zb = 0ull;
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        z[j] = tz[j] - rf[j];
+                        z[j] = tz[j];
                         Xn[k * D + j] = xf[j] + z[j];
                         const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
                         zb = b > zb ? b : zb;

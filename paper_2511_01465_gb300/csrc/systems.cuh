@@ -7,6 +7,7 @@
 //                              that depend on xp (a compact Jacobian)
 //   jmul(jv, M, out):     out = J M   (M, out: D x D row-major)
 //   jvec(jv, v, out):     out = J v
+//   jvec_sub(jv, v, r, out): out = J v - r (fused)
 //   jtvec(jv, v, out):    out = J^T v           (adjoint)
 //   vjp_param(xp, v, g):  g += (dphi/dp(xp))^T v  (adjoint, g has P entries)
 //   jac(xp, jv):          the compact Jacobian alone
@@ -54,6 +55,14 @@ struct Lorenz63 {
         o[1] = jv[0] * v0 + j11 * v1 - jv[1] * v2;
         o[2] = jv[2] * v0 + jv[1] * v1 + j22 * v2;
     }
+    // o = J v - r
+    __device__ __forceinline__ void jvec_sub(const double* jv, const double* v, const double* rr,
+                                             double* o) const {
+        double v0 = v[0], v1 = v[1], v2 = v[2];
+        o[0] = fma(j00, v0, fma(j01, v1, -rr[0]));
+        o[1] = fma(jv[0], v0, fma(j11, v1, fma(-jv[1], v2, -rr[1])));
+        o[2] = fma(jv[2], v0, fma(jv[1], v1, fma(j22, v2, -rr[2])));
+    }
     __device__ __forceinline__ void jtvec(const double* jv, const double* v, double* o) const {
         double v0 = v[0], v1 = v[1], v2 = v[2];
         o[0] = j00 * v0 + jv[0] * v1 + jv[2] * v2;
@@ -81,17 +90,28 @@ struct Lorenz63 {
 //   J = [[1, h], [h(-2 mu x v - 1), 1 + h mu (1-x^2)]]
 struct VanDerPol {
     static constexpr int D = 2, JN = 2, P = 1;
-    double mu, h;
-    __host__ __device__ void init(const double* p, double hh) { mu = p[0]; h = hh; }
+    double mu, h, hmu, m2hmu;
+    __host__ __device__ void init(const double* p, double hh) {
+        mu = p[0]; h = hh; hmu = h * mu; m2hmu = -2.0 * h * mu;
+    }
+    // r = xc - x - h f(x) written as r0 = (xc0 - x) - h v,
+    // r1 = (xc1 - v) - (h mu w) v + h x with w = 1 - x^2; 10 FP64 operations
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
                                          double* jv) const {
-        double x = xp[0], v = xp[1];
-        double w = 1.0 - x * x;
-        double f1 = mu * w * v - x;
-        res[0] = xc[0] - (x + h * v);
-        res[1] = xc[1] - (v + h * f1);
-        jv[0] = h * (-2.0 * mu * x * v - 1.0);
-        jv[1] = 1.0 + h * mu * w;
+        const double x = xp[0], v = xp[1];
+        const double w = fma(-x, x, 1.0);
+        const double t = hmu * w;
+        res[0] = fma(-h, v, xc[0] - x);
+        res[1] = fma(h, x, fma(-t, v, xc[1] - v));
+        jv[0] = fma(m2hmu * x, v, -h);
+        jv[1] = 1.0 + t;
+    }
+    // o = J v - r
+    __device__ __forceinline__ void jvec_sub(const double* jv, const double* v, const double* rr,
+                                             double* o) const {
+        const double v0 = v[0], v1 = v[1];
+        o[0] = fma(h, v1, v0 - rr[0]);
+        o[1] = fma(jv[0], v0, fma(jv[1], v1, -rr[1]));
     }
     __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
         double m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
@@ -150,6 +170,12 @@ struct LinearOsc {
         double v0 = v[0], v1 = v[1];
         o[0] = v0 + h * v1;
         o[1] = j10 * v0 + j11 * v1;
+    }
+    __device__ __forceinline__ void jvec_sub(const double*, const double* v, const double* rr,
+                                             double* o) const {
+        const double v0 = v[0], v1 = v[1];
+        o[0] = fma(h, v1, v0 - rr[0]);
+        o[1] = fma(j10, v0, fma(j11, v1, -rr[1]));
     }
     __device__ __forceinline__ void jtvec(const double*, const double* v, double* o) const {
         double v0 = v[0], v1 = v[1];
