@@ -187,8 +187,10 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                                 traj, offs, iters, status, res, opt)
         P.check(rc, "pitn_solve_batch")
 
+    P.pitn_tune_enable(not args.no_tune)
     for _ in range(args.warmup):
         solve_once()
+    P.pitn_tune_enable(False)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -365,8 +367,10 @@ def run_ours(args, rank, world, local_rank):
         P.check(rc, "pitn_solve_ex")
         return rc, res
 
+    P.pitn_tune_enable(not args.no_tune)  # the first warm-up solve picks the launch shape
     for _ in range(args.warmup):
         rc, res = solve_once()
+    P.pitn_tune_enable(False)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -442,6 +446,8 @@ def run_ours(args, rank, world, local_rank):
                        "status": P.pitn_status_string(res.status), "final_res": res.final_res,
                        "l2": "flushed (512 MiB write) between timed steps",
                        "step_ms": [round(t, 3) for t in times],
+                       "launch_shape": P.pitn_tune_get(f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:"
+                                                       f"{1 if spec['guard_B'] > 0 else 0}"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}
@@ -603,6 +609,7 @@ def main():
     ap.add_argument("--workload", default="vdp")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -222,6 +222,22 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
                        int d, double tol, int max_iter, double guard_B, double* traj_out,
                        pitn_result* result);
 
+/*
+ * Launch-shape autotuner (not in the paper).  While enabled, the first solve
+ * of a configuration class -- (entry point, system, d, floor(log2 size),
+ * guard on/off) -- times each candidate launch shape (threads per CTA and
+ * CTAs per SM for pitn_solve; threads per CTA and steps per thread for
+ * pitn_solve_batch) on the call's own inputs, keeps the fastest per Newton
+ * pass in a process-wide cache, and then returns the result computed with
+ * it; later solves of that class use the cached shape.  With the environment
+ * variable PITN_TUNE_CACHE naming a file, the cache is loaded from and saved
+ * to that file.  A solve with a user guess never tunes.  Different shapes
+ * associate the scan differently, so results may differ in the last bits.
+ * pitn_tune_get reads one entry (key as above, e.g. "small:2:2:22:1"). */
+int pitn_tune_enable(int on);
+int pitn_tune_clear(void);
+int pitn_tune_get(const char* key, int* a, int* b);
+
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream; pitn_timing_get returns
  * the summed device time and launch count of one kernel family since the

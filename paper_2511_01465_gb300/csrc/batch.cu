@@ -24,6 +24,7 @@
 // never copied.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -485,7 +486,8 @@ namespace {
 
 template <class Sys>
 int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned* h_running,
-              double* out, int* iters_out, int* status_out, double* res_out, long long* off_out) {
+              double* out, int* iters_out, int* status_out, double* res_out, long long* off_out,
+              int* iterations) {
     const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
     batch_init_kernel<<<eg, 256, 0, st>>>(a);
     count_launch(1);
@@ -507,11 +509,13 @@ int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned
     }
     if (rc == PITN_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = PITN_ECUDA;
     // the graph runs on the caller's stream (ordered after the init kernel)
+    *iterations = 0;
     for (int it = 0; rc == PITN_OK && it <= a.max_iter; ++it) {
         auto tok = timed_begin("batch", st);
         if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = PITN_ECUDA; break; }
         timed_end(tok, st);
         count_launch(4);
+        *iterations += 1;
         if (cudaStreamSynchronize(st) != cudaSuccess) { rc = PITN_ECUDA; break; }
         if (*h_running == 0) break;
     }
@@ -566,14 +570,28 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     }
     const long long M = hoff[B];
 
-    // launch shape
-    const int block = 256;
+    // launch shape: threads per CTA and steps per thread (autotuned, see tune.cpp)
+    int block = 256;
     long long chunk = o.tile_elems > 0 ? o.tile_elems : 32;
+    const bool guarded_b = o.guard_B > 0.0 && std::isfinite(o.guard_B);
+    char tkey[96];
+    std::snprintf(tkey, sizeof(tkey), "batch:%d:%d:%d:%d", system_id, d, tune_bucket(M), guarded_b ? 1 : 0);
+    int tb = 0, tc = 0;
+    bool tune_now = false;
+    if (o.tile_elems <= 0 && tune_lookup(tkey, &tb, &tc)) {
+        block = tb;
+        chunk = tc;
+    } else if (o.tile_elems <= 0 && tune_enabled()) {
+        tune_now = true;
+    }
+    static const int kShapes[][2] = {{256, 8}, {256, 16}, {256, 32}, {256, 64}, {128, 16}, {128, 32}};
+    const long long min_chunk = tune_now ? 8 : chunk;
+    const long long max_threads = (M + min_chunk - 1) / min_chunk + 256;
     const long long grid = (M + (long long)block * chunk - 1) / ((long long)block * chunk);
+    const long long grid_cap = (max_threads + 127) / 128 + 1;  // CTA count bound over all shapes
     const int JN = (system_id == PITN_LORENZ63) ? Lorenz63::JN
                    : (system_id == PITN_VDP ? VanDerPol::JN : LinearOsc::JN);
     const int W = JN + d, E = d * d + d;
-
     // device buffers: staged inputs | offsets | states | X1 | scratch | agg | texcl
     const bool out_dev = is_device_ptr(traj_out);
     size_t off = 0;
@@ -587,8 +605,9 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     char* small = (char*)workspace(off, kSlotStage);
     double* X1 = (double*)workspace(sizeof(double) * (size_t)M * d, kSlotX1);
     double* scratch = (double*)workspace(sizeof(double) * (size_t)M * W, kSlotAux);
-    const size_t aggB = sizeof(double) * (size_t)grid * E;
-    char* aux2 = (char*)workspace(aggB + sizeof(double) * (size_t)grid * block * E + 256, kSlotAux2);
+    const size_t aggB = sizeof(double) * (size_t)std::max(grid, grid_cap) * E;
+    const size_t texB = sizeof(double) * (size_t)std::max(grid * block, max_threads) * E;
+    char* aux2 = (char*)workspace(aggB + texB + 512, kSlotAux2);
     unsigned* h_running = (unsigned*)pinned(64);
     if (!small || !X1 || !scratch || !aux2 || !h_running) return PITN_ENOMEM;
 
@@ -630,18 +649,46 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     double* res_d = res_out ? (is_device_ptr(res_out) ? res_out : (double*)(small + o_res)) : nullptr;
     long long* offo_d = is_device_ptr(offsets_out) ? (long long*)offsets_out : (long long*)(small + o_offo);
 
-    int rc;
-    switch (system_id) {
-    case PITN_LORENZ63:
-        rc = batch_run<Lorenz63>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
-        break;
-    case PITN_VDP:
-        rc = batch_run<VanDerPol>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
-        break;
-    default:
-        rc = batch_run<LinearOsc>(a, block, grid, st, h_running, a.X0, it_d, stat_d, res_d, offo_d);
-        break;
+    auto run_shape = [&](int blk, long long ch, int* iters_run) -> int {
+        a.chunk = ch;
+        const long long g = (M + (long long)blk * ch - 1) / ((long long)blk * ch);
+        switch (system_id) {
+        case PITN_LORENZ63:
+            return batch_run<Lorenz63>(a, blk, g, st, h_running, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+        case PITN_VDP:
+            return batch_run<VanDerPol>(a, blk, g, st, h_running, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+        default:
+            return batch_run<LinearOsc>(a, blk, g, st, h_running, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+        }
+    };
+    if (tune_now) {
+        // time each shape on this batch; the cost per Newton iteration decides
+        double best = 1e300;
+        for (const auto& shp : kShapes) {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+            int its = 0;
+            const int rc1 = run_shape(shp[0], shp[1], &its);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc1 != PITN_OK) continue;
+            const double per = ms / std::max(1, its);
+            if (per < best) {
+                best = per;
+                block = shp[0];
+                chunk = shp[1];
+            }
+        }
+        tune_store(tkey, block, (int)chunk);
     }
+    int its_final = 0;
+    int rc = run_shape(block, chunk, &its_final);
     if (rc != PITN_OK) return rc;
     // host copies of the outputs given as host memory
     auto get = [&](void* dst, const void* src, size_t bytes) {

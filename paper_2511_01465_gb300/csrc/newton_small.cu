@@ -30,6 +30,7 @@
 // accept the step.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "common.cuh"
@@ -551,11 +552,13 @@ void small_default_config(int d, long long N, int* block, int* C) {
     *C = (int)cmin;
 }
 
-int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
-                     int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out) {
+// One solve with an explicit launch shape: `block` threads per CTA and at
+// most `per_sm_cap` co-resident CTAs per SM (cooperative launch).
+int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
+                 int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out, int block,
+                 int per_sm_cap) {
     using namespace pitn;
-    int block = 0, cmin = 0;
-    small_default_config(d, N, &block, &cmin);
+    int cmin = 4;
     if (o.tile_elems > 0) cmin = o.tile_elems;
     int per_sm = 0;
     switch (system_id) {
@@ -564,8 +567,8 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
     case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc>(block); break;
     default: return PITN_EINVAL;
     }
-    if (per_sm < 1) return PITN_ECUDA;
-    per_sm = std::min(per_sm, 2);
+    if (per_sm < 1) return PITN_EUNSUPPORTED;  // shape does not fit on an SM
+    per_sm = std::min(per_sm, per_sm_cap);
     const long long max_grid = (long long)per_sm * props().multiProcessorCount;
     const long long want = (N + (long long)block * cmin - 1) / ((long long)block * cmin);
     const int grid = (int)std::max(1LL, std::min(max_grid, want));
@@ -644,6 +647,50 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
         out->history[k] = v;
     }
     return PITN_OK;
+}
+
+// Launch shapes the autotuner tries (threads per CTA, CTAs per SM).
+static const int kSmallShapes[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
+
+int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
+                     int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out) {
+    int block = 0, cmin = 0;
+    small_default_config(d, N, &block, &cmin);
+    int cap = 2;
+    const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
+    char key[96];
+    std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d", system_id, d, tune_bucket(N), guarded ? 1 : 0);
+    int tb = 0, tc = 0;
+    if (tune_lookup(key, &tb, &tc)) {
+        block = tb;
+        cap = tc;
+    } else if (tune_enabled() && !io.have_guess) {
+        // time every shape on this very solve; the cost per Newton pass decides
+        double best = 1e300;
+        for (const auto& shp : kSmallShapes) {
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+            SolveOutcome tmp;
+            const int rc = small_launch(system_id, io, h, N, d, tol, max_iter, o, st, &tmp, shp[0], shp[1]);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc != PITN_OK) continue;
+            const double per_pass = ms / (double)(tmp.iters + 1);
+            if (per_pass < best) {
+                best = per_pass;
+                block = shp[0];
+                cap = shp[1];
+            }
+        }
+        tune_store(key, block, cap);
+    }
+    return small_launch(system_id, io, h, N, d, tol, max_iter, o, st, out, block, cap);
 }
 
 }  // namespace pitn_host

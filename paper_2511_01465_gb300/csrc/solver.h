@@ -69,6 +69,13 @@ int stage_inputs(int system_id, const double* params, const double* x0, int64_t 
                  double* traj_out, const double* guess, cudaStream_t st, SolveIO* io);
 int finish_outputs(const SolveIO& io, int64_t N, int d, double* traj_out, cudaStream_t st);
 
+// Autotuner: launch shapes cached per key (workload class and size bucket),
+// optionally persisted in the file named by PITN_TUNE_CACHE.
+bool tune_enabled();
+bool tune_lookup(const char* key, int* a, int* b);
+void tune_store(const char* key, int a, int b);
+int tune_bucket(long long n);  // floor(log2 n)
+
 // Small-state systems (d = 2, 3): one persistent cooperative kernel per solve.
 int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
                      int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out);

@@ -79,6 +79,12 @@ def lib():
         L.pitn_solve_noalloc.restype = c_int
         L.pitn_affine_combine_delta.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         L.pitn_affine_combine_delta.restype = c_int
+        L.pitn_tune_enable.argtypes = [c_int]
+        L.pitn_tune_enable.restype = c_int
+        L.pitn_tune_clear.argtypes = []
+        L.pitn_tune_clear.restype = c_int
+        L.pitn_tune_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        L.pitn_tune_get.restype = c_int
         L.pitn_timing_enable.argtypes = [c_int]
         L.pitn_timing_enable.restype = c_int
         L.pitn_timing_reset.argtypes = []
@@ -197,6 +203,21 @@ def pitn_release_workspace():
 
 def pitn_launch_count():
     return lib().pitn_launch_count()
+
+
+def pitn_tune_enable(on=True):
+    return lib().pitn_tune_enable(1 if on else 0)
+
+
+def pitn_tune_clear():
+    return lib().pitn_tune_clear()
+
+
+def pitn_tune_get(key):
+    """(a, b) of a cached launch shape, or None."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    rc = lib().pitn_tune_get(key.encode(), ctypes.byref(a), ctypes.byref(b))
+    return (a.value, b.value) if rc == 0 else None
 
 
 def pitn_timing_enable(on=True):

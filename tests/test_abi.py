@@ -73,3 +73,19 @@ def test_argument_errors_are_detected_on_the_host(lib):
     rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
     assert rc == E                                                                       # mixed needs d >= 64
     assert not out.any()  # nothing written on an argument error
+
+
+def test_tune_cache_file_is_read(tmp_path, lib):
+    """The autotuner's cache file (PITN_TUNE_CACHE) is loaded on first use."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    cache.write_text("small:2:2:22:1 128 3\nbatch:1:3:27:1 256 16\n")
+    code = ("from paper_2511_01465_gb300 import pitn as P; "
+            "print(P.pitn_tune_get('small:2:2:22:1'), P.pitn_tune_get('batch:1:3:27:1'), "
+            "P.pitn_tune_get('nope'))")
+    env = dict(os.environ, PITN_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "(128, 3) (256, 16) None"
