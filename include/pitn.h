@@ -63,9 +63,17 @@ enum {
                             f = (v, mu(1-x^2)v - x)  (Sec. 4.1, van der Pol) */
     PITN_LINEAR_OSC = 3, /* d = 2; params {omega, zeta}; state (x, dx/dt):
                             f = (v, -omega^2 x - 2 zeta omega v) (affine) */
-    PITN_FKPP = 4        /* d >= 3 interior nodes of [0,1], spacing 1/(d+1),
+    PITN_FKPP = 4,       /* d >= 3 interior nodes of [0,1], spacing 1/(d+1),
                             zero Dirichlet ends; params {D}:
                             f_i = D (u_{i-1} - 2u_i + u_{i+1})/dx^2 + u_i(1-u_i) */
+    PITN_LOGISTIC = 5    /* d = 1; params {r, K}: f = r P (1 - P/K)  (Sec. 4.1) */
+};
+
+/* One-step maps (Sec. 2.1). */
+enum {
+    PITN_STEP_EULER = 0,  /* explicit Euler, eq. 2.2 (every system, every entry point) */
+    PITN_STEP_RK4 = 1     /* classical Runge-Kutta, eq. 2.3; pitn_solve_ex only, for
+                             PITN_VDP and PITN_LOGISTIC (the paper's explicit tests) */
 };
 
 /* Arithmetic of the Newton step (the residual and the update are always FP64). */
@@ -101,11 +109,12 @@ typedef struct {
     void* stream;           /* cudaStream_t; NULL = legacy default stream */
     double* res_history;    /* NULL or host array of max_iter + 1 doubles:
                                ||h||_inf at every residual evaluation */
+    int32_t method;         /* PITN_STEP_*; default explicit Euler */
 } pitn_options;
 
 /*
  * Solve one IVP by the paper's plain Newton method in FP64.
- *   system_id  PITN_LORENZ63 / PITN_VDP / PITN_LINEAR_OSC / PITN_FKPP
+ *   system_id  PITN_LORENZ63 / PITN_VDP / PITN_LINEAR_OSC / PITN_FKPP / PITN_LOGISTIC
  *   params     system parameters (see the enum), host or device
  *   x0         initial value x_0, [d]
  *   h          step size (finite, > 0)

@@ -32,7 +32,8 @@ def _stream_ptr(stream, device):
 
 
 def solve(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, precision=P.PITN_PREC_FP64,
-          guess=None, device="cuda", stream=None, tile_elems=0, history=False, out=None):
+          guess=None, device="cuda", stream=None, tile_elems=0, history=False, out=None,
+          method=P.PITN_STEP_EULER):
     """Solves one IVP; returns (trajectory [N][d] tensor, info dict).
 
     info: iters (Newton updates), status (PITN_OK / NOT_CONVERGED / NONFINITE),
@@ -47,7 +48,7 @@ def solve(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, precision=P.P
     g = _as_f64(guess, device) if guess is not None else None
     hist = np.full(max_iter + 1, np.nan) if history else None
     opt = P.make_options(precision=precision, tile_elems=tile_elems, guard_B=guard_B, guess=g,
-                         stream=_stream_ptr(stream, device), res_history=hist)
+                         stream=_stream_ptr(stream, device), res_history=hist, method=method)
     rc, res = P.pitn_solve_ex(system, p_t, x0_t, h, N, d, tol, max_iter, traj, opt)
     P.check(rc, "pitn_solve_ex")
     info = dict(iters=res.iters, status=res.status, final_res=res.final_res,

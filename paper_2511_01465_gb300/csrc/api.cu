@@ -157,6 +157,7 @@ int system_dim_ok(int sys, int d) {
     case PITN_VDP: return d == 2;
     case PITN_LINEAR_OSC: return d == 2;
     case PITN_FKPP: return d >= 3 && d <= kFkppMaxD;
+    case PITN_LOGISTIC: return d == 1;
     default: return 0;
     }
 }
@@ -167,6 +168,7 @@ int num_params(int sys) {
     case PITN_VDP: return 1;
     case PITN_LINEAR_OSC: return 2;
     case PITN_FKPP: return 1;
+    case PITN_LOGISTIC: return 2;
     default: return -1;
     }
 }
@@ -304,6 +306,9 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
     if (o.precision != PITN_PREC_FP64 && o.precision != PITN_PREC_MIXED_BF16) return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
+    if (o.method != PITN_STEP_EULER && o.method != PITN_STEP_RK4) return PITN_EINVAL;
+    if (o.method == PITN_STEP_RK4 && system_id != PITN_VDP && system_id != PITN_LOGISTIC)
+        return PITN_EUNSUPPORTED;
 
     std::lock_guard<std::recursive_mutex> lk(api_mutex());
     cudaStream_t st = (cudaStream_t)o.stream;

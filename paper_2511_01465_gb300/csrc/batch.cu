@@ -540,11 +540,13 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
                                 int32_t* status_out, double* res_out, const pitn_options* opt) {
     pitn_options o{};
     if (opt) o = *opt;
-    if (system_id == PITN_FKPP || !system_dim_ok(system_id, d)) return PITN_EINVAL;
+    if (system_id == PITN_FKPP || system_id == PITN_LOGISTIC || !system_dim_ok(system_id, d))
+        return PITN_EINVAL;
     if (B < 1 || !params || !x0 || !h || !N || !traj_out || !offsets_out || !iters_out || !status_out)
         return PITN_EINVAL;
     if (!std::isfinite(tol) || !(tol >= 0.0) || max_iter < 0 || max_iter > kMaxIter) return PITN_EINVAL;
-    if (o.precision != PITN_PREC_FP64 || o.guess || o.res_history || std::isnan(o.guard_B))
+    if (o.precision != PITN_PREC_FP64 || o.guess || o.res_history || std::isnan(o.guard_B) ||
+        o.method != PITN_STEP_EULER)
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
     const int P = num_params(system_id);

@@ -121,8 +121,9 @@ struct __align__(1024) ComposeSmem {
     uint32_t tmem;
 };
 
-// One compose by a CTA of exactly 128 threads.  Returns false (after
-// releasing the TMEM it holds) if the MMA completion wait timed out.
+// One compose by a CTA of 128 or 256 threads (with 256, two threads share a
+// row in the epilogue, each taking 64 columns).  Returns false if the MMA
+// completion wait timed out.
 __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restrict__ S2,
                                            const float* __restrict__ b2, const float* __restrict__ S1,
                                            const float* __restrict__ b1, float* __restrict__ So,
@@ -158,7 +159,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
         pk.w = *reinterpret_cast<uint32_t*>(&h3);
         *reinterpret_cast<uint4*>(sm.B + core_off(n, kc)) = pk;
     }
-    sm.b1[tid] = b1[tid];
+    if (tid < kDim) sm.b1[tid] = b1[tid];
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -173,11 +174,14 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
     }
     const bool ok = mbar_wait(&sm.mbar, phase);
     fence_after();
-    // epilogue: thread m owns row m (TMEM lane m)
-    const int m = tid;
-    const uint32_t trow = sm.tmem + ((uint32_t)(warp * 32) << 16);
+    // epilogue: thread owns row m (TMEM lane m; a warp reaches the lane
+    // quarter warp % 4) and a range of columns
+    const int m = tid & (kDim - 1);
+    const int halves = blockDim.x / kDim;  // 1 or 2
+    const int cols = kDim / halves, c0 = (tid / kDim) * cols;
+    const uint32_t trow = sm.tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
-    for (int c = 0; c < kDim; c += 16) {
+    for (int c = c0; c < c0 + cols; c += 16) {
         float v[16];
         tmem_ld16(trow + (uint32_t)c, v);
 #pragma unroll
@@ -186,7 +190,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
             So[off] = S2[off] + S1[off] + (ok ? v[j] : 0.0f);
         }
     }
-    {
+    if (tid < kDim) {
         // S2 b1 from the staged BF16 row of S2 (the same operand the product
         // used), FP32 accumulation
         float s = b2[m] + sm.b1[m];

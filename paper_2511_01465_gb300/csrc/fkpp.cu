@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(256) fk_compose_f64(LevelArgs a) {
     }
 }
 
-// Mixed, tensor cores of the 5th generation: one CTA of 128 threads per
+// Mixed, tensor cores of the 5th generation: one CTA of 256 threads per
 // compose (see compose_tc.cuh); a lone last child is copied.
 struct CombineArgs {
     const float* S2; const float* b2;  // later elements (stride FD*FD / FD)
@@ -310,7 +310,7 @@ struct CombineArgs {
 
 constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
 
-__global__ void __launch_bounds__(128) fk_compose_tc_kernel(CombineArgs a) {
+__global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     tc::ComposeSmem& sm =
         *reinterpret_cast<tc::ComposeSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(128) fk_compose_tc_kernel(CombineArgs a) {
         const float4* src = reinterpret_cast<const float4*>(a.S1 + (size_t)m * a.stride_in * MM);
         float4* dst = reinterpret_cast<float4*>(a.S + (size_t)m * MM);
         for (int i = tid; i < (int)(MM / 4); i += blockDim.x) dst[i] = src[i];
-        a.b[m * FD + tid] = a.b1[m * a.stride_in * FD + tid];
+        if (tid < FD) a.b[m * FD + tid] = a.b1[m * a.stride_in * FD + tid];
         return;
     }
     if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
@@ -554,7 +554,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
             ca.stride_in = 2;
             ca.n_lone = (la.n_in & 1) ? la.n_in / 2 : -1;
             ca.err = err;
-            fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 128, kTcSmem, st>>>(ca);
+            fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 256, kTcSmem, st>>>(ca);
         } else {
             const size_t sm = (size_t)(FD * FD + 32 * FD) * sizeof(double);
             fk_compose_f64<<<dim3((unsigned)tr.n[lv], 4), 256, sm, st>>>(la);
@@ -729,7 +729,7 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
     ca.S2 = S2; ca.b2 = b2; ca.S1 = S1; ca.b1 = b1; ca.S = S; ca.b = b;
     ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err;
     auto tok = timed_begin("fkpp_compose", st);
-    fk_compose_tc_kernel<<<(unsigned)n, 128, kTcSmem, st>>>(ca);
+    fk_compose_tc_kernel<<<(unsigned)n, 256, kTcSmem, st>>>(ca);
     timed_end(tok, st);
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;

@@ -560,12 +560,25 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     using namespace pitn;
     int cmin = 4;
     if (o.tile_elems > 0) cmin = o.tile_elems;
+    const bool rk4 = o.method == PITN_STEP_RK4;
     int per_sm = 0;
-    switch (system_id) {
-    case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63>(block); break;
-    case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol>(block); break;
-    case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc>(block); break;
-    default: return PITN_EINVAL;
+    int W = 0;
+    if (rk4 && system_id == PITN_VDP) {
+        per_sm = max_blocks_per_sm<RK4Map<VdpRhs>>(block);
+        W = RK4Map<VdpRhs>::JN + 2;
+    } else if (rk4 && system_id == PITN_LOGISTIC) {
+        per_sm = max_blocks_per_sm<RK4Map<LogisticRhs>>(block);
+        W = RK4Map<LogisticRhs>::JN + 1;
+    } else if (rk4) {
+        return PITN_EUNSUPPORTED;
+    } else {
+        switch (system_id) {
+        case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63>(block); W = Lorenz63::JN + 3; break;
+        case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol>(block); W = VanDerPol::JN + 2; break;
+        case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc>(block); W = LinearOsc::JN + 2; break;
+        case PITN_LOGISTIC: per_sm = max_blocks_per_sm<EulerMap<LogisticRhs>>(block); W = 2; break;
+        default: return PITN_EINVAL;
+        }
     }
     if (per_sm < 1) return PITN_EUNSUPPORTED;  // shape does not fit on an SM
     per_sm = std::min(per_sm, per_sm_cap);
@@ -573,7 +586,6 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     const long long want = (N + (long long)block * cmin - 1) / ((long long)block * cmin);
     const int grid = (int)std::max(1LL, std::min(max_grid, want));
     const long long chunk = (N + (long long)grid * block - 1) / ((long long)grid * block);
-    const int W = (d == 3) ? (Lorenz63::JN + 3) : (system_id == PITN_VDP ? VanDerPol::JN + 2 : LinearOsc::JN + 2);
     const int E = d * d + d;
 
     double* X1 = (double*)workspace((size_t)N * d * sizeof(double), kSlotX1);
@@ -619,10 +631,15 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
     cudaError_t e;
-    switch (system_id) {
-    case PITN_LORENZ63: e = launch_small<Lorenz63>(a, grid, block, st); break;
-    case PITN_VDP: e = launch_small<VanDerPol>(a, grid, block, st); break;
-    default: e = launch_small<LinearOsc>(a, grid, block, st); break;
+    if (rk4 && system_id == PITN_VDP) e = launch_small<RK4Map<VdpRhs>>(a, grid, block, st);
+    else if (rk4) e = launch_small<RK4Map<LogisticRhs>>(a, grid, block, st);
+    else {
+        switch (system_id) {
+        case PITN_LORENZ63: e = launch_small<Lorenz63>(a, grid, block, st); break;
+        case PITN_VDP: e = launch_small<VanDerPol>(a, grid, block, st); break;
+        case PITN_LOGISTIC: e = launch_small<EulerMap<LogisticRhs>>(a, grid, block, st); break;
+        default: e = launch_small<LinearOsc>(a, grid, block, st); break;
+        }
     }
     if (e != cudaSuccess) { cudaGetLastError(); return PITN_ECUDA; }
     int* h_err = (int*)hbuf;
@@ -659,7 +676,8 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
     int cap = 2;
     const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
     char key[96];
-    std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d", system_id, d, tune_bucket(N), guarded ? 1 : 0);
+    std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d%s", system_id, d, tune_bucket(N), guarded ? 1 : 0,
+                  o.method == PITN_STEP_RK4 ? ":rk4" : "");
     int tb = 0, tc = 0;
     if (tune_lookup(key, &tb, &tc)) {
         block = tb;

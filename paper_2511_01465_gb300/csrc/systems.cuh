@@ -194,3 +194,141 @@ struct LinearOsc {
 };
 
 }  // namespace pitn
+
+// ---------------------------------------------------------------------------
+// Classical four-stage Runge-Kutta step map (eq. 2.3, tableau a21 = a32 = 1/2,
+// a43 = 1, b = (1/6, 1/3, 1/3, 1/6)) over a right-hand side Rhs, with its
+// Jacobian by the chain rule through the stages:
+//   K_1 = Jf(x),  K_i = Jf(y_i) (I + h a_{i,i-1} K_{i-1}),
+//   dphi/dx = I + h sum_i b_i K_i.
+// Rhs provides D, P, init(p), f(x, out) and jf(x, J) (dense D x D).
+// The compact Jacobian of this map is the dense one (JN = D * D).
+// ---------------------------------------------------------------------------
+namespace pitn {
+
+struct LogisticRhs {
+    static constexpr int D = 1, P = 2;
+    double r, K;
+    __host__ __device__ void init(const double* p) { r = p[0]; K = p[1]; }
+    __device__ __forceinline__ void f(const double* x, double* o) const { o[0] = r * x[0] * (1.0 - x[0] / K); }
+    __device__ __forceinline__ void jf(const double* x, double* J) const { J[0] = r * (1.0 - 2.0 * x[0] / K); }
+};
+
+struct VdpRhs {
+    static constexpr int D = 2, P = 1;
+    double mu;
+    __host__ __device__ void init(const double* p) { mu = p[0]; }
+    __device__ __forceinline__ void f(const double* x, double* o) const {
+        o[0] = x[1];
+        o[1] = mu * (1.0 - x[0] * x[0]) * x[1] - x[0];
+    }
+    __device__ __forceinline__ void jf(const double* x, double* J) const {
+        J[0] = 0.0;
+        J[1] = 1.0;
+        J[2] = -2.0 * mu * x[0] * x[1] - 1.0;
+        J[3] = mu * (1.0 - x[0] * x[0]);
+    }
+};
+
+template <class Rhs>
+struct RK4Map {
+    static constexpr int D = Rhs::D, JN = D * D, P = Rhs::P;
+    Rhs rhs;
+    double h;
+    __host__ __device__ void init(const double* p, double hh) {
+        rhs.init(p);
+        h = hh;
+    }
+    // r = xc - phi(xp), jv = dphi/dx(xp) (dense, row-major)
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
+        double k[4][D], Kj[4][D * D], y[D], Y[D * D], Jf[D * D];
+        const double a[4] = {0.0, 0.5, 0.5, 1.0};
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = (s == 0) ? xp[i] : xp[i] + h * a[s] * k[s - 1][i];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i)
+                Y[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) + ((s == 0) ? 0.0 : h * a[s] * Kj[s - 1][i]);
+            rhs.f(y, k[s]);
+            rhs.jf(y, Jf);
+#pragma unroll
+            for (int i = 0; i < D; ++i)
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    double sacc = 0.0;
+#pragma unroll
+                    for (int l = 0; l < D; ++l) sacc = fma(Jf[i * D + l], Y[l * D + j], sacc);
+                    Kj[s][i * D + j] = sacc;
+                }
+        }
+        const double w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) sacc += w[s] * k[s][i];
+            res[i] = xc[i] - (xp[i] + h * sacc);
+        }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) sacc += w[s] * Kj[s][i];
+            jv[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) + h * sacc;
+        }
+    }
+    __device__ __forceinline__ void jfull(const double* jv, double* J) const {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) J[i] = jv[i];
+    }
+    __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                double sacc = 0.0;
+#pragma unroll
+                for (int l = 0; l < D; ++l) sacc = fma(jv[i * D + l], M[l * D + j], sacc);
+                o[i * D + j] = sacc;
+            }
+    }
+    __device__ __forceinline__ void jvec(const double* jv, const double* v, double* o) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int l = 0; l < D; ++l) sacc = fma(jv[i * D + l], v[l], sacc);
+            o[i] = sacc;
+        }
+    }
+    __device__ __forceinline__ void jvec_sub(const double* jv, const double* v, const double* rr, double* o) const {
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            double sacc = -rr[i];
+#pragma unroll
+            for (int l = 0; l < D; ++l) sacc = fma(jv[i * D + l], v[l], sacc);
+            o[i] = sacc;
+        }
+    }
+};
+
+// Explicit Euler over a right-hand side Rhs with a dense Jacobian
+// (phi = x + h f(x), dphi/dx = I + h Jf(x)), for systems without a
+// hand-specialised compact form.
+template <class Rhs>
+struct EulerMap : RK4Map<Rhs> {
+    using Base = RK4Map<Rhs>;
+    static constexpr int D = Rhs::D, JN = D * D, P = Rhs::P;
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
+        double fx[D], Jf[D * D];
+        this->rhs.f(xp, fx);
+        this->rhs.jf(xp, Jf);
+#pragma unroll
+        for (int i = 0; i < D; ++i) res[i] = xc[i] - (xp[i] + this->h * fx[i]);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) jv[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) + this->h * Jf[i];
+    }
+};
+
+}  // namespace pitn

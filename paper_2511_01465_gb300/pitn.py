@@ -22,7 +22,9 @@ LIB_PATH = os.path.join(_HERE, "libpitn.so")
 PITN_OK, PITN_NOT_CONVERGED, PITN_NONFINITE = 0, 1, 2
 PITN_EINVAL, PITN_ENOMEM, PITN_ECUDA, PITN_ETIMEOUT, PITN_EUNSUPPORTED = -1, -2, -3, -4, -5
 # systems
-PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP = 1, 2, 3, 4
+PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP, PITN_LOGISTIC = 1, 2, 3, 4, 5
+# one-step maps
+PITN_STEP_EULER, PITN_STEP_RK4 = 0, 1
 # precisions
 PITN_PREC_FP64, PITN_PREC_MIXED_BF16 = 0, 1
 
@@ -35,7 +37,8 @@ class pitn_result(ctypes.Structure):
 class pitn_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_elems", ctypes.c_int32),
                 ("guard_B", ctypes.c_double), ("guess", ctypes.c_void_p),
-                ("stream", ctypes.c_void_p), ("res_history", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("res_history", ctypes.c_void_p),
+                ("method", ctypes.c_int32)]
 
 
 _lib = None
@@ -117,8 +120,9 @@ def _ptr(a, dtype=np.float64):
 
 
 def make_options(precision=PITN_PREC_FP64, tile_elems=0, guard_B=0.0, guess=None, stream=None,
-                 res_history=None):
+                 res_history=None, method=PITN_STEP_EULER):
     o = pitn_options()
+    o.method = int(method)
     o.precision = int(precision)
     o.tile_elems = int(tile_elems)
     o.guard_B = float(guard_B)
