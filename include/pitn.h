@@ -79,10 +79,13 @@ enum {
 /* Arithmetic of the Newton step (the residual and the update are always FP64). */
 enum {
     PITN_PREC_FP64 = 0,        /* every operation in FP64 */
-    PITN_PREC_MIXED_BF16 = 1   /* d >= 64 only: dense composes of the scan on
-                                  tensor cores (BF16 operands, FP32
+    PITN_PREC_MIXED_BF16 = 1,  /* PITN_FKPP with d >= 64: dense composes of the
+                                  scan on tensor cores (BF16 operands, FP32
                                   accumulation) in the delta form A = J - I;
                                   an inexact Newton step */
+    PITN_PREC_MIXED_FP32 = 2   /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
+                                  Euler: the scan's elements in FP32 delta form
+                                  (I + S, c); an inexact Newton step */
 };
 
 /* Per-solve outcome. */

@@ -303,8 +303,13 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
     if (!std::isfinite(tol) || !(tol >= 0.0)) return PITN_EINVAL;
     if (max_iter < 0 || max_iter > kMaxIter) return PITN_EINVAL;
     if (std::isnan(o.guard_B)) return PITN_EINVAL;
-    if (o.precision != PITN_PREC_FP64 && o.precision != PITN_PREC_MIXED_BF16) return PITN_EINVAL;
+    if (o.precision != PITN_PREC_FP64 && o.precision != PITN_PREC_MIXED_BF16 &&
+        o.precision != PITN_PREC_MIXED_FP32)
+        return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
+    if (o.precision == PITN_PREC_MIXED_FP32 &&
+        (system_id == PITN_FKPP || system_id == PITN_LOGISTIC || o.method != PITN_STEP_EULER))
+        return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
     if (o.method != PITN_STEP_EULER && o.method != PITN_STEP_RK4) return PITN_EINVAL;
     if (o.method == PITN_STEP_RK4 && system_id != PITN_VDP && system_id != PITN_LOGISTIC)

@@ -32,6 +32,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <cfloat>
 
 #include "common.cuh"
 #include "solver.h"
@@ -514,23 +515,32 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
     }
 }
 
-template <class Sys>
+}  // namespace pitn
+
+#include "newton_small_mixed.cuh"
+
+namespace pitn {
+
+template <class Sys, bool MIXED = false>
 static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
     void* args[] = {(void*)&a};
     auto tok = pitn_host::timed_begin("newton_small", st);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)newton_small_kernel<Sys>, dim3(grid),
-                                                dim3(block), args, 0, st);
+    const void* kern;
+    if constexpr (MIXED) kern = (const void*)newton_small_mixed_kernel<Sys>;
+    else kern = (const void*)newton_small_kernel<Sys>;
+    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
     pitn_host::timed_end(tok, st);
     pitn_host::count_launch(1);
     return e;
 }
 
-template <class Sys>
+template <class Sys, bool MIXED = false>
 static int max_blocks_per_sm(int block) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Sys>, block, 0) !=
-        cudaSuccess)
-        return 0;
+    cudaError_t e;
+    if constexpr (MIXED) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_mixed_kernel<Sys>, block, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Sys>, block, 0);
+    if (e != cudaSuccess) return 0;
     return per_sm;
 }
 
@@ -561,9 +571,18 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     int cmin = 4;
     if (o.tile_elems > 0) cmin = o.tile_elems;
     const bool rk4 = o.method == PITN_STEP_RK4;
+    const bool mixed = o.precision == PITN_PREC_MIXED_FP32;
     int per_sm = 0;
     int W = 0;
-    if (rk4 && system_id == PITN_VDP) {
+    if (mixed) {
+        // FP32 scratch: W floats per step fit in the W-double slots
+        switch (system_id) {
+        case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63, true>(block); W = Lorenz63::JN + 3; break;
+        case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol, true>(block); W = VanDerPol::JN + 2; break;
+        case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc, true>(block); W = LinearOsc::JN + 2; break;
+        default: return PITN_EUNSUPPORTED;
+        }
+    } else if (rk4 && system_id == PITN_VDP) {
         per_sm = max_blocks_per_sm<RK4Map<VdpRhs>>(block);
         W = RK4Map<VdpRhs>::JN + 2;
     } else if (rk4 && system_id == PITN_LOGISTIC) {
@@ -631,7 +650,13 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
     cudaError_t e;
-    if (rk4 && system_id == PITN_VDP) e = launch_small<RK4Map<VdpRhs>>(a, grid, block, st);
+    if (mixed) {
+        switch (system_id) {
+        case PITN_LORENZ63: e = launch_small<Lorenz63, true>(a, grid, block, st); break;
+        case PITN_VDP: e = launch_small<VanDerPol, true>(a, grid, block, st); break;
+        default: e = launch_small<LinearOsc, true>(a, grid, block, st); break;
+        }
+    } else if (rk4 && system_id == PITN_VDP) e = launch_small<RK4Map<VdpRhs>>(a, grid, block, st);
     else if (rk4) e = launch_small<RK4Map<LogisticRhs>>(a, grid, block, st);
     else {
         switch (system_id) {
@@ -676,8 +701,8 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
     int cap = 2;
     const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
     char key[96];
-    std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d%s", system_id, d, tune_bucket(N), guarded ? 1 : 0,
-                  o.method == PITN_STEP_RK4 ? ":rk4" : "");
+    std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d%s%s", system_id, d, tune_bucket(N), guarded ? 1 : 0,
+                  o.method == PITN_STEP_RK4 ? ":rk4" : "", o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : "");
     int tb = 0, tc = 0;
     if (tune_lookup(key, &tb, &tc)) {
         block = tb;

@@ -1,0 +1,450 @@
+// newton_small_mixed.cuh -- the small-state Newton solve with a reduced-
+// precision scan (an inexact Newton step), included by newton_small.cu.
+//
+// Same three-phase persistent kernel as the FP64 one (residual + fold, fixed-
+// order scan of the CTA aggregates, replay + update, two grid barriers per
+// iteration), with one change of arithmetic: the residual, the stopping test
+// and the update x + dx stay FP64, while the affine elements are kept in FP32
+// in the delta form A = I + S (S = J - I = h df/dx keeps its full relative
+// precision, where rounding J itself to FP32 would lose the O(h) part):
+//   (I + S2, c2) o (I + S1, c1) = (I + S2 + S1 + S2 S1, c2 + c1 + S2 c1),
+//   (I + S) v + c = v + S v + c,   head element a_0 = (S = -I, c = -r_0).
+// The Newton step therefore carries FP32 rounding; the outer iteration
+// converges to the FP64 tolerance because every residual is exact FP64.
+#pragma once
+
+namespace pitn {
+
+template <int D>
+__device__ __forceinline__ void dz_zero(float* Q, float* c) {
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) Q[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = 0.f;
+}
+
+// (Q, c) <- (Q2, c2) o (Q1, c1) in the delta form
+template <int D>
+__device__ __forceinline__ void dz_compose(const float* Q2, const float* c2, const float* Q1, const float* c1,
+                                           float* Q, float* c) {
+    float tQ[D * D], tc[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float s = Q2[i * D + j] + Q1[i * D + j];
+#pragma unroll
+            for (int l = 0; l < D; ++l) s = fmaf(Q2[i * D + l], Q1[l * D + j], s);
+            tQ[i * D + j] = s;
+        }
+        float s = c2[i] + c1[i];
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fmaf(Q2[i * D + l], c1[l], s);
+        tc[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) Q[i] = tQ[i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = tc[i];
+}
+
+// o = v + Q v + c
+template <int D>
+__device__ __forceinline__ void dz_apply(const float* Q, const float* c, const float* v, float* o) {
+    float t[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        float s = v[i] + c[i];
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fmaf(Q[i * D + l], v[l], s);
+        t[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) o[i] = t[i];
+}
+
+template <int D>
+__device__ __forceinline__ void dz_warp_scan(float* Q, float* c, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        float uQ[D * D], uc[D];
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) uQ[j] = __shfl_up_sync(0xffffffffu, Q[j], off);
+#pragma unroll
+        for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, c[j], off);
+        if (lane >= off) dz_compose<D>(Q, c, uQ, uc, Q, c);
+    }
+}
+
+// Exclusive block scan in the delta form (same fixed order as block_scan).
+template <int D>
+__device__ __forceinline__ void dz_block_scan(float* Q, float* c, float* eQ, float* ec,
+                                              float (*s_wex)[D * D + D], float* s_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    dz_warp_scan<D>(Q, c, lane);
+#pragma unroll
+    for (int j = 0; j < D * D; ++j) eQ[j] = __shfl_up_sync(0xffffffffu, Q[j], 1);
+#pragma unroll
+    for (int j = 0; j < D; ++j) ec[j] = __shfl_up_sync(0xffffffffu, c[j], 1);
+    if (lane == 0) dz_zero<D>(eQ, ec);
+    __syncthreads();
+    if (lane == 31) {
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) s_wex[warp][j] = Q[j];
+#pragma unroll
+        for (int j = 0; j < D; ++j) s_wex[warp][D * D + j] = c[j];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        float wQ[D * D], wc[D];
+        if (lane < nwarps) {
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) wQ[j] = s_wex[lane][j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) wc[j] = s_wex[lane][D * D + j];
+        } else {
+            dz_zero<D>(wQ, wc);
+        }
+#pragma unroll
+        for (int off = 1; off < kMaxWarps; off <<= 1) {
+            float uQ[D * D], uc[D];
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) uQ[j] = __shfl_up_sync(0xffffffffu, wQ[j], off);
+#pragma unroll
+            for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, wc[j], off);
+            if (lane >= off) dz_compose<D>(wQ, wc, uQ, uc, wQ, wc);
+        }
+        float xQ[D * D], xc[D];
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) xQ[j] = __shfl_up_sync(0xffffffffu, wQ[j], 1);
+#pragma unroll
+        for (int j = 0; j < D; ++j) xc[j] = __shfl_up_sync(0xffffffffu, wc[j], 1);
+        __syncwarp();
+        if (lane < nwarps) {
+            if (lane == 0) dz_zero<D>(xQ, xc);
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) s_wex[lane][j] = xQ[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_wex[lane][D * D + j] = xc[j];
+        }
+        if (lane == nwarps - 1) {
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) s_tot[j] = wQ[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_tot[D * D + j] = wc[j];
+        }
+    }
+    __syncthreads();
+}
+
+// (Q, c) <- (S, -r) o (Q, c) for one leaf: Q' = S + Q + S Q, c' = c + S c - r
+template <int D>
+__device__ __forceinline__ void dz_leaf(const float* S, const float* r, float* Q, float* c) {
+    float tQ[D * D], tc[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            float s = S[i * D + j] + Q[i * D + j];
+#pragma unroll
+            for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], Q[l * D + j], s);
+            tQ[i * D + j] = s;
+        }
+        float s = c[i] - r[i];
+#pragma unroll
+        for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], c[l], s);
+        tc[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) Q[i] = tQ[i];
+#pragma unroll
+    for (int i = 0; i < D; ++i) c[i] = tc[i];
+}
+
+template <class Sys>
+__global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
+    Sys sys;
+    sys.init(a.params, a.h);
+
+    __shared__ float s_wex[kMaxWarps][E];
+    __shared__ float s_tot[E];
+    __shared__ float s_g[kMaxWarps][E];
+    __shared__ float s_gtot[E];
+    __shared__ float s_zin[D];
+
+    const int lane = threadIdx.x & 31;
+    const long long N = a.N;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const unsigned G = gridDim.x;
+    float* __restrict__ scr = reinterpret_cast<float*>(a.scratch);
+    float* __restrict__ agg = reinterpret_cast<float*>(a.agg);
+    double capd;
+    {
+        const unsigned long long cb = a.cap_bits;
+        capd = __longlong_as_double((long long)cb);
+    }
+    const float capf = (float)fmin(capd, (double)FLT_MAX);
+
+    int cur = 0;
+    long long q = a.q_init;
+    long long last_cut = N;
+    int it = 0, status = PITN_NOT_CONVERGED;
+    double final_res = 0.0;
+
+    for (;;) {
+        const double* __restrict__ Xc = cur ? a.X1 : a.X0;
+        double* __restrict__ Xn = cur ? a.X0 : a.X1;
+        const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
+        long long k0, k1;
+        {
+            const long long wreg = 4 * sfill;
+            const long long wtot = wreg + (N - sfill);
+            const long long per = (wtot + nthreads - 1) / nthreads;
+            const long long w0 = gt * per, w1 = w0 + per;
+            k0 = (w0 <= wreg) ? (w0 + 3) / 4 : sfill + (w0 - wreg);
+            k1 = (w1 <= wreg) ? (w1 + 3) / 4 : sfill + (w1 - wreg);
+            k0 = min(N, k0);
+            k1 = min(N, k1);
+        }
+        const long long kreg = min(k1, max(k0, sfill));
+        // ---- phase 1: FP64 residual, FP32 delta fold (two interleaved halves) ----
+        unsigned long long my_res = 0ull;
+        const long long Lr = kreg - k0;
+        const long long LA = (Lr + 1) / 2, LB = Lr - LA, km = k0 + LA;
+        float QA[D * D], cA[D], QB[D * D], cB[D];
+        double xpA[D], xpB[D];
+        dz_zero<D>(QA, cA);
+        dz_zero<D>(QB, cB);
+        if (LA > 0) load_state<D>(Xc, a.x0, k0 - 1, q, xpA);
+        if (LB > 0) load_state<D>(Xc, a.x0, km - 1, q, xpB);
+        auto fold_step = [&](long long k, double* xp, float* Q, float* c) {
+            double x[D], r[D];
+            float sv[JN], rf[D];
+            load_state<D>(Xc, a.x0, k, q, x);
+            sys.eval_mixed(xp, x, r, sv);
+#pragma unroll
+            for (int j = 0; j < JN; ++j) scr[k * W + j] = sv[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                rf[j] = (float)r[j];
+                scr[k * W + JN + j] = rf[j];
+                const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
+                my_res = b > my_res ? b : my_res;
+            }
+            if (k == 0) {  // a_0 = (0, -r_0): S = -I
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) Q[j] = (j % (D + 1) == 0) ? -1.f : 0.f;
+#pragma unroll
+                for (int j = 0; j < D; ++j) c[j] = -rf[j];
+            } else {
+                float S[D * D];
+                sys.sfull(sv, S);
+                dz_leaf<D>(S, rf, Q, c);
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) xp[j] = x[j];
+        };
+        for (long long i = 0; i < LA; ++i) {
+            fold_step(k0 + i, xpA, QA, cA);
+            if (i < LB) fold_step(km + i, xpB, QB, cB);
+        }
+        float Q[D * D], c[D];
+        dz_compose<D>(QB, cB, QA, cA, Q, c);
+        if (kreg < k1) {  // fill region: identical elements, binary powering
+            double xf[D], rf64[D];
+            float svf[JN], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
+            load_state<D>(Xc, a.x0, q - 1, q, xf);
+            sys.eval_mixed(xf, xf, rf64, svf);
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(rf64[j]) & kAbsMask;
+                my_res = b > my_res ? b : my_res;
+                Ec[j] = -(float)rf64[j];
+            }
+            sys.sfull(svf, EQ);
+            dz_zero<D>(RQ, Rc);
+            for (long long e = k1 - kreg;;) {
+                if (e & 1) dz_compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
+                e >>= 1;
+                if (!e) break;
+                dz_compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
+            }
+            dz_compose<D>(RQ, Rc, Q, c, Q, c);
+        }
+        float eQ[D * D], ec[D];
+        dz_block_scan<D>(Q, c, eQ, ec, s_wex, s_tot);
+        if (threadIdx.x < E) agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_res, off);
+            my_res = o > my_res ? o : my_res;
+        }
+        if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+
+        const unsigned long long rb = __ldcg(a.res_bits + it);
+        const double res = __longlong_as_double((long long)rb);
+        final_res = res;
+        if (rb >= kInfBits) { status = PITN_NONFINITE; break; }
+        if (res <= a.tol) { status = PITN_OK; break; }
+        if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
+
+        // ---- incoming prefix: fixed-order scan of the CTA aggregates ----
+        {
+            const unsigned m = (G + blockDim.x - 1) / blockDim.x;
+            float gQ[D * D], gc[D];
+            dz_zero<D>(gQ, gc);
+            for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
+                float sQ[D * D], sc[D];
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+                for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+                dz_compose<D>(sQ, sc, gQ, gc, gQ, gc);
+            }
+            float xQ[D * D], xc[D];
+            dz_block_scan<D>(gQ, gc, xQ, xc, s_g, s_gtot);
+            if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
+                float v[D], t[D], zero[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) zero[j] = 0.f;
+                dz_apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
+                dz_apply<D>(xQ, xc, t, v);
+                for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
+                    float sQ[D * D], sc[D];
+#pragma unroll
+                    for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+                    dz_apply<D>(sQ, sc, v, t);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) v[j] = t[j];
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = v[j];
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = 0.f;
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 3: FP32 replay, FP64 update ----
+        unsigned long long my_q = 0ull;
+        {
+            float zw[D], zA[D], zB[D];
+            dz_apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
+            dz_apply<D>(eQ, ec, zw, zA);
+            dz_apply<D>(QA, cA, zA, zB);
+            bool foundA = false, foundB = false;
+            long long firstA = 0, firstB = 0;
+            auto replay_step = [&](long long k, float* z) -> bool {
+                float sv[JN], rf[D], S[D * D];
+                double x[D];
+#pragma unroll
+                for (int j = 0; j < JN; ++j) sv[j] = __ldcg(scr + k * W + j);
+#pragma unroll
+                for (int j = 0; j < D; ++j) rf[j] = __ldcg(scr + k * W + JN + j);
+                load_state<D>(Xc, a.x0, k, q, x);
+                if (k == 0) {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) z[j] = -rf[j];
+                } else {
+                    sys.sfull(sv, S);
+                    float t[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float s = z[i] - rf[i];
+#pragma unroll
+                        for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], z[l], s);
+                        t[i] = s;
+                    }
+#pragma unroll
+                    for (int j = 0; j < D; ++j) z[j] = t[j];
+                }
+                bool bad = false;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    Xn[k * D + j] = x[j] + (double)z[j];
+                    bad |= !(fabsf(z[j]) <= capf);
+                }
+                return bad;
+            };
+            for (long long i = 0; i < LA && !foundA; ++i) {
+                if (replay_step(k0 + i, zA)) { foundA = true; firstA = k0 + i; }
+                if (i < LB && !foundB && replay_step(km + i, zB)) { foundB = true; firstB = km + i; }
+            }
+            const bool found = foundA || foundB;
+            if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
+            float z[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) z[j] = (LB > 0) ? zB[j] : zA[j];
+            if (!found && kreg < k1) {
+                double xf[D], rf64[D];
+                float svf[JN], S[D * D], rfl[D];
+                load_state<D>(Xc, a.x0, q - 1, q, xf);
+                sys.eval_mixed(xf, xf, rf64, svf);
+                sys.sfull(svf, S);
+#pragma unroll
+                for (int j = 0; j < D; ++j) rfl[j] = (float)rf64[j];
+                for (long long k = kreg; k < k1; ++k) {
+                    float t[D];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        float s = z[i] - rfl[i];
+#pragma unroll
+                        for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], z[l], s);
+                        t[i] = s;
+                    }
+                    bool bad = false;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        z[j] = t[j];
+                        Xn[k * D + j] = xf[j] + (double)z[j];
+                        bad |= !(fabsf(z[j]) <= capf);
+                    }
+                    if (bad) {
+                        my_q = ~(unsigned long long)k;
+                        break;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+            my_q = o > my_q ? o : my_q;
+        }
+        if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        const unsigned long long qe = __ldcg(a.qenc + it);
+        const long long cut = qe ? (long long)(~qe) : N;
+        if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }
+        cur ^= 1;
+        q = a.guarded ? cut : N;
+        last_cut = cut;
+        ++it;
+    }
+
+    const double* Xc = cur ? a.X1 : a.X0;
+    const bool same = (Xc == a.out);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = gt; k < N; k += stride) {
+        if (same && k < q) continue;
+        double v[D];
+        load_state<D>(Xc, a.x0, k, q, v);
+#pragma unroll
+        for (int j = 0; j < D; ++j) a.out[k * D + j] = v[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.rec->iters = it;
+        a.rec->status = status;
+        a.rec->final_res = final_res;
+        a.rec->guard_index = last_cut;
+    }
+}
+
+}  // namespace pitn

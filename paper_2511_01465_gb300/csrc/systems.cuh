@@ -11,6 +11,8 @@
 //   jtvec(jv, v, out):    out = J^T v           (adjoint)
 //   vjp_param(xp, v, g):  g += (dphi/dp(xp))^T v  (adjoint, g has P entries)
 //   jac(xp, jv):          the compact Jacobian alone
+//   eval_mixed(xp, xc, r, sv), sfull(sv, S): FP64 residual with the compact
+//                         Jacobian in FP32 delta form S = J - I (mixed scan)
 //   jfull(jv, J):         the dense D x D Jacobian from its compact form
 // The compact form stores only the state-dependent entries of J, so an
 // element of the scan costs D + JN registers instead of D + D*D.
@@ -69,6 +71,20 @@ struct Lorenz63 {
         o[1] = j01 * v0 + j11 * v1 + jv[1] * v2;
         o[2] = -jv[1] * v1 + j22 * v2;
     }
+    // mixed precision: FP64 residual, FP32 delta form S = J - I
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res,
+                                               float* sv) const {
+        double jv[3];
+        eval(xp, xc, res, jv);
+        sv[0] = (float)jv[0];
+        sv[1] = (float)jv[1];
+        sv[2] = (float)jv[2];
+    }
+    __device__ __forceinline__ void sfull(const float* sv, float* S) const {
+        S[0] = (float)(-h * s); S[1] = (float)(h * s); S[2] = 0.f;
+        S[3] = sv[0];           S[4] = (float)(-h);    S[5] = -sv[1];
+        S[6] = sv[2];           S[7] = sv[1];          S[8] = (float)(-h * b);
+    }
     __device__ __forceinline__ void jfull(const double* jv, double* J) const {
         J[0] = j00;   J[1] = j01;   J[2] = 0.0;
         J[3] = jv[0]; J[4] = j11;   J[5] = -jv[1];
@@ -112,6 +128,21 @@ struct VanDerPol {
         const double v0 = v[0], v1 = v[1];
         o[0] = fma(h, v1, v0 - rr[0]);
         o[1] = fma(jv[0], v0, fma(jv[1], v1, -rr[1]));
+    }
+    // mixed precision: FP64 residual, FP32 delta form S = J - I = [[0, h], [a, h mu w]]
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res,
+                                               float* sv) const {
+        const double x = xp[0], v = xp[1];
+        const double w = fma(-x, x, 1.0);
+        const double t = hmu * w;
+        res[0] = fma(-h, v, xc[0] - x);
+        res[1] = fma(h, x, fma(-t, v, xc[1] - v));
+        sv[0] = (float)fma(m2hmu * x, v, -h);
+        sv[1] = (float)t;
+    }
+    __device__ __forceinline__ void sfull(const float* sv, float* S) const {
+        S[0] = 0.f; S[1] = (float)h;
+        S[2] = sv[0]; S[3] = sv[1];
     }
     __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
         double m00 = M[0], m01 = M[1], m10 = M[2], m11 = M[3];
@@ -176,6 +207,16 @@ struct LinearOsc {
         const double v0 = v[0], v1 = v[1];
         o[0] = fma(h, v1, v0 - rr[0]);
         o[1] = fma(j10, v0, fma(j11, v1, -rr[1]));
+    }
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res,
+                                               float* sv) const {
+        double jv[1];
+        eval(xp, xc, res, jv);
+        sv[0] = 0.f;
+    }
+    __device__ __forceinline__ void sfull(const float*, float* S) const {
+        S[0] = 0.f; S[1] = (float)h;
+        S[2] = (float)j10; S[3] = (float)(-2.0 * h * z * w);
     }
     __device__ __forceinline__ void jtvec(const double*, const double* v, double* o) const {
         double v0 = v[0], v1 = v[1];

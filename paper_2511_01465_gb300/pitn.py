@@ -26,7 +26,7 @@ PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP, PITN_LOGISTIC = 1, 2, 3, 4,
 # one-step maps
 PITN_STEP_EULER, PITN_STEP_RK4 = 0, 1
 # precisions
-PITN_PREC_FP64, PITN_PREC_MIXED_BF16 = 0, 1
+PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32 = 0, 1, 2
 
 
 class pitn_result(ctypes.Structure):

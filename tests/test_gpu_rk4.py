@@ -46,9 +46,10 @@ def test_rk4_against_oracle(pk, key, N):
     with open(GOLD) as f:
         g = json.load(f)[key]
     d = len(g["x0"])
+    guess = np.full((N, d), g["guess"])  # the paper's initial guess (plain Newton converges from it)
     traj, info = pk.solve(SYS[key], g["params"], g["x0"], g["h"], N, 1e-12, 40, history=True,
-                          method=pk.PITN_STEP_RK4)
-    o = O.newton(SYS[key], g["params"], g["x0"], g["h"], N, 1e-12, 40, method=O.RK4)
+                          method=pk.PITN_STEP_RK4, guess=guess)
+    o = O.newton(SYS[key], g["params"], g["x0"], g["h"], N, 1e-12, 40, method=O.RK4, guess=guess)
     assert (info["iters"], info["status"]) == (o["iters"], o["status"])
     t = traj.cpu().numpy()
     assert np.abs(t - o["traj"]).max() <= 1e-10 * np.abs(o["traj"]).max()
