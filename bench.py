@@ -50,7 +50,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP64 flops per step executed by the small-state kernel, counted from its
 # source (FMA = 2): phase 1 (residual, compact Jacobian, thread fold) runs on
 # every residual evaluation, phase 3 (replay, update) once per Newton update.
-SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0)}
+SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
+               "vdp_mixed": (34.0, 9.0), "lorenz_mixed": (76.0, 19.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -73,6 +74,13 @@ def workload(name):
     if name == "lorenz":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0,
                     desc="lorenz63 sigma=10 rho=28 beta=8/3 x0=(1,1,1) h=1e-3 N=8192, guarded Newton B=100")
+    if name == "vdp_mixed":
+        return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=2,
+                    desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
+                         "scan in FP32 delta form (inexact Newton), FP64 residual and update")
+    if name == "lorenz_mixed":
+        return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0, precision=2,
+                    desc="lorenz63 N=8192 h=1e-3, guarded Newton B=100, scan in FP32 delta form")
     if name == "fkpp":
         return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=0,
                     desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, FP64 scan")
@@ -447,7 +455,8 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "flushed (512 MiB write) between timed steps",
                        "step_ms": [round(t, 3) for t in times],
                        "launch_shape": P.pitn_tune_get(f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:"
-                                                       f"{1 if spec['guard_B'] > 0 else 0}"),
+                                                       f"{1 if spec['guard_B'] > 0 else 0}"
+                                                       f"{':f32' if spec.get('precision', 0) == 2 else ''}"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()}}
@@ -460,7 +469,14 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
     ms, launches = ktimes[kern]
     passes = res.iters + 1
     per_step_s = ms / 1e3 / steps
-    if kern == "newton_small":
+    if kern == "newton_small" and spec.get("precision", 0) == 2:
+        # mixed: the FP64 part per step is the residual (van der Pol 12, Lorenz 21 flops)
+        # and the update (d flops); the scan runs in FP32
+        f64 = {"vdp_mixed": 12.0 + 2.0, "lorenz_mixed": 21.0 + 3.0}[name]
+        flops = wl.N * f64 * passes
+        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
+        note = "FP64 flops (residual + update) of the mixed kernel; peak = nominal GB300 FP64"
+    elif kern == "newton_small":
         p1, p3 = SMALL_FLOPS[name]
         flops = wl.N * (p1 * passes + p3 * res.iters)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
@@ -519,6 +535,8 @@ def oracle_passes(name, fallback):
     """Residual evaluations the oracle's own full solve needs (stored by
     tests/golden/make_oracle_golden.py, which runs only the oracle)."""
     key = {"vdp": "vdp_2^22_guard100_tol1e-12_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
+           "vdp_mixed": "vdp_2^22_guard100_tol1e-12_it400",
+           "lorenz_mixed": "lorenz_8192_guard100_tol1e-12_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-12_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
@@ -540,7 +558,8 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
-SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3}
+SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6,
+                "lorenz_mixed": 62}
 
 
 def cpu_baseline_batch(spec, n_ivps=24):
