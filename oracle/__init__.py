@@ -24,8 +24,8 @@ _lock = threading.Lock()
 _lib = None
 
 # identifiers understood by the C oracle
-LORENZ63, VDP, LINEAR_OSC, FKPP, LOGISTIC = 1, 2, 3, 4, 5
-EULER, RK4 = 0, 1
+LORENZ63, VDP, LINEAR_OSC, FKPP, LOGISTIC, DAHLQUIST, ROBERTSON = 1, 2, 3, 4, 5, 6, 7
+EULER, RK4, BACKWARD_EULER = 0, 1, 2
 OK, NOT_CONVERGED, NONFINITE = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)

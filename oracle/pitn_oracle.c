@@ -16,13 +16,17 @@
  * What each routine follows:
  *   rhs / rhs_jac / rhs_dparam  the ODE right-hand sides, eq. (2.1); the test
  *                               systems of Sec. 4.1 (logistic, van der Pol)
- *                               plus the Lorenz-63, damped oscillator and
- *                               Fisher-KPP method-of-lines systems used as
- *                               synthetic workloads.
+ *                               and Sec. 4.2 (Dahlquist, Robertson) plus the
+ *                               Lorenz-63, damped oscillator and Fisher-KPP
+ *                               method-of-lines systems used as synthetic
+ *                               workloads.
  *   step                        one-step maps: explicit Euler, eq. (2.2), and
  *                               the classical four-stage Runge-Kutta rule,
  *                               eq. (2.3), with their Jacobians by the chain
- *                               rule through the stages.
+ *                               rule through the stages; backward Euler,
+ *                               eq. (2.5), in the residual and Newton step of
+ *                               eqs. (3.15)-(3.19) (Dahlquist and Robertson
+ *                               systems of Sec. 4.2).
  *   oracle_sequential           the sequential solver, Sec. 2.1.
  *   oracle_residual             the root-finding residual h(xi), eq. (3.8),
  *                               and its infinity norm, Sec. 4 (stopping rule).
@@ -42,6 +46,9 @@
  * Readings of the paper that this file takes (the paper is silent on them):
  *   - K in the paper counts residual evaluations; `iters` here counts Newton
  *     updates actually applied (paper K - 1).
+ *   - implicit rule: the stopping quantity is ||(I - dg/dx_n)^{-1} h_n||_inf,
+ *     the preconditioned residual (it reproduces the paper's implicit traces,
+ *     e.g. 1/1.1 and 1/1.004 at iteration 0 from a zero guess).
  *   - converged iff ||h||_inf <= tol; a NaN or infinite residual entry ends
  *     the solve with status NONFINITE, checked before the tolerance.
  *   - guard (not in the paper, optional): after the Newton step is computed,
@@ -59,8 +66,9 @@
 #include <float.h>
 
 /* System and method identifiers (the numbers a caller passes). */
-enum { OR_LORENZ63 = 1, OR_VDP = 2, OR_LINEAR_OSC = 3, OR_FKPP = 4, OR_LOGISTIC = 5 };
-enum { OR_EULER = 0, OR_RK4 = 1 };
+enum { OR_LORENZ63 = 1, OR_VDP = 2, OR_LINEAR_OSC = 3, OR_FKPP = 4, OR_LOGISTIC = 5,
+       OR_DAHLQUIST = 6, OR_ROBERTSON = 7 };
+enum { OR_EULER = 0, OR_RK4 = 1, OR_BACKWARD_EULER = 2 };
 enum { OR_OK = 0, OR_NOT_CONVERGED = 1, OR_NONFINITE = 2, OR_EINVAL = -1, OR_ENOMEM = -2 };
 
 int oracle_nparams(int sys)
@@ -71,6 +79,8 @@ int oracle_nparams(int sys)
     case OR_LINEAR_OSC: return 2; /* omega, zeta */
     case OR_FKPP: return 1;       /* D */
     case OR_LOGISTIC: return 2;   /* r, K */
+    case OR_DAHLQUIST: return 1;  /* lambda */
+    case OR_ROBERTSON: return 3;  /* k1, k2, k3 */
     default: return -1;
     }
 }
@@ -83,6 +93,8 @@ static int dim_ok(int sys, int d)
     case OR_LINEAR_OSC: return d == 2;
     case OR_FKPP: return d >= 1;
     case OR_LOGISTIC: return d == 1;
+    case OR_DAHLQUIST: return d == 1;
+    case OR_ROBERTSON: return d == 3;
     default: return 0;
     }
 }
@@ -139,6 +151,18 @@ int oracle_rhs(int sys, const double *p, int d, const double *x, double *f)
         f[0] = r * x[0] * (1.0 - x[0] / K);
         break;
     }
+    case OR_DAHLQUIST:
+        /* y' = lambda y (Sec. 4.2) */
+        f[0] = p[0] * x[0];
+        break;
+    case OR_ROBERTSON: {
+        /* Robertson's reaction (Sec. 4.2) */
+        double k1 = p[0], k2 = p[1], k3 = p[2];
+        f[0] = -k1 * x[0] + k3 * x[1] * x[2];
+        f[1] = k1 * x[0] - k2 * x[1] * x[1] - k3 * x[1] * x[2];
+        f[2] = k2 * x[1] * x[1];
+        break;
+    }
     }
     return OR_OK;
 }
@@ -182,6 +206,16 @@ int oracle_rhs_jac(int sys, const double *p, int d, const double *x, double *J)
         J[0] = r * (1.0 - 2.0 * x[0] / K);
         break;
     }
+    case OR_DAHLQUIST:
+        J[0] = p[0];
+        break;
+    case OR_ROBERTSON: {
+        double k1 = p[0], k2 = p[1], k3 = p[2];
+        J[0] = -k1; J[1] = k3 * x[2];                       J[2] = k3 * x[1];
+        J[3] = k1;  J[4] = -2.0 * k2 * x[1] - k3 * x[2];    J[5] = -k3 * x[1];
+        J[6] = 0.0; J[7] = 2.0 * k2 * x[1];                 J[8] = 0.0;
+        break;
+    }
     }
     return OR_OK;
 }
@@ -222,6 +256,17 @@ int oracle_rhs_dparam(int sys, const double *p, int d, const double *x, double *
         G[1] = r * x[0] * x[0] / (K * K);
         break;
     }
+    case OR_DAHLQUIST:
+        G[0] = x[0];
+        break;
+    case OR_ROBERTSON:
+        G[0 * 3 + 0] = -x[0];
+        G[1 * 3 + 0] = x[0];
+        G[1 * 3 + 1] = -x[1] * x[1];
+        G[2 * 3 + 1] = x[1] * x[1];
+        G[0 * 3 + 2] = x[1] * x[2];
+        G[1 * 3 + 2] = -x[1] * x[2];
+        break;
     }
     return OR_OK;
 }
@@ -239,6 +284,54 @@ static void matmul(int n, int m, int k, const double *A, const double *B, double
             for (int l = 0; l < m; ++l) s += A[(size_t)i * m + l] * B[(size_t)l * k + j];
             C[(size_t)i * k + j] = s;
         }
+}
+
+/* Solves A y = b in place (b <- y) by Gaussian elimination with partial
+ * pivoting; A (d x d, row-major) is overwritten.  Returns 0, or -1 for a
+ * singular matrix. */
+static int solve_dense(int d, double *A, double *b)
+{
+    for (int c = 0; c < d; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < d; ++r)
+            if (fabs(A[(size_t)r * d + c]) > fabs(A[(size_t)piv * d + c])) piv = r;
+        if (A[(size_t)piv * d + c] == 0.0) return -1;
+        if (piv != c) {
+            for (int j = 0; j < d; ++j) {
+                double t = A[(size_t)c * d + j];
+                A[(size_t)c * d + j] = A[(size_t)piv * d + j];
+                A[(size_t)piv * d + j] = t;
+            }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < d; ++r) {
+            double m = A[(size_t)r * d + c] / A[(size_t)c * d + c];
+            for (int j = c; j < d; ++j) A[(size_t)r * d + j] -= m * A[(size_t)c * d + j];
+            b[r] -= m * b[c];
+        }
+    }
+    for (int r = d - 1; r >= 0; --r) {
+        double sacc = b[r];
+        for (int j = r + 1; j < d; ++j) sacc -= A[(size_t)r * d + j] * b[j];
+        b[r] = sacc / A[(size_t)r * d + r];
+    }
+    return 0;
+}
+
+/* Backward Euler (eq. 2.5): x_n = x_{n-1} + h f(x_n), i.e. g = h f(x_n).
+ * implicit_parts computes, for the states xp = x_{n-1} and xc = x_n,
+ *   the residual h_n = xc - xp - h f(xc)                     (eq. 3.15),
+ *   A_n = I - h df/dx(xc) = I - dg/dx_n (the diagonal block of eq. 3.16). */
+static void implicit_parts(int sys, const double *p, int d, double h, const double *xp,
+                           const double *xc, double *hn, double *A)
+{
+    double *f = (double *)malloc(sizeof(double) * d);
+    oracle_rhs(sys, p, d, xc, f);
+    for (int i = 0; i < d; ++i) hn[i] = xc[i] - xp[i] - h * f[i];
+    oracle_rhs_jac(sys, p, d, xc, A);
+    for (int i = 0; i < d * d; ++i) A[i] = -h * A[i];
+    for (int i = 0; i < d; ++i) A[(size_t)i * d + i] += 1.0;
+    free(f);
 }
 
 /*
@@ -353,6 +446,31 @@ int oracle_sequential(int sys, int method, const double *p, const double *x0, do
                       int64_t N, int d, double *traj)
 {
     if (!dim_ok(sys, d) || N < 0) return OR_EINVAL;
+    if (method == OR_BACKWARD_EULER) {
+        /* each step solves x_n - x_{n-1} - h f(x_n) = 0 by Newton from x_{n-1},
+         * to the last bit (correction below 1e-15 relative, at most 100 steps) */
+        double *hn = (double *)malloc(sizeof(double) * d);
+        double *A = (double *)malloc(sizeof(double) * (size_t)d * d);
+        const double *prev = x0;
+        for (int64_t n = 0; n < N; ++n) {
+            double *y = traj + (size_t)n * d;
+            memcpy(y, prev, sizeof(double) * d);
+            for (int it = 0; it < 100; ++it) {
+                implicit_parts(sys, p, d, h, prev, y, hn, A);
+                if (solve_dense(d, A, hn)) break;
+                double nrm = 0.0, ny = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    y[i] -= hn[i];
+                    if (fabs(hn[i]) > nrm) nrm = fabs(hn[i]);
+                    if (fabs(y[i]) > ny) ny = fabs(y[i]);
+                }
+                if (nrm <= 1e-15 * ny || nrm == 0.0) break;
+            }
+            prev = y;
+        }
+        free(hn); free(A);
+        return OR_OK;
+    }
     const double *prev = x0;
     for (int64_t n = 0; n < N; ++n) {
         int rc = oracle_step(sys, method, p, d, h, prev, traj + (size_t)n * d, NULL, NULL);
@@ -373,12 +491,23 @@ int oracle_residual(int sys, int method, const double *p, const double *x0, doub
 {
     if (!dim_ok(sys, d) || N < 0) return OR_EINVAL;
     double *phi = (double *)malloc(sizeof(double) * d);
-    if (!phi) return OR_ENOMEM;
+    double *A = (double *)malloc(sizeof(double) * (size_t)d * d);
+    if (!phi || !A) { free(phi); free(A); return OR_ENOMEM; }
     double m = 0.0;
     int saw_nan = 0, nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         const double *prev = (n == 0) ? x0 : traj + (size_t)(n - 1) * d;
-        oracle_step(sys, method, p, d, h, prev, phi, NULL, NULL);
+        if (method == OR_BACKWARD_EULER) {
+            /* implicit rule: the residual h_n of eq. 3.15 preconditioned by
+             * (I - dg/dx_n)^{-1}, the quantity the paper's implicit residual
+             * figure reports (reading taken here) */
+            implicit_parts(sys, p, d, h, prev, traj + (size_t)n * d, phi, A);
+            if (solve_dense(d, A, phi))
+                for (int c = 0; c < d; ++c) phi[c] = NAN;
+            for (int c = 0; c < d; ++c) phi[c] = traj[(size_t)n * d + c] - phi[c];
+        } else {
+            oracle_step(sys, method, p, d, h, prev, phi, NULL, NULL);
+        }
         for (int c = 0; c < d; ++c) {
             double v = traj[(size_t)n * d + c] - phi[c];
             if (r) r[(size_t)n * d + c] = v;
@@ -389,6 +518,7 @@ int oracle_residual(int sys, int method, const double *p, const double *x0, doub
         }
     }
     free(phi);
+    free(A);
     if (res) *res = saw_nan ? NAN : m;
     if (nonfinite) *nonfinite = nf;
     return OR_OK;
@@ -494,13 +624,26 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
 
         /* Newton step, eq. (3.13): dx[n] holds Delta x_{n+1}. */
         for (int i = 0; i < d; ++i) dx[i] = -r[i];
-        for (int64_t n = 1; n < (int64_t)N; ++n) {
-            const double *xn = traj + (size_t)(n - 1) * d;   /* x_n, state n (1-based) */
-            oracle_step(sys, method, p, d, h, xn, phi, J, NULL);
-            for (int i = 0; i < d; ++i) {
-                double s = 0.0;
-                for (int j = 0; j < d; ++j) s += J[(size_t)i * d + j] * dx[(size_t)(n - 1) * d + j];
-                dx[(size_t)n * d + i] = s - r[(size_t)n * d + i];
+        if (method == OR_BACKWARD_EULER) {
+            /* eq. 3.19 with dg/dx_{n-1} = 0:
+             *   dx_n = (I - dg/dx_n)^{-1} (dx_{n-1} - h_n) = A_n^{-1} dx_{n-1} - r_n,
+             * r_n the preconditioned residual above */
+            for (int64_t n = 1; n < (int64_t)N; ++n) {
+                const double *xp = traj + (size_t)(n - 1) * d;
+                implicit_parts(sys, p, d, h, xp, traj + (size_t)n * d, phi, J);
+                for (int i = 0; i < d; ++i) phi[i] = dx[(size_t)(n - 1) * d + i];
+                solve_dense(d, J, phi);
+                for (int i = 0; i < d; ++i) dx[(size_t)n * d + i] = phi[i] - r[(size_t)n * d + i];
+            }
+        } else {
+            for (int64_t n = 1; n < (int64_t)N; ++n) {
+                const double *xn = traj + (size_t)(n - 1) * d;   /* x_n, state n (1-based) */
+                oracle_step(sys, method, p, d, h, xn, phi, J, NULL);
+                for (int i = 0; i < d; ++i) {
+                    double s = 0.0;
+                    for (int j = 0; j < d; ++j) s += J[(size_t)i * d + j] * dx[(size_t)(n - 1) * d + j];
+                    dx[(size_t)n * d + i] = s - r[(size_t)n * d + i];
+                }
             }
         }
         /* first correction that is not finite (or exceeds the guard bound) */
@@ -579,6 +722,7 @@ int oracle_adjoint(int sys, int method, const double *p, const double *x0, doubl
 {
     int P = oracle_nparams(sys);
     if (P < 0 || !dim_ok(sys, d) || N < 1) return OR_EINVAL;
+    if (method != OR_EULER && method != OR_RK4) return OR_EINVAL;   /* explicit maps only */
     size_t dd = (size_t)d * d, dp = (size_t)d * P;
     double *lam = (double *)calloc((size_t)d, sizeof(double));
     double *nl = (double *)calloc((size_t)d, sizeof(double));

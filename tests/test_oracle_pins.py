@@ -79,6 +79,10 @@ SYSTEMS = [
     (O.LINEAR_OSC, [1.7, 0.2], 2),
     (O.FKPP, [1e-3], 7),
     (O.LOGISTIC, [1.0, 2.0], 1),
+    (O.DAHLQUIST, [-0.7], 1),
+    # Robertson's structure with moderate rate constants: central differences of
+    # the quadratic right-hand side stay exact to well inside the tolerance
+    (O.ROBERTSON, [0.04, 30.0, 10.0], 3),
 ]
 
 
@@ -290,3 +294,91 @@ def test_batch_equals_single_solves():
         s, e = out["offsets"][b], out["offsets"][b + 1]
         assert np.array_equal(out["traj"][s:e], r["traj"])
         assert out["iters"][b] == r["iters"] and out["status"][b] == r["status"]
+
+
+# --------------------------------------------------------------------------
+# Implicit rule (Sec. 3.4, eqs. 3.15-3.19; Sec. 4.2 experiments).
+# --------------------------------------------------------------------------
+GOLD_IMPLICIT = os.path.join(os.path.dirname(__file__), "golden", "paper_implicit_traces.json")
+
+
+def _load_gold_implicit():
+    with open(GOLD_IMPLICIT) as f:
+        return json.load(f)
+
+
+IMPLICIT = {"dahlquist": O.DAHLQUIST, "robertson": O.ROBERTSON}
+
+
+@pytest.mark.parametrize("key", ["dahlquist", "robertson"])
+def test_paper_implicit_residual_trace(key):
+    g = _load_gold_implicit()[key]
+    N, d = g["N"], len(g["x0"])
+    r = O.newton(IMPLICIT[key], g["params"], g["x0"], g["h"], N, 2e-14, 60,
+                 guess=np.full((N, d), g["guess"]), method=O.BACKWARD_EULER)
+    paper = np.array(g["residuals"])
+    assert r["status"] == O.OK
+    assert r["iters"] + 1 == g["K"] == len(paper)
+    for k, (a, b) in enumerate(zip(r["res_hist"], paper)):
+        assert abs(a - b) <= 1e-8 * abs(b) + 1e-15, (k, a, b)
+
+
+@pytest.mark.parametrize("key,dt", [("dahlquist", 1e-2), ("dahlquist", 1e-3), ("dahlquist", 1e-4),
+                                    ("robertson", 1e-2)])
+def test_paper_implicit_iteration_count(key, dt):
+    g = _load_gold_implicit()[key]
+    N, d = int(round(g["t_end"] / dt)), len(g["x0"])
+    r = O.newton(IMPLICIT[key], g["params"], g["x0"], dt, N, 2e-14, 60,
+                 guess=np.zeros((N, d)), method=O.BACKWARD_EULER)
+    assert r["status"] == O.OK
+    assert r["iters"] + 1 == g["K_vs_dt"][repr(dt) if repr(dt) in g["K_vs_dt"] else str(dt)]
+
+
+def test_backward_euler_dahlquist_closed_form():
+    # backward Euler on y' = lambda y: y_n = (1 - h lambda)^{-n} exactly
+    lam, h, N = -2.5, 0.03, 200
+    ref = (1.0 / (1.0 - h * lam)) ** np.arange(1, N + 1)
+    seq = O.sequential(O.DAHLQUIST, [lam], [1.0], h, N, method=O.BACKWARD_EULER)[:, 0]
+    np.testing.assert_allclose(seq, ref, rtol=1e-12)
+    r = O.newton(O.DAHLQUIST, [lam], [1.0], h, N, 1e-14, 5, guess=np.zeros((N, 1)),
+                 method=O.BACKWARD_EULER)
+    assert r["status"] == O.OK and r["iters"] == 1      # affine in xi: one update
+    np.testing.assert_allclose(r["traj"][:, 0], ref, rtol=1e-12)
+
+
+def test_backward_euler_root_and_mass_conservation():
+    # x_n - x_{n-1} - h f(x_n) = 0 checked with the right-hand side alone, and
+    # y1 + y2 + y3 = 1 (the Robertson rates sum to zero, so every backward
+    # Euler state conserves the total)
+    p, x0, h, N = [0.04, 3e7, 1e4], np.array([1.0, 0.0, 0.0]), 0.05, 400
+    r = O.newton(O.ROBERTSON, p, x0, h, N, 1e-14, 60, guess=np.zeros((N, 3)),
+                 method=O.BACKWARD_EULER)
+    assert r["status"] == O.OK
+    x = r["traj"]
+    prev = np.vstack([x0, x[:-1]])
+    resid = np.array([x[n] - prev[n] - h * O.rhs(O.ROBERTSON, p, x[n]) for n in range(N)])
+    assert np.abs(resid).max() < 1e-12
+    np.testing.assert_allclose(x.sum(axis=1), 1.0, atol=1e-13)
+    seq = O.sequential(O.ROBERTSON, p, x0, h, N, method=O.BACKWARD_EULER)
+    np.testing.assert_allclose(x, seq, rtol=1e-10, atol=1e-14)
+
+
+@pytest.mark.parametrize("sys,p,d", [(O.DAHLQUIST, [-3.0], 1), (O.ROBERTSON, [0.04, 3e2, 1e2], 3),
+                                     (O.VDP, [2.0], 2)])
+def test_implicit_newton_step_equals_dense_solve(sys, p, d):
+    # eq. (3.17): dxi = -H^{-1} h(xi), H block lower bidiagonal with diagonal
+    # I - h df/dx(x_n) and sub-diagonal -I (eq. 3.16), solved densely
+    N, h = 7, 0.05
+    rng = np.random.default_rng(11)
+    x0 = rng.uniform(0, 1, d)
+    guess = rng.uniform(0, 1, (N, d))
+    prev = np.vstack([x0, guess[:-1]])
+    hv = np.concatenate([guess[n] - prev[n] - h * O.rhs(sys, p, guess[n]) for n in range(N)])
+    H = np.zeros((N * d, N * d))
+    for i in range(N):
+        H[i * d:(i + 1) * d, i * d:(i + 1) * d] = np.eye(d) - h * O.rhs_jac(sys, p, guess[i])
+        if i > 0:
+            H[i * d:(i + 1) * d, (i - 1) * d:i * d] = -np.eye(d)
+    dxi = -np.linalg.solve(H, hv)
+    out = O.newton(sys, p, x0, h, N, 0.0, 1, guess=guess, guard_B=1e300, method=O.BACKWARD_EULER)
+    np.testing.assert_allclose(out["traj"] - guess, dxi.reshape(N, d), rtol=1e-11, atol=1e-13)
