@@ -51,7 +51,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # source (FMA = 2): phase 1 (residual, compact Jacobian, thread fold) runs on
 # every residual evaluation, phase 3 (replay, update) once per Newton update.
 SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
-               "vdp_mixed": (34.0, 9.0), "lorenz_mixed": (76.0, 19.0)}
+               "vdp_mixed": (34.0, 9.0), "lorenz_mixed": (76.0, 19.0),
+               # backward Euler Robertson: f 8, Jf 9, I - h Jf 12, h_n 9, 3x3 inverse 42
+               # (one division counted as 1), M^-1 h_n 18, dense fold 72; replay 18 + update 3
+               "robertson": (170.0, 21.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -81,6 +84,11 @@ def workload(name):
     if name == "lorenz_mixed":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0, precision=2,
                     desc="lorenz63 N=8192 h=1e-3, guarded Newton B=100, scan in FP32 delta form")
+    if name == "robertson":
+        return dict(kind="single", wl=W.robertson(h=1e-4), tol=1e-8, max_iter=60, guard_B=0.0, method=2,
+                    guess=0.0,
+                    desc="robertson k=(0.04,3e7,1e4) y0=(1,0,0) on [0,500], backward Euler h=1e-4 N=5e6, "
+                         "plain Newton from the zero guess (Sec. 4.2), preconditioned residual")
     if name == "fkpp":
         return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=0,
                     desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, FP64 scan")
@@ -367,7 +375,12 @@ def run_ours(args, rank, world, local_rank):
     traj = torch.empty((wl.N, wl.d), dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     prec = spec.get("precision", 0)
-    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec)
+    method = spec.get("method", 0)
+    guess = None
+    if "guess" in spec:  # constant initial guess, copied into the trajectory by every solve
+        guess = torch.full((wl.N, wl.d), spec["guess"], dtype=torch.float64, device=dev)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec, guess=guess,
+                         method=method)
 
     def solve_once():
         rc, res = P.pitn_solve_ex(wl.system, params, x0, wl.h, wl.N, wl.d, spec["tol"],
@@ -429,7 +442,11 @@ def run_ours(args, rank, world, local_rank):
         h_x0 = torch.tensor(wl.x0, dtype=torch.float64).pin_memory()
         h_traj = torch.empty((wl.N, wl.d), dtype=torch.float64).pin_memory()
         hp, hx, ht = h_params.numpy(), h_x0.numpy(), h_traj.numpy()
-        opt_h = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec)
+        h_guess = None
+        if guess is not None:
+            h_guess = torch.full((wl.N, wl.d), spec["guess"], dtype=torch.float64).pin_memory().numpy()
+        opt_h = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec,
+                               guess=h_guess, method=method)
         P.pitn_solve_ex(wl.system, hp, hx, wl.h, wl.N, wl.d, spec["tol"], spec["max_iter"], ht, opt_h)
         et = []
         for _ in range(max(1, min(args.steps, 5))):
@@ -442,7 +459,8 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = statistics.median(et)
         e2e_ok = r2.status == P.PITN_OK and r2.final_res <= spec["tol"]
         e2e = {"value": (world * wl.N / e2e_s) if e2e_ok else 0.0, "unit": UNIT,
-               "h2d_bytes_per_step": int((wl.d + len(wl.params)) * 8),
+               "h2d_bytes_per_step": int((wl.d + len(wl.params)) * 8 +
+                                         (wl.N * wl.d * 8 if h_guess is not None else 0)),
                "d2h_bytes_per_step": int(wl.N * wl.d * 8), "ms_per_step": e2e_s * 1e3}
 
     roofline = roofline_for(args.workload, spec, wl, res, ktimes, args.steps)
@@ -456,6 +474,7 @@ def run_ours(args, rank, world, local_rank):
                        "step_ms": [round(t, 3) for t in times],
                        "launch_shape": P.pitn_tune_get(f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:"
                                                        f"{1 if spec['guard_B'] > 0 else 0}"
+                                                       f"{':be' if method == 2 else ''}"
                                                        f"{':f32' if spec.get('precision', 0) == 2 else ''}"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -523,9 +542,10 @@ def oracle_sample(spec, sample_iters):
     of Newton iterations and projects to the full solve's residual count."""
     import oracle as O
     wl = spec["wl"]
+    guess = np.full((wl.N, wl.d), spec["guess"]) if "guess" in spec else None
     t0 = time.perf_counter()
     r = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, spec["tol"], sample_iters,
-                 guard_B=spec["guard_B"])
+                 guard_B=spec["guard_B"], guess=guess, method=spec.get("method", O.EULER))
     dt = time.perf_counter() - t0
     evals = r["iters"] + 1
     return dt / evals, r
@@ -538,7 +558,8 @@ def oracle_passes(name, fallback):
            "vdp_mixed": "vdp_2^22_guard100_tol1e-12_it400",
            "lorenz_mixed": "lorenz_8192_guard100_tol1e-12_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-12_it100",
-           "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50"}
+           "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
+           "robertson": "robertson_5e6_be_zeros_tol1e-8_it60"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     try:
         with open(p) as f:
@@ -559,7 +580,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6,
-                "lorenz_mixed": 62}
+                "lorenz_mixed": 62, "robertson": 9}
 
 
 def cpu_baseline_batch(spec, n_ivps=24):

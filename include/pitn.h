@@ -66,14 +66,28 @@ enum {
     PITN_FKPP = 4,       /* d >= 3 interior nodes of [0,1], spacing 1/(d+1),
                             zero Dirichlet ends; params {D}:
                             f_i = D (u_{i-1} - 2u_i + u_{i+1})/dx^2 + u_i(1-u_i) */
-    PITN_LOGISTIC = 5    /* d = 1; params {r, K}: f = r P (1 - P/K)  (Sec. 4.1) */
+    PITN_LOGISTIC = 5,   /* d = 1; params {r, K}: f = r P (1 - P/K)  (Sec. 4.1) */
+    PITN_DAHLQUIST = 6,  /* d = 1; params {lambda}: f = lambda y  (Sec. 4.2) */
+    PITN_ROBERTSON = 7   /* d = 3; params {k1, k2, k3}: f = (-k1 y1 + k3 y2 y3,
+                            k1 y1 - k2 y2^2 - k3 y2 y3, k2 y2^2)  (Sec. 4.2, stiff) */
 };
 
 /* One-step maps (Sec. 2.1). */
 enum {
-    PITN_STEP_EULER = 0,  /* explicit Euler, eq. 2.2 (every system, every entry point) */
-    PITN_STEP_RK4 = 1     /* classical Runge-Kutta, eq. 2.3; pitn_solve_ex only, for
+    PITN_STEP_EULER = 0,  /* explicit Euler, eq. 2.2: every system in pitn_solve_ex;
+                             LORENZ63 / VDP / LINEAR_OSC in the batched, adjoint and
+                             no-allocation entry points */
+    PITN_STEP_RK4 = 1,    /* classical Runge-Kutta, eq. 2.3; pitn_solve_ex only, for
                              PITN_VDP and PITN_LOGISTIC (the paper's explicit tests) */
+    PITN_STEP_BACKWARD_EULER = 2, /* implicit Euler, eq. 2.5, with the implicit Newton
+                             step of Sec. 3.4 (eqs. 3.14-3.19); pitn_solve_ex only, for
+                             PITN_DAHLQUIST, PITN_ROBERTSON, PITN_VDP, PITN_LOGISTIC.
+                             The residual an implicit rule reports, stops on and returns
+                             in final_res / res_history is the preconditioned one,
+                             ||(I - dg/dx_n)^{-1} h_n||_inf (h_n of eq. 3.15). */
+    PITN_STEP_TRAPEZOID = 3 /* trapezoidal rule, g = (h/2)(f(x_{n-1}) + f(x_n))
+                             (Sec. 3.4); same entry point, systems and residual as
+                             PITN_STEP_BACKWARD_EULER */
 };
 
 /* Arithmetic of the Newton step (the residual and the update are always FP64). */
@@ -117,7 +131,8 @@ typedef struct {
 
 /*
  * Solve one IVP by the paper's plain Newton method in FP64.
- *   system_id  PITN_LORENZ63 / PITN_VDP / PITN_LINEAR_OSC / PITN_FKPP / PITN_LOGISTIC
+ *   system_id  PITN_LORENZ63 / PITN_VDP / PITN_LINEAR_OSC / PITN_FKPP / PITN_LOGISTIC /
+ *              PITN_DAHLQUIST / PITN_ROBERTSON
  *   params     system parameters (see the enum), host or device
  *   x0         initial value x_0, [d]
  *   h          step size (finite, > 0)

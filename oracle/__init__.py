@@ -25,7 +25,7 @@ _lib = None
 
 # identifiers understood by the C oracle
 LORENZ63, VDP, LINEAR_OSC, FKPP, LOGISTIC, DAHLQUIST, ROBERTSON = 1, 2, 3, 4, 5, 6, 7
-EULER, RK4, BACKWARD_EULER = 0, 1, 2
+EULER, RK4, BACKWARD_EULER, TRAPEZOID = 0, 1, 2, 3
 OK, NOT_CONVERGED, NONFINITE = 0, 1, 2
 
 _dp = ctypes.POINTER(ctypes.c_double)

@@ -23,10 +23,11 @@
  *   step                        one-step maps: explicit Euler, eq. (2.2), and
  *                               the classical four-stage Runge-Kutta rule,
  *                               eq. (2.3), with their Jacobians by the chain
- *                               rule through the stages; backward Euler,
- *                               eq. (2.5), in the residual and Newton step of
- *                               eqs. (3.15)-(3.19) (Dahlquist and Robertson
- *                               systems of Sec. 4.2).
+ *                               rule through the stages; the implicit rules
+ *                               of Sec. 3.4 (backward Euler, eq. (2.5), and
+ *                               the trapezoidal rule) in the residual and
+ *                               Newton step of eqs. (3.15)-(3.19) (Dahlquist
+ *                               and Robertson systems of Sec. 4.2).
  *   oracle_sequential           the sequential solver, Sec. 2.1.
  *   oracle_residual             the root-finding residual h(xi), eq. (3.8),
  *                               and its infinity norm, Sec. 4 (stopping rule).
@@ -68,7 +69,7 @@
 /* System and method identifiers (the numbers a caller passes). */
 enum { OR_LORENZ63 = 1, OR_VDP = 2, OR_LINEAR_OSC = 3, OR_FKPP = 4, OR_LOGISTIC = 5,
        OR_DAHLQUIST = 6, OR_ROBERTSON = 7 };
-enum { OR_EULER = 0, OR_RK4 = 1, OR_BACKWARD_EULER = 2 };
+enum { OR_EULER = 0, OR_RK4 = 1, OR_BACKWARD_EULER = 2, OR_TRAPEZOID = 3 };
 enum { OR_OK = 0, OR_NOT_CONVERGED = 1, OR_NONFINITE = 2, OR_EINVAL = -1, OR_ENOMEM = -2 };
 
 int oracle_nparams(int sys)
@@ -318,19 +319,38 @@ static int solve_dense(int d, double *A, double *b)
     return 0;
 }
 
-/* Backward Euler (eq. 2.5): x_n = x_{n-1} + h f(x_n), i.e. g = h f(x_n).
+/* Implicit rules x_n = x_{n-1} + g(x_{n-1}, x_n) (Sec. 3.4):
+ *   backward Euler (eq. 2.5):  g = h f(x_n);
+ *   trapezoidal rule (Sec. 3.4): g = (h/2) (f(x_{n-1}) + f(x_n)).
  * implicit_parts computes, for the states xp = x_{n-1} and xc = x_n,
- *   the residual h_n = xc - xp - h f(xc)                     (eq. 3.15),
- *   A_n = I - h df/dx(xc) = I - dg/dx_n (the diagonal block of eq. 3.16). */
-static void implicit_parts(int sys, const double *p, int d, double h, const double *xp,
-                           const double *xc, double *hn, double *A)
+ *   the residual h_n = xc - xp - g(xp, xc)                    (eq. 3.15),
+ *   A_n = I - dg/dx_n, the diagonal block of eq. 3.16, and, if B is not
+ *   NULL, B_n = I + dg/dx_{n-1}, minus the sub-diagonal block of eq. 3.16. */
+static int is_implicit(int method) { return method == OR_BACKWARD_EULER || method == OR_TRAPEZOID; }
+
+static void implicit_parts(int sys, int method, const double *p, int d, double h, const double *xp,
+                           const double *xc, double *hn, double *A, double *B)
 {
     double *f = (double *)malloc(sizeof(double) * d);
+    double w = (method == OR_TRAPEZOID) ? 0.5 * h : h;   /* weight of f(x_n) in g */
     oracle_rhs(sys, p, d, xc, f);
-    for (int i = 0; i < d; ++i) hn[i] = xc[i] - xp[i] - h * f[i];
+    for (int i = 0; i < d; ++i) hn[i] = xc[i] - xp[i] - w * f[i];
+    if (method == OR_TRAPEZOID) {
+        oracle_rhs(sys, p, d, xp, f);
+        for (int i = 0; i < d; ++i) hn[i] -= w * f[i];
+    }
     oracle_rhs_jac(sys, p, d, xc, A);
-    for (int i = 0; i < d * d; ++i) A[i] = -h * A[i];
+    for (int i = 0; i < d * d; ++i) A[i] = -w * A[i];
     for (int i = 0; i < d; ++i) A[(size_t)i * d + i] += 1.0;
+    if (B) {
+        if (method == OR_TRAPEZOID) {
+            oracle_rhs_jac(sys, p, d, xp, B);
+            for (int i = 0; i < d * d; ++i) B[i] = w * B[i];
+        } else {
+            for (int i = 0; i < d * d; ++i) B[i] = 0.0;
+        }
+        for (int i = 0; i < d; ++i) B[(size_t)i * d + i] += 1.0;
+    }
     free(f);
 }
 
@@ -446,8 +466,8 @@ int oracle_sequential(int sys, int method, const double *p, const double *x0, do
                       int64_t N, int d, double *traj)
 {
     if (!dim_ok(sys, d) || N < 0) return OR_EINVAL;
-    if (method == OR_BACKWARD_EULER) {
-        /* each step solves x_n - x_{n-1} - h f(x_n) = 0 by Newton from x_{n-1},
+    if (is_implicit(method)) {
+        /* each step solves x_n - x_{n-1} - g(x_{n-1}, x_n) = 0 by Newton from x_{n-1},
          * to the last bit (correction below 1e-15 relative, at most 100 steps) */
         double *hn = (double *)malloc(sizeof(double) * d);
         double *A = (double *)malloc(sizeof(double) * (size_t)d * d);
@@ -456,7 +476,7 @@ int oracle_sequential(int sys, int method, const double *p, const double *x0, do
             double *y = traj + (size_t)n * d;
             memcpy(y, prev, sizeof(double) * d);
             for (int it = 0; it < 100; ++it) {
-                implicit_parts(sys, p, d, h, prev, y, hn, A);
+                implicit_parts(sys, method, p, d, h, prev, y, hn, A, NULL);
                 if (solve_dense(d, A, hn)) break;
                 double nrm = 0.0, ny = 0.0;
                 for (int i = 0; i < d; ++i) {
@@ -497,11 +517,11 @@ int oracle_residual(int sys, int method, const double *p, const double *x0, doub
     int saw_nan = 0, nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         const double *prev = (n == 0) ? x0 : traj + (size_t)(n - 1) * d;
-        if (method == OR_BACKWARD_EULER) {
+        if (is_implicit(method)) {
             /* implicit rule: the residual h_n of eq. 3.15 preconditioned by
              * (I - dg/dx_n)^{-1}, the quantity the paper's implicit residual
              * figure reports (reading taken here) */
-            implicit_parts(sys, p, d, h, prev, traj + (size_t)n * d, phi, A);
+            implicit_parts(sys, method, p, d, h, prev, traj + (size_t)n * d, phi, A, NULL);
             if (solve_dense(d, A, phi))
                 for (int c = 0; c < d; ++c) phi[c] = NAN;
             for (int c = 0; c < d; ++c) phi[c] = traj[(size_t)n * d + c] - phi[c];
@@ -605,8 +625,12 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
     double *r = (double *)malloc(sizeof(double) * nd);
     double *dx = (double *)malloc(sizeof(double) * nd);
     double *J = (double *)malloc(sizeof(double) * dd);
+    double *Bm = (double *)malloc(sizeof(double) * dd);
     double *phi = (double *)malloc(sizeof(double) * d);
-    if (!r || !dx || !J || !phi) { free(r); free(dx); free(J); free(phi); return OR_ENOMEM; }
+    if (!r || !dx || !J || !Bm || !phi) {
+        free(r); free(dx); free(J); free(Bm); free(phi);
+        return OR_ENOMEM;
+    }
 
     if (guess) memcpy(traj, guess, sizeof(double) * nd);
     else for (int64_t n = 0; n < N; ++n) memcpy(traj + (size_t)n * d, x0, sizeof(double) * d);
@@ -624,14 +648,19 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
 
         /* Newton step, eq. (3.13): dx[n] holds Delta x_{n+1}. */
         for (int i = 0; i < d; ++i) dx[i] = -r[i];
-        if (method == OR_BACKWARD_EULER) {
-            /* eq. 3.19 with dg/dx_{n-1} = 0:
-             *   dx_n = (I - dg/dx_n)^{-1} (dx_{n-1} - h_n) = A_n^{-1} dx_{n-1} - r_n,
+        if (is_implicit(method)) {
+            /* eq. 3.19:
+             *   dx_n = (I - dg/dx_n)^{-1} [(I + dg/dx_{n-1}) dx_{n-1} - h_n]
+             *        = A_n^{-1} B_n dx_{n-1} - r_n,
              * r_n the preconditioned residual above */
             for (int64_t n = 1; n < (int64_t)N; ++n) {
                 const double *xp = traj + (size_t)(n - 1) * d;
-                implicit_parts(sys, p, d, h, xp, traj + (size_t)n * d, phi, J);
-                for (int i = 0; i < d; ++i) phi[i] = dx[(size_t)(n - 1) * d + i];
+                implicit_parts(sys, method, p, d, h, xp, traj + (size_t)n * d, phi, J, Bm);
+                for (int i = 0; i < d; ++i) {
+                    double sacc = 0.0;
+                    for (int j = 0; j < d; ++j) sacc += Bm[(size_t)i * d + j] * dx[(size_t)(n - 1) * d + j];
+                    phi[i] = sacc;
+                }
                 solve_dense(d, J, phi);
                 for (int i = 0; i < d; ++i) dx[(size_t)n * d + i] = phi[i] - r[(size_t)n * d + i];
             }
@@ -666,7 +695,7 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
     if (iters) *iters = it;
     if (status) *status = st;
     if (guard_index) *guard_index = q_last;
-    free(r); free(dx); free(J); free(phi);
+    free(r); free(dx); free(J); free(Bm); free(phi);
     return OR_OK;
 }
 

@@ -364,7 +364,8 @@ extern "C" int pitn_backward(int system_id, int64_t B, const double* params, con
                              double* grad_x0_out, double* grad_params_out, const pitn_options* opt) {
     pitn_options o{};
     if (opt) o = *opt;
-    if (system_id == PITN_FKPP || system_id == PITN_LOGISTIC || !system_dim_ok(system_id, d))
+    if ((system_id != PITN_LORENZ63 && system_id != PITN_VDP && system_id != PITN_LINEAR_OSC) ||
+        !system_dim_ok(system_id, d))
         return PITN_EINVAL;
     if (B < 1 || !params || !x0 || !h || !N || !traj || !grad_x0_out || !grad_params_out) return PITN_EINVAL;
     if (ckpt_every < 0) return PITN_EINVAL;

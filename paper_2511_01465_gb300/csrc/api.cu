@@ -158,6 +158,8 @@ int system_dim_ok(int sys, int d) {
     case PITN_LINEAR_OSC: return d == 2;
     case PITN_FKPP: return d >= 3 && d <= kFkppMaxD;
     case PITN_LOGISTIC: return d == 1;
+    case PITN_DAHLQUIST: return d == 1;
+    case PITN_ROBERTSON: return d == 3;
     default: return 0;
     }
 }
@@ -169,6 +171,8 @@ int num_params(int sys) {
     case PITN_LINEAR_OSC: return 2;
     case PITN_FKPP: return 1;
     case PITN_LOGISTIC: return 2;
+    case PITN_DAHLQUIST: return 1;
+    case PITN_ROBERTSON: return 3;
     default: return -1;
     }
 }
@@ -308,11 +312,16 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
         return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_FP32 &&
-        (system_id == PITN_FKPP || system_id == PITN_LOGISTIC || o.method != PITN_STEP_EULER))
+        ((system_id != PITN_LORENZ63 && system_id != PITN_VDP && system_id != PITN_LINEAR_OSC) ||
+         o.method != PITN_STEP_EULER))
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
-    if (o.method != PITN_STEP_EULER && o.method != PITN_STEP_RK4) return PITN_EINVAL;
+    if (o.method < PITN_STEP_EULER || o.method > PITN_STEP_TRAPEZOID) return PITN_EINVAL;
     if (o.method == PITN_STEP_RK4 && system_id != PITN_VDP && system_id != PITN_LOGISTIC)
+        return PITN_EUNSUPPORTED;
+    if ((o.method == PITN_STEP_BACKWARD_EULER || o.method == PITN_STEP_TRAPEZOID) &&
+        system_id != PITN_DAHLQUIST && system_id != PITN_ROBERTSON && system_id != PITN_VDP &&
+        system_id != PITN_LOGISTIC)
         return PITN_EUNSUPPORTED;
 
     std::lock_guard<std::recursive_mutex> lk(api_mutex());

@@ -540,7 +540,8 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
                                 int32_t* status_out, double* res_out, const pitn_options* opt) {
     pitn_options o{};
     if (opt) o = *opt;
-    if (system_id == PITN_FKPP || system_id == PITN_LOGISTIC || !system_dim_ok(system_id, d))
+    if ((system_id != PITN_LORENZ63 && system_id != PITN_VDP && system_id != PITN_LINEAR_OSC) ||
+        !system_dim_ok(system_id, d))
         return PITN_EINVAL;
     if (B < 1 || !params || !x0 || !h || !N || !traj_out || !offsets_out || !iters_out || !status_out)
         return PITN_EINVAL;

@@ -1,0 +1,46 @@
+// newton_implicit.cu -- instantiations of the persistent small-state Newton
+// kernel for the implicit step maps of Sec. 3.4 (backward Euler and the
+// trapezoidal rule) and for the stiff test systems of Sec. 4.2 (Dahlquist,
+// Robertson).
+//
+// The kernel is the explicit one (newton_small.cuh): it only needs a map
+// whose eval(x_{n-1}, x_n) yields the scan element of step n; for backward
+// Euler that element is (M_n^{-1}, -M_n^{-1} h_n) with M_n = I - h Jf(x_n)
+// (eqs. 3.16-3.19), built by BackwardEulerMap in systems.cuh; TrapezoidMap
+// builds the trapezoidal rule's.  The FP32
+// delta form and the batched and adjoint entry points are explicit-only.
+#include "newton_small.cuh"
+
+namespace pitn_host {
+
+int select_implicit_kernel(int system_id, int method, pitn::SmallKernel* K) {
+    using namespace pitn;
+    if (method == PITN_STEP_BACKWARD_EULER) {
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (method == PITN_STEP_TRAPEZOID) {
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<TrapezoidMap<DahlquistRhs>>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<TrapezoidMap<RobertsonRhs>>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<TrapezoidMap<VdpRhs>>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<TrapezoidMap<LogisticRhs>>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (method == PITN_STEP_EULER) {
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<EulerMap<DahlquistRhs>>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<EulerMap<RobertsonRhs>>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    return PITN_EUNSUPPORTED;
+}
+
+}  // namespace pitn_host

@@ -28,523 +28,8 @@
 // NONFINITE; ||r|| <= tol -> OK; max_iter updates -> NOT_CONVERGED; plain
 // Newton with a non-finite correction -> NONFINITE (iterate kept); otherwise
 // accept the step.
-#include <algorithm>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <cfloat>
+#include "newton_small.cuh"
 
-#include "common.cuh"
-#include "solver.h"
-#include "systems.cuh"
-
-namespace pitn {
-
-struct SolveRecord {
-    int iters;
-    int status;
-    double final_res;
-    long long guard_index;
-};
-
-struct SmallArgs {
-    const double* x0;   // [D] device
-    double* X0;         // trajectory buffer 0 [N][D]
-    double* X1;         // trajectory buffer 1 [N][D]
-    double* out;        // destination of the final iterate
-    double* scratch;    // [N][JN + D]: compact Jacobian and residual of every step
-    double* agg;        // [gridDim][D*D + D]: CTA aggregates
-    long long N;
-    long long chunk;    // consecutive steps per thread
-    double h, tol;
-    unsigned long long cap_bits;  // |dx| bits above this are cut (guard bound or DBL_MAX)
-    int guarded;
-    int max_iter;
-    long long q_init;   // 0: constant guess x0 (buffer contents ignored); N: buffer 0 holds the guess
-    double params[4];
-    unsigned long long* res_bits;  // [max_iter + 1]  ||r||_inf bits per iteration
-    unsigned long long* qenc;      // [max_iter + 1]  max of ~q (0 = no cut)
-    unsigned* bar;                 // [2] grid barrier
-    int* err;
-    SolveRecord* rec;
-};
-
-constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
-constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-
-template <int D>
-__device__ __forceinline__ void mat_identity(double* P) {
-#pragma unroll
-    for (int i = 0; i < D * D; ++i) P[i] = (i % (D + 1) == 0) ? 1.0 : 0.0;
-}
-
-// (P, c) <- (P2, c2) o (P1, c1) = (P2 P1, P2 c1 + c2)   (eq. 3.3, 2 = later)
-template <int D>
-__device__ __forceinline__ void compose(const double* P2, const double* c2, const double* P1,
-                                        const double* c1, double* P, double* c) {
-    double tP[D * D], tc[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-            double s = P2[i * D] * P1[j];
-#pragma unroll
-            for (int l = 1; l < D; ++l) s = fma(P2[i * D + l], P1[l * D + j], s);
-            tP[i * D + j] = s;
-        }
-        double s = c2[i];
-#pragma unroll
-        for (int l = 0; l < D; ++l) s = fma(P2[i * D + l], c1[l], s);
-        tc[i] = s;
-    }
-#pragma unroll
-    for (int i = 0; i < D * D; ++i) P[i] = tP[i];
-#pragma unroll
-    for (int i = 0; i < D; ++i) c[i] = tc[i];
-}
-
-// o = P v + c
-template <int D>
-__device__ __forceinline__ void apply(const double* P, const double* c, const double* v, double* o) {
-    double t[D];
-#pragma unroll
-    for (int i = 0; i < D; ++i) {
-        double s = c[i];
-#pragma unroll
-        for (int l = 0; l < D; ++l) s = fma(P[i * D + l], v[l], s);
-        t[i] = s;
-    }
-#pragma unroll
-    for (int i = 0; i < D; ++i) o[i] = t[i];
-}
-
-// x_k of the current iterate with the guard's lazy fill (L2-coherent loads).
-template <int D>
-__device__ __forceinline__ void load_state(const double* __restrict__ X, const double* __restrict__ x0,
-                                           long long k, long long q, double* o) {
-    const double* src;
-    if (k < 0) src = x0;
-    else if (k < q) src = X + k * D;
-    else if (q > 0) src = X + (q - 1) * D;
-    else src = x0;
-#pragma unroll
-    for (int i = 0; i < D; ++i) o[i] = ldcg(src + i);
-}
-
-constexpr int kMaxWarps = 8;  // BLOCK <= 256
-
-// Inclusive Kogge-Stone scan of (P, c) across the warp (later lanes on the left).
-template <int D>
-__device__ __forceinline__ void warp_scan(double* P, double* c, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        double uP[D * D], uc[D];
-#pragma unroll
-        for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, P[j], off);
-#pragma unroll
-        for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, c[j], off);
-        if (lane >= off) compose<D>(P, c, uP, uc, P, c);
-    }
-}
-
-// Exclusive block scan of per-thread elements.  On return (eP, ec) is the
-// lane-exclusive prefix within the warp, s_wex[warp] the warp-exclusive
-// prefix, and s_tot the block total.  All in a fixed order.
-template <int D>
-__device__ __forceinline__ void block_scan(double* P, double* c, double* eP, double* ec,
-                                           double (*s_wex)[D * D + D], double* s_tot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    warp_scan<D>(P, c, lane);
-#pragma unroll
-    for (int j = 0; j < D * D; ++j) eP[j] = __shfl_up_sync(0xffffffffu, P[j], 1);
-#pragma unroll
-    for (int j = 0; j < D; ++j) ec[j] = __shfl_up_sync(0xffffffffu, c[j], 1);
-    if (lane == 0) {
-        mat_identity<D>(eP);
-#pragma unroll
-        for (int j = 0; j < D; ++j) ec[j] = 0.0;
-    }
-    __syncthreads();  // s_wex may still be read from a previous use
-    if (lane == 31) {
-#pragma unroll
-        for (int j = 0; j < D * D; ++j) s_wex[warp][j] = P[j];
-#pragma unroll
-        for (int j = 0; j < D; ++j) s_wex[warp][D * D + j] = c[j];
-    }
-    __syncthreads();
-    if (warp == 0) {
-        double wP[D * D], wc[D];
-        if (lane < nwarps) {
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) wP[j] = s_wex[lane][j];
-#pragma unroll
-            for (int j = 0; j < D; ++j) wc[j] = s_wex[lane][D * D + j];
-        } else {
-            mat_identity<D>(wP);
-#pragma unroll
-            for (int j = 0; j < D; ++j) wc[j] = 0.0;
-        }
-#pragma unroll
-        for (int off = 1; off < kMaxWarps; off <<= 1) {
-            double uP[D * D], uc[D];
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, wP[j], off);
-#pragma unroll
-            for (int j = 0; j < D; ++j) uc[j] = __shfl_up_sync(0xffffffffu, wc[j], off);
-            if (lane >= off) compose<D>(wP, wc, uP, uc, wP, wc);
-        }
-        double xP[D * D], xc[D];
-#pragma unroll
-        for (int j = 0; j < D * D; ++j) xP[j] = __shfl_up_sync(0xffffffffu, wP[j], 1);
-#pragma unroll
-        for (int j = 0; j < D; ++j) xc[j] = __shfl_up_sync(0xffffffffu, wc[j], 1);
-        __syncwarp();
-        if (lane < nwarps) {
-            if (lane == 0) {
-                mat_identity<D>(xP);
-#pragma unroll
-                for (int j = 0; j < D; ++j) xc[j] = 0.0;
-            }
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) s_wex[lane][j] = xP[j];
-#pragma unroll
-            for (int j = 0; j < D; ++j) s_wex[lane][D * D + j] = xc[j];
-        }
-        if (lane == nwarps - 1) {
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) s_tot[j] = wP[j];
-#pragma unroll
-            for (int j = 0; j < D; ++j) s_tot[D * D + j] = wc[j];
-        }
-    }
-    __syncthreads();
-}
-
-// Deterministic three-phase Newton kernel (persistent, cooperative launch).
-// Thread g owns steps [g*chunk, (g+1)*chunk).  Per Newton iteration:
-//   phase 1: residuals + compact Jacobians (stored to scratch), thread fold,
-//            block scan, CTA aggregate to global;   grid barrier;
-//   decision on ||r||_inf (identical in every CTA);
-//   scan of the CTA aggregates in a fixed order (every CTA derives its own
-//   incoming prefix the same way), replay of the thread's steps from its
-//   incoming vector, update into the other buffer, first guard cut;
-//   grid barrier.
-template <class Sys>
-__global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
-    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
-    Sys sys;
-    sys.init(a.params, a.h);
-
-    __shared__ double s_wex[kMaxWarps][E];
-    __shared__ double s_tot[E];
-    __shared__ double s_g[kMaxWarps][E];
-    __shared__ double s_gtot[E];
-    __shared__ double s_zin[D];
-
-    const int lane = threadIdx.x & 31;
-    const long long N = a.N;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nthreads = (long long)gridDim.x * blockDim.x;
-    const unsigned G = gridDim.x;
-    double* __restrict__ scr = a.scratch;
-
-    int cur = 0;
-    long long q = a.q_init;
-    long long last_cut = N;
-    int it = 0, status = PITN_NOT_CONVERGED;
-    double final_res = 0.0;
-
-    for (;;) {
-        const double* __restrict__ Xc = cur ? a.X1 : a.X0;
-        double* __restrict__ Xn = cur ? a.X0 : a.X1;
-        // ---- phase 1: residual, Jacobian, fold -------------------------------
-        // Elements from sfill on lie in the guard's fill region: all their
-        // states equal x_{q-1}, so every one of them is the same element
-        // (J(x_{q-1}), -r_f); a thread folds its share of them by binary
-        // powering instead of one by one.
-        const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
-        // Work partition of this iteration: a regular element costs about four
-        // times a fill element (phase 1 + phase 3 against phase 3 only), so the
-        // steps are split over all threads by that weight; every thread derives
-        // its contiguous range [k0, k1) from (N, sfill) alone.
-        long long k0, k1;
-        {
-            const long long wreg = 4 * sfill;
-            const long long wtot = wreg + (N - sfill);
-            const long long per = (wtot + nthreads - 1) / nthreads;
-            const long long w0 = gt * per, w1 = w0 + per;
-            k0 = (w0 <= wreg) ? (w0 + 3) / 4 : sfill + (w0 - wreg);
-            k1 = (w1 <= wreg) ? (w1 + 3) / 4 : sfill + (w1 - wreg);
-            k0 = min(N, k0);
-            k1 = min(N, k1);
-        }
-        const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
-        // The regular part is folded as two interleaved halves A = [k0, km) and
-        // B = [km, kreg): two independent FP64 dependency chains per thread.
-        unsigned long long my_res = 0ull;
-        const long long Lr = kreg - k0;
-        const long long LA = (Lr + 1) / 2, LB = Lr - LA, km = k0 + LA;
-        double PA[D * D], cA[D], PB[D * D], cB[D], xpA[D], xpB[D];
-        mat_identity<D>(PA);
-        mat_identity<D>(PB);
-#pragma unroll
-        for (int j = 0; j < D; ++j) { cA[j] = 0.0; cB[j] = 0.0; }
-        if (LA > 0) load_state<D>(Xc, a.x0, k0 - 1, q, xpA);
-        if (LB > 0) load_state<D>(Xc, a.x0, km - 1, q, xpB);
-        auto fold_step = [&](long long k, double* xp, double* P, double* c) {
-            double x[D], r[D], jv[JN];
-            load_state<D>(Xc, a.x0, k, q, x);
-            sys.eval(xp, x, r, jv);
-#pragma unroll
-            for (int j = 0; j < JN; ++j) scr[k * W + j] = jv[j];
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                scr[k * W + JN + j] = r[j];
-                const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
-                my_res = b > my_res ? b : my_res;
-            }
-            if (k == 0) {  // a_0 = (0, -r_0), eq. 3.4
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) P[j] = 0.0;
-#pragma unroll
-                for (int j = 0; j < D; ++j) c[j] = -r[j];
-            } else {
-                double tP[D * D], tc[D];
-                sys.jmul(jv, P, tP);
-                sys.jvec_sub(jv, c, r, tc);
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) P[j] = tP[j];
-#pragma unroll
-                for (int j = 0; j < D; ++j) c[j] = tc[j];
-            }
-#pragma unroll
-            for (int j = 0; j < D; ++j) xp[j] = x[j];
-        };
-        for (long long i = 0; i < LA; ++i) {
-            fold_step(k0 + i, xpA, PA, cA);
-            if (i < LB) fold_step(km + i, xpB, PB, cB);
-        }
-        double P[D * D], c[D];
-        compose<D>(PB, cB, PA, cA, P, c);
-        if (kreg < k1) {
-            double xf[D], rf[D], jvf[JN], EP[D * D], Ec[D], RP[D * D], Rc[D];
-            load_state<D>(Xc, a.x0, q - 1, q, xf);
-            sys.eval(xf, xf, rf, jvf);
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                const unsigned long long b = (unsigned long long)__double_as_longlong(rf[j]) & kAbsMask;
-                my_res = b > my_res ? b : my_res;
-                Ec[j] = -rf[j];
-                Rc[j] = 0.0;
-            }
-            sys.jfull(jvf, EP);
-            mat_identity<D>(RP);
-            for (long long e = k1 - kreg;;) {
-                if (e & 1) compose<D>(EP, Ec, RP, Rc, RP, Rc);
-                e >>= 1;
-                if (!e) break;
-                compose<D>(EP, Ec, EP, Ec, EP, Ec);
-            }
-            compose<D>(RP, Rc, P, c, P, c);
-        }
-        double eP[D * D], ec[D];
-        block_scan<D>(P, c, eP, ec, s_wex, s_tot);
-        if (threadIdx.x < E) a.agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_res, off);
-            my_res = o > my_res ? o : my_res;
-        }
-        if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
-
-        // ---- decision --------------------------------------------------------
-        const unsigned long long rb = __ldcg(a.res_bits + it);
-        const double res = __longlong_as_double((long long)rb);
-        final_res = res;
-        if (rb >= kInfBits) { status = PITN_NONFINITE; break; }
-        if (res <= a.tol) { status = PITN_OK; break; }
-        if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
-
-        // ---- incoming prefix of this CTA: fixed-order scan of the aggregates ----
-        {
-            const unsigned m = (G + blockDim.x - 1) / blockDim.x;   // aggregates per thread
-            double gP[D * D], gc[D];
-            mat_identity<D>(gP);
-#pragma unroll
-            for (int j = 0; j < D; ++j) gc[j] = 0.0;
-            for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
-                double sP[D * D], sc[D];
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(a.agg + (size_t)i * E + j);
-#pragma unroll
-                for (int j = 0; j < D; ++j) sc[j] = __ldcg(a.agg + (size_t)i * E + D * D + j);
-                compose<D>(sP, sc, gP, gc, gP, gc);
-            }
-            double xP[D * D], xc[D];
-            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot);
-            // CTA b needs the prefix through aggregate b-1, held by thread (b-1)/m:
-            // its exclusive prefix (warp part, then lane part) applied to the zero
-            // vector -- every prefix from aggregate 0 has matrix 0 -- then the
-            // aggregates it owns up to b-1, in order.
-            if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
-                double v[D], t[D], zero[D];
-#pragma unroll
-                for (int j = 0; j < D; ++j) zero[j] = 0.0;
-                apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
-                apply<D>(xP, xc, t, v);
-                for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
-                    double sP[D * D], sc[D];
-#pragma unroll
-                    for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(a.agg + (size_t)i * E + j);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(a.agg + (size_t)i * E + D * D + j);
-                    apply<D>(sP, sc, v, t);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) v[j] = t[j];
-                }
-#pragma unroll
-                for (int j = 0; j < D; ++j) s_zin[j] = v[j];
-            }
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-#pragma unroll
-                for (int j = 0; j < D; ++j) s_zin[j] = 0.0;
-            }
-            __syncthreads();
-        }
-
-        // ---- phase 3: replay + update ------------------------------------------
-        // A thread stops at its first cut index: every later state of its
-        // chunk lies beyond the iteration's cut and is never read again.
-        unsigned long long my_q = 0ull;
-        {
-            double zw[D], zA[D], zB[D];
-            apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
-            apply<D>(eP, ec, zw, zA);
-            apply<D>(PA, cA, zA, zB);  // state entering half B
-            bool foundA = false, foundB = false;
-            long long firstA = 0, firstB = 0;
-            auto replay_step = [&](long long k, double* z) -> bool {
-                double jv[JN], r[D], x[D];
-#pragma unroll
-                for (int j = 0; j < JN; ++j) jv[j] = __ldcg(scr + k * W + j);
-#pragma unroll
-                for (int j = 0; j < D; ++j) r[j] = __ldcg(scr + k * W + JN + j);
-                load_state<D>(Xc, a.x0, k, q, x);
-                if (k == 0) {
-#pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = -r[j];
-                } else {
-                    double tz[D];
-                    sys.jvec_sub(jv, z, r, tz);
-#pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = tz[j];
-                }
-                unsigned long long zb = 0ull;
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    Xn[k * D + j] = x[j] + z[j];
-                    const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
-                    zb = b > zb ? b : zb;
-                }
-                return zb > a.cap_bits;
-            };
-            for (long long i = 0; i < LA && !foundA; ++i) {
-                if (replay_step(k0 + i, zA)) { foundA = true; firstA = k0 + i; }
-                if (i < LB && !foundB && replay_step(km + i, zB)) { foundB = true; firstB = km + i; }
-            }
-            bool found = foundA || foundB;
-            if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
-            double z[D];
-#pragma unroll
-            for (int j = 0; j < D; ++j) z[j] = (LB > 0) ? zB[j] : zA[j];
-            if (!found && kreg < k1) {
-                double xf[D], rf[D], jvf[JN];
-                load_state<D>(Xc, a.x0, q - 1, q, xf);
-                sys.eval(xf, xf, rf, jvf);
-                for (long long k = kreg; k < k1; ++k) {
-                    double tz[D];
-                    sys.jvec_sub(jvf, z, rf, tz);
-                    unsigned long long zb = 0ull;
-#pragma unroll
-                    for (int j = 0; j < D; ++j) {
-                        z[j] = tz[j];
-                        Xn[k * D + j] = xf[j] + z[j];
-                        const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
-                        zb = b > zb ? b : zb;
-                    }
-                    if (zb > a.cap_bits) {
-                        my_q = ~(unsigned long long)k;
-                        break;
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
-            my_q = o > my_q ? o : my_q;
-        }
-        if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
-        const unsigned long long qe = __ldcg(a.qenc + it);
-        const long long cut = qe ? (long long)(~qe) : N;
-        if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }
-        cur ^= 1;
-        q = a.guarded ? cut : N;
-        last_cut = cut;
-        ++it;
-    }
-
-    // ---- write the final iterate (with its fill) to the destination ---------
-    const double* Xc = cur ? a.X1 : a.X0;
-    const bool same = (Xc == a.out);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k = gt; k < N; k += stride) {
-        if (same && k < q) continue;
-        double v[D];
-        load_state<D>(Xc, a.x0, k, q, v);
-#pragma unroll
-        for (int j = 0; j < D; ++j) a.out[k * D + j] = v[j];
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.rec->iters = it;
-        a.rec->status = status;
-        a.rec->final_res = final_res;
-        a.rec->guard_index = last_cut;
-    }
-}
-
-}  // namespace pitn
-
-#include "newton_small_mixed.cuh"
-
-namespace pitn {
-
-template <class Sys, bool MIXED = false>
-static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
-    void* args[] = {(void*)&a};
-    auto tok = pitn_host::timed_begin("newton_small", st);
-    const void* kern;
-    if constexpr (MIXED) kern = (const void*)newton_small_mixed_kernel<Sys>;
-    else kern = (const void*)newton_small_kernel<Sys>;
-    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
-    pitn_host::timed_end(tok, st);
-    pitn_host::count_launch(1);
-    return e;
-}
-
-template <class Sys, bool MIXED = false>
-static int max_blocks_per_sm(int block) {
-    int per_sm = 0;
-    cudaError_t e;
-    if constexpr (MIXED) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_mixed_kernel<Sys>, block, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Sys>, block, 0);
-    if (e != cudaSuccess) return 0;
-    return per_sm;
-}
-
-}  // namespace pitn
 
 namespace pitn_host {
 
@@ -562,6 +47,39 @@ void small_default_config(int d, long long N, int* block, int* C) {
     *C = (int)cmin;
 }
 
+// The kernel instantiation for a system, step map and precision.  Explicit
+// maps are instantiated here; the implicit (backward Euler) ones and the
+// stiff test systems live in newton_implicit.cu.
+int select_small_kernel(int system_id, int method, bool mixed, pitn::SmallKernel* K) {
+    using namespace pitn;
+    if (mixed) {
+        if (method != PITN_STEP_EULER) return PITN_EUNSUPPORTED;
+        switch (system_id) {
+        case PITN_LORENZ63: *K = small_kernel_of<Lorenz63, true>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<VanDerPol, true>(); return PITN_OK;
+        case PITN_LINEAR_OSC: *K = small_kernel_of<LinearOsc, true>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (method == PITN_STEP_RK4) {
+        switch (system_id) {
+        case PITN_VDP: *K = small_kernel_of<RK4Map<VdpRhs>>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<RK4Map<LogisticRhs>>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (method == PITN_STEP_EULER) {
+        switch (system_id) {
+        case PITN_LORENZ63: *K = small_kernel_of<Lorenz63>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<VanDerPol>(); return PITN_OK;
+        case PITN_LINEAR_OSC: *K = small_kernel_of<LinearOsc>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<EulerMap<LogisticRhs>>(); return PITN_OK;
+        default: break;
+        }
+    }
+    return select_implicit_kernel(system_id, method, K);
+}
+
 // One solve with an explicit launch shape: `block` threads per CTA and at
 // most `per_sm_cap` co-resident CTAs per SM (cooperative launch).
 int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
@@ -570,35 +88,11 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     using namespace pitn;
     int cmin = 4;
     if (o.tile_elems > 0) cmin = o.tile_elems;
-    const bool rk4 = o.method == PITN_STEP_RK4;
-    const bool mixed = o.precision == PITN_PREC_MIXED_FP32;
-    int per_sm = 0;
-    int W = 0;
-    if (mixed) {
-        // FP32 scratch: W floats per step fit in the W-double slots
-        switch (system_id) {
-        case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63, true>(block); W = Lorenz63::JN + 3; break;
-        case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol, true>(block); W = VanDerPol::JN + 2; break;
-        case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc, true>(block); W = LinearOsc::JN + 2; break;
-        default: return PITN_EUNSUPPORTED;
-        }
-    } else if (rk4 && system_id == PITN_VDP) {
-        per_sm = max_blocks_per_sm<RK4Map<VdpRhs>>(block);
-        W = RK4Map<VdpRhs>::JN + 2;
-    } else if (rk4 && system_id == PITN_LOGISTIC) {
-        per_sm = max_blocks_per_sm<RK4Map<LogisticRhs>>(block);
-        W = RK4Map<LogisticRhs>::JN + 1;
-    } else if (rk4) {
-        return PITN_EUNSUPPORTED;
-    } else {
-        switch (system_id) {
-        case PITN_LORENZ63: per_sm = max_blocks_per_sm<Lorenz63>(block); W = Lorenz63::JN + 3; break;
-        case PITN_VDP: per_sm = max_blocks_per_sm<VanDerPol>(block); W = VanDerPol::JN + 2; break;
-        case PITN_LINEAR_OSC: per_sm = max_blocks_per_sm<LinearOsc>(block); W = LinearOsc::JN + 2; break;
-        case PITN_LOGISTIC: per_sm = max_blocks_per_sm<EulerMap<LogisticRhs>>(block); W = 2; break;
-        default: return PITN_EINVAL;
-        }
-    }
+    pitn::SmallKernel K{};
+    int rc = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
+    if (rc != PITN_OK) return rc;
+    int per_sm = K.per_sm(block);
+    const int W = K.W;
     if (per_sm < 1) return PITN_EUNSUPPORTED;  // shape does not fit on an SM
     per_sm = std::min(per_sm, per_sm_cap);
     const long long max_grid = (long long)per_sm * props().multiProcessorCount;
@@ -649,23 +143,7 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     a.rec = (SolveRecord*)(ctrl + off_rec);
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
-    cudaError_t e;
-    if (mixed) {
-        switch (system_id) {
-        case PITN_LORENZ63: e = launch_small<Lorenz63, true>(a, grid, block, st); break;
-        case PITN_VDP: e = launch_small<VanDerPol, true>(a, grid, block, st); break;
-        default: e = launch_small<LinearOsc, true>(a, grid, block, st); break;
-        }
-    } else if (rk4 && system_id == PITN_VDP) e = launch_small<RK4Map<VdpRhs>>(a, grid, block, st);
-    else if (rk4) e = launch_small<RK4Map<LogisticRhs>>(a, grid, block, st);
-    else {
-        switch (system_id) {
-        case PITN_LORENZ63: e = launch_small<Lorenz63>(a, grid, block, st); break;
-        case PITN_VDP: e = launch_small<VanDerPol>(a, grid, block, st); break;
-        case PITN_LOGISTIC: e = launch_small<EulerMap<LogisticRhs>>(a, grid, block, st); break;
-        default: e = launch_small<LinearOsc>(a, grid, block, st); break;
-        }
-    }
+    cudaError_t e = K.launch(a, grid, block, st);
     if (e != cudaSuccess) { cudaGetLastError(); return PITN_ECUDA; }
     int* h_err = (int*)hbuf;
     SolveRecord* h_rec = (SolveRecord*)(hbuf + 16);
@@ -702,15 +180,31 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
     const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
     char key[96];
     std::snprintf(key, sizeof(key), "small:%d:%d:%d:%d%s%s", system_id, d, tune_bucket(N), guarded ? 1 : 0,
-                  o.method == PITN_STEP_RK4 ? ":rk4" : "", o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : "");
+                  o.method == PITN_STEP_RK4 ? ":rk4"
+                  : o.method == PITN_STEP_BACKWARD_EULER ? ":be"
+                  : o.method == PITN_STEP_TRAPEZOID ? ":tr" : "",
+                  o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : "");
     int tb = 0, tc = 0;
     if (tune_lookup(key, &tb, &tc)) {
         block = tb;
         cap = tc;
-    } else if (tune_enabled() && !io.have_guess) {
-        // time every shape on this very solve; the cost per Newton pass decides
+    } else if (tune_enabled()) {
+        // time every shape on this very solve; the cost per Newton pass decides.
+        // A caller's guess lives in the trajectory buffer, which every trial
+        // overwrites: keep a copy and put it back before each trial and the
+        // final solve.
+        const size_t gbytes = (size_t)N * d * sizeof(double);
+        double* saved = nullptr;
+        if (io.have_guess) {
+            saved = (double*)workspace(gbytes, kSlotAux2);
+            if (!saved) return PITN_ENOMEM;
+            if (cudaMemcpyAsync(saved, io.traj_dev, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return PITN_ECUDA;
+        }
         double best = 1e300;
         for (const auto& shp : kSmallShapes) {
+            if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return PITN_ECUDA;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
@@ -732,6 +226,8 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
             }
         }
         tune_store(key, block, cap);
+        if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return PITN_ECUDA;
     }
     return small_launch(system_id, io, h, N, d, tol, max_iter, o, st, out, block, cap);
 }

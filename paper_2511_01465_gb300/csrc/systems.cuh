@@ -372,4 +372,121 @@ struct EulerMap : RK4Map<Rhs> {
     }
 };
 
+
+// Dahlquist test equation (Sec. 4.2): f = lambda y.
+struct DahlquistRhs {
+    static constexpr int D = 1, P = 1;
+    double lam;
+    __host__ __device__ void init(const double* p) { lam = p[0]; }
+    __device__ __forceinline__ void f(const double* x, double* o) const { o[0] = lam * x[0]; }
+    __device__ __forceinline__ void jf(const double*, double* J) const { J[0] = lam; }
+};
+
+// Robertson's stiff chemical kinetics (Sec. 4.2), rates {k1, k2, k3}:
+//   f = (-k1 y1 + k3 y2 y3,  k1 y1 - k2 y2^2 - k3 y2 y3,  k2 y2^2).
+struct RobertsonRhs {
+    static constexpr int D = 3, P = 3;
+    double k1, k2, k3;
+    __host__ __device__ void init(const double* p) { k1 = p[0]; k2 = p[1]; k3 = p[2]; }
+    __device__ __forceinline__ void f(const double* x, double* o) const {
+        const double a = k1 * x[0], b = k3 * x[1] * x[2], c = k2 * x[1] * x[1];
+        o[0] = b - a;
+        o[1] = a - c - b;
+        o[2] = c;
+    }
+    __device__ __forceinline__ void jf(const double* x, double* J) const {
+        J[0] = -k1;  J[1] = k3 * x[2];                       J[2] = k3 * x[1];
+        J[3] = k1;   J[4] = -2.0 * k2 * x[1] - k3 * x[2];    J[5] = -k3 * x[1];
+        J[6] = 0.0;  J[7] = 2.0 * k2 * x[1];                 J[8] = 0.0;
+    }
+};
+
+// Inverse of a D x D matrix (D <= 3, row-major) by the adjugate over the
+// determinant: the diagonal blocks I - dg/dx_n of the implicit Newton
+// Jacobian are small and, for a step size the rule is used with, well
+// conditioned.  A zero determinant gives non-finite entries, which the
+// solver's non-finite checks report.
+template <int D>
+__device__ __forceinline__ void small_inverse(const double* A, double* R) {
+    static_assert(D >= 1 && D <= 3, "closed-form inverse for D <= 3");
+    if constexpr (D == 1) {
+        R[0] = 1.0 / A[0];
+    } else if constexpr (D == 2) {
+        const double inv = 1.0 / (A[0] * A[3] - A[1] * A[2]);
+        R[0] = A[3] * inv;
+        R[1] = -A[1] * inv;
+        R[2] = -A[2] * inv;
+        R[3] = A[0] * inv;
+    } else {
+        const double c00 = A[4] * A[8] - A[5] * A[7];
+        const double c01 = A[5] * A[6] - A[3] * A[8];
+        const double c02 = A[3] * A[7] - A[4] * A[6];
+        const double inv = 1.0 / (A[0] * c00 + A[1] * c01 + A[2] * c02);
+        R[0] = c00 * inv;
+        R[1] = (A[2] * A[7] - A[1] * A[8]) * inv;
+        R[2] = (A[1] * A[5] - A[2] * A[4]) * inv;
+        R[3] = c01 * inv;
+        R[4] = (A[0] * A[8] - A[2] * A[6]) * inv;
+        R[5] = (A[2] * A[3] - A[0] * A[5]) * inv;
+        R[6] = c02 * inv;
+        R[7] = (A[1] * A[6] - A[0] * A[7]) * inv;
+        R[8] = (A[0] * A[4] - A[1] * A[3]) * inv;
+    }
+}
+
+// Backward Euler (eq. 2.5), x_n = x_{n-1} + h f(x_n), i.e. g = h f(x_n) in
+// eq. 3.14.  Its Newton Jacobian (eq. 3.16) has diagonal blocks
+// M_n = I - h Jf(x_n) and sub-diagonal blocks -I, so the Newton step
+// (eqs. 3.17-3.19) is the affine recursion
+//   dx_n = M_n^{-1} dx_{n-1} - M_n^{-1} h_n,   h_n = x_n - x_{n-1} - h f(x_n),
+// with element (M_n^{-1}, -M_n^{-1} h_n).  eval returns r = M_n^{-1} h_n, the
+// preconditioned residual (the solver's stopping quantity for this rule,
+// whose iteration-0 value from a zero guess is the paper's 1/(1 - h lambda)
+// for the Dahlquist test), and the dense M_n^{-1} as the compact Jacobian;
+// unlike the explicit maps both depend on x_n as well as x_{n-1}.
+template <class Rhs>
+struct BackwardEulerMap : RK4Map<Rhs> {
+    static constexpr int D = Rhs::D, JN = D * D, P = Rhs::P;
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
+        double fx[D], M[D * D], hn[D];
+        this->rhs.f(xc, fx);
+        this->rhs.jf(xc, M);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) M[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) - this->h * M[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) hn[i] = xc[i] - xp[i] - this->h * fx[i];
+        small_inverse<D>(M, jv);
+        this->jvec(jv, hn, res);
+    }
+};
+
+
+// Trapezoidal rule (Sec. 3.4): g = (h/2) (f(x_{n-1}) + f(x_n)).  Now both
+// blocks of eq. 3.16 are state dependent: M_n = I - (h/2) Jf(x_n) and the
+// sub-diagonal -(I + (h/2) Jf(x_{n-1})), so the scan element of step n is
+// (M_n^{-1} (I + (h/2) Jf(x_{n-1})), -M_n^{-1} h_n) (eq. 3.19).
+template <class Rhs>
+struct TrapezoidMap : RK4Map<Rhs> {
+    static constexpr int D = Rhs::D, JN = D * D, P = Rhs::P;
+    __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
+        double fp[D], fc[D], Jp[D * D], M[D * D], Mi[D * D], hn[D];
+        const double w = 0.5 * this->h;
+        this->rhs.f(xp, fp);
+        this->rhs.f(xc, fc);
+        this->rhs.jf(xc, M);
+        this->rhs.jf(xp, Jp);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) {
+            const double e = (i % (D + 1) == 0) ? 1.0 : 0.0;
+            M[i] = e - w * M[i];
+            Jp[i] = e + w * Jp[i];
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) hn[i] = xc[i] - xp[i] - w * (fp[i] + fc[i]);
+        small_inverse<D>(M, Mi);
+        this->jmul(Mi, Jp, jv);
+        this->jvec(Mi, hn, res);
+    }
+};
+
 }  // namespace pitn

@@ -23,8 +23,9 @@ PITN_OK, PITN_NOT_CONVERGED, PITN_NONFINITE = 0, 1, 2
 PITN_EINVAL, PITN_ENOMEM, PITN_ECUDA, PITN_ETIMEOUT, PITN_EUNSUPPORTED = -1, -2, -3, -4, -5
 # systems
 PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP, PITN_LOGISTIC = 1, 2, 3, 4, 5
+PITN_DAHLQUIST, PITN_ROBERTSON = 6, 7
 # one-step maps
-PITN_STEP_EULER, PITN_STEP_RK4 = 0, 1
+PITN_STEP_EULER, PITN_STEP_RK4, PITN_STEP_BACKWARD_EULER, PITN_STEP_TRAPEZOID = 0, 1, 2, 3
 # precisions
 PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32 = 0, 1, 2
 

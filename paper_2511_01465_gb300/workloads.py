@@ -5,7 +5,7 @@ it contains none of the solver's arithmetic and imports nothing else from the
 package, so the CUDA path, the tests and the CPU oracle can all draw the same
 inputs from it.
 
-Workloads (all explicit-Euler, FP64):
+Workloads (explicit Euler unless stated, FP64):
   * Lorenz-63, sigma=10, rho=28, beta=8/3, x0=(1,1,1), h=1e-3, N=8192;
   * Van der Pol, mu=1, x0=(2,0), h=1e-4, N=2^22;
   * damped linear oscillator x''+2 zeta omega x'+omega^2 x=0, omega=1,
@@ -16,7 +16,10 @@ Workloads (all explicit-Euler, FP64):
     arrays in the order sigma~U[8,12], rho~U[20,35], beta~U[2,3],
     x0~N(0, 5^2 I) (B x 3), N_i~integers in [n_min, n_max] inclusive;
   * adjoint Van der Pol batch: default_rng(seed), mu~U[0.5,2] (B),
-    x0~U[-2,2]^2 (B x 2), h=1e-3, N=2^14.
+    x0~U[-2,2]^2 (B x 2), h=1e-3, N=2^14;
+  * backward Euler (Sec. 4.2): Dahlquist lambda=-1, y0=1 on [0, 4];
+    Robertson k=(0.04, 3e7, 1e4), y0=(1,0,0) on [0, 500]; N = t_end / h,
+    Newton guess = zeros (the paper's).
 """
 from __future__ import annotations
 
@@ -27,6 +30,7 @@ import numpy as np
 
 # system identifiers shared by the C ABI and the binding
 LORENZ63, VDP, LINEAR_OSC, FKPP = 1, 2, 3, 4
+DAHLQUIST, ROBERTSON = 6, 7
 
 
 @dataclass
@@ -102,3 +106,12 @@ def vdp_adjoint_batch(B: int = 256, seed: int = 0, N: int = 1 << 14, h: float = 
     x0 = rng.uniform(-2.0, 2.0, (B, 2))
     return Batch("van_der_pol_adjoint", VDP, np.ascontiguousarray(mu[:, None]), np.ascontiguousarray(x0),
                  np.full(B, h), np.full(B, N, dtype=np.int64))
+
+
+def dahlquist(h: float = 1e-1, lam: float = -1.0, t_end: float = 4.0) -> Single:
+    return Single("dahlquist", DAHLQUIST, np.array([lam]), np.array([1.0]), h, int(round(t_end / h)))
+
+
+def robertson(h: float = 1e-1, t_end: float = 500.0) -> Single:
+    return Single("robertson", ROBERTSON, np.array([0.04, 3e7, 1e4]), np.array([1.0, 0.0, 0.0]), h,
+                  int(round(t_end / h)))

@@ -47,6 +47,9 @@ def test_status_strings_and_params(lib):
     assert P.pitn_num_params(P.PITN_VDP) == 1
     assert P.pitn_num_params(P.PITN_LINEAR_OSC) == 2
     assert P.pitn_num_params(P.PITN_FKPP) == 1
+    assert P.pitn_num_params(P.PITN_LOGISTIC) == 2
+    assert P.pitn_num_params(P.PITN_DAHLQUIST) == 1
+    assert P.pitn_num_params(P.PITN_ROBERTSON) == 3
     assert P.pitn_num_params(99) == -1
     for code in (0, 1, 2, -1, -2, -3, -4, -5):
         assert P.pitn_status_string(code)
@@ -72,6 +75,16 @@ def test_argument_errors_are_detected_on_the_host(lib):
     opt = P.make_options(precision=P.PITN_PREC_MIXED_BF16)
     rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
     assert rc == E                                                                       # mixed needs d >= 64
+    for m in (4, -1):
+        opt = P.make_options(method=m)
+        rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+        assert rc == E                                                                   # unknown step map
+    opt = P.make_options(method=P.PITN_STEP_BACKWARD_EULER)
+    rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+    assert rc == P.PITN_EUNSUPPORTED                                                     # not instantiated
+    opt = P.make_options(method=P.PITN_STEP_BACKWARD_EULER, precision=P.PITN_PREC_MIXED_FP32)
+    rc, _ = P.pitn_solve_ex(P.PITN_ROBERTSON, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+    assert rc == E                                                                       # FP32 form: explicit only
     assert not out.any()  # nothing written on an argument error
 
 

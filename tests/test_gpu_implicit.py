@@ -1,0 +1,135 @@
+"""The implicit rules of Sec. 3.4 (backward Euler, eq. 2.5, and the
+trapezoidal rule) with the implicit Newton step on the GPU path: the paper's
+printed implicit residual traces and iteration counts (Sec. 4.2, backward
+Euler, zero guess) reproduced by the CUDA kernel, and element-wise parity with
+the oracle on the same seeded inputs for both rules."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2511_01465_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_implicit_traces.json")
+SYS = {"dahlquist": O.DAHLQUIST, "robertson": O.ROBERTSON}
+
+
+@pytest.fixture(scope="module")
+def pk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01465_gb300 as pk
+    return pk
+
+
+def _gold(key):
+    with open(GOLD) as f:
+        return json.load(f)[key]
+
+
+@pytest.mark.parametrize("key", ["dahlquist", "robertson"])
+def test_gpu_reproduces_paper_implicit_trace(pk, key):
+    g = _gold(key)
+    N, d = g["N"], len(g["x0"])
+    traj, info = pk.solve(SYS[key], g["params"], g["x0"], g["h"], N, 2e-14, 60,
+                          guess=np.zeros((N, d)), history=True, method=pk.PITN_STEP_BACKWARD_EULER)
+    paper = np.array(g["residuals"])
+    assert info["status"] == pk.PITN_OK
+    assert info["iters"] + 1 == g["K"] == len(paper)
+    for k, (a, b) in enumerate(zip(info["res_history"], paper)):
+        assert abs(a - b) <= 1e-8 * abs(b) + 1e-15, (k, a, b)
+
+
+@pytest.mark.parametrize("key,dt", [("dahlquist", 1e-4), ("robertson", 1e-2), ("robertson", 5e-3)])
+def test_gpu_paper_iteration_counts(pk, key, dt):
+    # Sec. 4.2 iteration-count figure: K independent of delta t
+    g = _gold(key)
+    wl = W.dahlquist(h=dt) if key == "dahlquist" else W.robertson(h=dt)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 2e-14, 60,
+                          guess=np.zeros((wl.N, wl.d)), method=pk.PITN_STEP_BACKWARD_EULER)
+    k_paper = {float(k): v for k, v in g["K_vs_dt"].items()}[dt]
+    assert info["status"] == pk.PITN_OK and info["iters"] + 1 == k_paper
+    # sampled states against the oracle's sequential backward Euler
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N, method=O.BACKWARD_EULER)
+    t = traj.cpu().numpy()
+    idx = np.unique(np.linspace(0, wl.N - 1, 257).astype(np.int64))
+    scale = np.abs(seq).max(axis=0)
+    assert (np.abs(t[idx] - seq[idx]) <= 1e-9 * scale + 1e-15).all()
+    if key == "robertson":
+        np.testing.assert_allclose(t.sum(axis=1), 1.0, atol=1e-12)   # y1 + y2 + y3 conserved
+
+
+CASES = [
+    # name, system, params, x0, h, N, guess (None = x0), guard B
+    ("dahlquist_ragged", O.DAHLQUIST, [-1.0], [1.0], 1e-2, 4001, 0.0, 0.0),
+    ("robertson_5000", O.ROBERTSON, [0.04, 3e7, 1e4], [1.0, 0.0, 0.0], 0.1, 5000, 0.0, 0.0),
+    ("robertson_ragged_x0", O.ROBERTSON, [0.04, 3e7, 1e4], [1.0, 0.0, 0.0], 0.05, 12347, None, 0.0),
+    ("robertson_1", O.ROBERTSON, [0.04, 3e7, 1e4], [1.0, 0.0, 0.0], 0.1, 1, 0.0, 0.0),
+    ("vdp_stiff", O.VDP, [10.0], [2.0, 0.0], 1e-2, 3001, None, 100.0),
+    ("vdp_plain", O.VDP, [1.0], [2.0, 0.0], 1e-2, 999, None, 0.0),
+    ("logistic", O.LOGISTIC, [1.0, 1.0], [0.1], 1e-2, 1000, 1.0, 0.0),
+]
+
+
+@pytest.mark.parametrize("rule", ["backward_euler", "trapezoid"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_implicit_against_oracle(pk, case, rule):
+    _, sys, p, x0, h, N, gv, B = case
+    d = len(x0)
+    guess = None if gv is None else np.full((N, d), gv)
+    m_gpu, m_or = ((pk.PITN_STEP_BACKWARD_EULER, O.BACKWARD_EULER) if rule == "backward_euler"
+                   else (pk.PITN_STEP_TRAPEZOID, O.TRAPEZOID))
+    traj, info = pk.solve(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, history=True,
+                          method=m_gpu)
+    o = O.newton(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, method=m_or)
+    assert o["status"] == O.OK
+    assert info["status"] == pk.PITN_OK
+    if B == 0.0:
+        # plain Newton: the same iterates up to rounding, so the same count and trace
+        assert info["iters"] == o["iters"]
+        np.testing.assert_allclose(info["res_history"][:-1], o["res_hist"][:-1], rtol=1e-6)
+    t = traj.cpu().numpy()
+    scale = np.abs(o["traj"]).max(axis=0)
+    assert (np.abs(t - o["traj"]) <= 1e-9 * scale + 1e-15).all()
+    # the returned trajectory satisfies the implicit residual test on its own
+    _, res, nf = O.residual(sys, p, x0, h, t, method=m_or)
+    assert not nf and res <= 1e-12 * (1 + 1e-6)
+
+
+def test_explicit_euler_on_stiff_systems(pk):
+    # the stiff test systems also run through the explicit map (eq. 2.2);
+    # plain Newton from the constant guess diverges on Robertson (the oracle
+    # ends NONFINITE too), so the guard is on
+    wl = W.robertson(h=1e-4, t_end=1.0)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 400, guard_B=1.0)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 400, guard_B=1.0)
+    assert info["status"] == o["status"] == O.OK
+    scale = np.abs(o["traj"]).max(axis=0)
+    assert (np.abs(traj.cpu().numpy() - o["traj"]) <= 1e-9 * scale + 1e-15).all()
+    wl = W.dahlquist(h=1e-3, lam=-3.0)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 5)
+    ref = (1.0 + wl.h * -3.0) ** np.arange(1, wl.N + 1)
+    assert info["iters"] == 1
+    np.testing.assert_allclose(traj.cpu().numpy()[:, 0], ref, rtol=1e-11)
+
+
+def test_trapezoid_dahlquist_closed_form(pk):
+    lam, h, N = -2.5, 0.03, 200
+    ref = ((1.0 + 0.5 * h * lam) / (1.0 - 0.5 * h * lam)) ** np.arange(1, N + 1)
+    traj, info = pk.solve(O.DAHLQUIST, [lam], [1.0], h, N, 1e-14, 5, guess=np.zeros((N, 1)),
+                          method=pk.PITN_STEP_TRAPEZOID)
+    assert info["status"] == pk.PITN_OK and info["iters"] == 1   # affine: one update
+    np.testing.assert_allclose(traj.cpu().numpy()[:, 0], ref, rtol=1e-12)
+
+
+def test_implicit_unsupported_combinations(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    with pytest.raises(P.PitnError):   # no backward Euler instantiation for Lorenz-63
+        pk.solve(1, [10, 28, 8 / 3], [1, 1, 1], 1e-3, 100, 1e-10, 5, method=pk.PITN_STEP_BACKWARD_EULER)
+    with pytest.raises(P.PitnError):   # the FP32 delta form is explicit-only
+        pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
+                 method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)

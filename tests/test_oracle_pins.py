@@ -382,3 +382,56 @@ def test_implicit_newton_step_equals_dense_solve(sys, p, d):
     dxi = -np.linalg.solve(H, hv)
     out = O.newton(sys, p, x0, h, N, 0.0, 1, guess=guess, guard_B=1e300, method=O.BACKWARD_EULER)
     np.testing.assert_allclose(out["traj"] - guess, dxi.reshape(N, d), rtol=1e-11, atol=1e-13)
+
+
+def test_trapezoid_dahlquist_closed_form_and_order():
+    # trapezoidal rule on y' = lambda y: y_n = ((1 + h lambda/2) / (1 - h lambda/2))^n,
+    # and its global error at t = 1 falls 4x when h halves (second order)
+    lam, h, N = -2.5, 0.03, 200
+    ref = ((1.0 + 0.5 * h * lam) / (1.0 - 0.5 * h * lam)) ** np.arange(1, N + 1)
+    seq = O.sequential(O.DAHLQUIST, [lam], [1.0], h, N, method=O.TRAPEZOID)[:, 0]
+    np.testing.assert_allclose(seq, ref, rtol=1e-12)
+    r = O.newton(O.DAHLQUIST, [lam], [1.0], h, N, 1e-14, 5, guess=np.zeros((N, 1)), method=O.TRAPEZOID)
+    assert r["status"] == O.OK and r["iters"] == 1
+    np.testing.assert_allclose(r["traj"][:, 0], ref, rtol=1e-12)
+    errs = []
+    for n in (50, 100, 200):
+        y = O.newton(O.DAHLQUIST, [lam], [1.0], 1.0 / n, n, 1e-14, 5, method=O.TRAPEZOID)["traj"][-1, 0]
+        errs.append(abs(y - math.exp(lam)))
+    assert 3.8 < errs[0] / errs[1] < 4.2 and 3.8 < errs[1] / errs[2] < 4.2
+
+
+def test_trapezoid_root_and_mass_conservation():
+    p, x0, h, N = [0.04, 3e7, 1e4], np.array([1.0, 0.0, 0.0]), 0.05, 400
+    r = O.newton(O.ROBERTSON, p, x0, h, N, 1e-14, 80, guess=np.zeros((N, 3)), method=O.TRAPEZOID)
+    assert r["status"] == O.OK
+    x = r["traj"]
+    prev = np.vstack([x0, x[:-1]])
+    resid = np.array([x[n] - prev[n] - 0.5 * h * (O.rhs(O.ROBERTSON, p, prev[n]) + O.rhs(O.ROBERTSON, p, x[n]))
+                      for n in range(N)])
+    assert np.abs(resid).max() < 1e-12
+    np.testing.assert_allclose(x.sum(axis=1), 1.0, atol=1e-13)
+    seq = O.sequential(O.ROBERTSON, p, x0, h, N, method=O.TRAPEZOID)
+    np.testing.assert_allclose(x, seq, rtol=1e-9, atol=1e-14)
+
+
+@pytest.mark.parametrize("sys,p,d", [(O.DAHLQUIST, [-3.0], 1), (O.ROBERTSON, [0.04, 3e2, 1e2], 3),
+                                     (O.VDP, [2.0], 2), (O.LOGISTIC, [1.0, 2.0], 1)])
+def test_trapezoid_newton_step_equals_dense_solve(sys, p, d):
+    # eq. (3.17) with H of eq. (3.16): diagonal I - (h/2) df/dx(x_n),
+    # sub-diagonal -(I + (h/2) df/dx(x_{n-1})), solved densely
+    N, h = 7, 0.05
+    rng = np.random.default_rng(12)
+    x0 = rng.uniform(0, 1, d)
+    guess = rng.uniform(0, 1, (N, d))
+    prev = np.vstack([x0, guess[:-1]])
+    hv = np.concatenate([guess[n] - prev[n] - 0.5 * h * (O.rhs(sys, p, prev[n]) + O.rhs(sys, p, guess[n]))
+                         for n in range(N)])
+    H = np.zeros((N * d, N * d))
+    for i in range(N):
+        H[i * d:(i + 1) * d, i * d:(i + 1) * d] = np.eye(d) - 0.5 * h * O.rhs_jac(sys, p, guess[i])
+        if i > 0:
+            H[i * d:(i + 1) * d, (i - 1) * d:i * d] = -np.eye(d) - 0.5 * h * O.rhs_jac(sys, p, guess[i - 1])
+    dxi = -np.linalg.solve(H, hv)
+    out = O.newton(sys, p, x0, h, N, 0.0, 1, guess=guess, guard_B=1e300, method=O.TRAPEZOID)
+    np.testing.assert_allclose(out["traj"] - guess, dxi.reshape(N, d), rtol=1e-11, atol=1e-13)
