@@ -258,12 +258,19 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
  * pass in a process-wide cache, and then returns the result computed with
  * it; later solves of that class use the cached shape.  With the environment
  * variable PITN_TUNE_CACHE naming a file, the cache is loaded from and saved
- * to that file.  A solve with a user guess never tunes.  Different shapes
- * associate the scan differently, so results may differ in the last bits.
- * pitn_tune_get reads one entry (key as above, e.g. "small:2:2:22:1"). */
+ * to that file.  A user guess is saved and put back around the trials.
+ * Different shapes associate the scan differently, so results may differ in
+ * the last bits.  Keys: "small:<system>:<d>:<floor log2 N>:<guarded 0/1>"
+ * plus ":rk4", ":be" or ":tr" for the RK4, backward Euler and trapezoidal
+ * maps and ":f32" for PITN_PREC_MIXED_FP32 (e.g. "small:2:2:22:1"), and
+ * "batch:<system>:<d>:<floor log2 B>:<guarded>".
+ * pitn_tune_get reads one entry; pitn_tune_set pins one (a, b > 0; a shape
+ * that does not fit the device makes the solve return PITN_EUNSUPPORTED),
+ * so that a deployment can fix its launch shapes without tuning. */
 int pitn_tune_enable(int on);
 int pitn_tune_clear(void);
 int pitn_tune_get(const char* key, int* a, int* b);
+int pitn_tune_set(const char* key, int a, int b);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel launch of the
  * library is bracketed by CUDA events on its stream; pitn_timing_get returns

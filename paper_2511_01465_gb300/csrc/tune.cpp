@@ -8,6 +8,7 @@
 // processes start tuned.
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
@@ -100,6 +101,12 @@ int pitn_tune_clear(void) {
 int pitn_tune_get(const char* key, int* a, int* b) {
     if (!key || !a || !b) return PITN_EINVAL;
     return pitn_host::tune_lookup(key, a, b) ? PITN_OK : PITN_EINVAL;
+}
+
+int pitn_tune_set(const char* key, int a, int b) {
+    if (!key || !key[0] || a <= 0 || b <= 0 || std::strlen(key) >= 128) return PITN_EINVAL;
+    pitn_host::tune_store(key, a, b);
+    return PITN_OK;
 }
 
 }  // extern "C"

@@ -89,6 +89,8 @@ def lib():
         L.pitn_tune_clear.restype = c_int
         L.pitn_tune_get.argtypes = [ctypes.c_char_p, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
         L.pitn_tune_get.restype = c_int
+        L.pitn_tune_set.argtypes = [ctypes.c_char_p, c_int, c_int]
+        L.pitn_tune_set.restype = c_int
         L.pitn_timing_enable.argtypes = [c_int]
         L.pitn_timing_enable.restype = c_int
         L.pitn_timing_reset.argtypes = []
@@ -216,6 +218,10 @@ def pitn_tune_enable(on=True):
 
 def pitn_tune_clear():
     return lib().pitn_tune_clear()
+
+
+def pitn_tune_set(key, a, b):
+    return lib().pitn_tune_set(key.encode(), int(a), int(b))
 
 
 def pitn_tune_get(key):

@@ -91,7 +91,8 @@ def test_implicit_against_oracle(pk, case, rule):
     if B == 0.0:
         # plain Newton: the same iterates up to rounding, so the same count and trace
         assert info["iters"] == o["iters"]
-        np.testing.assert_allclose(info["res_history"][:-1], o["res_hist"][:-1], rtol=1e-6)
+        # (relative 1e-6 down to the FP64 floor of states of size 1)
+        np.testing.assert_allclose(info["res_history"][:-1], o["res_hist"][:-1], rtol=1e-6, atol=1e-15)
     t = traj.cpu().numpy()
     scale = np.abs(o["traj"]).max(axis=0)
     assert (np.abs(t - o["traj"]) <= 1e-9 * scale + 1e-15).all()
@@ -114,7 +115,9 @@ def test_explicit_euler_on_stiff_systems(pk):
     traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 5)
     ref = (1.0 + wl.h * -3.0) ** np.arange(1, wl.N + 1)
     assert info["iters"] == 1
-    np.testing.assert_allclose(traj.cpu().numpy()[:, 0], ref, rtol=1e-11)
+    # one update from the constant guess 1 adds corrections of size ~1, so the
+    # error is absolute (a few ulps of 1): the global relative measure applies
+    assert np.abs(traj.cpu().numpy()[:, 0] - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
 def test_trapezoid_dahlquist_closed_form(pk):
