@@ -170,7 +170,9 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
 }
 
 // Launch shapes the autotuner tries (threads per CTA, CTAs per SM).
-static const int kSmallShapes[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
+// (Shapes beyond a kernel's occupancy are capped by it; repeats are skipped.)
+static const int kSmallShapes[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {128, 6}, {128, 8},
+                                      {256, 1}, {256, 2}, {256, 3}, {256, 4}};
 
 int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
                      int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out) {
@@ -201,8 +203,21 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
             if (cudaMemcpyAsync(saved, io.traj_dev, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return PITN_ECUDA;
         }
+        pitn::SmallKernel K{};
+        int rk = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
+        if (rk != PITN_OK) return rk;
         double best = 1e300;
+        int tried[sizeof(kSmallShapes) / sizeof(kSmallShapes[0])][2];
+        int ntried = 0;
         for (const auto& shp : kSmallShapes) {
+            const int eff = std::min(K.per_sm(shp[0]), shp[1]);  // CTAs per SM this shape gets
+            if (eff < 1) continue;
+            bool seen = false;
+            for (int i = 0; i < ntried; ++i) seen |= tried[i][0] == shp[0] && tried[i][1] == eff;
+            if (seen) continue;
+            tried[ntried][0] = shp[0];
+            tried[ntried][1] = eff;
+            ++ntried;
             if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
                 return PITN_ECUDA;
             cudaEvent_t e0, e1;

@@ -11,6 +11,11 @@
 //   (I + S) v + c = v + S v + c,   head element a_0 = (S = -I, c = -r_0).
 // The Newton step therefore carries FP32 rounding; the outer iteration
 // converges to the FP64 tolerance because every residual is exact FP64.
+// FP64 <-> FP32 conversions of per-step values (the residual into the scan,
+// the correction into the update, the states feeding the FP32 Jacobian) use
+// the integer-pipe routines of fpconv.cuh: a hardware conversion issues on
+// the FP64 pipe, the resource this kernel is bound by.  Per step the FP64
+// pipe then sees only the residual and the update.
 #pragma once
 
 namespace pitn {
@@ -217,18 +222,28 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
         double xpA[D], xpB[D];
         dz_zero<D>(QA, cA);
         dz_zero<D>(QB, cB);
-        if (LA > 0) load_state<D>(Xc, a.x0, k0 - 1, q, xpA);
-        if (LB > 0) load_state<D>(Xc, a.x0, km - 1, q, xpB);
-        auto fold_step = [&](long long k, double* xp, float* Q, float* c) {
+        // x of each half's next step is loaded one step ahead
+        double xnA[D], xnB[D];
+        if (LA > 0) {
+            load_state<D>(Xc, a.x0, k0 - 1, q, xpA);
+            load_state<D>(Xc, a.x0, k0, q, xnA);
+        }
+        if (LB > 0) {
+            load_state<D>(Xc, a.x0, km - 1, q, xpB);
+            load_state<D>(Xc, a.x0, km, q, xnB);
+        }
+        auto fold_step = [&](long long k, bool more, double* xp, double* xn, float* Q, float* c) {
             double x[D], r[D];
             float sv[JN], rf[D];
-            load_state<D>(Xc, a.x0, k, q, x);
+#pragma unroll
+            for (int j = 0; j < D; ++j) x[j] = xn[j];
+            if (more) load_state<D>(Xc, a.x0, k + 1, q, xn);
             sys.eval_mixed(xp, x, r, sv);
 #pragma unroll
             for (int j = 0; j < JN; ++j) scr[k * W + j] = sv[j];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                rf[j] = (float)r[j];
+                rf[j] = d2f_int(r[j]);
                 scr[k * W + JN + j] = rf[j];
                 const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
                 my_res = b > my_res ? b : my_res;
@@ -247,8 +262,8 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             for (int j = 0; j < D; ++j) xp[j] = x[j];
         };
         for (long long i = 0; i < LA; ++i) {
-            fold_step(k0 + i, xpA, QA, cA);
-            if (i < LB) fold_step(km + i, xpB, QB, cB);
+            fold_step(k0 + i, i + 1 < LA, xpA, xnA, QA, cA);
+            if (i < LB) fold_step(km + i, i + 1 < LB, xpB, xnB, QB, cB);
         }
         float Q[D * D], c[D];
         dz_compose<D>(QB, cB, QA, cA, Q, c);
@@ -341,14 +356,27 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             dz_apply<D>(QA, cA, zA, zB);
             bool foundA = false, foundB = false;
             long long firstA = 0, firstB = 0;
-            auto replay_step = [&](long long k, float* z) -> bool {
+            // each half's next (S entries, r, x) is loaded one step ahead
+            float fsA[W], fsB[W];
+            double fxA[D], fxB[D];
+            auto fetch = [&](long long k, float* fs, double* fx) {
+#pragma unroll
+                for (int j = 0; j < W; ++j) fs[j] = __ldcg(scr + k * W + j);
+                load_state<D>(Xc, a.x0, k, q, fx);
+            };
+            if (LA > 0) fetch(k0, fsA, fxA);
+            if (LB > 0) fetch(km, fsB, fxB);
+            auto replay_step = [&](long long k, bool more, float* fs, double* fx, float* z) -> bool {
                 float sv[JN], rf[D], S[D * D];
                 double x[D];
 #pragma unroll
-                for (int j = 0; j < JN; ++j) sv[j] = __ldcg(scr + k * W + j);
+                for (int j = 0; j < JN; ++j) sv[j] = fs[j];
 #pragma unroll
-                for (int j = 0; j < D; ++j) rf[j] = __ldcg(scr + k * W + JN + j);
-                load_state<D>(Xc, a.x0, k, q, x);
+                for (int j = 0; j < D; ++j) {
+                    rf[j] = fs[JN + j];
+                    x[j] = fx[j];
+                }
+                if (more) fetch(k + 1, fs, fx);
                 if (k == 0) {
 #pragma unroll
                     for (int j = 0; j < D; ++j) z[j] = -rf[j];
@@ -368,14 +396,17 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
                 bool bad = false;
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    Xn[k * D + j] = x[j] + (double)z[j];
+                    Xn[k * D + j] = x[j] + f2d_int(z[j]);
                     bad |= !(fabsf(z[j]) <= capf);
                 }
                 return bad;
             };
             for (long long i = 0; i < LA && !foundA; ++i) {
-                if (replay_step(k0 + i, zA)) { foundA = true; firstA = k0 + i; }
-                if (i < LB && !foundB && replay_step(km + i, zB)) { foundB = true; firstB = km + i; }
+                if (replay_step(k0 + i, i + 1 < LA, fsA, fxA, zA)) { foundA = true; firstA = k0 + i; }
+                if (i < LB && !foundB && replay_step(km + i, i + 1 < LB, fsB, fxB, zB)) {
+                    foundB = true;
+                    firstB = km + i;
+                }
             }
             const bool found = foundA || foundB;
             if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
@@ -403,7 +434,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
                         z[j] = t[j];
-                        Xn[k * D + j] = xf[j] + (double)z[j];
+                        Xn[k * D + j] = xf[j] + f2d_int(z[j]);
                         bad |= !(fabsf(z[j]) <= capf);
                     }
                     if (bad) {

@@ -12,11 +12,15 @@
 //   vjp_param(xp, v, g):  g += (dphi/dp(xp))^T v  (adjoint, g has P entries)
 //   jac(xp, jv):          the compact Jacobian alone
 //   eval_mixed(xp, xc, r, sv), sfull(sv, S): FP64 residual with the compact
-//                         Jacobian in FP32 delta form S = J - I (mixed scan)
+//                         Jacobian in FP32 delta form S = J - I (mixed scan),
+//                         the latter computed in FP32 from the states rounded
+//                         on the integer pipes (no FP64-pipe work for it)
 //   jfull(jv, J):         the dense D x D Jacobian from its compact form
 // The compact form stores only the state-dependent entries of J, so an
 // element of the scan costs D + JN registers instead of D + D*D.
 #pragma once
+
+#include "fpconv.cuh"
 
 namespace pitn {
 
@@ -26,9 +30,11 @@ struct Lorenz63 {
     static constexpr int D = 3, JN = 3, P = 3;
     double s, r, b, h;
     double j00, j01, j11, j22;
+    float hs_f, h_f, hb_f, r_f;
     __host__ __device__ void init(const double* p, double hh) {
         s = p[0]; r = p[1]; b = p[2]; h = hh;
         j00 = 1.0 - h * s; j01 = h * s; j11 = 1.0 - h; j22 = 1.0 - h * b;
+        hs_f = (float)(h * s); h_f = (float)h; hb_f = (float)(h * b); r_f = (float)r;
     }
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
                                          double* jv) const {
@@ -74,16 +80,21 @@ struct Lorenz63 {
     // mixed precision: FP64 residual, FP32 delta form S = J - I
     __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res,
                                                float* sv) const {
-        double jv[3];
-        eval(xp, xc, res, jv);
-        sv[0] = (float)jv[0];
-        sv[1] = (float)jv[1];
-        sv[2] = (float)jv[2];
+        const double f0 = s * (xp[1] - xp[0]);
+        const double f1 = xp[0] * (r - xp[2]) - xp[1];
+        const double f2 = xp[0] * xp[1] - b * xp[2];
+        res[0] = xc[0] - (xp[0] + h * f0);
+        res[1] = xc[1] - (xp[1] + h * f1);
+        res[2] = xc[2] - (xp[2] + h * f2);
+        const float xf = d2f_int(xp[0]), yf = d2f_int(xp[1]), zf = d2f_int(xp[2]);
+        sv[0] = h_f * (r_f - zf);
+        sv[1] = h_f * xf;
+        sv[2] = h_f * yf;
     }
     __device__ __forceinline__ void sfull(const float* sv, float* S) const {
-        S[0] = (float)(-h * s); S[1] = (float)(h * s); S[2] = 0.f;
-        S[3] = sv[0];           S[4] = (float)(-h);    S[5] = -sv[1];
-        S[6] = sv[2];           S[7] = sv[1];          S[8] = (float)(-h * b);
+        S[0] = -hs_f; S[1] = hs_f;  S[2] = 0.f;
+        S[3] = sv[0]; S[4] = -h_f;  S[5] = -sv[1];
+        S[6] = sv[2]; S[7] = sv[1]; S[8] = -hb_f;
     }
     __device__ __forceinline__ void jfull(const double* jv, double* J) const {
         J[0] = j00;   J[1] = j01;   J[2] = 0.0;
@@ -107,8 +118,10 @@ struct Lorenz63 {
 struct VanDerPol {
     static constexpr int D = 2, JN = 2, P = 1;
     double mu, h, hmu, m2hmu;
+    float h_f, hmu_f, m2hmu_f;
     __host__ __device__ void init(const double* p, double hh) {
         mu = p[0]; h = hh; hmu = h * mu; m2hmu = -2.0 * h * mu;
+        h_f = (float)h; hmu_f = (float)hmu; m2hmu_f = (float)m2hmu;
     }
     // r = xc - x - h f(x) written as r0 = (xc0 - x) - h v,
     // r1 = (xc1 - v) - (h mu w) v + h x with w = 1 - x^2; 10 FP64 operations
@@ -137,11 +150,12 @@ struct VanDerPol {
         const double t = hmu * w;
         res[0] = fma(-h, v, xc[0] - x);
         res[1] = fma(h, x, fma(-t, v, xc[1] - v));
-        sv[0] = (float)fma(m2hmu * x, v, -h);
-        sv[1] = (float)t;
+        const float xf = d2f_int(x), vf = d2f_int(v);
+        sv[0] = fmaf(m2hmu_f * xf, vf, -h_f);
+        sv[1] = hmu_f * fmaf(-xf, xf, 1.f);
     }
     __device__ __forceinline__ void sfull(const float* sv, float* S) const {
-        S[0] = 0.f; S[1] = (float)h;
+        S[0] = 0.f; S[1] = h_f;
         S[2] = sv[0]; S[3] = sv[1];
     }
     __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
@@ -179,9 +193,11 @@ struct VanDerPol {
 struct LinearOsc {
     static constexpr int D = 2, JN = 1, P = 2;  // JN = 1 keeps arrays non-empty
     double w, z, h, j10, j11;
+    float h_f, j10_f, s11_f;
     __host__ __device__ void init(const double* p, double hh) {
         w = p[0]; z = p[1]; h = hh;
         j10 = -h * w * w; j11 = 1.0 - 2.0 * h * z * w;
+        h_f = (float)h; j10_f = (float)j10; s11_f = (float)(-2.0 * h * z * w);
     }
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
                                          double* jv) const {
@@ -215,8 +231,8 @@ struct LinearOsc {
         sv[0] = 0.f;
     }
     __device__ __forceinline__ void sfull(const float*, float* S) const {
-        S[0] = 0.f; S[1] = (float)h;
-        S[2] = (float)j10; S[3] = (float)(-2.0 * h * z * w);
+        S[0] = 0.f; S[1] = h_f;
+        S[2] = j10_f; S[3] = s11_f;
     }
     __device__ __forceinline__ void jtvec(const double*, const double* v, double* o) const {
         double v0 = v[0], v1 = v[1];

@@ -4,7 +4,9 @@
     ncu --set full --clock-control none -k regex:newton_small -s 1 -c 1 \\
         python -m paper_2511_01465_gb300.profile_workload --workload vdp --N 1048576 --max-iter 10
 
-Workloads: vdp, lorenz, osc (single IVP), fkpp, fkpp_mixed (d = 128),
+Workloads: vdp, lorenz, osc (single IVP; --precision 2 for the FP32 delta
+scan), robertson (backward Euler from the zero guess, h = 500 / N), fkpp,
+fkpp_mixed (d = 128),
 batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]), adjoint
 (Van der Pol batch forward + backward).  Sizes default to the small cases
 used for full captures; prints the outcome of the last repetition.
@@ -27,18 +29,24 @@ def main():
     ap.add_argument("--B", type=int, default=512)
     ap.add_argument("--nmin", type=int, default=1 << 10)
     ap.add_argument("--nmax", type=int, default=1 << 13)
+    ap.add_argument("--precision", type=int, default=0)
     a = ap.parse_args()
 
     import torch
 
     from . import api, workloads as W
-    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16
+    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_STEP_BACKWARD_EULER
 
     out = None
     for _ in range(a.repeat):
         if a.workload in ("vdp", "lorenz", "osc"):
             wl = {"vdp": W.vdp, "lorenz": W.lorenz, "osc": W.damped_oscillator}[a.workload](N=a.N)
-            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, guard_B=a.guard)[1]
+            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, guard_B=a.guard,
+                            precision=a.precision)[1]
+        elif a.workload == "robertson":
+            wl = W.robertson(h=500.0 / a.N)
+            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter,
+                            guess=np.zeros((wl.N, wl.d)), method=PITN_STEP_BACKWARD_EULER)[1]
         elif a.workload in ("fkpp", "fkpp_mixed"):
             wl = W.fkpp(N=a.N)
             prec = PITN_PREC_MIXED_BF16 if a.workload == "fkpp_mixed" else PITN_PREC_FP64
