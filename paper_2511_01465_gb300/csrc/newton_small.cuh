@@ -93,7 +93,12 @@ __device__ __forceinline__ void apply(const double* P, const double* c, const do
     for (int i = 0; i < D; ++i) o[i] = t[i];
 }
 
-// x_k of the current iterate with the guard's lazy fill (L2-coherent loads).
+// x_k of the current iterate with the guard's lazy fill.  L1-cacheable
+// loads (ld.global.ca, never the non-coherent read-only path: the buffers
+// alternate roles between iterations): every state read in a phase was
+// written before the grid barrier that opens it, and the barrier's gpu-scope
+// acquire orders the loads after those writes; a thread's consecutive steps
+// then share L1 sectors instead of each going to L2.
 template <int D>
 __device__ __forceinline__ void load_state(const double* __restrict__ X, const double* __restrict__ x0,
                                            long long k, long long q, double* o) {
@@ -103,7 +108,7 @@ __device__ __forceinline__ void load_state(const double* __restrict__ X, const d
     else if (q > 0) src = X + (q - 1) * D;
     else src = x0;
 #pragma unroll
-    for (int i = 0; i < D; ++i) o[i] = ldcg(src + i);
+    for (int i = 0; i < D; ++i) o[i] = __ldca(src + i);
 }
 
 constexpr int kMaxWarps = 8;  // BLOCK <= 256
@@ -402,9 +407,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             auto replay_step = [&](long long k, double* z) -> bool {
                 double jv[JN], r[D], x[D];
 #pragma unroll
-                for (int j = 0; j < JN; ++j) jv[j] = __ldcg(scr + k * W + j);
+                for (int j = 0; j < JN; ++j) jv[j] = scr[k * W + j];   // this thread's phase-1 writes
 #pragma unroll
-                for (int j = 0; j < D; ++j) r[j] = __ldcg(scr + k * W + JN + j);
+                for (int j = 0; j < D; ++j) r[j] = scr[k * W + JN + j];
                 load_state<D>(Xc, a.x0, k, q, x);
                 if (k == 0) {
 #pragma unroll

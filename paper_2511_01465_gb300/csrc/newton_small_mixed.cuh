@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             double fxA[D], fxB[D];
             auto fetch = [&](long long k, float* fs, double* fx) {
 #pragma unroll
-                for (int j = 0; j < W; ++j) fs[j] = __ldcg(scr + k * W + j);
+                for (int j = 0; j < W; ++j) fs[j] = scr[k * W + j];   // this thread's phase-1 writes
                 load_state<D>(Xc, a.x0, k, q, fx);
             };
             if (LA > 0) fetch(k0, fsA, fxA);
