@@ -270,6 +270,34 @@ def run_ours_batch(args, rank, world, local_rank, spec):
         dt1 = time.perf_counter() - t0
         single = {"value": solved1 / dt1, "unit": UNIT,
                   "sample": f"first {n_s} IVPs, one pitn_solve_ex call each ({dt1 * 1e3:.1f} ms)"}
+    # ---- end to end through the C ABI with pinned host buffers ----
+    pin = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt).pin_memory()
+    hp, hx, hh, hN = (pin(bt.params).numpy(), pin(bt.x0).numpy(), pin(bt.h).numpy(),
+                      pin(bt.N, torch.int64).numpy())
+    htraj = torch.empty((M, d), dtype=torch.float64).pin_memory().numpy()
+    hoffs = torch.empty(bt.B + 1, dtype=torch.int64).pin_memory().numpy()
+    hit = torch.empty(bt.B, dtype=torch.int32).pin_memory().numpy()
+    hst = torch.empty(bt.B, dtype=torch.int32).pin_memory().numpy()
+    hres = torch.empty(bt.B, dtype=torch.float64).pin_memory().numpy()
+
+    def solve_host():
+        P.check(P.pitn_solve_batch(bt.system, bt.B, hp, hx, hh, hN, d, spec["tol"], spec["max_iter"],
+                                   htraj, hoffs, hit, hst, hres, opt), "pitn_solve_batch")
+
+    solve_host()
+    et = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        solve_host()
+        et.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(et)
+    ok_h = (hst == P.PITN_OK) & (hres <= spec["tol"])
+    solved_e, e2e_max = D.aggregate(int(bt.N[ok_h].sum()), e2e_s)
+    e2e = {"value": solved_e / e2e_max, "unit": UNIT,
+           "h2d_bytes_per_step": int(hp.nbytes + hx.nbytes + hh.nbytes + hN.nbytes),
+           "d2h_bytes_per_step": int(htraj.nbytes + hoffs.nbytes + hit.nbytes + hst.nbytes + hres.nbytes),
+           "ms_per_step": e2e_max * 1e3}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -282,7 +310,7 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                        "step_ms": [round(x, 3) for x in times],
                        "l2": "inputs (>3 GB per trajectory buffer) larger than L2",
                        "parallelism": f"IVP shards x{world}"},
-            "roofline": roofline, "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
     return line
 
 
@@ -320,6 +348,14 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
     P.pitn_timing_reset()
     P.pitn_timing_enable(True)
     launches0 = pk.pitn_launch_count()
@@ -335,6 +371,45 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
         times.append(e0.elapsed_time(e1))
     launches = pk.pitn_launch_count() - launches0
     P.pitn_timing_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+
+    # ---- end to end through the C ABI with pinned host buffers: forward solve,
+    # loss gradient on the host, adjoint ----
+    pin = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt).pin_memory()
+    hp, hx, hh, hN = (pin(bt.params).numpy(), pin(bt.x0).numpy(), pin(bt.h).numpy(),
+                      pin(bt.N, torch.int64).numpy())
+    htraj = torch.empty((M, d), dtype=torch.float64).pin_memory().numpy()
+    hoffs = torch.empty(bt.B + 1, dtype=torch.int64).pin_memory().numpy()
+    hit = torch.empty(bt.B, dtype=torch.int32).pin_memory().numpy()
+    hst = torch.empty(bt.B, dtype=torch.int32).pin_memory().numpy()
+    hres = torch.empty(bt.B, dtype=torch.float64).pin_memory().numpy()
+    hgN = torch.empty((bt.B, d), dtype=torch.float64).pin_memory().numpy()
+    hgx0 = torch.empty((bt.B, d), dtype=torch.float64).pin_memory().numpy()
+    hgp = torch.empty((bt.B, bt.params.shape[1]), dtype=torch.float64).pin_memory().numpy()
+
+    def step_host():
+        P.check(P.pitn_solve_batch(bt.system, bt.B, hp, hx, hh, hN, d, spec["tol"], spec["max_iter"],
+                                   htraj, hoffs, hit, hst, hres, opt), "pitn_solve_batch")
+        hgN[:] = 2.0 * (htraj[hoffs[1:] - 1] - np.array([1.0, 0.0]))
+        P.check(P.pitn_backward(bt.system, bt.B, hp, hx, hh, hN, d, htraj, None, hgN, 1024, hgx0, hgp, opt),
+                "pitn_backward")
+
+    step_host()
+    et = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        step_host()
+        et.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(et)
+    e2e = {"value": float(bt.N[hst == P.PITN_OK].sum()) / e2e_s * world, "unit": UNIT,
+           "h2d_bytes_per_step": int(2 * (hp.nbytes + hx.nbytes + hh.nbytes + hN.nbytes) + htraj.nbytes
+                                     + hgN.nbytes),
+           "d2h_bytes_per_step": int(htraj.nbytes + hoffs.nbytes + hit.nbytes + hst.nbytes + hres.nbytes
+                                     + hgx0.nbytes + hgp.nbytes),
+           "ms_per_step": e2e_s * 1e3}
     fwd_ms, fwd_n = P.pitn_timing_get("batch")
     adj_ms, adj_n = P.pitn_timing_get("adjoint")
     ms_per_step = float(sum(times)) / args.steps
@@ -357,7 +432,7 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
                        "forward_ms_per_step": fwd_ms / args.steps,
                        "adjoint_ms_per_step": adj_ms / args.steps,
                        "step_ms": [round(x, 3) for x in times], "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "e2e": None, "gpu_launches": int(launches), "clocks": None}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
 
 
 def run_ours(args, rank, world, local_rank):

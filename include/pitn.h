@@ -227,7 +227,7 @@ int64_t pitn_launch_count(void);
  * control loop whose time budget cannot absorb cudaMalloc's implicit device
  * synchronisation, or a host application whose own allocator has reserved
  * the device memory.  This entry point allocates nothing.  Its scratch is one
- * fixed file-scope __device__ array (about 4.8 MB, held on every GPU that
+ * fixed file-scope __device__ array (about 8 MB, held on every GPU that
  * loads the library until the process exits), sized for at most
  * PITN_NOALLOC_MAX_STEPS steps and PITN_NOALLOC_MAX_ITER Newton updates;
  * larger requests return PITN_EINVAL.

@@ -100,9 +100,13 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     const int grid = (int)std::max(1LL, std::min(max_grid, want));
     const long long chunk = (N + (long long)grid * block - 1) / ((long long)grid * block);
     const int E = d * d + d;
+    // a thread's regular steps per iteration are at most ceil(N / threads) (the
+    // weighted partition gives a regular step a quarter of a thread's share)
+    const long long nthr = (long long)grid * block;
+    const long long lcap = (N + nthr - 1) / nthr + 1;
 
     double* X1 = (double*)workspace((size_t)N * d * sizeof(double), kSlotX1);
-    double* scratch = (double*)workspace((size_t)N * W * sizeof(double), kSlotAux);
+    double* scratch = (double*)workspace((size_t)lcap * nthr * W * sizeof(double), kSlotAux);
     // control block: agg | res_bits | qenc | bar | err | record
     size_t off_agg = 0;
     size_t off_res = off_agg + (size_t)grid * E * sizeof(double);
@@ -123,6 +127,7 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     a.X1 = X1;
     a.out = io.traj_dev;
     a.scratch = scratch;
+    a.lcap = lcap;
     a.agg = (double*)(ctrl + off_agg);
     a.N = N;
     a.chunk = chunk;
@@ -267,8 +272,9 @@ constexpr long long kNaMaxSteps = 1LL << 16;  // N limit
 constexpr int kNaMaxIter = 1024;              // max_iter limit
 constexpr int kNaMaxCtas = 1024;              // CTA aggregates
 constexpr size_t kNaX1 = 0;                                            // [N][3]
-constexpr size_t kNaScratch = kNaX1 + (size_t)kNaMaxSteps * 3;         // [N][6]
-constexpr size_t kNaAgg = kNaScratch + (size_t)kNaMaxSteps * 6;        // [CTAs][12]
+constexpr size_t kNaScratch = kNaX1 + (size_t)kNaMaxSteps * 3;         // [6][lcap][threads]
+constexpr size_t kNaScratchDoubles = (size_t)kNaMaxSteps * 6 * 2;      // >= 6 (N + 2 threads)
+constexpr size_t kNaAgg = kNaScratch + kNaScratchDoubles;               // [CTAs][12]
 constexpr size_t kNaRes = kNaAgg + (size_t)kNaMaxCtas * 12;            // [iter+1] bits
 constexpr size_t kNaQ = kNaRes + (size_t)(kNaMaxIter + 1);             // [iter+1] bits
 constexpr size_t kNaCtl = kNaQ + (size_t)(kNaMaxIter + 1);             // bar, err, record, x0
@@ -361,6 +367,11 @@ extern "C" int pitn_solve_noalloc(int system_id, const double* params, const dou
     a.X1 = base + kNaX1;
     a.out = traj_out;
     a.scratch = base + kNaScratch;
+    {
+        const long long nthr = (long long)grid * block;
+        a.lcap = (N + nthr - 1) / nthr + 1;
+        if ((size_t)(a.lcap * nthr * 6) > kNaScratchDoubles) return PITN_EINVAL;  // cannot happen: N/cmin + block threads
+    }
     a.agg = base + kNaAgg;
     a.N = N;
     a.chunk = chunk;

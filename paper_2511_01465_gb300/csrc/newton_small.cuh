@@ -27,7 +27,10 @@ struct SmallArgs {
     double* X0;         // trajectory buffer 0 [N][D]
     double* X1;         // trajectory buffer 1 [N][D]
     double* out;        // destination of the final iterate
-    double* scratch;    // [N][JN + D]: compact Jacobian and residual of every step
+    double* scratch;    // [JN + D][lcap][threads]: compact Jacobian and residual of every
+                        // regular step, component-major and interleaved over the threads so
+                        // that a warp's accesses to step i of its chunks are coalesced
+    long long lcap;     // upper bound on a thread's regular steps per iteration
     double* agg;        // [gridDim][D*D + D]: CTA aggregates
     long long N;
     long long chunk;    // consecutive steps per thread
@@ -259,6 +262,8 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             k1 = min(N, k1);
         }
         const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
+        // scratch slot of component j of this thread's i-th regular element
+        auto sidx = [&](long long i, int j) -> long long { return ((long long)j * a.lcap + i) * nthreads + gt; };
         // The regular part is folded as two interleaved halves A = [k0, km) and
         // B = [km, kreg): two independent FP64 dependency chains per thread.
         unsigned long long my_res = 0ull;
@@ -276,10 +281,10 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             load_state<D>(Xc, a.x0, k, q, x);
             sys.eval(xp, x, r, jv);
 #pragma unroll
-            for (int j = 0; j < JN; ++j) scr[k * W + j] = jv[j];
+            for (int j = 0; j < JN; ++j) scr[sidx(k - k0, j)] = jv[j];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                scr[k * W + JN + j] = r[j];
+                scr[sidx(k - k0, JN + j)] = r[j];
                 const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
                 my_res = b > my_res ? b : my_res;
             }
@@ -407,9 +412,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             auto replay_step = [&](long long k, double* z) -> bool {
                 double jv[JN], r[D], x[D];
 #pragma unroll
-                for (int j = 0; j < JN; ++j) jv[j] = scr[k * W + j];   // this thread's phase-1 writes
+                for (int j = 0; j < JN; ++j) jv[j] = scr[sidx(k - k0, j)];   // this thread's phase-1 writes
 #pragma unroll
-                for (int j = 0; j < D; ++j) r[j] = scr[k * W + JN + j];
+                for (int j = 0; j < D; ++j) r[j] = scr[sidx(k - k0, JN + j)];
                 load_state<D>(Xc, a.x0, k, q, x);
                 if (k == 0) {
 #pragma unroll

@@ -214,6 +214,9 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             k1 = min(N, k1);
         }
         const long long kreg = min(k1, max(k0, sfill));
+        // scratch slot of component j of this thread's i-th regular element
+        // (component-major, interleaved over the threads: coalesced)
+        auto sidx = [&](long long i, int j) -> long long { return ((long long)j * a.lcap + i) * nthreads + gt; };
         // ---- phase 1: FP64 residual, FP32 delta fold (two interleaved halves) ----
         unsigned long long my_res = 0ull;
         const long long Lr = kreg - k0;
@@ -240,11 +243,11 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             if (more) load_state<D>(Xc, a.x0, k + 1, q, xn);
             sys.eval_mixed(xp, x, r, sv);
 #pragma unroll
-            for (int j = 0; j < JN; ++j) scr[k * W + j] = sv[j];
+            for (int j = 0; j < JN; ++j) scr[sidx(k - k0, j)] = sv[j];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 rf[j] = d2f_int(r[j]);
-                scr[k * W + JN + j] = rf[j];
+                scr[sidx(k - k0, JN + j)] = rf[j];
                 const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
                 my_res = b > my_res ? b : my_res;
             }
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             double fxA[D], fxB[D];
             auto fetch = [&](long long k, float* fs, double* fx) {
 #pragma unroll
-                for (int j = 0; j < W; ++j) fs[j] = scr[k * W + j];   // this thread's phase-1 writes
+                for (int j = 0; j < W; ++j) fs[j] = scr[sidx(k - k0, j)];   // this thread's phase-1 writes
                 load_state<D>(Xc, a.x0, k, q, fx);
             };
             if (LA > 0) fetch(k0, fsA, fxA);
