@@ -45,6 +45,8 @@ struct SmallArgs {
     unsigned* bar;                 // [2] grid barrier
     int* err;
     SolveRecord* rec;
+    int stage_rows;                // > 0: rows of the next iterate leave through shared-memory
+                                   // tiles and bulk copies (dynamic smem sized by stage_bytes)
 };
 
 constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
@@ -115,6 +117,69 @@ __device__ __forceinline__ void load_state(const double* __restrict__ X, const d
 }
 
 constexpr int kMaxWarps = 8;  // BLOCK <= 256
+
+// ---------------------------------------------------------------------------
+// Staged stores of the next iterate (rows of 2 doubles).  A thread's rows are
+// contiguous in the trajectory, but a warp's row-by-row stores land in 32
+// different lines; instead each thread collects kStageT consecutive rows in a
+// private shared-memory tile and sends the tile with one bulk copy (TMA, an
+// async-proxy write of one contiguous 16 B-aligned span).  Two tiles per
+// chain alternate, so a tile is refilled only after its copy has read it.
+// ---------------------------------------------------------------------------
+constexpr int kStageT = 4;                   // rows per tile
+constexpr int kStageSeg = kStageT * 2 + 2;   // doubles per tile slot (+16 B: bank spread)
+
+__host__ __device__ constexpr size_t stage_bytes(int block) {
+    return (size_t)2 * 2 * block * kStageSeg * sizeof(double);
+}
+
+__device__ __forceinline__ void bulk_store_rows(double* gdst, const double* ssrc, unsigned bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(ssrc);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 :: "l"(gdst), "r"(s), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+struct RowStage {
+    double* seg;      // this thread's first slot; slot (c, s) at seg + (c * 2 + s) * stride
+    int stride;       // doubles between slots (blockDim * kStageSeg)
+    int n[2], slot[2];
+    long long start[2];
+    __device__ __forceinline__ void init(double* smem) {
+        stride = blockDim.x * kStageSeg;
+        seg = smem + (size_t)threadIdx.x * kStageSeg;
+        n[0] = n[1] = 0;
+        slot[0] = slot[1] = 0;
+        start[0] = start[1] = 0;
+    }
+    __device__ __forceinline__ double* tile(int c) { return seg + (size_t)(c * 2 + slot[c]) * stride; }
+    __device__ __forceinline__ void flush(int c, double* X) {
+        if (n[c] == 0) return;
+        bulk_store_rows(X + start[c] * 2, tile(c), (unsigned)(n[c] * 16));
+        slot[c] ^= 1;
+        n[c] = 0;
+    }
+    // row k (2 doubles) of chain c; rows of one chain arrive in increasing order
+    __device__ __forceinline__ void put(int c, long long k, double v0, double v1, double* X) {
+        if (n[c] > 0 && k != start[c] + n[c]) flush(c, X);
+        if (n[c] == 0) {
+            // the slot's previous copy is at least two groups old
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            start[c] = k;
+        }
+        double2* t = reinterpret_cast<double2*>(tile(c)) + n[c];
+        *t = make_double2(v0, v1);
+        if (++n[c] == kStageT) flush(c, X);
+    }
+    // all tiles written to global memory and ordered before later generic accesses
+    __device__ __forceinline__ void finish(double* X) {
+        flush(0, X);
+        flush(1, X);
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+};
 
 // Inclusive Kogge-Stone scan of (P, c) across the warp (later lanes on the left).
 template <int D>
@@ -223,6 +288,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
     __shared__ double s_g[kMaxWarps][E];
     __shared__ double s_gtot[E];
     __shared__ double s_zin[D];
+    extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
 
     const int lane = threadIdx.x & 31;
     const long long N = a.N;
@@ -409,7 +475,18 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             apply<D>(PA, cA, zA, zB);  // state entering half B
             bool foundA = false, foundB = false;
             long long firstA = 0, firstB = 0;
-            auto replay_step = [&](long long k, double* z) -> bool {
+            const bool staged = (D == 2) && a.stage_rows > 0;
+            RowStage stg;
+            if (staged) stg.init(s_dyn);
+            // x_{k+1} = x + dx of chain c into the other buffer
+            auto put_row = [&](int c, long long k, const double* v) {
+                if constexpr (D == 2) {
+                    if (staged) { stg.put(c, k, v[0], v[1], Xn); return; }
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
+            };
+            auto replay_step = [&](int c, long long k, double* z) -> bool {
                 double jv[JN], r[D], x[D];
 #pragma unroll
                 for (int j = 0; j < JN; ++j) jv[j] = scr[sidx(k - k0, j)];   // this thread's phase-1 writes
@@ -426,17 +503,19 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     for (int j = 0; j < D; ++j) z[j] = tz[j];
                 }
                 unsigned long long zb = 0ull;
+                double xn[D];
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    Xn[k * D + j] = x[j] + z[j];
+                    xn[j] = x[j] + z[j];
                     const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
                     zb = b > zb ? b : zb;
                 }
+                put_row(c, k, xn);
                 return zb > a.cap_bits;
             };
             for (long long i = 0; i < LA && !foundA; ++i) {
-                if (replay_step(k0 + i, zA)) { foundA = true; firstA = k0 + i; }
-                if (i < LB && !foundB && replay_step(km + i, zB)) { foundB = true; firstB = km + i; }
+                if (replay_step(0, k0 + i, zA)) { foundA = true; firstA = k0 + i; }
+                if (i < LB && !foundB && replay_step(1, km + i, zB)) { foundB = true; firstB = km + i; }
             }
             bool found = foundA || foundB;
             if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
@@ -451,19 +530,22 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     double tz[D];
                     sys.jvec_sub(jvf, z, rf, tz);
                     unsigned long long zb = 0ull;
+                    double xn[D];
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
                         z[j] = tz[j];
-                        Xn[k * D + j] = xf[j] + z[j];
+                        xn[j] = xf[j] + z[j];
                         const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
                         zb = b > zb ? b : zb;
                     }
+                    put_row(1, k, xn);
                     if (zb > a.cap_bits) {
                         my_q = ~(unsigned long long)k;
                         break;
                     }
                 }
             }
+            if (staged) stg.finish(Xn);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -506,14 +588,30 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 
 namespace pitn {
 
+// Dynamic shared memory of a launch: the row-stage tiles for d = 2.
+template <class Sys>
+static size_t small_dyn_smem(int block) {
+    return Sys::D == 2 ? stage_bytes(block) : 0;
+}
+
+template <class Sys, bool MIXED>
+static const void* small_kernel_ptr() {
+    if constexpr (MIXED) return (const void*)newton_small_mixed_kernel<Sys>;
+    else return (const void*)newton_small_kernel<Sys>;
+}
+
 template <class Sys, bool MIXED = false>
 static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
+    const void* kern = small_kernel_ptr<Sys, MIXED>();
+    const size_t dyn = small_dyn_smem<Sys>(block);
+    if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+        return cudaErrorInvalidValue;
+    // bulk copies need 16 B-aligned rows in both trajectory buffers
+    const bool aligned = ((reinterpret_cast<uintptr_t>(a.X0) | reinterpret_cast<uintptr_t>(a.X1)) & 15) == 0;
+    a.stage_rows = (dyn > 0 && aligned) ? kStageT : 0;
     void* args[] = {(void*)&a};
     auto tok = pitn_host::timed_begin("newton_small", st);
-    const void* kern;
-    if constexpr (MIXED) kern = (const void*)newton_small_mixed_kernel<Sys>;
-    else kern = (const void*)newton_small_kernel<Sys>;
-    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st);
+    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, dyn, st);
     pitn_host::timed_end(tok, st);
     pitn_host::count_launch(1);
     return e;
@@ -521,11 +619,12 @@ static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t 
 
 template <class Sys, bool MIXED = false>
 static int max_blocks_per_sm(int block) {
+    const void* kern = small_kernel_ptr<Sys, MIXED>();
+    const size_t dyn = small_dyn_smem<Sys>(block);
+    if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+        return 0;
     int per_sm = 0;
-    cudaError_t e;
-    if constexpr (MIXED) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_mixed_kernel<Sys>, block, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Sys>, block, 0);
-    if (e != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, dyn) != cudaSuccess) return 0;
     return per_sm;
 }
 

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
     __shared__ float s_g[kMaxWarps][E];
     __shared__ float s_gtot[E];
     __shared__ float s_zin[D];
+    extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
 
     const int lane = threadIdx.x & 31;
     const long long N = a.N;
@@ -369,7 +370,17 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             };
             if (LA > 0) fetch(k0, fsA, fxA);
             if (LB > 0) fetch(km, fsB, fxB);
-            auto replay_step = [&](long long k, bool more, float* fs, double* fx, float* z) -> bool {
+            const bool staged = (D == 2) && a.stage_rows > 0;
+            RowStage stg;
+            if (staged) stg.init(s_dyn);
+            auto put_row = [&](int c, long long k, const double* v) {
+                if constexpr (D == 2) {
+                    if (staged) { stg.put(c, k, v[0], v[1], Xn); return; }
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
+            };
+            auto replay_step = [&](int c, long long k, bool more, float* fs, double* fx, float* z) -> bool {
                 float sv[JN], rf[D], S[D * D];
                 double x[D];
 #pragma unroll
@@ -397,16 +408,18 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
                     for (int j = 0; j < D; ++j) z[j] = t[j];
                 }
                 bool bad = false;
+                double xn[D];
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    Xn[k * D + j] = x[j] + f2d_int(z[j]);
+                    xn[j] = x[j] + f2d_int(z[j]);
                     bad |= !(fabsf(z[j]) <= capf);
                 }
+                put_row(c, k, xn);
                 return bad;
             };
             for (long long i = 0; i < LA && !foundA; ++i) {
-                if (replay_step(k0 + i, i + 1 < LA, fsA, fxA, zA)) { foundA = true; firstA = k0 + i; }
-                if (i < LB && !foundB && replay_step(km + i, i + 1 < LB, fsB, fxB, zB)) {
+                if (replay_step(0, k0 + i, i + 1 < LA, fsA, fxA, zA)) { foundA = true; firstA = k0 + i; }
+                if (i < LB && !foundB && replay_step(1, km + i, i + 1 < LB, fsB, fxB, zB)) {
                     foundB = true;
                     firstB = km + i;
                 }
@@ -434,18 +447,21 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
                         t[i] = s;
                     }
                     bool bad = false;
+                    double xn[D];
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
                         z[j] = t[j];
-                        Xn[k * D + j] = xf[j] + f2d_int(z[j]);
+                        xn[j] = xf[j] + f2d_int(z[j]);
                         bad |= !(fabsf(z[j]) <= capf);
                     }
+                    put_row(1, k, xn);
                     if (bad) {
                         my_q = ~(unsigned long long)k;
                         break;
                     }
                 }
             }
+            if (staged) stg.finish(Xn);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
