@@ -3,7 +3,8 @@
 // trapezoidal rule) and for the stiff test systems of Sec. 4.2 (Dahlquist,
 // Robertson).
 //
-// The kernel is the explicit one (newton_small.cuh): it only needs a map
+// The implicit maps run in the fused kernel (newton_fused.cuh; the explicit
+// Euler ones in the three-phase kernel): either only needs a map
 // whose eval(x_{n-1}, x_n) yields the scan element of step n; for backward
 // Euler that element is (M_n^{-1}, -M_n^{-1} h_n) with M_n = I - h Jf(x_n)
 // (eqs. 3.16-3.19), built by BackwardEulerMap in systems.cuh; TrapezoidMap
@@ -17,26 +18,26 @@ int select_implicit_kernel(int system_id, int method, pitn::SmallKernel* K) {
     using namespace pitn;
     if (method == PITN_STEP_BACKWARD_EULER) {
         switch (system_id) {
-        case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>>(); return PITN_OK;
-        case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>>(); return PITN_OK;
-        case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>>(); return PITN_OK;
-        case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>>(); return PITN_OK;
+        case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>, kVarFused>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>, kVarFused>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>, kVarFused>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>, kVarFused>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }
     }
     if (method == PITN_STEP_TRAPEZOID) {
         switch (system_id) {
-        case PITN_DAHLQUIST: *K = small_kernel_of<TrapezoidMap<DahlquistRhs>>(); return PITN_OK;
-        case PITN_ROBERTSON: *K = small_kernel_of<TrapezoidMap<RobertsonRhs>>(); return PITN_OK;
-        case PITN_VDP: *K = small_kernel_of<TrapezoidMap<VdpRhs>>(); return PITN_OK;
-        case PITN_LOGISTIC: *K = small_kernel_of<TrapezoidMap<LogisticRhs>>(); return PITN_OK;
+        case PITN_DAHLQUIST: *K = small_kernel_of<TrapezoidMap<DahlquistRhs>, kVarFused>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<TrapezoidMap<RobertsonRhs>, kVarFused>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<TrapezoidMap<VdpRhs>, kVarFused>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<TrapezoidMap<LogisticRhs>, kVarFused>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }
     }
     if (method == PITN_STEP_EULER) {
         switch (system_id) {
-        case PITN_DAHLQUIST: *K = small_kernel_of<EulerMap<DahlquistRhs>>(); return PITN_OK;
-        case PITN_ROBERTSON: *K = small_kernel_of<EulerMap<RobertsonRhs>>(); return PITN_OK;
+        case PITN_DAHLQUIST: *K = small_kernel_of<EulerMap<DahlquistRhs>, kVarPlain>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<EulerMap<RobertsonRhs>, kVarPlain>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }
     }

@@ -585,8 +585,13 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 }  // namespace pitn
 
 #include "newton_small_mixed.cuh"
+#include "newton_fused.cuh"
 
 namespace pitn {
+
+// Kernel variants behind a SmallKernel: the three-phase FP64 kernel, its
+// FP32 delta-form twin, and the fused FP64 kernel.
+enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2 };
 
 // Dynamic shared memory of a launch: the row-stage tiles for d = 2.
 template <class Sys>
@@ -594,15 +599,16 @@ static size_t small_dyn_smem(int block) {
     return Sys::D == 2 ? stage_bytes(block) : 0;
 }
 
-template <class Sys, bool MIXED>
+template <class Sys, int VAR>
 static const void* small_kernel_ptr() {
-    if constexpr (MIXED) return (const void*)newton_small_mixed_kernel<Sys>;
+    if constexpr (VAR == kVarMixed) return (const void*)newton_small_mixed_kernel<Sys>;
+    else if constexpr (VAR == kVarFused) return (const void*)newton_fused_kernel<Sys>;
     else return (const void*)newton_small_kernel<Sys>;
 }
 
-template <class Sys, bool MIXED = false>
+template <class Sys, int VAR = kVarPlain>
 static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
-    const void* kern = small_kernel_ptr<Sys, MIXED>();
+    const void* kern = small_kernel_ptr<Sys, VAR>();
     const size_t dyn = small_dyn_smem<Sys>(block);
     if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return cudaErrorInvalidValue;
@@ -617,9 +623,9 @@ static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t 
     return e;
 }
 
-template <class Sys, bool MIXED = false>
+template <class Sys, int VAR = kVarPlain>
 static int max_blocks_per_sm(int block) {
-    const void* kern = small_kernel_ptr<Sys, MIXED>();
+    const void* kern = small_kernel_ptr<Sys, VAR>();
     const size_t dyn = small_dyn_smem<Sys>(block);
     if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return 0;
@@ -637,9 +643,9 @@ struct SmallKernel {
     int W;
 };
 
-template <class Sys, bool MIXED = false>
+template <class Sys, int VAR = kVarPlain>
 static SmallKernel small_kernel_of() {
-    return SmallKernel{&launch_small<Sys, MIXED>, &max_blocks_per_sm<Sys, MIXED>, Sys::JN + Sys::D};
+    return SmallKernel{&launch_small<Sys, VAR>, &max_blocks_per_sm<Sys, VAR>, Sys::JN + Sys::D};
 }
 
 }  // namespace pitn

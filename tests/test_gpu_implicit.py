@@ -109,8 +109,10 @@ def test_explicit_euler_on_stiff_systems(pk):
     traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 400, guard_B=1.0)
     o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 400, guard_B=1.0)
     assert info["status"] == o["status"] == O.OK
-    scale = np.abs(o["traj"]).max(axis=0)
-    assert (np.abs(traj.cpu().numpy() - o["traj"]) <= 1e-9 * scale + 1e-15).all()
+    # both solves stop at ||h||_inf <= 1e-13 (absolute), so they agree to that
+    # level against the largest state (global measure, R10), not against y2's 1e-5 scale
+    t = traj.cpu().numpy()
+    assert np.abs(t - o["traj"]).max() <= 1e-10 * np.abs(o["traj"]).max()
     wl = W.dahlquist(h=1e-3, lam=-3.0)
     traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-13, 5)
     ref = (1.0 + wl.h * -3.0) ** np.arange(1, wl.N + 1)
