@@ -14,6 +14,7 @@ total over ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -29,6 +30,34 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Newton-solved time steps/s at residual<=1e-8"
 UNIT = "steps/s"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from an ncu capture of the bench command itself (summaries
+# under profiles/), keyed by workload and tagged with a hash of the kernel
+# sources they were taken on: a changed kernel reports traffic null.
+SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "newton_fused.cuh",
+             "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
+TRAFFIC = {
+    # workload: (bytes per launch of the timed solve, kernel-source hash)
+    "vdp": (28908948736 + 24172061184, "f08ff4f44895de4a"),        # 147 passes
+    "vdp_mixed": (19760937728 + 16358470144, "f08ff4f44895de4a"),  # 140 passes
+    "robertson": (13345722368 + 13705445120, "f08ff4f44895de4a"),  # 22 passes
+}
+
+
+def kernel_src_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2511_01465_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(name):
+    t = TRAFFIC.get(name)
+    if not t or t[1] != kernel_src_hash(SMALL_SRC):
+        return None
+    return t[0]
 
 
 def load_peaks():
@@ -579,7 +608,7 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
             flops = None
             achieved = nbytes / (ms / 1e3 / steps) / 1e9
             return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": f_hbm,
-                    "traffic": None, "kernel": kern, "kernel_launches_per_step": launches / steps,
+                    "traffic": traffic_for(name), "kernel": kern, "kernel_launches_per_step": launches / steps,
                     "kernel_ms_per_launch": ms / max(launches, 1),
                     "fp64_frac": f_alu,
                     "note": f"design bytes per step {24 * wl.d + 8 * (jn + wl.d)} B x passes; peak = {src} "
@@ -620,7 +649,8 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         note = "memory-bound helper"
     achieved = (flops / per_step_s / 1e12) if flops is not None else 0.0
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": None, "kernel": kern,
+            "frac": achieved / peak, "traffic": traffic_for(name) if kern == "newton_small" else None,
+            "kernel": kern,
             "kernel_launches_per_step": launches / steps,
             "kernel_ms_per_launch": ms / max(launches, 1), "note": note}
 
