@@ -4,13 +4,15 @@
 //   (I + S2, b2) o (I + S1, b1) = (I + S, b),
 //   S = S2 + S1 + S2 S1,   b = b2 + b1 + S2 b1                       (eq. 3.3)
 //
-// S2 S1 is one M = N = K = 128 product: BF16 operands staged in shared memory
-// in the canonical K-major core-matrix layout (8 rows x 16 bytes per core
-// matrix, no swizzle), eight tcgen05.mma (K = 16 each) issued by one thread
-// into a 128-lane x 128-column FP32 accumulator in TMEM, completion signalled
-// through an mbarrier, and read back with tcgen05.ld: TMEM lane m is row m of
-// the product, so thread m of the CTA owns row m in the epilogue, which adds
-// S2 + S1 in FP32 and stores column-major (coalesced across the warp).
+// Both FP32 inputs arrive in shared memory by bulk copies (TMA, completion
+// counted on an mbarrier); S2 S1 is then one M = N = K = 128 product: BF16
+// operands converted into the canonical K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix, no swizzle), eight tcgen05.mma (K = 16 each)
+// issued by one thread into a 128-lane x 128-column FP32 accumulator in TMEM,
+// completion signalled through a second mbarrier, and read back with
+// tcgen05.ld: TMEM lane m is row m of the product, so thread m of the CTA
+// owns row m in the epilogue, which adds S2 + S1 (FP32, from the staged
+// copies) and stores column-major (coalesced across the warp).
 // The vector part uses the same BF16 rows of S2 with FP32 accumulation.
 // Matrices are column-major FP32 (S[col][row]), 128 x 128.
 #pragma once
@@ -99,6 +101,16 @@ __device__ __forceinline__ void fence_after() {
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(smem_addr(mbar)), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared (16 B-aligned addresses, size a multiple of 16),
+// completion counted in bytes on the mbarrier
+__device__ __forceinline__ void bulk_load(void* sdst, const void* gsrc, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(sdst)), "l"(gsrc), "r"(bytes), "r"(smem_addr(mbar)) : "memory");
+}
 // 16 consecutive FP32 columns of this thread's TMEM lane
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
@@ -112,14 +124,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared memory of one compose: A and B tiles, the mbarrier and the TMEM address.
+// Shared memory of one compose: the FP32 inputs, the BF16 A and B tiles, the
+// mbarriers (loads, MMA) and the TMEM address.
 struct __align__(1024) ComposeSmem {
-    uint8_t A[kTileBytes];   // S2 (rows m, K-major)
-    uint8_t B[kTileBytes];   // S1 (rows n = columns of S1, K-major)
+    uint8_t A[kTileBytes];     // S2 (rows m, K-major)
+    uint8_t B[kTileBytes];     // S1 (rows n = columns of S1, K-major)
+    float S2f[kDim * kDim];    // S2 column-major, as loaded
+    float S1f[kDim * kDim];    // S1 column-major, as loaded
     float b1[kDim];
-    uint64_t mbar;
+    uint64_t mbar;             // MMA completion
+    uint64_t mbar_ld;          // bulk-load completion
     uint32_t tmem;
 };
+constexpr uint32_t kMatBytes = kDim * kDim * sizeof(float);
+constexpr uint32_t kLoadChunk = 16384;  // bytes per bulk copy
 
 // One compose by a CTA of 128 or 256 threads (with 256, two threads share a
 // row in the epilogue, each taking 64 columns).  Returns false if the MMA
@@ -129,13 +147,26 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
                                            const float* __restrict__ b1, float* __restrict__ So,
                                            float* __restrict__ bo, uint32_t phase) {
     const int tid = threadIdx.x, warp = tid >> 5;
+    // both inputs by bulk copies; b1 by plain loads meanwhile
+    if (tid == 0) {
+        mbar_expect_tx(&sm.mbar_ld, 2 * kMatBytes);
+        for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk) {
+            bulk_load(reinterpret_cast<uint8_t*>(sm.S2f) + o, reinterpret_cast<const uint8_t*>(S2) + o,
+                      kLoadChunk, &sm.mbar_ld);
+            bulk_load(reinterpret_cast<uint8_t*>(sm.S1f) + o, reinterpret_cast<const uint8_t*>(S1) + o,
+                      kLoadChunk, &sm.mbar_ld);
+        }
+    }
+    if (tid < kDim) sm.b1[tid] = b1[tid];
+    bool ok = mbar_wait(&sm.mbar_ld, phase);
+    if (!ok) (void)mbar_wait(&sm.mbar_ld, phase);  // give the copies a second bounded wait; still a failure
     // A(m, k) = S2[m][k] = S2 column-major [k][m]: thread gathers 8 consecutive
-    // k of one row m (coalesced across the warp) into one 16-byte core row
+    // k of one row m (conflict-free across the warp) into one 16-byte core row
     for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
         const int m = idx % kDim, kc = (idx / kDim) * 8;
         float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) v[j] = S2[(size_t)(kc + j) * kDim + m];
+        for (int j = 0; j < 8; ++j) v[j] = sm.S2f[(kc + j) * kDim + m];
         __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
         __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
         uint4 pk;
@@ -148,8 +179,8 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
     // B(n, k) = S1[k][n] = S1 column-major [n][k]: 8 consecutive k are contiguous
     for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
         const int n = idx / (kDim / 8), kc = (idx % (kDim / 8)) * 8;
-        const float4 lo = *reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + kc);
-        const float4 hi = *reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + kc + 4);
+        const float4 lo = *reinterpret_cast<const float4*>(sm.S1f + n * kDim + kc);
+        const float4 hi = *reinterpret_cast<const float4*>(sm.S1f + n * kDim + kc + 4);
         __nv_bfloat162 h0 = __floats2bfloat162_rn(lo.x, lo.y), h1 = __floats2bfloat162_rn(lo.z, lo.w);
         __nv_bfloat162 h2 = __floats2bfloat162_rn(hi.x, hi.y), h3 = __floats2bfloat162_rn(hi.z, hi.w);
         uint4 pk;
@@ -159,12 +190,11 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
         pk.w = *reinterpret_cast<uint32_t*>(&h3);
         *reinterpret_cast<uint4*>(sm.B + core_off(n, kc)) = pk;
     }
-    if (tid < kDim) sm.b1[tid] = b1[tid];
     fence_proxy_async();
     fence_before();
     __syncthreads();
     fence_after();
-    if (tid == 0) {
+    if (tid == 0 && ok) {
         const uint32_t a0 = smem_addr(sm.A), b0 = smem_addr(sm.B), idesc = make_idesc();
 #pragma unroll
         for (int s = 0; s < kDim / 16; ++s)
@@ -172,7 +202,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
                      s > 0 ? 1u : 0u);
         mma_commit(&sm.mbar);
     }
-    const bool ok = mbar_wait(&sm.mbar, phase);
+    ok = ok && mbar_wait(&sm.mbar, phase);
     fence_after();
     // epilogue: thread owns row m (TMEM lane m; a warp reaches the lane
     // quarter warp % 4) and a range of columns
@@ -187,7 +217,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const size_t off = (size_t)(c + j) * kDim + m;
-            So[off] = S2[off] + S1[off] + (ok ? v[j] : 0.0f);
+            So[off] = sm.S2f[off] + sm.S1f[off] + (ok ? v[j] : 0.0f);
         }
     }
     if (tid < kDim) {

@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
     if (tid == 0) {
         tc::mbar_init(&sm.mbar, 1);
+        tc::mbar_init(&sm.mbar_ld, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::fence_before();
@@ -341,28 +342,44 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
 
 // ---------------------------------------------------------------------------
 // B2. down-sweep: z(child 2m) = z(m); z(child 2m+1) = z(m) + S_{2m} z(m) + b_{2m}.
+// kDownParts threads share a row: part p sums k in [p FD/kDownParts, ...) with
+// its own loads in flight, the parts meet in shared memory.
 // ---------------------------------------------------------------------------
+constexpr int kDownParts = 4;
+constexpr int kDownThreads = FD * kDownParts;
+
 template <typename Real>
-__global__ void __launch_bounds__(128) fk_down_kernel(const Real* __restrict__ S_child,
-                                                      const Real* __restrict__ b_child,
-                                                      const Real* __restrict__ z_parent,
-                                                      Real* __restrict__ z_child, long long n_child,
-                                                      const double* __restrict__ r0, int d) {
+__global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __restrict__ S_child,
+                                                               const Real* __restrict__ b_child,
+                                                               const Real* __restrict__ z_parent,
+                                                               Real* __restrict__ z_child, long long n_child,
+                                                               const double* __restrict__ r0, int d) {
     __shared__ Real zs[FD];
+    __shared__ Real part[kDownParts][FD];
     const long long m = blockIdx.x;
-    const int i = threadIdx.x;
-    Real zi;
-    if (r0) zi = (i < d) ? (Real)(-r0[i]) : (Real)0.0;  // root: dx_1 = -h_1
-    else zi = z_parent[m * FD + i];
-    zs[i] = zi;
+    const int i = threadIdx.x % FD, pt = threadIdx.x / FD;
+    if (pt == 0) {
+        Real zi;
+        if (r0) zi = (i < d) ? (Real)(-r0[i]) : (Real)0.0;  // root: dx_1 = -h_1
+        else zi = z_parent[m * FD + i];
+        zs[i] = zi;
+        z_child[(2 * m) * FD + i] = zi;
+    }
     __syncthreads();
-    z_child[(2 * m) * FD + i] = zi;
     if (2 * m + 1 < n_child) {
         const Real* S = S_child + (size_t)(2 * m) * FD * FD;
-        Real s = zi + b_child[(2 * m) * FD + i];
+        constexpr int KP = FD / kDownParts;
+        Real s = 0;
 #pragma unroll 8
-        for (int k = 0; k < FD; ++k) s = fma(S[(size_t)k * FD + i], zs[k], s);
-        z_child[(2 * m + 1) * FD + i] = s;
+        for (int k = pt * KP; k < (pt + 1) * KP; ++k) s = fma(S[(size_t)k * FD + i], zs[k], s);
+        part[pt][i] = s;
+        __syncthreads();
+        if (pt == 0) {
+            Real t = zs[i] + b_child[(2 * m) * FD + i];
+#pragma unroll
+            for (int q = 0; q < kDownParts; ++q) t += part[q][i];
+            z_child[(2 * m + 1) * FD + i] = t;
+        }
     }
 }
 
@@ -566,7 +583,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
     const int L = (int)tr.n.size() - 1;
     if (L == 0) {
         auto tok = timed_begin("fkpp_down", st);
-        fk_down_kernel<Real><<<1, FD, 0, st>>>(S, b, z, z, 1, p.r, p.d);  // z(tile 0) = -r_0
+        fk_down_kernel<Real><<<1, kDownThreads, 0, st>>>(S, b, z, z, 1, p.r, p.d);  // z(tile 0) = -r_0
         timed_end(tok, st);
         count_launch(1);
     }
@@ -574,7 +591,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
         const Real* zpar = z + (size_t)tr.off[lv] * FD;
         Real* zch = z + (size_t)tr.off[lv - 1] * FD;
         auto tok = timed_begin("fkpp_down", st);
-        fk_down_kernel<Real><<<(unsigned)tr.n[lv], FD, 0, st>>>(
+        fk_down_kernel<Real><<<(unsigned)tr.n[lv], kDownThreads, 0, st>>>(
             S + (size_t)tr.off[lv - 1] * FD * FD, b + (size_t)tr.off[lv - 1] * FD, zpar, zch,
             tr.n[lv - 1], lv == L ? p.r : nullptr, p.d);
         timed_end(tok, st);
