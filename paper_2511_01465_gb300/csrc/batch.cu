@@ -66,7 +66,6 @@ struct BatchArgs {
     int guarded, max_iter;
 };
 
-constexpr unsigned long long kAbs = 0x7fffffffffffffffull;
 constexpr unsigned long long kInf = 0x7ff0000000000000ull;
 constexpr int kBWarps = 8;
 
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             a.scratch[k * W + JN + i] = r[i];
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(r[i]) & kAbs;
+            const unsigned long long bits = abs_bits(r[i]);
             mres = bits > mres ? bits : mres;
         }
         if (j == 0) {
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
 #pragma unroll
         for (int i = 0; i < D; ++i) {
             Xn[k * D + i] = x[i] + z[i];
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(z[i]) & kAbs;
+            const unsigned long long bits = abs_bits(z[i]);
             zb = bits > zb ? bits : zb;
         }
         if (!found && zb > a.cap_bits) {

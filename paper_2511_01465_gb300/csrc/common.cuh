@@ -73,10 +73,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
     return s_ok != 0;
 }
 
+// |x| as its IEEE bit pattern, computed on the integer pipe: the register
+// pair is split and the sign bit cleared in the high word by a 32-bit AND.
+// (fabs(), or a 64-bit mask on the bit pattern, compiles to an FP64-pipe
+// instruction, which on GB300 costs as much as a DFMA.)  Non-negative doubles
+// order like their bit patterns; NaN orders above +inf.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    unsigned lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
+    hi &= 0x7fffffffu;
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+constexpr unsigned long long kInfBitsAbs = 0x7ff0000000000000ull;  // bits of +inf
+
 // atomicMax on non-negative doubles (and NaN, which orders above +inf) via
 // their IEEE bit patterns.
 __device__ __forceinline__ void atomic_max_abs_bits(unsigned long long* p, double a) {
-    atomicMax(p, (unsigned long long)__double_as_longlong(fabs(a)));
+    atomicMax(p, abs_bits(a));
 }
 
 }  // namespace pitn

@@ -50,6 +50,7 @@ struct FkParams {
     long long q;       // lazy fill index of X
     long long T;       // tiles
     double h, Dc, o, cap;
+    unsigned long long cap_bits;  // bits of cap: |dz| bits above it are cut
     unsigned long long* res_bits;  // this iteration's slot
     int* nonfinite;
     unsigned long long* qenc;
@@ -124,9 +125,9 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
             const Real uR = (Real)u;
             a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
             p.r[k * d + i] = rr;
-            const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(rr));
+            const unsigned long long b = abs_bits(rr);
             my_res = b > my_res ? b : my_res;
-            my_nf |= !isfinite(rr);
+            my_nf |= b >= kInfBitsAbs;
         }
         a_out[idx] = a;
     }
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
             for (int i = 0; i < 4; ++i) {
                 const int row = r0 + i;
                 if (row < d) {
-                    bad |= !(fabs(z[i]) <= p.cap);
+                    bad |= abs_bits(z[i]) > p.cap_bits;
                     p.Xn[row] = xprev[i] + z[i];
                 }
             }
@@ -456,7 +457,7 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
                     z[i] = nz[i];
                     const int row = r0 + i;
                     if (row < d) {
-                        bad |= !(fabs(z[i]) <= p.cap);
+                        bad |= abs_bits(z[i]) > p.cap_bits;
                         p.Xn[k * d + row] = xc[gq][i] + z[i];
                     }
                     xprev[i] = xc[gq][i];
@@ -658,6 +659,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     p.Dc = io.params[0] / (dx * dx);
     p.o = h * p.Dc;
     p.cap = guarded ? o.guard_B : DBL_MAX;
+    std::memcpy(&p.cap_bits, &p.cap, sizeof(p.cap));
     double* bufs[2] = {io.traj_dev, X1};
     int cur = 0;
     long long q = io.have_guess ? N : 0;

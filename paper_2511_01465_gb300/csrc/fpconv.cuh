@@ -17,20 +17,20 @@ namespace pitn {
 // fraction bits); magnitudes below the smallest normal float give signed
 // zero, above the largest finite float +-inf; NaN stays NaN.
 __device__ __forceinline__ float d2f_int(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi = (unsigned)(b >> 32);
+    unsigned lo, hi;   // the register pair, split without any FP64 instruction
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "d"(x));
     const unsigned s = hi & 0x80000000u;
     const unsigned ea = (hi >> 20) & 0x7ffu;                // biased binary64 exponent
     // add half an ulp of the result at bit 28; a carry out of the fraction
     // moves into the exponent field, which is the correctly rounded result
-    const unsigned long long rb = (b & 0x7fffffffffffffffull) + (1ull << 28);
+    const unsigned long long rb = ((unsigned long long)(hi & 0x7fffffffu) << 32 | lo) + (1ull << 28);
     const unsigned rhi = (unsigned)(rb >> 32), rlo = (unsigned)rb;
     const int e = (int)((rhi >> 20) & 0x7ffu) - 1023 + 127;  // rebiased exponent after rounding
     const unsigned frac = ((rhi & 0xfffffu) << 3) | (rlo >> 29);
     unsigned f = s | ((unsigned)e << 23) | frac;
     f = (e <= 0) ? s : f;                                   // underflow: signed zero
     f = (e >= 255) ? (s | 0x7f800000u) : f;                 // overflow: infinity
-    const bool nan = ea == 0x7ffu && ((hi & 0xfffffu) | (unsigned)b) != 0u;
+    const bool nan = ea == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
     f = nan ? (s | 0x7fc00000u) : f;                        // NaN stays NaN (inf handled above)
     return __uint_as_float(f);
 }
@@ -47,7 +47,9 @@ __device__ __forceinline__ double f2d_int(float v) {
     hi = (e == 0u) ? s : hi;
     lo = (e == 0u) ? 0u : lo;
     hi = (e == 0xffu) ? (s | 0x7ff00000u | (m >> 3)) : hi;
-    return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+    double r;
+    asm("mov.b64 %0, {%1, %2};" : "=d"(r) : "r"(lo), "r"(hi));
+    return r;
 }
 
 }  // namespace pitn

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(256) newton_fused_kernel(SmallArgs a) {
     auto absmax = [](unsigned long long m, const double* v) {
 #pragma unroll
         for (int j = 0; j < D; ++j) {
-            const unsigned long long b = (unsigned long long)__double_as_longlong(v[j]) & kAbsMask;
+            const unsigned long long b = abs_bits(v[j]);
             m = b > m ? b : m;
         }
         return m;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(256) newton_fused_kernel(SmallArgs a) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 xn[j] = x[j] + z[j];
-                const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
+                const unsigned long long b = abs_bits(z[j]);
                 zb = b > zb ? b : zb;
             }
             put_row(ch, k, xn);

@@ -49,7 +49,6 @@ struct SmallArgs {
                                    // tiles and bulk copies (dynamic smem sized by stage_bytes)
 };
 
-constexpr unsigned long long kAbsMask = 0x7fffffffffffffffull;
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 
 template <int D>
@@ -351,7 +350,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 scr[sidx(k - k0, JN + j)] = r[j];
-                const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
+                const unsigned long long b = abs_bits(r[j]);
                 my_res = b > my_res ? b : my_res;
             }
             if (k == 0) {  // a_0 = (0, -r_0), eq. 3.4
@@ -383,7 +382,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             sys.eval(xf, xf, rf, jvf);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned long long b = (unsigned long long)__double_as_longlong(rf[j]) & kAbsMask;
+                const unsigned long long b = abs_bits(rf[j]);
                 my_res = b > my_res ? b : my_res;
                 Ec[j] = -rf[j];
                 Rc[j] = 0.0;
@@ -507,7 +506,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
                     xn[j] = x[j] + z[j];
-                    const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
+                    const unsigned long long b = abs_bits(z[j]);
                     zb = b > zb ? b : zb;
                 }
                 put_row(c, k, xn);
@@ -535,7 +534,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                     for (int j = 0; j < D; ++j) {
                         z[j] = tz[j];
                         xn[j] = xf[j] + z[j];
-                        const unsigned long long b = (unsigned long long)__double_as_longlong(z[j]) & kAbsMask;
+                        const unsigned long long b = abs_bits(z[j]);
                         zb = b > zb ? b : zb;
                     }
                     put_row(1, k, xn);

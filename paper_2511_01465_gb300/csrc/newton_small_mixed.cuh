@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             for (int j = 0; j < D; ++j) {
                 rf[j] = d2f_int(r[j]);
                 scr[sidx(k - k0, JN + j)] = rf[j];
-                const unsigned long long b = (unsigned long long)__double_as_longlong(r[j]) & kAbsMask;
+                const unsigned long long b = abs_bits(r[j]);
                 my_res = b > my_res ? b : my_res;
             }
             if (k == 0) {  // a_0 = (0, -r_0): S = -I
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             sys.eval_mixed(xf, xf, rf64, svf);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                const unsigned long long b = (unsigned long long)__double_as_longlong(rf64[j]) & kAbsMask;
+                const unsigned long long b = abs_bits(rf64[j]);
                 my_res = b > my_res ? b : my_res;
                 Ec[j] = -(float)rf64[j];
             }
