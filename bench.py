@@ -39,9 +39,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28908948736 + 24172061184, "f08ff4f44895de4a"),        # 147 passes
-    "vdp_mixed": (19760937728 + 16358470144, "f08ff4f44895de4a"),  # 140 passes
-    "robertson": (13345722368 + 13705445120, "f08ff4f44895de4a"),  # 22 passes
+    "vdp": (28937728256 + 24178671104, "980238ab6ea0d891"),        # 147 passes
+    "vdp_mixed": (19735694592 + 16361848320, "980238ab6ea0d891"),  # 140 passes
+    "robertson": (13346079232 + 13704996352, "980238ab6ea0d891"),  # 22 passes
 }
 
 

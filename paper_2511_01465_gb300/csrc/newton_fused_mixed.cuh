@@ -1,0 +1,374 @@
+// newton_fused_mixed.cuh -- the fused small-state pass (newton_fused.cuh) with
+// the scan's elements in the FP32 delta form of newton_small_mixed.cuh: one
+// pass per Newton iteration replays the step in FP32, updates the FP64 state,
+// and builds the next iteration's elements from an exact FP64 residual.  The
+// thread-boundary and guard fix-ups after the pass's grid barrier are those of
+// the FP64 fused kernel.  Included by newton_small.cuh.
+#pragma once
+
+namespace pitn {
+
+template <class Sys>
+__global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
+    Sys sys;
+    sys.init(a.params, a.h);
+
+    __shared__ float s_wex[kMaxWarps][E];
+    __shared__ float s_tot[E];
+    __shared__ float s_g[kMaxWarps][E];
+    __shared__ float s_gtot[E];
+    __shared__ float s_zin[D];
+    extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
+
+    const int lane = threadIdx.x & 31;
+    const long long N = a.N;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const unsigned G = gridDim.x;
+    float* __restrict__ scr = reinterpret_cast<float*>(a.scratch);
+    float* __restrict__ agg = reinterpret_cast<float*>(a.agg);
+    float capf;
+    {
+        const double capd = __longlong_as_double((long long)a.cap_bits);
+        capf = (float)fmin(capd, (double)FLT_MAX);
+    }
+
+    const long long C = (N + nthreads - 1) / nthreads;
+    const long long k0 = min(N, gt * C), k1 = min(N, k0 + C);
+    const long long L = k1 - k0, LA = (L + 1) / 2, LB = L - LA, km = k0 + LA;
+    auto sidx = [&](long long k, int j) -> long long { return ((long long)j * a.lcap + (k - k0)) * nthreads + gt; };
+
+    int cur = 0;
+    long long q = a.q_init;
+    long long last_cut = N;
+    int it = 0, status = PITN_NOT_CONVERGED;
+    double final_res = 0.0;
+
+    float QA[D * D], cA[D], QB[D * D], cB[D];
+    unsigned long long my_res = 0ull;
+
+    // element k from the state pair (xp, xc): FP64 residual, FP32 delta-form
+    // element into scratch, folded into (Q, c)
+    auto fold_elem = [&](long long k, const double* xp, const double* xc, float* Q, float* c,
+                         unsigned long long& res) {
+        double r[D];
+        float sv[JN], rf[D];
+        sys.eval_mixed(xp, xc, r, sv);
+#pragma unroll
+        for (int j = 0; j < JN; ++j) scr[sidx(k, j)] = sv[j];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const unsigned long long b = abs_bits(r[j]);
+            res = b > res ? b : res;
+            rf[j] = d2f_int(r[j]);
+            scr[sidx(k, JN + j)] = rf[j];
+        }
+        if (k == 0) {  // a_0 = (0, -r_0): S = -I
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) Q[j] = (j % (D + 1) == 0) ? -1.f : 0.f;
+#pragma unroll
+            for (int j = 0; j < D; ++j) c[j] = -rf[j];
+        } else {
+            float S[D * D];
+            sys.sfull(sv, S);
+            dz_leaf<D>(S, rf, Q, c);
+        }
+    };
+    auto prepend_elem = [&](long long k, const double* xp, const double* xc, float* Q, float* c,
+                            unsigned long long& res) {
+        float EQ[D * D], Ec[D];
+        dz_zero<D>(EQ, Ec);
+        fold_elem(k, xp, xc, EQ, Ec, res);
+        dz_compose<D>(Q, c, EQ, Ec, Q, c);
+    };
+    auto append_fill = [&](long long count, const double* xf, float* Q, float* c, unsigned long long& res) {
+        if (count <= 0) return;
+        double rf64[D];
+        float svf[JN], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
+        sys.eval_mixed(xf, xf, rf64, svf);
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            const unsigned long long b = abs_bits(rf64[j]);
+            res = b > res ? b : res;
+            Ec[j] = -d2f_int(rf64[j]);
+        }
+        sys.sfull(svf, EQ);
+        dz_zero<D>(RQ, Rc);
+        for (long long e = count;;) {
+            if (e & 1) dz_compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
+            e >>= 1;
+            if (!e) break;
+            dz_compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
+        }
+        dz_compose<D>(RQ, Rc, Q, c, Q, c);
+    };
+    auto build_chain = [&](const double* X, long long s, long long e, long long qq, float* Q, float* c,
+                           unsigned long long& res) {
+        dz_zero<D>(Q, c);
+        if (s >= e) return;
+        const long long sf = (qq < N) ? (qq > 1 ? qq : 1LL) : N;
+        const long long er = min(e, max(s, sf));
+        if (s < er) {
+            double xp[D];
+            load_state<D>(X, a.x0, s - 1, qq, xp);
+            for (long long k = s; k < er; ++k) {
+                double x[D];
+                load_state<D>(X, a.x0, k, qq, x);
+                fold_elem(k, xp, x, Q, c, res);
+#pragma unroll
+                for (int j = 0; j < D; ++j) xp[j] = x[j];
+            }
+        }
+        if (er < e) {
+            double xf[D];
+            load_state<D>(X, a.x0, qq - 1, qq, xf);
+            append_fill(e - er, xf, Q, c, res);
+        }
+    };
+
+    build_chain(a.X0, k0, km, q, QA, cA, my_res);
+    build_chain(a.X0, km, k1, q, QB, cB, my_res);
+
+    for (;;) {
+        const double* __restrict__ Xc = cur ? a.X1 : a.X0;
+        double* __restrict__ Xn = cur ? a.X0 : a.X1;
+
+        float Q[D * D], c[D], eQ[D * D], ec[D];
+        dz_compose<D>(QB, cB, QA, cA, Q, c);
+        dz_block_scan<D>(Q, c, eQ, ec, s_wex, s_tot);
+        if (threadIdx.x < E) agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_res, off);
+            my_res = o > my_res ? o : my_res;
+        }
+        if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+
+        const unsigned long long rb = __ldcg(a.res_bits + it);
+        const double res = __longlong_as_double((long long)rb);
+        final_res = res;
+        if (rb >= kInfBits) { status = PITN_NONFINITE; break; }
+        if (res <= a.tol) { status = PITN_OK; break; }
+        if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
+
+        {
+            const unsigned m = (G + blockDim.x - 1) / blockDim.x;
+            float gQ[D * D], gc[D];
+            dz_zero<D>(gQ, gc);
+            for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
+                float sQ[D * D], sc[D];
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+                for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+                dz_compose<D>(sQ, sc, gQ, gc, gQ, gc);
+            }
+            float xQ[D * D], xc[D];
+            dz_block_scan<D>(gQ, gc, xQ, xc, s_g, s_gtot);
+            if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
+                float v[D], t[D], zero[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) zero[j] = 0.f;
+                dz_apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
+                dz_apply<D>(xQ, xc, t, v);
+                for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
+                    float sQ[D * D], sc[D];
+#pragma unroll
+                    for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+                    dz_apply<D>(sQ, sc, v, t);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) v[j] = t[j];
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = v[j];
+            }
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) s_zin[j] = 0.f;
+            }
+            __syncthreads();
+        }
+
+        // ---- fused pass ----------------------------------------------------
+        float zA[D], zB[D];
+        {
+            float zw[D];
+            dz_apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
+            dz_apply<D>(eQ, ec, zw, zA);
+            dz_apply<D>(QA, cA, zA, zB);
+        }
+        const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
+        double xf[D];
+        float Sf[D * D], rff[D];
+        if (sfill < k1 && k0 < k1) {
+            double rf64[D];
+            float svf[JN];
+            load_state<D>(Xc, a.x0, q - 1, q, xf);
+            sys.eval_mixed(xf, xf, rf64, svf);
+            sys.sfull(svf, Sf);
+#pragma unroll
+            for (int j = 0; j < D; ++j) rff[j] = d2f_int(rf64[j]);
+        }
+        float NA[D * D], nA[D], NB[D * D], nB[D];
+        dz_zero<D>(NA, nA);
+        dz_zero<D>(NB, nB);
+        unsigned long long resA = 0ull, resB = 0ull;
+        double prevA[D], prevB[D], firstA[D], firstB[D];
+        long long cutA = N, cutB = N;
+        const bool staged = (D == 2) && a.stage_rows > 0;
+        RowStage stg;
+        if (staged) stg.init(s_dyn);
+        auto put_row = [&](int ch, long long k, const double* v) {
+            if constexpr (D == 2) {
+                if (staged) { stg.put(ch, k, v[0], v[1], Xn); return; }
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
+        };
+        auto step = [&](int ch, long long k, long long s, float* z, double* prev, double* first, float* NQ,
+                        float* nc, long long& cut, unsigned long long& res) {
+            float S[D * D], r[D];
+            if (k < sfill) {
+                float sv[JN];
+#pragma unroll
+                for (int j = 0; j < JN; ++j) sv[j] = scr[sidx(k, j)];
+#pragma unroll
+                for (int j = 0; j < D; ++j) r[j] = scr[sidx(k, JN + j)];
+                sys.sfull(sv, S);
+            } else {
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) S[j] = Sf[j];
+#pragma unroll
+                for (int j = 0; j < D; ++j) r[j] = rff[j];
+            }
+            double x[D];
+            load_state<D>(Xc, a.x0, k, q, x);
+            if (k == 0) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) z[j] = -r[j];
+            } else {
+                float t[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    float sacc = z[i] - r[i];
+#pragma unroll
+                    for (int l = 0; l < D; ++l) sacc = fmaf(S[i * D + l], z[l], sacc);
+                    t[i] = sacc;
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) z[j] = t[j];
+            }
+            double xn[D];
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                xn[j] = x[j] + f2d_int(z[j]);
+                bad |= !(fabsf(z[j]) <= capf);
+            }
+            put_row(ch, k, xn);
+            if (bad) {
+                cut = k;
+                return false;
+            }
+            if (k > s) fold_elem(k, prev, xn, NQ, nc, res);
+            else {
+#pragma unroll
+                for (int j = 0; j < D; ++j) first[j] = xn[j];
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) prev[j] = xn[j];
+            return true;
+        };
+        bool liveA = LA > 0, liveB = LB > 0;
+        for (long long i = 0; i < LA && liveA; ++i) {
+            liveA = step(0, k0 + i, k0, zA, prevA, firstA, NA, nA, cutA, resA);
+            if (liveB && i < LB) liveB = step(1, km + i, km, zB, prevB, firstB, NB, nB, cutB, resB);
+        }
+        if (cutA < N) {
+            cutB = N;
+            resB = 0ull;
+        }
+        if (staged) stg.finish(Xn);
+        const long long kc = (cutA < N) ? cutA : cutB;
+        if (LB > 0 && kc > km) {
+            float EQ[D * D], Ec[D];
+            dz_zero<D>(EQ, Ec);
+            fold_elem(km, prevA, firstB, EQ, Ec, resB);
+            dz_compose<D>(NB, nB, EQ, Ec, NB, nB);
+        }
+        unsigned long long my_q = (kc < N) ? ~(unsigned long long)kc : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+            my_q = o > my_q ? o : my_q;
+        }
+        if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        const unsigned long long qe = __ldcg(a.qenc + it);
+        const long long cut = qe ? (long long)(~qe) : N;
+        if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }
+
+        const long long qn = a.guarded ? cut : N;
+        const long long sfn = (qn < N) ? (qn > 1 ? qn : 1LL) : N;
+        my_res = 0ull;
+        if (k0 < k1) {
+            if (sfn <= k0) {
+                build_chain(Xn, k0, km, qn, NA, nA, my_res);
+                build_chain(Xn, km, k1, qn, NB, nB, my_res);
+            } else {
+                my_res = resA > resB ? resA : resB;
+                double xp[D], xc0[D];
+                load_state<D>(Xn, a.x0, k0 - 1, qn, xp);
+                if (k0 < qn) {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) xc0[j] = firstA[j];
+                } else {
+                    load_state<D>(Xn, a.x0, k0, qn, xc0);
+                }
+                prepend_elem(k0, xp, xc0, NA, nA, my_res);
+                if (sfn < k1) {
+                    double xfn[D];
+                    load_state<D>(Xn, a.x0, qn - 1, qn, xfn);
+                    if (sfn < km) {
+                        append_fill(km - sfn, xfn, NA, nA, my_res);
+                        dz_zero<D>(NB, nB);
+                        append_fill(LB, xfn, NB, nB, my_res);
+                    } else {
+                        append_fill(k1 - sfn, xfn, NB, nB, my_res);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D * D; ++j) { QA[j] = NA[j]; QB[j] = NB[j]; }
+#pragma unroll
+        for (int j = 0; j < D; ++j) { cA[j] = nA[j]; cB[j] = nB[j]; }
+        cur ^= 1;
+        q = qn;
+        last_cut = cut;
+        ++it;
+    }
+
+    const double* Xc = cur ? a.X1 : a.X0;
+    const bool same = (Xc == a.out);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k = gt; k < N; k += stride) {
+        if (same && k < q) continue;
+        double v[D];
+        load_state<D>(Xc, a.x0, k, q, v);
+#pragma unroll
+        for (int j = 0; j < D; ++j) a.out[k * D + j] = v[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.rec->iters = it;
+        a.rec->status = status;
+        a.rec->final_res = final_res;
+        a.rec->guard_index = last_cut;
+    }
+}
+
+}  // namespace pitn

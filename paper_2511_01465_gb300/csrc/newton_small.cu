@@ -56,7 +56,7 @@ int select_small_kernel(int system_id, int method, bool mixed, pitn::SmallKernel
         if (method != PITN_STEP_EULER) return PITN_EUNSUPPORTED;
         switch (system_id) {
         case PITN_LORENZ63: *K = small_kernel_of<Lorenz63, kVarMixed>(); return PITN_OK;
-        case PITN_VDP: *K = small_kernel_of<VanDerPol, kVarMixed>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<VanDerPol, kVarFusedMixed>(); return PITN_OK;
         case PITN_LINEAR_OSC: *K = small_kernel_of<LinearOsc, kVarMixed>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }

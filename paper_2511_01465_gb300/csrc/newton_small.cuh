@@ -585,12 +585,13 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 
 #include "newton_small_mixed.cuh"
 #include "newton_fused.cuh"
+#include "newton_fused_mixed.cuh"
 
 namespace pitn {
 
 // Kernel variants behind a SmallKernel: the three-phase FP64 kernel, its
-// FP32 delta-form twin, and the fused FP64 kernel.
-enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2 };
+// FP32 delta-form twin, and the fused FP64 and FP32-delta kernels.
+enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3 };
 
 // Dynamic shared memory of a launch: the row-stage tiles for d = 2.
 template <class Sys>
@@ -602,6 +603,7 @@ template <class Sys, int VAR>
 static const void* small_kernel_ptr() {
     if constexpr (VAR == kVarMixed) return (const void*)newton_small_mixed_kernel<Sys>;
     else if constexpr (VAR == kVarFused) return (const void*)newton_fused_kernel<Sys>;
+    else if constexpr (VAR == kVarFusedMixed) return (const void*)newton_fused_mixed_kernel<Sys>;
     else return (const void*)newton_small_kernel<Sys>;
 }
 
