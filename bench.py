@@ -36,7 +36,7 @@ UNIT = "steps/s"
 # under profiles/), keyed by workload and tagged with a hash of the kernel
 # sources they were taken on: a changed kernel reports traffic null.
 SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "newton_fused.cuh",
-             "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
+             "newton_fused_mixed.cuh", "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
     "vdp": (28937728256 + 24178671104, "980238ab6ea0d891"),        # 147 passes
@@ -675,10 +675,10 @@ def oracle_sample(spec, sample_iters):
 def oracle_passes(name, fallback):
     """Residual evaluations the oracle's own full solve needs (stored by
     tests/golden/make_oracle_golden.py, which runs only the oracle)."""
-    key = {"vdp": "vdp_2^22_guard100_tol1e-12_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
-           "vdp_mixed": "vdp_2^22_guard100_tol1e-12_it400",
-           "lorenz_mixed": "lorenz_8192_guard100_tol1e-12_it100",
-           "lorenz": "lorenz_8192_guard100_tol1e-12_it100",
+    key = {"vdp": "vdp_2^22_guard100_tol1e-8_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
+           "vdp_mixed": "vdp_2^22_guard100_tol1e-8_it400",
+           "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100",
+           "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "robertson": "robertson_5e6_be_zeros_tol1e-8_it60"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")

@@ -31,6 +31,9 @@ CASES = {
     "vdp_2^22_plain_tol1e-8_it200": (W.vdp(), 1e-8, 200, 0.0),
     "vdp_2^22_guard100_tol1e-12_it400": (W.vdp(), 1e-12, 400, 100.0),
     "osc_2^22_plain_tol1e-8_it10": (W.damped_oscillator(), 1e-8, 10, 0.0),
+    # the bench's tolerance for the guarded van der Pol and Lorenz solves
+    "vdp_2^22_guard100_tol1e-8_it400": (W.vdp(), 1e-8, 400, 100.0),
+    "lorenz_8192_guard100_tol1e-8_it100": (W.lorenz(), 1e-8, 100, 100.0),
     "fkpp_d128_2^15_plain_tol1e-8_it50": (W.fkpp(), 1e-8, 50, 0.0),
     # backward Euler, the paper's zero guess, Robertson on [0, 500] at h = 1e-4
     "robertson_5e6_be_zeros_tol1e-8_it60": (W.robertson(h=1e-4), 1e-8, 60, 0.0, O.BACKWARD_EULER, 0.0),
