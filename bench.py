@@ -597,10 +597,12 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         # and the update (d flops); the scan runs in FP32.  Its design traffic per
         # step and pass is x read twice and written once (24 d B) plus the FP32
         # scratch (Jacobian entries and residual, JN + d floats) written and read.
+        # (the d = 2 solve runs fused: the state is read once per pass, 16 d B)
         f64 = {"vdp_mixed": 11.0 + 2.0, "lorenz_mixed": 17.0 + 3.0}[name]
         jn = {"vdp_mixed": 2, "lorenz_mixed": 3}[name]
+        xb = 16 * wl.d if wl.d == 2 else 24 * wl.d
         flops = wl.N * f64 * passes
-        nbytes = wl.N * (24 * wl.d + 8 * (jn + wl.d)) * passes
+        nbytes = wl.N * (xb + 8 * (jn + wl.d)) * passes
         hbm, _, _, src = load_peaks()
         f_alu = flops / (ms / 1e3 / steps) / 1e12 / FP64_PEAK_TFLOPS
         f_hbm = nbytes / (ms / 1e3 / steps) / 1e9 / hbm
@@ -611,7 +613,7 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
                     "traffic": traffic_for(name), "kernel": kern, "kernel_launches_per_step": launches / steps,
                     "kernel_ms_per_launch": ms / max(launches, 1),
                     "fp64_frac": f_alu,
-                    "note": f"design bytes per step {24 * wl.d + 8 * (jn + wl.d)} B x passes; peak = {src} "
+                    "note": f"design bytes per step {xb + 8 * (jn + wl.d)} B x passes; peak = {src} "
                             f"copy bandwidth; fp64_frac = FP64 residual+update flops vs nominal 1.25 TFLOP/s"}
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
         note = "FP64 flops (residual + update) of the mixed kernel; peak = nominal GB300 FP64"
