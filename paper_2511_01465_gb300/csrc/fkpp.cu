@@ -26,12 +26,14 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
 #include "compose_tc.cuh"
+#include "fpconv.cuh"
 #include "solver.h"
 
 namespace pitn {
@@ -70,7 +72,7 @@ __device__ __forceinline__ double fk_x(const FkParams& p, long long k, int i) {
 // different banks.
 template <typename Real> struct FoldTraits;
 template <> struct FoldTraits<float> {
-    static constexpr int R = 32, TPC = 4, PADR = 8, THREADS = FD * TPC;
+    static constexpr int R = 16, TPC = 8, PADR = 4, THREADS = FD * TPC;
 };
 template <> struct FoldTraits<double> {
     static constexpr int R = 32, TPC = 4, PADR = 2, THREADS = FD * TPC;
@@ -122,7 +124,11 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
             const double un = fk_x(p, k, i);
             const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
             const double rr = un - (u + p.h * f);
-            const Real uR = (Real)u;
+            // (an FP32 leaf takes u by the integer-pipe conversion: a hardware
+            // F2F would issue on the FP64 pipe)
+            Real uR;
+            if constexpr (std::is_same<Real, float>::value) uR = d2f_int(u);
+            else uR = u;
             a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
             p.r[k * d + i] = rr;
             const unsigned long long b = abs_bits(rr);
@@ -163,7 +169,10 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
         if (s < len) {
             const long long k = k0 + s;
             a = a_in[k * FD + i];
-            if (i < d) rr = (Real)p.r[k * d + i];
+            if (i < d) {
+                if constexpr (std::is_same<Real, float>::value) rr = d2f_int(p.r[k * d + i]);
+                else rr = p.r[k * d + i];
+            }
         }
         a_s[s * FDP + pidx<Real>(i)] = a;
         r_s[s * FDP + pidx<Real>(i)] = rr;
@@ -181,7 +190,23 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
         for (int i = 0; i < R; ++i) s[i] = (row0 + i == j) ? (Real)1.0 : (Real)0.0;
         const int nrow_live = max(0, min(R, d - row0));  // rows at or beyond d couple to nothing
         for (int st = 0; st < len; ++st) {
+            // this thread's R leaf diagonals; in FP32 by 16-byte shared-memory
+            // loads (the segment starts at a multiple of 16 bytes: FDP and sbase
+            // are), 4x fewer load instructions for the FP32 pipe's fast steps
+            Real a_reg[std::is_same<Real, float>::value ? R : 1];
             const Real* a = a_s + st * FDP + sbase;
+            if constexpr (std::is_same<Real, float>::value) {
+                const uint4* src = reinterpret_cast<const uint4*>(a);
+#pragma unroll
+                for (int v = 0; v < R / 4; ++v) {
+                    const uint4 w = src[v];
+                    a_reg[4 * v] = __uint_as_float(w.x);
+                    a_reg[4 * v + 1] = __uint_as_float(w.y);
+                    a_reg[4 * v + 2] = __uint_as_float(w.z);
+                    a_reg[4 * v + 3] = __uint_as_float(w.w);
+                }
+                a = a_reg;
+            }
             const Real above = __shfl_up_sync(0xffffffffu, s[R - 1], 1);
             const Real below = __shfl_down_sync(0xffffffffu, s[0], 1);
             const Real bot = (part < TPC - 1) ? below : (Real)0.0;

@@ -186,7 +186,11 @@ __global__ void __launch_bounds__(256) newton_fused_kernel(SmallArgs a) {
         if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
 
         // ---- incoming prefix of this CTA: fixed-order scan of the aggregates ----
-        {
+        // (a grid of at most 64 CTAs: warp 0 alone, its serial part stays short;
+        // larger grids: every thread takes a share and the CTA scans)
+        if (G <= 64) {
+            cta_incoming<D>(a.agg, G, s_zin);
+        } else {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;
             double gP[D * D], gc[D];
             mat_identity<D>(gP);

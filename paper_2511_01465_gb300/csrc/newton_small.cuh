@@ -267,6 +267,63 @@ __device__ __forceinline__ void block_scan(double* P, double* c, double* eP, dou
     __syncthreads();
 }
 
+// Incoming correction vector of this CTA for small grids: the vector part of
+// the composition of the CTA aggregates 0 .. b-1, in a fixed order, computed
+// by warp 0 alone (the other warps wait at the closing barrier).  Lane l folds
+// aggregates [l m, (l+1) m), m = ceil(G / 32); a warp scan gives each lane the
+// prefix before its group, whose vector part is its whole effect on the zero
+// initial correction (every prefix from aggregate 0 has matrix 0, eq. 3.4);
+// the lane holding aggregate b - 1 applies its group's aggregates up to b - 1
+// to that vector.  With few aggregates this avoids the CTA-wide scan; with
+// many, the lanes' serial folds make it slower than the CTA-wide one.
+template <int D>
+__device__ __forceinline__ void cta_incoming(const double* __restrict__ agg, unsigned G, double* s_zin) {
+    constexpr int E = D * D + D;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const unsigned m = (G + 31) / 32;
+        double gP[D * D], gc[D];
+        mat_identity<D>(gP);
+#pragma unroll
+        for (int j = 0; j < D; ++j) gc[j] = 0.0;
+        for (unsigned i = lane * m; i < min(G, (lane + 1) * m); ++i) {
+            double sP[D * D], sc[D];
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+            for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+            compose<D>(sP, sc, gP, gc, gP, gc);
+        }
+        warp_scan<D>(gP, gc, lane);
+        double v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = __shfl_up_sync(0xffffffffu, gc[j], 1);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) v[j] = 0.0;
+        }
+        if (blockIdx.x > 0 && (unsigned)lane == (blockIdx.x - 1) / m) {
+            for (unsigned i = lane * m; i <= blockIdx.x - 1; ++i) {
+                double sP[D * D], sc[D], t[D];
+#pragma unroll
+                for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(agg + (size_t)i * E + j);
+#pragma unroll
+                for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
+                apply<D>(sP, sc, v, t);
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = t[j];
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_zin[j] = v[j];
+        }
+        if (blockIdx.x == 0 && lane == 0) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_zin[j] = 0.0;
+        }
+    }
+    __syncthreads();
+}
+
 // Deterministic three-phase Newton kernel (persistent, cooperative launch).
 // Thread g owns steps [g*chunk, (g+1)*chunk).  Per Newton iteration:
 //   phase 1: residuals + compact Jacobians (stored to scratch), thread fold,
@@ -417,7 +474,11 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         if (it == a.max_iter) { status = PITN_NOT_CONVERGED; break; }
 
         // ---- incoming prefix of this CTA: fixed-order scan of the aggregates ----
-        {
+        // (a grid of at most 64 CTAs: warp 0 alone, its serial part stays short;
+        // larger grids: every thread takes a share and the CTA scans)
+        if (G <= 64) {
+            cta_incoming<D>(a.agg, G, s_zin);
+        } else {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;   // aggregates per thread
             double gP[D * D], gc[D];
             mat_identity<D>(gP);
