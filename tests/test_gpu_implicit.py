@@ -138,3 +138,22 @@ def test_implicit_unsupported_combinations(pk):
     with pytest.raises(P.PitnError):   # the FP32 delta form is explicit-only
         pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
                  method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)
+
+
+def test_bench_size_robertson(pk):
+    """The implicit bench workload at full size (backward Euler, h = 1e-4,
+    N = 5e6, zero guess, tol 1e-8): Newton count and status equal the oracle's
+    stored outcome, the first residuals match its history, and the returned
+    trajectory passes the implicit residual test on its own."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_full_size.json")) as f:
+        gold = json.load(f)["robertson_5e6_be_zeros_tol1e-8_it60"]
+    wl = W.robertson(h=1e-4)
+    assert (wl.N, wl.h) == (gold["N"], gold["h"])
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, gold["tol"], gold["max_iter"],
+                          guess=np.zeros((wl.N, wl.d)), history=True, method=pk.PITN_STEP_BACKWARD_EULER)
+    assert (info["iters"], info["status"]) == (gold["iters"], gold["status"])
+    np.testing.assert_allclose(info["res_history"][:-1], gold["res_history"][:-1], rtol=1e-6, atol=1e-15)
+    t = traj.cpu().numpy()
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, t, method=O.BACKWARD_EULER)
+    assert not nf and res <= gold["tol"]
+    np.testing.assert_allclose(t.sum(axis=1), 1.0, atol=1e-9)   # y1 + y2 + y3 conserved

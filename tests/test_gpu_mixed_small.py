@@ -49,3 +49,18 @@ def test_mixed_small_rejects_other_systems(pk):
     wl = W.fkpp(d=64, N=10)
     with pytest.raises(P.PitnError):
         pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 5, precision=P.PITN_PREC_MIXED_FP32)
+
+
+def test_bench_size_vdp_mixed(pk):
+    """The FP32-scan bench workload at full size (van der Pol N = 2^22, guard
+    B = 100, tol 1e-8): converged to the FP64 tolerance, its FP64 residual
+    re-checked by the oracle, within 1e-6 of the sequential FP64 trajectory."""
+    wl = W.vdp()
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 400, guard_B=100.0,
+                          precision=pk.PITN_PREC_MIXED_FP32)
+    assert info["status"] == O.OK and info["final_res"] <= 1e-8
+    g = traj.cpu().numpy()
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, g)
+    assert not nf and res <= 1e-8 * (1 + 1e-6)
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
+    assert float(np.abs(g - seq).max() / np.abs(seq).max()) <= 1e-6
