@@ -157,3 +157,12 @@ def test_bench_size_robertson(pk):
     _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, t, method=O.BACKWARD_EULER)
     assert not nf and res <= gold["tol"]
     np.testing.assert_allclose(t.sum(axis=1), 1.0, atol=1e-9)   # y1 + y2 + y3 conserved
+
+
+@pytest.mark.parametrize("rule", ["backward_euler", "trapezoid"])
+def test_implicit_singular_step_matrix(pk, rule):
+    # 1 - h lam (or 1 - h lam / 2) is exactly 0 at h = 0.5: non-finite
+    # residual at the first evaluation, as in the oracle
+    m, lam = ((pk.PITN_STEP_BACKWARD_EULER, 2.0) if rule == "backward_euler" else (pk.PITN_STEP_TRAPEZOID, 4.0))
+    traj, info = pk.solve(O.DAHLQUIST, [lam], [1.0], 0.5, 20, 1e-12, 10, guess=np.zeros((20, 1)), method=m)
+    assert info["status"] == pk.PITN_NONFINITE and info["iters"] == 0

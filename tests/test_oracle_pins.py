@@ -435,3 +435,12 @@ def test_trapezoid_newton_step_equals_dense_solve(sys, p, d):
     dxi = -np.linalg.solve(H, hv)
     out = O.newton(sys, p, x0, h, N, 0.0, 1, guess=guess, guard_B=1e300, method=O.TRAPEZOID)
     np.testing.assert_allclose(out["traj"] - guess, dxi.reshape(N, d), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("method,lam", [(O.BACKWARD_EULER, 2.0), (O.TRAPEZOID, 4.0)])
+def test_implicit_singular_step_matrix(method, lam):
+    # h = 0.5: I - dg/dx_n = 1 - h lam (backward Euler) or 1 - h lam / 2
+    # (trapezoid) is exactly 0, so the implicit residual is not finite and the
+    # solve ends NONFINITE at its first evaluation (reading R9)
+    r = O.newton(O.DAHLQUIST, [lam], [1.0], 0.5, 20, 1e-12, 10, guess=np.zeros((20, 1)), method=method)
+    assert r["status"] == O.NONFINITE and r["iters"] == 0
