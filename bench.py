@@ -84,6 +84,10 @@ SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
                # backward Euler Robertson: f 8, Jf 9, I - h Jf 12, h_n 9, 3x3 inverse 42
                # (one division counted as 1), M^-1 h_n 18, dense fold 72; replay 18 + update 3
                "robertson": (170.0, 21.0)}
+# FP64 instructions per step (phase 1, phase 3) of the three-phase kernel,
+# as counted by ncu (DADD + DFMA + DMUL thread instructions at 1 and 11 passes;
+# equal to the count of the source)
+FP64_OPS = {"vdp": (20.0, 6.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -589,6 +593,7 @@ def run_ours(args, rank, world, local_rank):
 def roofline_for(name, spec, wl, res, ktimes, steps):
     """Roofline of the kernel family with the largest device time."""
     kern = max(ktimes, key=lambda k: ktimes[k][0])
+    extra = {}
     ms, launches = ktimes[kern]
     passes = res.iters + 1
     per_step_s = ms / 1e3 / steps
@@ -622,6 +627,14 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         flops = wl.N * (p1 * passes + p3 * res.iters)
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
         note = "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"
+        if name in FP64_OPS:
+            # the pipe view: a DADD or DMUL takes an FP64 issue slot like a DFMA
+            o1, o3 = FP64_OPS[name]
+            ops = wl.N * (o1 * passes + o3 * res.iters) / (ms / 1e3 / steps) / 1e12
+            extra = {"fp64_ops_tops": ops, "fp64_ops_frac": ops / (FP64_PEAK_TFLOPS / 2)}
+            note += ("; fp64_ops_frac: FP64 instructions (DADD, DMUL, DFMA each one, per step: "
+                     f"{o1:g} phase 1 + {o3:g} phase 3, ncu counters) against the DFMA issue rate "
+                     f"{FP64_PEAK_TFLOPS / 2:g} T/s")
     elif kern == "fkpp_residual":
         flops = wl.N * passes * 128 * 15
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
@@ -652,7 +665,7 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
     achieved = (flops / per_step_s / 1e12) if flops is not None else 0.0
     return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
             "frac": achieved / peak, "traffic": traffic_for(name) if kern == "newton_small" else None,
-            "kernel": kern,
+            **extra, "kernel": kern,
             "kernel_launches_per_step": launches / steps,
             "kernel_ms_per_launch": ms / max(launches, 1), "note": note}
 
