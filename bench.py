@@ -4,7 +4,8 @@ One step = one complete Newton solve (every residual evaluation, scan and
 update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|lorenz|osc|fkpp|fkpp_mixed|batch|batch_small|adjoint]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_rk4|lorenz|lorenz_mixed|osc|robertson|fkpp|fkpp_mixed|
+                                                      batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica of
@@ -83,7 +84,11 @@ SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
                "vdp_mixed": (34.0, 9.0), "lorenz_mixed": (76.0, 19.0),
                # backward Euler Robertson: f 8, Jf 9, I - h Jf 12, h_n 9, 3x3 inverse 42
                # (one division counted as 1), M^-1 h_n 18, dense fold 72; replay 18 + update 3
-               "robertson": (170.0, 21.0)}
+               "robertson": (170.0, 21.0),
+               # RK4 van der Pol (fused kernel): four stages with their Jacobian chain
+               # (8 + 3 x 24), weighted sums for phi and dphi/dx (20 + 34), fold 20;
+               # replay 8 + update 2
+               "vdp_rk4": (154.0, 10.0)}
 # FP64 instructions per step (phase 1, phase 3) of the three-phase kernel,
 # as counted by ncu (DADD + DFMA + DMUL thread instructions at 1 and 11 passes;
 # equal to the count of the source)
@@ -110,6 +115,11 @@ def workload(name):
     if name == "lorenz":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0,
                     desc="lorenz63 sigma=10 rho=28 beta=8/3 x0=(1,1,1) h=1e-3 N=8192, guarded Newton B=100")
+    if name == "vdp_rk4":
+        return dict(kind="single", wl=W.vdp_paper(h=1e-5), tol=1e-8, max_iter=50, guard_B=0.0, method=1,
+                    guess=1.0,
+                    desc="van_der_pol mu=1 x0=(0,1) on [0,10], classical RK4 h=1e-5 N=1e6, plain Newton "
+                         "from the ones guess (Sec. 4.1)")
     if name == "vdp_mixed":
         return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=2,
                     desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
@@ -582,7 +592,7 @@ def run_ours(args, rank, world, local_rank):
                        "step_ms": [round(t, 3) for t in times],
                        "launch_shape": P.pitn_tune_get(f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:"
                                                        f"{1 if spec['guard_B'] > 0 else 0}"
-                                                       f"{':be' if method == 2 else ''}"
+                                                       f"{ {1: ':rk4', 2: ':be', 3: ':tr'}.get(method, '')}"
                                                        f"{':f32' if spec.get('precision', 0) == 2 else ''}"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
@@ -695,7 +705,7 @@ def oracle_passes(name, fallback):
            "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
-           "robertson": "robertson_5e6_be_zeros_tol1e-8_it60"}
+           "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     try:
         with open(p) as f:
@@ -716,7 +726,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6,
-                "lorenz_mixed": 62, "robertson": 9}
+                "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7}
 
 
 def cpu_baseline_batch(spec, n_ivps=24):

@@ -84,6 +84,13 @@ def _ptr(a):
     return a.ctypes.data_as(_dp)
 
 
+def _need(a, size, what):
+    """The C routines read exactly `size` doubles from each buffer: refuse others."""
+    if a.size != size:
+        raise ValueError(f"{what}: expected {size} values, got {a.size}")
+    return a
+
+
 def _check(rc):
     if rc != 0:
         raise ValueError(f"oracle call failed with code {rc}")
@@ -95,6 +102,7 @@ def nparams(sys: int) -> int:
 
 def rhs(sys, p, x):
     p, x = _f64(p), _f64(x)
+    _need(p, nparams(sys), "p")
     out = np.empty_like(x)
     _check(_load().oracle_rhs(sys, _ptr(p), x.size, _ptr(x), _ptr(out)))
     return out
@@ -102,6 +110,7 @@ def rhs(sys, p, x):
 
 def rhs_jac(sys, p, x):
     p, x = _f64(p), _f64(x)
+    _need(p, nparams(sys), "p")
     d = x.size
     out = np.empty((d, d))
     _check(_load().oracle_rhs_jac(sys, _ptr(p), d, _ptr(x), _ptr(out)))
@@ -110,6 +119,7 @@ def rhs_jac(sys, p, x):
 
 def rhs_dparam(sys, p, x):
     p, x = _f64(p), _f64(x)
+    _need(p, nparams(sys), "p")
     d = x.size
     out = np.empty((d, nparams(sys)))
     _check(_load().oracle_rhs_dparam(sys, _ptr(p), d, _ptr(x), _ptr(out)))
@@ -119,6 +129,7 @@ def rhs_dparam(sys, p, x):
 def step(sys, p, h, x, method=EULER, jac=False, dparam=False):
     """phi(x) and optionally dphi/dx, dphi/dp."""
     p, x = _f64(p), _f64(x)
+    _need(p, nparams(sys), "p")
     d = x.size
     phi = np.empty(d)
     J = np.empty((d, d)) if jac else None
@@ -129,6 +140,7 @@ def step(sys, p, h, x, method=EULER, jac=False, dparam=False):
 
 def sequential(sys, p, x0, h, N, method=EULER):
     p, x0 = _f64(p), _f64(x0)
+    _need(p, nparams(sys), "p")
     d = x0.size
     traj = np.empty((int(N), d))
     _check(_load().oracle_sequential(sys, method, _ptr(p), _ptr(x0), float(h), int(N), d, _ptr(traj)))
@@ -139,6 +151,7 @@ def residual(sys, p, x0, h, traj, method=EULER):
     """(r [N][d], ||r||_inf, nonfinite flag) of eq. (3.8) for trajectory x_1..x_N."""
     p, x0, traj = _f64(p), _f64(x0), _f64(traj)
     N, d = traj.shape
+    _need(p, nparams(sys), "p"), _need(x0, d, "x0")
     r = np.empty_like(traj)
     res = ctypes.c_double()
     nf = ctypes.c_int()
@@ -151,6 +164,7 @@ def combine(A2, b2, A1, b1):
     """(A2, b2) (x) (A1, b1) of eq. (3.3)."""
     A2, b2, A1, b1 = map(_f64, (A2, b2, A1, b1))
     d = b1.size
+    _need(A2, d * d, "A2"), _need(A1, d * d, "A1"), _need(b2, d, "b2")
     A, b = np.empty((d, d)), np.empty(d)
     _check(_load().oracle_combine(d, _ptr(A2), _ptr(b2), _ptr(A1), _ptr(b1), _ptr(A), _ptr(b)))
     return A, b
@@ -160,6 +174,7 @@ def affine_scan(A, c):
     """Sequential states z[n] of z <- A_n z + c_n from z = 0 (element 0's matrix ignored)."""
     A, c = _f64(A), _f64(c)
     N, d = c.shape
+    _need(A, N * d * d, "A")
     z = np.empty_like(c)
     _check(_load().oracle_affine_scan(N, d, _ptr(A), _ptr(c), _ptr(z)))
     return z
@@ -168,11 +183,14 @@ def affine_scan(A, c):
 def newton(sys, p, x0, h, N, tol, max_iter, guard_B=0.0, guess=None, method=EULER):
     """Returns dict(traj, res_hist, iters, status, guard_index)."""
     p, x0 = _f64(p), _f64(x0)
+    _need(p, nparams(sys), "p")
     d = x0.size
     traj = np.empty((int(N), d))
     hist = np.full(max_iter + 1, np.nan)
     iters, status, gi = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
-    g = _f64(guess) if guess is not None else None
+    g = None
+    if guess is not None:   # a scalar or d-vector fills every step; else one row per step
+        g = _f64(np.broadcast_to(_f64(guess), (int(N), d)))
     _check(_load().oracle_newton(sys, method, _ptr(p), _ptr(x0), float(h), int(N), d, float(tol),
                                  int(max_iter), float(guard_B), _ptr(g), _ptr(traj), _ptr(hist),
                                  ctypes.byref(iters), ctypes.byref(status), ctypes.byref(gi)))
@@ -184,6 +202,7 @@ def newton_batch(sys, params, x0, h, N, tol, max_iter, guard_B=0.0, method=EULER
     params, x0, h = _f64(params), _f64(x0), _f64(h)
     N = np.ascontiguousarray(np.asarray(N, dtype=np.int64))
     B, d = x0.shape
+    _need(params, B * nparams(sys), "params"), _need(h, B, "h"), _need(N, B, "N")
     traj = np.empty((int(N.sum()), d))
     offsets = np.empty(B + 1, dtype=np.int64)
     iters = np.empty(B, dtype=np.int32)
@@ -200,8 +219,9 @@ def adjoint(sys, p, x0, h, traj, grad_traj=None, grad_xN=None, method=EULER):
     """(dL/dx0, dL/dp) by the reverse recursion."""
     p, x0, traj = _f64(p), _f64(x0), _f64(traj)
     N, d = traj.shape
-    gt = _f64(grad_traj) if grad_traj is not None else None
-    gN = _f64(grad_xN) if grad_xN is not None else None
+    _need(p, nparams(sys), "p"), _need(x0, d, "x0")
+    gt = _need(_f64(grad_traj), N * d, "grad_traj") if grad_traj is not None else None
+    gN = _need(_f64(grad_xN), d, "grad_xN") if grad_xN is not None else None
     gx0 = np.empty(d)
     gp = np.empty(nparams(sys))
     _check(_load().oracle_adjoint(sys, method, _ptr(p), _ptr(x0), float(h), N, d, _ptr(traj),

@@ -5,7 +5,9 @@
         python -m paper_2511_01465_gb300.profile_workload --workload vdp --N 1048576 --max-iter 10
 
 Workloads: vdp, lorenz, osc (single IVP; --precision 2 for the FP32 delta
-scan), robertson (backward Euler from the zero guess, h = 500 / N), fkpp,
+scan), vdp_rk4 (RK4 van der Pol on [0, 10], h = 10 / N, from the ones
+guess, or from the root with --from-root), robertson (backward Euler from
+the zero guess, h = 500 / N), fkpp,
 fkpp_mixed (d = 128),
 batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]), adjoint
 (Van der Pol batch forward + backward).  Sizes default to the small cases
@@ -38,7 +40,7 @@ def main():
     import torch
 
     from . import api, workloads as W
-    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_STEP_BACKWARD_EULER
+    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_STEP_BACKWARD_EULER, PITN_STEP_RK4
 
     out = None
     root = None
@@ -52,6 +54,16 @@ def main():
                 guess = root
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, guard_B=a.guard,
                             precision=a.precision, guess=guess)[1]
+        elif a.workload == "vdp_rk4":
+            wl = W.vdp_paper(h=10.0 / a.N)
+            guess = np.ones((wl.N, wl.d))
+            if a.from_root:
+                if root is None:
+                    root = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-12, 50, guess=guess,
+                                     method=PITN_STEP_RK4)[0]
+                guess = root
+            out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, guess=guess,
+                            method=PITN_STEP_RK4)[1]
         elif a.workload == "robertson":
             wl = W.robertson(h=500.0 / a.N)
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter,

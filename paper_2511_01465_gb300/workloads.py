@@ -17,6 +17,8 @@ Workloads (explicit Euler unless stated, FP64):
     x0~N(0, 5^2 I) (B x 3), N_i~integers in [n_min, n_max] inclusive;
   * adjoint Van der Pol batch: default_rng(seed), mu~U[0.5,2] (B),
     x0~U[-2,2]^2 (B x 2), h=1e-3, N=2^14;
+  * RK4 (Sec. 4.1): Van der Pol mu=1, x0=(0,1) on [0, 10], N = t_end / h,
+    Newton guess = ones (the paper's);
   * backward Euler (Sec. 4.2): Dahlquist lambda=-1, y0=1 on [0, 4];
     Robertson k=(0.04, 3e7, 1e4), y0=(1,0,0) on [0, 500]; N = t_end / h,
     Newton guess = zeros (the paper's).
@@ -72,6 +74,10 @@ def lorenz(N: int = 8192, h: float = 1e-3) -> Single:
 
 def vdp(N: int = 1 << 22, h: float = 1e-4, mu: float = 1.0) -> Single:
     return Single("van_der_pol", VDP, np.array([mu]), np.array([2.0, 0.0]), h, N)
+
+
+def vdp_paper(h: float = 1e-5, t_end: float = 10.0, mu: float = 1.0) -> Single:
+    return Single("van_der_pol_rk4", VDP, np.array([mu]), np.array([0.0, 1.0]), h, int(round(t_end / h)))
 
 
 def damped_oscillator(N: int = 1 << 22, h: float = 1e-4) -> Single:

@@ -37,6 +37,8 @@ CASES = {
     "fkpp_d128_2^15_plain_tol1e-8_it50": (W.fkpp(), 1e-8, 50, 0.0),
     # backward Euler, the paper's zero guess, Robertson on [0, 500] at h = 1e-4
     "robertson_5e6_be_zeros_tol1e-8_it60": (W.robertson(h=1e-4), 1e-8, 60, 0.0, O.BACKWARD_EULER, 0.0),
+    # classical RK4, the paper's ones guess, van der Pol on [0, 10] at h = 1e-5
+    "vdp_rk4_1e6_ones_tol1e-8_it50": (W.vdp_paper(h=1e-5), 1e-8, 50, 0.0, O.RK4, 1.0),
 }
 
 

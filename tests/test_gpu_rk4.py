@@ -67,3 +67,22 @@ def test_rk4_unsupported_systems(pk):
     from paper_2511_01465_gb300 import pitn as P
     with pytest.raises(P.PitnError):
         pk.solve(1, [10, 28, 8 / 3], [1, 1, 1], 1e-3, 100, 1e-10, 5, method=pk.PITN_STEP_RK4)
+
+
+def test_bench_size_vdp_rk4(pk):
+    """The RK4 bench workload at full size (Sec. 4.1's van der Pol on [0, 10]
+    at h = 1e-5, N = 1e6, guess ones, tol 1e-8): Newton count and status equal
+    the oracle's stored outcome, the residual history matches it, and the
+    returned trajectory passes the oracle's residual test on its own."""
+    from paper_2511_01465_gb300 import workloads as W
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_full_size.json")) as f:
+        gold = json.load(f)["vdp_rk4_1e6_ones_tol1e-8_it50"]
+    wl = W.vdp_paper(h=1e-5)
+    assert (wl.N, wl.h, gold["method"]) == (gold["N"], gold["h"], O.RK4)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, gold["tol"], gold["max_iter"],
+                          guess=np.full((wl.N, wl.d), gold["guess"]), history=True,
+                          method=pk.PITN_STEP_RK4)
+    assert (info["iters"], info["status"]) == (gold["iters"], gold["status"])
+    np.testing.assert_allclose(info["res_history"][:-1], gold["res_history"][:-1], rtol=1e-6, atol=1e-15)
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, traj.cpu().numpy(), method=O.RK4)
+    assert not nf and res <= gold["tol"]
