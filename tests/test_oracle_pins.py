@@ -444,3 +444,17 @@ def test_implicit_singular_step_matrix(method, lam):
     # solve ends NONFINITE at its first evaluation (reading R9)
     r = O.newton(O.DAHLQUIST, [lam], [1.0], 0.5, 20, 1e-12, 10, guess=np.zeros((20, 1)), method=method)
     assert r["status"] == O.NONFINITE and r["iters"] == 0
+
+
+def test_oracle_wrapper_checks_buffer_sizes():
+    # the C routines read fixed-size buffers: the wrapper refuses short ones and
+    # broadcasts a constant guess to every step
+    with pytest.raises(ValueError):
+        O.newton(O.VDP, [1.0, 2.0], [0.0, 1.0], 1e-2, 10, 1e-10, 5)
+    with pytest.raises(ValueError):
+        O.newton(O.VDP, [1.0], [0.0, 1.0], 1e-2, 10, 1e-10, 5, guess=np.ones((9, 2)))
+    a = O.newton(O.VDP, [1.0], [0.0, 1.0], 1e-2, 50, 1e-12, 30, guess=1.0, method=O.RK4)
+    b = O.newton(O.VDP, [1.0], [0.0, 1.0], 1e-2, 50, 1e-12, 30, guess=np.ones((50, 2)), method=O.RK4)
+    assert a["iters"] == b["iters"] and np.array_equal(a["traj"], b["traj"])
+    with pytest.raises(ValueError):
+        O.adjoint(O.VDP, [1.0], [0.0, 1.0], 1e-2, np.zeros((5, 2)), grad_xN=np.ones(3))
