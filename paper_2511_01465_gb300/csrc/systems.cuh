@@ -258,7 +258,10 @@ struct LinearOsc {
 // Jacobian by the chain rule through the stages:
 //   K_1 = Jf(x),  K_i = Jf(y_i) (I + h a_{i,i-1} K_{i-1}),
 //   dphi/dx = I + h sum_i b_i K_i.
-// Rhs provides D, P, init(p), f(x, out) and jf(x, J) (dense D x D).
+// Rhs provides D, P, init(p), f(x, out), jf(x, J) (dense D x D) and
+// jf_times(x, Y, K) = Jf(x) Y written for its own sparsity: a product by a
+// structural 0 or 1 of Jf is not an exact no-op in IEEE arithmetic (0 * inf),
+// so the compiler keeps it; FP64 instructions are the cost of this map.
 // The compact Jacobian of this map is the dense one (JN = D * D).
 // ---------------------------------------------------------------------------
 namespace pitn {
@@ -269,6 +272,11 @@ struct LogisticRhs {
     __host__ __device__ void init(const double* p) { r = p[0]; K = p[1]; }
     __device__ __forceinline__ void f(const double* x, double* o) const { o[0] = r * x[0] * (1.0 - x[0] / K); }
     __device__ __forceinline__ void jf(const double* x, double* J) const { J[0] = r * (1.0 - 2.0 * x[0] / K); }
+    __device__ __forceinline__ void jf_times(const double* x, const double* Y, double* Ko) const {
+        double J;
+        jf(x, &J);
+        Ko[0] = J * Y[0];
+    }
 };
 
 struct VdpRhs {
@@ -285,6 +293,15 @@ struct VdpRhs {
         J[2] = -2.0 * mu * x[0] * x[1] - 1.0;
         J[3] = mu * (1.0 - x[0] * x[0]);
     }
+    // Jf = [[0, 1], [a, b]]: the first row of Jf Y is Y's second row
+    __device__ __forceinline__ void jf_times(const double* x, const double* Y, double* Ko) const {
+        double J[4];
+        jf(x, J);
+        Ko[0] = Y[2];
+        Ko[1] = Y[3];
+        Ko[2] = fma(J[3], Y[2], J[2] * Y[0]);
+        Ko[3] = fma(J[3], Y[3], J[2] * Y[1]);
+    }
 };
 
 template <class Rhs>
@@ -298,41 +315,36 @@ struct RK4Map {
     }
     // r = xc - phi(xp), jv = dphi/dx(xp) (dense, row-major)
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
-        double k[4][D], Kj[4][D * D], y[D], Y[D * D], Jf[D * D];
+        double k[4][D], Kj[4][D * D], y[D], Y[D * D];
         const double a[4] = {0.0, 0.5, 0.5, 1.0};
+        // stage 1 at x itself: K_1 = Jf(x) (the identity factor is not multiplied out)
+        rhs.f(xp, k[0]);
+        rhs.jf(xp, Kj[0]);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 1; s < 4; ++s) {
+            const double ha = h * a[s];
 #pragma unroll
-            for (int i = 0; i < D; ++i) y[i] = (s == 0) ? xp[i] : xp[i] + h * a[s] * k[s - 1][i];
+            for (int i = 0; i < D; ++i) y[i] = fma(ha, k[s - 1][i], xp[i]);
 #pragma unroll
             for (int i = 0; i < D * D; ++i)
-                Y[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) + ((s == 0) ? 0.0 : h * a[s] * Kj[s - 1][i]);
+                Y[i] = (i % (D + 1) == 0) ? fma(ha, Kj[s - 1][i], 1.0) : ha * Kj[s - 1][i];
             rhs.f(y, k[s]);
-            rhs.jf(y, Jf);
-#pragma unroll
-            for (int i = 0; i < D; ++i)
-#pragma unroll
-                for (int j = 0; j < D; ++j) {
-                    double sacc = 0.0;
-#pragma unroll
-                    for (int l = 0; l < D; ++l) sacc = fma(Jf[i * D + l], Y[l * D + j], sacc);
-                    Kj[s][i * D + j] = sacc;
-                }
+            rhs.jf_times(y, Y, Kj[s]);
         }
         const double w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            double sacc = 0.0;
+            double sacc = w[0] * k[0][i];
 #pragma unroll
-            for (int s = 0; s < 4; ++s) sacc += w[s] * k[s][i];
+            for (int s = 1; s < 4; ++s) sacc = fma(w[s], k[s][i], sacc);
             res[i] = xc[i] - (xp[i] + h * sacc);
         }
 #pragma unroll
         for (int i = 0; i < D * D; ++i) {
-            double sacc = 0.0;
+            double sacc = w[0] * Kj[0][i];
 #pragma unroll
-            for (int s = 0; s < 4; ++s) sacc += w[s] * Kj[s][i];
-            jv[i] = ((i % (D + 1) == 0) ? 1.0 : 0.0) + h * sacc;
+            for (int s = 1; s < 4; ++s) sacc = fma(w[s], Kj[s][i], sacc);
+            jv[i] = (i % (D + 1) == 0) ? fma(h, sacc, 1.0) : h * sacc;
         }
     }
     __device__ __forceinline__ void jfull(const double* jv, double* J) const {
