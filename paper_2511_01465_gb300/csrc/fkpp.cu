@@ -52,6 +52,9 @@ struct FkParams {
     long long q;       // lazy fill index of X
     long long T;       // tiles
     double h, Dc, o, cap;
+    double a0;         // 1 - 2 o + h: the leaf diagonal is a0 - 2 h u
+    int rs;            // > 0: the fold runs scaled by o^-k, renormalised every rs steps (0: unscaled)
+    double o_rs;       // o^rs
     unsigned long long cap_bits;  // bits of cap: |dz| bits above it are cut
     unsigned long long* res_bits;  // this iteration's slot
     int* nonfinite;
@@ -122,14 +125,16 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
             const double u = fk_x(p, k - 1, i);
             const double up = (i < d - 1) ? fk_x(p, k - 1, i + 1) : 0.0;
             const double un = fk_x(p, k, i);
-            const double f = p.Dc * (um - 2.0 * u + up) + u * (1.0 - u);
+            const double f = fma(p.Dc, fma(-2.0, u, um) + up, fma(-u, u, u));   // D Lu + u (1 - u)
             const double rr = un - (u + p.h * f);
             // (an FP32 leaf takes u by the integer-pipe conversion: a hardware
             // F2F would issue on the FP64 pipe)
-            Real uR;
-            if constexpr (std::is_same<Real, float>::value) uR = d2f_int(u);
-            else uR = u;
-            a = (Real)1.0 + (hR * ((Real)1.0 - (Real)2.0 * uR) - (Real)2.0 * oR);
+            if constexpr (std::is_same<Real, float>::value) {
+                const float uR = d2f_int(u);
+                a = 1.f + (hR * (1.f - 2.f * uR) - 2.f * oR);
+            } else {
+                a = fma(-2.0 * p.h, u, p.a0);   // one FP64 instruction, as in the replay
+            }
             p.r[k * d + i] = rr;
             const unsigned long long b = abs_bits(rr);
             my_res = b > my_res ? b : my_res;
@@ -145,6 +150,14 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
 // threads per column, R rows each, in registers); halo rows move by warp
 // shuffles, so the fold needs no block barrier per step.  Warp 0 then folds
 // the vector b (4 rows per lane).
+//
+// A leaf is L = diag(a) + o (sub + super) with one off-diagonal value o, so
+// its product with P costs an add, a multiply and an FMA per entry.  With
+// rs > 0 the fold carries P / o^k instead (k = steps since the last
+// renormalisation): then (L P) / o^(k+1) = diag(a / o) P~ + (sub + super) P~,
+// an add and an FMA per entry; every rs steps P~ is multiplied by o^rs, and
+// at the end by o^k, so its magnitude stays within the working precision's
+// range (rs is chosen on the host from |log2 o|).
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
@@ -162,7 +175,10 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
     const int len = (int)max(0LL, k1 - k0);
     const int d = p.d;
 
-    // leaf diagonals and residuals of this tile's elements, staged in shared memory
+    // leaf diagonals (divided by o when the fold runs scaled) and residuals of
+    // this tile's elements, staged in shared memory
+    const bool scaled = p.rs > 0;
+    const Real inv_o = scaled ? (Real)(1.0 / p.o) : (Real)1.0;
     for (int idx = threadIdx.x; idx < p.TS * FD; idx += blockDim.x) {
         const int s = idx / FD, i = idx - s * FD;
         Real a = (Real)1.0, rr = (Real)0.0;
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
                 else rr = p.r[k * d + i];
             }
         }
-        a_s[s * FDP + pidx<Real>(i)] = a;
+        a_s[s * FDP + pidx<Real>(i)] = scaled ? a * inv_o : a;
         r_s[s * FDP + pidx<Real>(i)] = rr;
     }
     __syncthreads();
@@ -189,40 +205,62 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
 #pragma unroll
         for (int i = 0; i < R; ++i) s[i] = (row0 + i == j) ? (Real)1.0 : (Real)0.0;
         const int nrow_live = max(0, min(R, d - row0));  // rows at or beyond d couple to nothing
-        for (int st = 0; st < len; ++st) {
-            // this thread's R leaf diagonals; in FP32 by 16-byte shared-memory
-            // loads (the segment starts at a multiple of 16 bytes: FDP and sbase
-            // are), 4x fewer load instructions for the FP32 pipe's fast steps
-            Real a_reg[std::is_same<Real, float>::value ? R : 1];
-            const Real* a = a_s + st * FDP + sbase;
-            if constexpr (std::is_same<Real, float>::value) {
-                const uint4* src = reinterpret_cast<const uint4*>(a);
+        // the unscaled fold multiplies the neighbour sum by o; the scaled one by
+        // 1 (live rows) -- with every row live, not at all
+        const Real ow = scaled ? (Real)1.0 : o;
+        const bool all_live = scaled && nrow_live == R;
+        const Real o_rs = (Real)p.o_rs;
+        int since = 0;                                   // steps since the last renormalisation
+        auto fold_steps = [&](auto all_live_c) {
+            constexpr bool kAllLive = decltype(all_live_c)::value;
+            for (int st = 0; st < len; ++st) {
+                // this thread's R leaf diagonals; in FP32 by 16-byte shared-memory
+                // loads (the segment starts at a multiple of 16 bytes: FDP and sbase
+                // are), 4x fewer load instructions for the FP32 pipe's fast steps
+                Real a_reg[std::is_same<Real, float>::value ? R : 1];
+                const Real* a = a_s + st * FDP + sbase;
+                if constexpr (std::is_same<Real, float>::value) {
+                    const uint4* src = reinterpret_cast<const uint4*>(a);
 #pragma unroll
-                for (int v = 0; v < R / 4; ++v) {
-                    const uint4 w = src[v];
-                    a_reg[4 * v] = __uint_as_float(w.x);
-                    a_reg[4 * v + 1] = __uint_as_float(w.y);
-                    a_reg[4 * v + 2] = __uint_as_float(w.z);
-                    a_reg[4 * v + 3] = __uint_as_float(w.w);
+                    for (int v = 0; v < R / 4; ++v) {
+                        const uint4 w = src[v];
+                        a_reg[4 * v] = __uint_as_float(w.x);
+                        a_reg[4 * v + 1] = __uint_as_float(w.y);
+                        a_reg[4 * v + 2] = __uint_as_float(w.z);
+                        a_reg[4 * v + 3] = __uint_as_float(w.w);
+                    }
+                    a = a_reg;
                 }
-                a = a_reg;
-            }
-            const Real above = __shfl_up_sync(0xffffffffu, s[R - 1], 1);
-            const Real below = __shfl_down_sync(0xffffffffu, s[0], 1);
-            const Real bot = (part < TPC - 1) ? below : (Real)0.0;
-            Real prev = (part > 0) ? above : (Real)0.0;
+                const Real above = __shfl_up_sync(0xffffffffu, s[R - 1], 1);
+                const Real below = __shfl_down_sync(0xffffffffu, s[0], 1);
+                const Real bot = (part < TPC - 1) ? below : (Real)0.0;
+                Real prev = (part > 0) ? above : (Real)0.0;
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const Real cur = s[i];
-                const Real nxt = (i < R - 1) ? s[i + 1] : bot;
-                const Real oi = (i < nrow_live) ? o : (Real)0.0;
-                s[i] = fma(cur, a[i], oi * (prev + nxt));
-                prev = cur;
+                for (int i = 0; i < R; ++i) {
+                    const Real cur = s[i];
+                    const Real nxt = (i < R - 1) ? s[i + 1] : bot;
+                    if constexpr (kAllLive) {
+                        s[i] = fma(cur, a[i], prev + nxt);
+                    } else {
+                        const Real oi = (i < nrow_live) ? ow : (Real)0.0;
+                        s[i] = fma(cur, a[i], oi * (prev + nxt));
+                    }
+                    prev = cur;
+                }
+                if (scaled && ++since == p.rs) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) s[i] *= o_rs;
+                    since = 0;
+                }
             }
-        }
+        };
+        if (all_live) fold_steps(std::true_type{});
+        else fold_steps(std::false_type{});
+        Real tail = (Real)1.0;                           // o^since
+        for (int c = 0; c < since; ++c) tail *= o;
         Real* col = S_out + ((size_t)t * FD + j) * FD + row0;
 #pragma unroll
-        for (int i = 0; i < R; ++i) col[i] = s[i] - ((row0 + i == j) ? (Real)1.0 : (Real)0.0);
+        for (int i = 0; i < R; ++i) col[i] = s[i] * tail - ((row0 + i == j) ? (Real)1.0 : (Real)0.0);
     }
     if (warp == 0) {
         // vector part of the aggregate, in the working precision
@@ -238,8 +276,14 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
             for (int i = 0; i < 4; ++i) {
                 const Real cur = b[i];
                 const Real nxt = (i < 3) ? b[i + 1] : ((lane == 31) ? (Real)0.0 : dn);
-                const Real oi = (r0 + i < d) ? o : (Real)0.0;
-                b[i] = a[pidx<Real>(r0 + i)] * cur + oi * (prev + nxt) - rr[pidx<Real>(r0 + i)];
+                const Real ai = a[pidx<Real>(r0 + i)], ri = rr[pidx<Real>(r0 + i)];
+                if (scaled) {   // a / o is staged: b' = o (a/o b + [live] (prev + nxt)) - r
+                    const Real nb = (r0 + i < d) ? prev + nxt : (Real)0.0;
+                    b[i] = fma(o, fma(ai, cur, nb), -ri);
+                } else {
+                    const Real oi = (r0 + i < d) ? o : (Real)0.0;
+                    b[i] = ai * cur + oi * (prev + nxt) - ri;
+                }
                 prev = cur;
             }
         }
@@ -260,11 +304,16 @@ struct LevelArgs {
     long long n_in;     // child count
 };
 
-// FP64: grid (nodes, 4): each CTA computes 32 columns of S2 + S1 + S2 S1.
+// FP64: grid (nodes, 128 / CW): each CTA computes CW = 8 CPT columns of
+// S2 + S1 + S2 S1 (thread (tm, tn): rows 4tm.., columns CPT tn..).  The host
+// takes narrower column blocks on the levels near the root, where the nodes
+// alone would leave most SMs idle.
+template <int CPT>
 __global__ void __launch_bounds__(256) fk_compose_f64(LevelArgs a) {
+    constexpr int CW = 8 * CPT;
     extern __shared__ __align__(16) unsigned char smem[];
     double* As = reinterpret_cast<double*>(smem);   // [k][m] 128 x 128 (S2, column-major copy)
-    double* Bs = As + FD * FD;                      // [n][k] 32 x 128  (S1 columns)
+    double* Bs = As + FD * FD;                      // [n][k] CW x 128  (S1 columns)
     const long long m = blockIdx.x;
     const int cb = blockIdx.y;
     const double* Sin = (const double*)a.S_in;
@@ -275,41 +324,41 @@ __global__ void __launch_bounds__(256) fk_compose_f64(LevelArgs a) {
     const double* S1 = Sin + (size_t)ce * FD * FD;
     double* So = Sout + (size_t)m * FD * FD;
     if (cl >= a.n_in) {  // copy
-        for (int idx = threadIdx.x; idx < 32 * FD; idx += blockDim.x)
-            So[(size_t)cb * 32 * FD + idx] = S1[(size_t)cb * 32 * FD + idx];
+        for (int idx = threadIdx.x; idx < CW * FD; idx += blockDim.x)
+            So[(size_t)cb * CW * FD + idx] = S1[(size_t)cb * CW * FD + idx];
         if (cb == 0)
             for (int i = threadIdx.x; i < FD; i += blockDim.x) bout[m * FD + i] = bin[ce * FD + i];
         return;
     }
     const double* S2 = Sin + (size_t)cl * FD * FD;
     for (int idx = threadIdx.x; idx < FD * FD; idx += blockDim.x) As[idx] = S2[idx];
-    for (int idx = threadIdx.x; idx < 32 * FD; idx += blockDim.x) Bs[idx] = S1[(size_t)cb * 32 * FD + idx];
+    for (int idx = threadIdx.x; idx < CW * FD; idx += blockDim.x) Bs[idx] = S1[(size_t)cb * CW * FD + idx];
     __syncthreads();
-    const int tm = threadIdx.x & 31, tn = threadIdx.x >> 5;  // rows 4tm.., cols 4tn..
-    double acc[4][4];
+    const int tm = threadIdx.x & 31, tn = threadIdx.x >> 5;
+    double acc[4][CPT];
 #pragma unroll
     for (int x = 0; x < 4; ++x)
 #pragma unroll
-        for (int y = 0; y < 4; ++y) acc[x][y] = 0.0;
+        for (int y = 0; y < CPT; ++y) acc[x][y] = 0.0;
 #pragma unroll 4
     for (int k = 0; k < FD; ++k) {
-        double av[4], bv[4];
+        double av[4], bv[CPT];
 #pragma unroll
         for (int x = 0; x < 4; ++x) av[x] = As[k * FD + 4 * tm + x];
 #pragma unroll
-        for (int y = 0; y < 4; ++y) bv[y] = Bs[(4 * tn + y) * FD + k];
+        for (int y = 0; y < CPT; ++y) bv[y] = Bs[(CPT * tn + y) * FD + k];
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+            for (int y = 0; y < CPT; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
     }
 #pragma unroll
-    for (int y = 0; y < 4; ++y) {
-        const int n = cb * 32 + 4 * tn + y;
+    for (int y = 0; y < CPT; ++y) {
+        const int n = cb * CW + CPT * tn + y;
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
             const int mm = 4 * tm + x;
-            So[(size_t)n * FD + mm] = As[n * FD + mm] + Bs[(4 * tn + y) * FD + mm] + acc[x][y];
+            So[(size_t)n * FD + mm] = As[n * FD + mm] + Bs[(CPT * tn + y) * FD + mm] + acc[x][y];
         }
     }
     if (cb == 0 && threadIdx.x < FD) {
@@ -444,6 +493,7 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
         // steps in groups of G: the loads of a group are issued together so
         // their latency overlaps; the recurrence itself is serial in k
         constexpr int G = 4;
+        const double m2h = -2.0 * p.h;
         for (long long kg = k0; kg < k1; kg += G) {
             double xc[G][4], rk[G][4];
 #pragma unroll
@@ -461,9 +511,11 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
             for (int gq = 0; gq < G; ++gq) {
                 const long long k = kg + gq;
                 if (k >= k1) break;
+                // dz_{k+1} = J_k dz_k - r_k with J_k = diag(a0 - 2 h x_k) + o (sub + super):
+                // 4 FP64 instructions per entry
                 double a[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = 1.0 + (p.h * (1.0 - 2.0 * xprev[i]) - 2.0 * p.o);
+                for (int i = 0; i < 4; ++i) a[i] = fma(m2h, xprev[i], p.a0);
                 const double up = __shfl_up_sync(0xffffffffu, z[3], 1);
                 const double dn = __shfl_down_sync(0xffffffffu, z[0], 1);
                 double prev = (lane == 0) ? 0.0 : up;
@@ -472,8 +524,7 @@ __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* 
                 for (int i = 0; i < 4; ++i) {
                     const double cur = z[i];
                     const double nxt = (i < 3) ? z[i + 1] : ((lane == 31) ? 0.0 : dn);
-                    const double oi = (r0 + i < d) ? p.o : 0.0;
-                    nz[i] = (r0 + i < d) ? (a[i] * cur + oi * (prev + nxt) - rk[gq][i]) : 0.0;
+                    nz[i] = (r0 + i < d) ? fma(a[i], cur, fma(p.o, prev + nxt, -rk[gq][i])) : 0.0;
                     prev = cur;
                 }
                 bool bad = false;
@@ -599,8 +650,14 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
             ca.err = err;
             fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 256, kTcSmem, st>>>(ca);
         } else {
-            const size_t sm = (size_t)(FD * FD + 32 * FD) * sizeof(double);
-            fk_compose_f64<<<dim3((unsigned)tr.n[lv], 4), 256, sm, st>>>(la);
+            // column block per CTA: enough CTAs for two per SM where the level allows
+            const long long nodes = tr.n[lv];
+            const int cpt = nodes >= 76 ? 4 : (nodes >= 19 ? 2 : 1);
+            const size_t sm = (size_t)(FD * FD + 8 * cpt * FD) * sizeof(double);
+            const dim3 grid((unsigned)nodes, (unsigned)(FD / (8 * cpt)));
+            if (cpt == 4) fk_compose_f64<4><<<grid, 256, sm, st>>>(la);
+            else if (cpt == 2) fk_compose_f64<2><<<grid, 256, sm, st>>>(la);
+            else fk_compose_f64<1><<<grid, 256, sm, st>>>(la);
         }
         timed_end(tok, st);
         count_launch(1);
@@ -665,8 +722,12 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     {
         const int smemA = (int)fold_smem_bytes<Real>(TS);
         cudaFuncSetAttribute(fk_fold_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smemA);
-        cudaFuncSetAttribute(fk_compose_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(fk_compose_f64<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((FD * FD + 32 * FD) * sizeof(double)));
+        cudaFuncSetAttribute(fk_compose_f64<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((FD * FD + 16 * FD) * sizeof(double)));
+        cudaFuncSetAttribute(fk_compose_f64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((FD * FD + 8 * FD) * sizeof(double)));
         cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTcSmem);
     }
@@ -683,6 +744,17 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     p.h = h;
     p.Dc = io.params[0] / (dx * dx);
     p.o = h * p.Dc;
+    p.a0 = 1.0 - 2.0 * p.o + h;
+    // scaled fold (see fk_fold_kernel): renormalise before the scaled product
+    // can move more than ~100 (FP32) / ~900 (FP64) binary orders of magnitude
+    p.rs = 0;
+    p.o_rs = 1.0;
+    if (std::isnormal(p.o) && std::isnormal(1.0 / p.o)) {
+        const double bits_per_step = std::fabs(std::log2(p.o)) + 2.0;
+        const double budget = std::is_same<Real, float>::value ? 100.0 : 900.0;
+        p.rs = (int)std::max(1.0, std::min((double)TS, std::floor(budget / bits_per_step)));
+        p.o_rs = std::pow(p.o, p.rs);
+    }
     p.cap = guarded ? o.guard_B : DBL_MAX;
     std::memcpy(&p.cap_bits, &p.cap, sizeof(p.cap));
     double* bufs[2] = {io.traj_dev, X1};
