@@ -40,9 +40,10 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "newton_fused_mixed.cuh", "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28937728256 + 24178671104, "980238ab6ea0d891"),        # 147 passes
-    "vdp_mixed": (19735694592 + 16361848320, "980238ab6ea0d891"),  # 140 passes
-    "robertson": (13346079232 + 13704996352, "980238ab6ea0d891"),  # 22 passes
+    "vdp": (28930810112 + 24176290560, "06df5b65c3726c75"),        # 147 passes
+    "vdp_mixed": (13213320448 + 15326085376, "06df5b65c3726c75"),  # 137 passes (fused kernel)
+    "vdp_rk4": (31019520 + 348874752, "06df5b65c3726c75"),         # 8 passes; the 16 MB state stays in L2
+    "robertson": (13344417280 + 13704811264, "06df5b65c3726c75"),  # 22 passes
 }
 
 
