@@ -669,8 +669,9 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
         note = "FP64 residual flops (15 per entry); peak = nominal GB300 FP64"
     elif kern == "fkpp_fold":
+        # the scan runs once per Newton update (a converged pass stops after its residual)
         mixed = spec.get("precision", 0) == 1
-        flops = wl.N * passes * FK_FOLD_REAL_FLOPS
+        flops = wl.N * res.iters * FK_FOLD_REAL_FLOPS
         peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
         bound, unit = "alu", "TFLOP/s"
         note = ("dense fold flops in " + ("FP32" if mixed else "FP64") +
@@ -678,7 +679,7 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
     elif kern == "fkpp_compose":
         mixed = spec.get("precision", 0) == 1
         T = (wl.N - 1 + 63) // 64
-        flops = (T - 1) * FK_COMPOSE_FLOPS * passes
+        flops = (T - 1) * FK_COMPOSE_FLOPS * res.iters
         if mixed:
             _, bf16, _, src = load_peaks()
             peak, bound, unit = bf16, "tensor", "TFLOP/s"

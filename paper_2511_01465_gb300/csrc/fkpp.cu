@@ -53,6 +53,9 @@ struct FkParams {
     long long T;       // tiles
     double h, Dc, o, cap;
     double a0;         // 1 - 2 o + h: the leaf diagonal is a0 - 2 h u
+    double tol;
+    int* stop;         // set on the device after the residual: converged or non-finite, so the
+                       // scan and the update of this pass are skipped
     int rs;            // > 0: the fold runs scaled by o^-k, renormalised every rs steps (0: unscaled)
     double o_rs;       // o^rs
     unsigned long long cap_bits;  // bits of cap: |dz| bits above it are cut
@@ -145,6 +148,14 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
     fk_reduce_res(my_res, my_nf, p);
 }
 
+// The pass's decision, on the device: the scan and the update that follow in
+// the stream return at once when the residual already meets tol (or is not
+// finite), so the converged pass costs its residual only.
+__global__ void fk_stop_kernel(FkParams p) {
+    const double res = __longlong_as_double((long long)*p.res_bits);
+    *p.stop = (*p.nonfinite != 0 || res <= p.tol) ? 1 : 0;
+}
+
 // ---------------------------------------------------------------------------
 // A. tile fold.  The threads own the 128 columns of P (TPC
 // threads per column, R rows each, in registers); halo rows move by warp
@@ -169,6 +180,7 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
     extern __shared__ __align__(16) unsigned char smem[];
     Real* a_s = reinterpret_cast<Real*>(smem);            // [TS][FDP]  1 + e (leaf diagonal)
     Real* r_s = a_s + (size_t)p.TS * FDP;                  // [TS][FDP]  residual (for the vector fold)
+    if (*p.stop) return;
     const long long t = blockIdx.x;
     const long long k0 = 1 + t * p.TS;
     const long long k1 = min(p.N, k0 + p.TS);
@@ -231,6 +243,7 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
                     }
                     a = a_reg;
                 }
+                (void)a_reg;
                 const Real above = __shfl_up_sync(0xffffffffu, s[R - 1], 1);
                 const Real below = __shfl_down_sync(0xffffffffu, s[0], 1);
                 const Real bot = (part < TPC - 1) ? below : (Real)0.0;
@@ -302,6 +315,7 @@ struct LevelArgs {
     void* S_out;
     void* b_out;
     long long n_in;     // child count
+    const int* stop;    // skip the level (converged pass)
 };
 
 // FP64: grid (nodes, 128 / CW): each CTA computes CW = 8 CPT columns of
@@ -320,6 +334,7 @@ __global__ void __launch_bounds__(256) fk_compose_f64(LevelArgs a) {
     const double* bin = (const double*)a.b_in;
     double* Sout = (double*)a.S_out;
     double* bout = (double*)a.b_out;
+    if (*a.stop) return;
     const long long ce = 2 * m, cl = 2 * m + 1;
     const double* S1 = Sin + (size_t)ce * FD * FD;
     double* So = Sout + (size_t)m * FD * FD;
@@ -381,6 +396,7 @@ struct CombineArgs {
     long long stride_in;               // element stride of the inputs in matrices (2 for tree levels)
     long long n_lone;                  // index of a lone earlier element to copy (or -1)
     int* err;
+    const int* stop;                   // nullable: skip the launch when set (converged pass)
 };
 
 constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
@@ -392,6 +408,7 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     const long long m = blockIdx.x;
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t MM = (size_t)FD * FD;
+    if (a.stop && *a.stop) return;
     if (m == a.n_lone) {  // copy the lone earlier element
         const float4* src = reinterpret_cast<const float4*>(a.S1 + (size_t)m * a.stride_in * MM);
         float4* dst = reinterpret_cast<float4*>(a.S + (size_t)m * MM);
@@ -428,7 +445,9 @@ __global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __res
                                                                const Real* __restrict__ b_child,
                                                                const Real* __restrict__ z_parent,
                                                                Real* __restrict__ z_child, long long n_child,
-                                                               const double* __restrict__ r0, int d) {
+                                                               const double* __restrict__ r0, int d,
+                                                               const int* __restrict__ stop) {
+    if (*stop) return;
     __shared__ Real zs[FD];
     __shared__ Real part[kDownParts][FD];
     const long long m = blockIdx.x;
@@ -463,6 +482,7 @@ __global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __res
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* __restrict__ z_tiles) {
+    if (*p.stop) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long t = (long long)blockIdx.x * 4 + warp;
     unsigned long long my_q = 0ull;
@@ -609,7 +629,7 @@ Tree make_tree(long long T) {
 
 template <typename Real>
 int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* abuf, bool mixed,
-                  int* err, cudaStream_t st) {
+                  int* err, cudaStream_t st, bool residual_only) {
     const size_t smemA = fold_smem_bytes<Real>(p.TS);
     {
         auto tok = timed_begin("fkpp_residual", st);
@@ -619,6 +639,9 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
         timed_end(tok, st);
         count_launch(1);
     }
+    if (residual_only) return cudaGetLastError() == cudaSuccess ? PITN_OK : PITN_ECUDA;
+    fk_stop_kernel<<<1, 1, 0, st>>>(p);
+    count_launch(1);
     {
         auto tok = timed_begin("fkpp_fold", st);
         fk_fold_kernel<Real><<<(unsigned)p.T, FoldTraits<Real>::THREADS, smemA, st>>>(p, abuf, S, b);
@@ -633,6 +656,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
         la.S_out = S + (size_t)tr.off[lv] * FD * FD;
         la.b_out = b + (size_t)tr.off[lv] * FD;
         la.n_in = tr.n[lv - 1];
+        la.stop = p.stop;
         auto tok = timed_begin("fkpp_compose", st);
         if (mixed) {
             CombineArgs ca;
@@ -648,6 +672,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
             ca.stride_in = 2;
             ca.n_lone = (la.n_in & 1) ? la.n_in / 2 : -1;
             ca.err = err;
+            ca.stop = p.stop;
             fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 256, kTcSmem, st>>>(ca);
         } else {
             // column block per CTA: enough CTAs for two per SM where the level allows
@@ -666,7 +691,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
     const int L = (int)tr.n.size() - 1;
     if (L == 0) {
         auto tok = timed_begin("fkpp_down", st);
-        fk_down_kernel<Real><<<1, kDownThreads, 0, st>>>(S, b, z, z, 1, p.r, p.d);  // z(tile 0) = -r_0
+        fk_down_kernel<Real><<<1, kDownThreads, 0, st>>>(S, b, z, z, 1, p.r, p.d, p.stop);  // z(tile 0) = -r_0
         timed_end(tok, st);
         count_launch(1);
     }
@@ -676,7 +701,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
         auto tok = timed_begin("fkpp_down", st);
         fk_down_kernel<Real><<<(unsigned)tr.n[lv], kDownThreads, 0, st>>>(
             S + (size_t)tr.off[lv - 1] * FD * FD, b + (size_t)tr.off[lv - 1] * FD, zpar, zch,
-            tr.n[lv - 1], lv == L ? p.r : nullptr, p.d);
+            tr.n[lv - 1], lv == L ? p.r : nullptr, p.d, p.stop);
         timed_end(tok, st);
         count_launch(1);
     }
@@ -707,13 +732,14 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     if (!S || !abuf) return PITN_ENOMEM;
     Real* b = S + (size_t)tr.total * FD * FD;
     Real* z = b + (size_t)tr.total * FD;
-    const size_t ctrlBytes = (size_t)(max_iter + 1) * (8 + 8 + 4) + 64;
+    const size_t ctrlBytes = (size_t)(max_iter + 1) * (8 + 8 + 4) + 64;   // + stop flag and error word
     char* ctrl = (char*)workspace(ctrlBytes, kSlotCtrl);
     if (!ctrl) return PITN_ENOMEM;
     unsigned long long* res_bits = (unsigned long long*)ctrl;
     unsigned long long* qenc = res_bits + (max_iter + 1);
     int* nonfinite = (int*)(qenc + (max_iter + 1));
     int* err_d = (int*)(ctrl + ctrlBytes - 16);
+    int* stop_d = (int*)(ctrl + ctrlBytes - 32);
     if (cudaMemsetAsync(ctrl, 0, ctrlBytes, st) != cudaSuccess) return PITN_ECUDA;
     struct HostCtl { unsigned long long res, q; int nf; int err; };
     HostCtl* hc = (HostCtl*)pinned(sizeof(HostCtl));
@@ -756,6 +782,8 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         p.o_rs = std::pow(p.o, p.rs);
     }
     p.cap = guarded ? o.guard_B : DBL_MAX;
+    p.tol = tol;
+    p.stop = stop_d;
     std::memcpy(&p.cap_bits, &p.cap, sizeof(p.cap));
     double* bufs[2] = {io.traj_dev, X1};
     int cur = 0;
@@ -771,7 +799,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         p.res_bits = res_bits + it;
         p.qenc = qenc + it;
         p.nonfinite = nonfinite + it;
-        int rc = run_iteration<Real>(p, tr, S, b, z, abuf, mixed, err_d, st);
+        int rc = run_iteration<Real>(p, tr, S, b, z, abuf, mixed, err_d, st, it == max_iter);
         if (rc != PITN_OK) return rc;
         if (cudaMemcpyAsync(&hc->res, res_bits + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&hc->q, qenc + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -843,7 +871,7 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
     cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
     CombineArgs ca;
     ca.S2 = S2; ca.b2 = b2; ca.S1 = S1; ca.b1 = b1; ca.S = S; ca.b = b;
-    ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err;
+    ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err; ca.stop = nullptr;
     auto tok = timed_begin("fkpp_compose", st);
     fk_compose_tc_kernel<<<(unsigned)n, 256, kTcSmem, st>>>(ca);
     timed_end(tok, st);
