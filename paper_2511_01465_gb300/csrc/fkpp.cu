@@ -478,96 +478,74 @@ __global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __res
 }
 
 // ---------------------------------------------------------------------------
-// C. replay: one warp per tile (4 rows per lane), exact FP64 leaves.
+// C. replay: one CTA of 128 threads per tile, one row per thread, exact FP64
+// leaves.  Neighbour rows come from the same warp by shuffles and, at the
+// four warps' edges, through shared memory (a slot per step parity and one
+// block barrier per step).  Four warps per tile keep four times as many
+// FP64 instruction streams in flight as one warp per tile would.
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(128) fk_replay_kernel(FkParams p, const Real* __restrict__ z_tiles) {
+__global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* __restrict__ z_tiles) {
     if (*p.stop) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long t = (long long)blockIdx.x * 4 + warp;
+    __shared__ double s_edge[2][2][4];   // [parity][first / last lane][warp]
+    const int row = threadIdx.x, warp = row >> 5, lane = row & 31;
+    const long long t = blockIdx.x;
+    const int d = p.d;
+    const bool live = row < d;
+    const long long k0 = 1 + t * p.TS;
+    const long long k1 = min(p.N, k0 + p.TS);
     unsigned long long my_q = 0ull;
-    if (t < p.T) {
-        const int d = p.d, r0 = 4 * lane;
-        const long long k0 = 1 + t * p.TS;
-        const long long k1 = min(p.N, k0 + p.TS);
-        double z[4], xprev[4];
+    double z = live ? (double)z_tiles[t * FD + row] : 0.0;
+    double xprev = live ? fk_x(p, k0 - 1, row) : 0.0;
+    if (t == 0 && live) {
+        // element 0: dx_1 = -r_0 (already the incoming vector of tile 0)
+        if (abs_bits(z) > p.cap_bits) my_q = ~0ull;  // ~0 = index 0
+        p.Xn[row] = xprev + z;
+    }
+    const double m2h = -2.0 * p.h;
+    // steps in groups of G: the loads of a group are issued together so their
+    // latency overlaps; the recurrence itself is serial in k
+    constexpr int G = 4;
+    int par = 0;
+    for (long long kg = k0; kg < k1; kg += G) {
+        double xc[G], rk[G];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int row = r0 + i;
-            z[i] = (row < d) ? (double)z_tiles[t * FD + row] : 0.0;
-            xprev[i] = (row < d) ? fk_x(p, k0 - 1, row) : 0.0;
+        for (int gq = 0; gq < G; ++gq) {
+            const long long k = kg + gq;
+            const bool ld = (k < k1) && live;
+            xc[gq] = ld ? fk_x(p, k, row) : 0.0;
+            rk[gq] = ld ? p.r[k * d + row] : 0.0;
         }
-        if (t == 0) {
-            // element 0: dx_1 = -r_0 (already the incoming vector of tile 0)
-            bool bad = false;
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int row = r0 + i;
-                if (row < d) {
-                    bad |= abs_bits(z[i]) > p.cap_bits;
-                    p.Xn[row] = xprev[i] + z[i];
-                }
-            }
-            if (bad) my_q = ~0ull;  // ~0 = index 0
-        }
-        // steps in groups of G: the loads of a group are issued together so
-        // their latency overlaps; the recurrence itself is serial in k
-        constexpr int G = 4;
-        const double m2h = -2.0 * p.h;
-        for (long long kg = k0; kg < k1; kg += G) {
-            double xc[G][4], rk[G][4];
-#pragma unroll
-            for (int gq = 0; gq < G; ++gq) {
-                const long long k = kg + gq;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int row = r0 + i;
-                    const bool live = (k < k1) && (row < d);
-                    xc[gq][i] = live ? fk_x(p, k, row) : 0.0;
-                    rk[gq][i] = live ? p.r[k * d + row] : 0.0;
-                }
-            }
-#pragma unroll
-            for (int gq = 0; gq < G; ++gq) {
-                const long long k = kg + gq;
-                if (k >= k1) break;
-                // dz_{k+1} = J_k dz_k - r_k with J_k = diag(a0 - 2 h x_k) + o (sub + super):
-                // 4 FP64 instructions per entry
-                double a[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) a[i] = fma(m2h, xprev[i], p.a0);
-                const double up = __shfl_up_sync(0xffffffffu, z[3], 1);
-                const double dn = __shfl_down_sync(0xffffffffu, z[0], 1);
-                double prev = (lane == 0) ? 0.0 : up;
-                double nz[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const double cur = z[i];
-                    const double nxt = (i < 3) ? z[i + 1] : ((lane == 31) ? 0.0 : dn);
-                    nz[i] = (r0 + i < d) ? fma(a[i], cur, fma(p.o, prev + nxt, -rk[gq][i])) : 0.0;
-                    prev = cur;
-                }
-                bool bad = false;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    z[i] = nz[i];
-                    const int row = r0 + i;
-                    if (row < d) {
-                        bad |= abs_bits(z[i]) > p.cap_bits;
-                        p.Xn[k * d + row] = xc[gq][i] + z[i];
-                    }
-                    xprev[i] = xc[gq][i];
-                }
-                if (bad) {
+        for (int gq = 0; gq < G; ++gq) {
+            const long long k = kg + gq;
+            if (k >= k1) break;
+            // dz_{k+1} = J_k dz_k - r_k with J_k = diag(a0 - 2 h x_k) + o (sub + super):
+            // 4 FP64 instructions per entry
+            if (lane == 0) s_edge[par][0][warp] = z;
+            if (lane == 31) s_edge[par][1][warp] = z;
+            __syncthreads();
+            double up = __shfl_up_sync(0xffffffffu, z, 1);
+            double dn = __shfl_down_sync(0xffffffffu, z, 1);
+            if (lane == 0) up = (warp > 0) ? s_edge[par][1][warp - 1] : 0.0;
+            if (lane == 31) dn = (warp < 3) ? s_edge[par][0][warp + 1] : 0.0;
+            par ^= 1;
+            const double a = fma(m2h, xprev, p.a0);
+            const double nz = live ? fma(a, z, fma(p.o, up + dn, -rk[gq])) : 0.0;
+            z = nz;
+            if (live) {
+                if (abs_bits(z) > p.cap_bits) {
                     const unsigned long long e = ~(unsigned long long)k;
                     my_q = e > my_q ? e : my_q;
                 }
+                p.Xn[k * d + row] = xc[gq] + z;
             }
+            xprev = xc[gq];
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
         my_q = o > my_q ? o : my_q;
     }
     if (lane == 0 && my_q) atomicMax(p.qenc, my_q);
@@ -707,7 +685,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
     }
     {
         auto tok = timed_begin("fkpp_replay", st);
-        fk_replay_kernel<Real><<<(unsigned)((p.T + 3) / 4), 128, 0, st>>>(p, z);
+        fk_replay_kernel<Real><<<(unsigned)p.T, FD, 0, st>>>(p, z);
         timed_end(tok, st);
         count_launch(1);
     }
