@@ -295,7 +295,7 @@ def run_ours_batch(args, rank, world, local_rank, spec):
     achieved = flops / (kms / 1e3 / nk) / 1e12 if kms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "batch iteration graph (fold, decide, replay, end)",
+                "kernel": "batch solve graph (conditional while loop over fold, decide, replay, end)",
                 "kernel_launches_per_step": kl / nk, "kernel_ms_per_launch": kms / max(kl, 1),
                 "note": "FP64 flops of the executed iterations counted from the kernel source; "
                         "peak = nominal GB300 FP64"}
@@ -475,7 +475,7 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
     ach = flops / (fwd_ms / 1e3 / nk) / 1e12 if fwd_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "batch iteration graph (forward solve)",
+                "kernel": "batch solve graph (forward solve)",
                 "kernel_launches_per_step": fwd_n / nk, "kernel_ms_per_launch": fwd_ms / max(fwd_n, 1),
                 "note": "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -59,7 +59,7 @@ struct BatchArgs {
     double* agg;            // [G][E]
     double* texcl;          // [G*block][E]
     IvpState* st;           // [B]
-    unsigned* running;      // IVPs still running after the iteration
+    unsigned* running;      // [0] IVPs still running after the iteration, [1] iterations run
     long long B, M, chunk;
     double tol;
     unsigned long long cap_bits;
@@ -483,6 +483,14 @@ using namespace pitn;
 
 namespace {
 
+// The loop condition of the batch graph: another iteration while an IVP is
+// running and at most max_iter + 1 iterations have run (so the device loop
+// always ends).
+__global__ void batch_loop_kernel(BatchArgs a, cudaGraphConditionalHandle h) {
+    const unsigned n = ++a.running[1];
+    cudaGraphSetConditional(h, (a.running[0] != 0u && n <= (unsigned)a.max_iter) ? 1u : 0u);
+}
+
 template <class Sys>
 int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned* h_running,
               double* out, int* iters_out, int* status_out, double* res_out, long long* off_out,
@@ -490,33 +498,57 @@ int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned
     const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
     batch_init_kernel<<<eg, 256, 0, st>>>(a);
     count_launch(1);
-    // one Newton iteration as a CUDA graph, replayed until no IVP is running
+    // the whole Newton loop as one CUDA graph: a conditional while node whose
+    // body is one iteration (fold, decide, replay, end) and the loop kernel
+    // that sets its condition, so the host waits once per solve
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PITN_ECUDA;
     int rc = PITN_OK;
-    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = PITN_ECUDA;
+    cudaGraphConditionalHandle cond{};
+    cudaGraph_t body = nullptr;
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess ||
+        cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault) != cudaSuccess)
+        rc = PITN_ECUDA;
+    if (rc == PITN_OK) {
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) != cudaSuccess) rc = PITN_ECUDA;
+        else body = cp.conditional.phGraph_out[0];
+    }
+    if (rc == PITN_OK &&
+        cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        rc = PITN_ECUDA;
     if (rc == PITN_OK) {
         cudaMemsetAsync(a.running, 0, sizeof(unsigned), cs);
         batch_fold_kernel<Sys><<<(unsigned)grid, block, 0, cs>>>(a);
         batch_decide_kernel<<<eg, 256, 0, cs>>>(a);
         batch_replay_kernel<Sys><<<(unsigned)grid, block, 0, cs>>>(a);
         batch_end_kernel<<<eg, 256, 0, cs>>>(a);
-        cudaMemcpyAsync(h_running, a.running, sizeof(unsigned), cudaMemcpyDeviceToHost, cs);
-        if (cudaStreamEndCapture(cs, &graph) != cudaSuccess) rc = PITN_ECUDA;
+        batch_loop_kernel<<<1, 1, 0, cs>>>(a, cond);
+        cudaGraph_t captured = nullptr;
+        if (cudaStreamEndCapture(cs, &captured) != cudaSuccess) rc = PITN_ECUDA;
     }
     if (rc == PITN_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = PITN_ECUDA;
     // the graph runs on the caller's stream (ordered after the init kernel)
     *iterations = 0;
-    for (int it = 0; rc == PITN_OK && it <= a.max_iter; ++it) {
+    if (rc == PITN_OK) {
         auto tok = timed_begin("batch", st);
-        if (cudaGraphLaunch(exec, st) != cudaSuccess) { rc = PITN_ECUDA; break; }
+        if (cudaMemsetAsync(a.running + 1, 0, sizeof(unsigned), st) != cudaSuccess ||
+            cudaGraphLaunch(exec, st) != cudaSuccess ||
+            cudaMemcpyAsync(h_running, a.running + 1, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = PITN_ECUDA;
         timed_end(tok, st);
-        count_launch(4);
-        *iterations += 1;
-        if (cudaStreamSynchronize(st) != cudaSuccess) { rc = PITN_ECUDA; break; }
-        if (*h_running == 0) break;
+        if (rc == PITN_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PITN_ECUDA;
+        if (rc == PITN_OK) {
+            *iterations = (int)*h_running;
+            count_launch(5 * (int64_t)*iterations);
+        }
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
