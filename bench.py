@@ -601,6 +601,12 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": int(wl.N * wl.d * 8), "ms_per_step": e2e_s * 1e3}
 
     roofline = roofline_for(args.workload, spec, wl, res, ktimes, nk)
+    tkey = (f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}"
+            f"{ {1: ':rk4', 2: ':be', 3: ':tr'}.get(method, '')}{':f32' if prec == 2 else ''}")
+    launch_shape = P.pitn_tune_get(tkey)   # (threads per CTA, CTAs per SM), + min steps per thread
+    if launch_shape is not None:
+        cm = P.pitn_tune_get(tkey + ":c")
+        launch_shape = list(launch_shape) + ([cm[0]] if cm is not None else [])
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -609,10 +615,7 @@ def run_ours(args, rank, world, local_rank):
                        "status": P.pitn_status_string(res.status), "final_res": res.final_res,
                        "l2": "flushed (512 MiB write) between timed steps",
                        "step_ms": [round(t, 3) for t in times],
-                       "launch_shape": P.pitn_tune_get(f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:"
-                                                       f"{1 if spec['guard_B'] > 0 else 0}"
-                                                       f"{ {1: ':rk4', 2: ':be', 3: ':tr'}.get(method, '')}"
-                                                       f"{':f32' if spec.get('precision', 0) == 2 else ''}"),
+                       "launch_shape": launch_shape,
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / nk for k, v in ktimes.items()}}

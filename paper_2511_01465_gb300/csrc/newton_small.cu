@@ -88,13 +88,14 @@ int select_small_kernel(int system_id, int method, bool mixed, pitn::SmallKernel
     return select_implicit_kernel(system_id, method, K);
 }
 
-// One solve with an explicit launch shape: `block` threads per CTA and at
-// most `per_sm_cap` co-resident CTAs per SM (cooperative launch).
+// One solve with an explicit launch shape: `block` threads per CTA, at most
+// `per_sm_cap` co-resident CTAs per SM (cooperative launch) and at least
+// `cmin` steps per thread (which bounds the grid of a short trajectory;
+// the caller's tile_elems overrides it).
 int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, double tol,
                  int max_iter, const pitn_options& o, cudaStream_t st, SolveOutcome* out, int block,
-                 int per_sm_cap) {
+                 int per_sm_cap, int cmin) {
     using namespace pitn;
-    int cmin = 4;
     if (o.tile_elems > 0) cmin = o.tile_elems;
     pitn::SmallKernel K{};
     int rc = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
@@ -199,10 +200,14 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
                   : o.method == PITN_STEP_BACKWARD_EULER ? ":be"
                   : o.method == PITN_STEP_TRAPEZOID ? ":tr" : "",
                   o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : "");
+    char ckey[104];
+    std::snprintf(ckey, sizeof(ckey), "%s:c", key);   // steps-per-thread floor of the shape
     int tb = 0, tc = 0;
     if (tune_lookup(key, &tb, &tc)) {
         block = tb;
         cap = tc;
+        int c2 = 0, unused = 0;
+        if (tune_lookup(ckey, &c2, &unused) && c2 > 0) cmin = c2;
     } else if (tune_enabled()) {
         // time every shape on this very solve; the cost per Newton pass decides.
         // A caller's guess lives in the trajectory buffer, which every trial
@@ -219,45 +224,60 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
         pitn::SmallKernel K{};
         int rk = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
         if (rk != PITN_OK) return rk;
+        // a short trajectory fills the GPU only with few steps per thread, and
+        // there the floor decides the grid: try 1, 2 and 4 steps as well
+        const bool short_n = N < 2LL * 256 * 4 * props().multiProcessorCount;
+        const int cmins_short[] = {1, 2, 4}, cmins_long[] = {4};
+        const int* cmins = short_n ? cmins_short : cmins_long;
+        const int ncm = short_n ? 3 : 1;
+        // the trials solve the same problem from the same start: the whole
+        // solve's time decides (the FP32-scan solve, an inexact Newton method,
+        // needs a number of iterations that depends on the shape)
         double best = 1e300;
-        int tried[sizeof(kSmallShapes) / sizeof(kSmallShapes[0])][2];
+        int tried[3 * sizeof(kSmallShapes) / sizeof(kSmallShapes[0])][3];
         int ntried = 0;
-        for (const auto& shp : kSmallShapes) {
-            const int eff = std::min(K.per_sm(shp[0]), shp[1]);  // CTAs per SM this shape gets
-            if (eff < 1) continue;
-            bool seen = false;
-            for (int i = 0; i < ntried; ++i) seen |= tried[i][0] == shp[0] && tried[i][1] == eff;
-            if (seen) continue;
-            tried[ntried][0] = shp[0];
-            tried[ntried][1] = eff;
-            ++ntried;
-            if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                return PITN_ECUDA;
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaEventRecord(e0, st);
-            SolveOutcome tmp;
-            const int rc = small_launch(system_id, io, h, N, d, tol, max_iter, o, st, &tmp, shp[0], shp[1]);
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            if (rc != PITN_OK) continue;
-            const double per_pass = ms / (double)(tmp.iters + 1);
-            if (per_pass < best) {
-                best = per_pass;
-                block = shp[0];
-                cap = shp[1];
+        for (int ci = 0; ci < ncm; ++ci) {
+            for (const auto& shp : kSmallShapes) {
+                const int eff = std::min(K.per_sm(shp[0]), shp[1]);  // CTAs per SM this shape gets
+                if (eff < 1) continue;
+                bool seen = false;
+                for (int i = 0; i < ntried; ++i)
+                    seen |= tried[i][0] == shp[0] && tried[i][1] == eff && tried[i][2] == cmins[ci];
+                if (seen) continue;
+                tried[ntried][0] = shp[0];
+                tried[ntried][1] = eff;
+                tried[ntried][2] = cmins[ci];
+                ++ntried;
+                if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return PITN_ECUDA;
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+                SolveOutcome tmp;
+                const int rc = small_launch(system_id, io, h, N, d, tol, max_iter, o, st, &tmp, shp[0], shp[1],
+                                            cmins[ci]);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (rc != PITN_OK) continue;
+                if (ms < best) {
+                    best = ms;
+                    block = shp[0];
+                    cap = shp[1];
+                    cmin = cmins[ci];
+                }
             }
         }
         tune_store(key, block, cap);
+        tune_store(ckey, cmin, 0);
         if (saved && cudaMemcpyAsync(io.traj_dev, saved, gbytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return PITN_ECUDA;
     }
-    return small_launch(system_id, io, h, N, d, tol, max_iter, o, st, out, block, cap);
+    return small_launch(system_id, io, h, N, d, tol, max_iter, o, st, out, block, cap, cmin);
 }
 
 }  // namespace pitn_host

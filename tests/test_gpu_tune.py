@@ -37,7 +37,10 @@ def test_tuned_single_solve(pk):
     assert P.pitn_tune_get(key) is None
     traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
     shape = P.pitn_tune_get(key)
-    assert shape is not None and shape[0] in (128, 256, 512) and 1 <= shape[1] <= 4
+    assert shape is not None and shape[0] in (128, 256, 512) and 1 <= shape[1] <= 8
+    # a short trajectory: the steps-per-thread floor is tuned too
+    cmin = P.pitn_tune_get(key + ":c")
+    assert cmin is not None and cmin[0] in (1, 2, 4)
     o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
     assert (info["iters"], info["status"]) == (o["iters"], o["status"])
     assert relerr(traj.cpu().numpy(), o["traj"]) <= 1e-10
