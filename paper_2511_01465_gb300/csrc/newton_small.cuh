@@ -233,6 +233,7 @@ __device__ __forceinline__ void block_scan(double* P, double* c, double* eP, dou
         }
 #pragma unroll
         for (int off = 1; off < kMaxWarps; off <<= 1) {
+            if (off >= nwarps) break;   // lanes from nwarps on hold identities
             double uP[D * D], uc[D];
 #pragma unroll
             for (int j = 0; j < D * D; ++j) uP[j] = __shfl_up_sync(0xffffffffu, wP[j], off);

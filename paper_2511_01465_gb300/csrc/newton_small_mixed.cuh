@@ -112,6 +112,7 @@ __device__ __forceinline__ void dz_block_scan(float* Q, float* c, float* eQ, flo
         }
 #pragma unroll
         for (int off = 1; off < kMaxWarps; off <<= 1) {
+            if (off >= nwarps) break;   // lanes from nwarps on hold identities
             float uQ[D * D], uc[D];
 #pragma unroll
             for (int j = 0; j < D * D; ++j) uQ[j] = __shfl_up_sync(0xffffffffu, wQ[j], off);
