@@ -140,6 +140,29 @@ __device__ __forceinline__ void b_flush_res(const BatchArgs& a, long long b, uns
     if (v) atomicMax(&a.st[b].res, v);
 }
 
+// Whether any IVP overlapping the steps [kf, kl) is active (stepping: has a
+// Newton step to apply).  A CTA whose steps all belong to frozen IVPs skips
+// the pass: late in a batch, when most IVPs have converged, the scans of
+// their identity elements would otherwise cost as much as real work.
+__device__ __forceinline__ bool cta_has_work(const BatchArgs& a, long long kf, long long kl, bool stepping) {
+    __shared__ int s_any;
+    if (threadIdx.x == 0) {
+        int any = 0;
+        if (kf < a.M) {
+            const long long kend = min(kl, a.M);
+            for (long long b = seg_of(a.off, a.B, kf); b < a.B && a.off[b] < kend; ++b) {
+                if (stepping ? a.st[b].stepping : a.st[b].active) {
+                    any = 1;
+                    break;
+                }
+            }
+        }
+        s_any = any;
+    }
+    __syncthreads();
+    return s_any != 0;
+}
+
 // ---- A ----------------------------------------------------------------------
 template <class Sys>
 __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
@@ -150,6 +173,16 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long k0 = gt * a.chunk;
     const long long k1 = min(a.M, k0 + a.chunk);
+    {
+        const long long kf = (long long)blockIdx.x * blockDim.x * a.chunk;
+        if (!cta_has_work(a, kf, kf + (long long)blockDim.x * a.chunk, false)) {
+            // all frozen: the CTA aggregate is the identity (no thread prefix is read)
+            if (threadIdx.x < E)
+                a.agg[(size_t)blockIdx.x * E + threadIdx.x] =
+                    (threadIdx.x < D * D && threadIdx.x % (D + 1) == 0) ? 1.0 : 0.0;
+            return;
+        }
+    }
 
     double P[D * D], c[D];
     b_identity<D>(P);
@@ -328,6 +361,7 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
     const long long k0 = gt * a.chunk;
     const long long k1 = min(a.M, k0 + a.chunk);
     const long long cta_span = (long long)blockDim.x * a.chunk;
+    if (!cta_has_work(a, (long long)blockIdx.x * cta_span, (long long)(blockIdx.x + 1) * cta_span, true)) return;
     if (threadIdx.x == 0) {
         // incoming prefix of this CTA
         double z[D];
