@@ -27,8 +27,6 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// L2-coherent load (bypasses L1, which other SMs' writes do not invalidate).
-__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 
 // Every spin-wait in the library gives up after this long and raises
 // PITN_ETIMEOUT instead of hanging the device.
@@ -87,12 +85,6 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return r;
 }
 constexpr unsigned long long kInfBitsAbs = 0x7ff0000000000000ull;  // bits of +inf
-
-// atomicMax on non-negative doubles (and NaN, which orders above +inf) via
-// their IEEE bit patterns.
-__device__ __forceinline__ void atomic_max_abs_bits(unsigned long long* p, double a) {
-    atomicMax(p, abs_bits(a));
-}
 
 }  // namespace pitn
 
