@@ -53,7 +53,10 @@ __global__ void __launch_bounds__(256) newton_fused_kernel(SmallArgs a) {
     const long long C = (N + nthreads - 1) / nthreads;
     const long long k0 = min(N, gt * C), k1 = min(N, k0 + C);
     const long long L = k1 - k0, LA = (L + 1) / 2, LB = L - LA, km = k0 + LA;
-    auto sidx = [&](long long k, int j) -> long long { return ((long long)j * a.lcap + (k - k0)) * nthreads + gt; };
+    // slot of component j of step k: (j lcap + k - k0) threads + gt, written so
+    // that a step costs one multiply and the components fixed offsets
+    const long long cstride = a.lcap * nthreads;
+    auto sidx = [&](long long k, int j) -> long long { return (k - k0) * nthreads + gt + j * cstride; };
 
     int cur = 0;
     long long q = a.q_init;

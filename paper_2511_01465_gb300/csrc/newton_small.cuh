@@ -386,7 +386,10 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         }
         const long long kreg = min(k1, max(k0, sfill));  // regular elements: [k0, kreg)
         // scratch slot of component j of this thread's i-th regular element
-        auto sidx = [&](long long i, int j) -> long long { return ((long long)j * a.lcap + i) * nthreads + gt; };
+        // slot of component j of step i: (j lcap + i) threads + gt, written so
+        // that a step costs one multiply and the components fixed offsets
+        const long long cstride = a.lcap * nthreads;
+        auto sidx = [&](long long i, int j) -> long long { return i * nthreads + gt + j * cstride; };
         // The regular part is folded as two interleaved halves A = [k0, km) and
         // B = [km, kreg): two independent FP64 dependency chains per thread.
         unsigned long long my_res = 0ull;

@@ -218,7 +218,10 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
         const long long kreg = min(k1, max(k0, sfill));
         // scratch slot of component j of this thread's i-th regular element
         // (component-major, interleaved over the threads: coalesced)
-        auto sidx = [&](long long i, int j) -> long long { return ((long long)j * a.lcap + i) * nthreads + gt; };
+        // slot of component j of step i: (j lcap + i) threads + gt, written so
+        // that a step costs one multiply and the components fixed offsets
+        const long long cstride = a.lcap * nthreads;
+        auto sidx = [&](long long i, int j) -> long long { return i * nthreads + gt + j * cstride; };
         // ---- phase 1: FP64 residual, FP32 delta fold (two interleaved halves) ----
         unsigned long long my_res = 0ull;
         const long long Lr = kreg - k0;
