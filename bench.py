@@ -40,10 +40,10 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "newton_fused_mixed.cuh", "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28925478656 + 24177816576, "a02550aa953d7e00"),        # 147 passes
-    "vdp_mixed": (13156881152 + 15277419264, "a02550aa953d7e00"),  # 137 passes (fused kernel)
-    "vdp_rk4": (29031424 + 347136512, "a02550aa953d7e00"),         # 8 passes; the 16 MB state stays in L2
-    "robertson": (13344046848 + 13704510208, "a02550aa953d7e00"),  # 22 passes
+    "vdp": (28926442752 + 24175795200, "f256e3c44be6de8f"),        # 147 passes
+    "vdp_mixed": (13101624320 + 15198681600, "f256e3c44be6de8f"),  # 137 passes (fused kernel)
+    "vdp_rk4": (29213696 + 347228928, "f256e3c44be6de8f"),         # 8 passes; the 16 MB state stays in L2
+    "robertson": (13364147456 + 13725263360, "f256e3c44be6de8f"),  # 22 passes
 }
 
 
