@@ -1,0 +1,68 @@
+"""Host logic of bench.py (no GPU): workload specs, the roofline arithmetic of
+the JSON line, the stored oracle pass counts and the CPU-baseline leg."""
+import os
+import sys
+from types import SimpleNamespace
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+SINGLE = ["vdp", "vdp_mixed", "vdp_rk4", "robertson", "osc", "lorenz", "lorenz_mixed", "fkpp", "fkpp_mixed"]
+
+
+@pytest.mark.parametrize("name", SINGLE + ["batch", "batch_small", "adjoint"])
+def test_workload_specs(name):
+    spec = bench.workload(name)
+    assert spec["kind"] in ("single", "batch", "adjoint")
+    assert spec["tol"] > 0 and spec["max_iter"] >= 1 and "desc" in spec
+    if spec["kind"] == "single":
+        wl = spec["wl"]
+        assert wl.N >= 1 and wl.d == len(wl.x0) and wl.h > 0
+        assert name in bench.SAMPLE_ITERS
+
+
+def test_unknown_workload():
+    with pytest.raises(SystemExit):
+        bench.workload("nope")
+
+
+@pytest.mark.parametrize("name", SINGLE)
+def test_oracle_passes_stored(name):
+    # every single-IVP bench workload has the oracle's own pass count stored
+    n = bench.oracle_passes(name, -1)
+    assert isinstance(n, int) and n >= 1
+
+
+def _fake_res(iters):
+    return SimpleNamespace(iters=iters, status=0, final_res=1e-9)
+
+
+@pytest.mark.parametrize("name,kern", [("vdp", "newton_small"), ("vdp_rk4", "newton_small"),
+                                       ("robertson", "newton_small"), ("vdp_mixed", "newton_small"),
+                                       ("fkpp", "fkpp_fold"), ("fkpp_mixed", "fkpp_compose")])
+def test_roofline_arithmetic(name, kern):
+    spec = bench.workload(name)
+    wl = spec["wl"]
+    steps, ms = 3, 30.0
+    rf = bench.roofline_for(name, spec, wl, _fake_res(10), {kern: (ms, steps)}, steps)
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel"):
+        assert k in rf
+    assert rf["kernel"] == kern and rf["peak"] > 0
+    assert abs(rf["frac"] - rf["achieved"] / rf["peak"]) < 1e-12
+    assert rf["bound"] in ("alu", "hbm", "tensor")
+    if kern != "newton_small":
+        assert rf["traffic"] is None
+    # the achieved rate scales inversely with the kernel time
+    rf2 = bench.roofline_for(name, spec, wl, _fake_res(10), {kern: (2 * ms, steps)}, steps)
+    assert abs(rf2["achieved"] * 2 - rf["achieved"]) <= 1e-9 * rf["achieved"]
+
+
+def test_cpu_baseline_leg(monkeypatch):
+    monkeypatch.setattr(bench, "CPU_SAMPLE_S", 0.05)
+    spec = bench.workload("lorenz")
+    cb = bench.cpu_baseline(spec, bench.oracle_passes("lorenz", 63), 3)
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0 and cb["unit"] == bench.UNIT
+    assert "residual evaluations" in cb["sample"]
