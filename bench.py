@@ -219,6 +219,16 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def batch_kernel_name(shape):
+    """The batch solver's timed kernel for a (threads per CTA, steps per
+    thread) launch shape: steps per thread 0 is the per-IVP path."""
+    if shape is None:
+        return "batch solve (untuned default launch shape)"
+    if shape[1] == 0:
+        return f"batch_ivp_kernel (persistent {shape[0]}-thread CTAs, one IVP each, longest first)"
+    return "batch solve graph (conditional while loop over fold, decide, replay, end)"
+
+
 def run_ours_batch(args, rank, world, local_rank, spec):
     import torch
     import paper_2511_01465_gb300 as pk
@@ -293,9 +303,10 @@ def run_ours_batch(args, rank, world, local_rank, spec):
     p1, p3 = SMALL_FLOPS["lorenz"]
     flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
     achieved = flops / (kms / 1e3 / nk) / 1e12 if kms > 0 else 0.0
+    shape = P.pitn_tune_get(f"batch:{bt.system}:{d}:{M.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}")
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "batch solve graph (conditional while loop over fold, decide, replay, end)",
+                "kernel": batch_kernel_name(shape),
                 "kernel_launches_per_step": kl / nk, "kernel_ms_per_launch": kms / max(kl, 1),
                 "note": "FP64 flops of the executed iterations counted from the kernel source; "
                         "peak = nominal GB300 FP64"}
@@ -358,6 +369,7 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                        "mean_newton_updates": float(it_h.mean()),
                        "step_ms": [round(x, 3) for x in times],
                        "l2": "inputs (>3 GB per trajectory buffer) larger than L2",
+                       "launch_shape": shape,
                        "parallelism": f"IVP shards x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
     return line
@@ -394,8 +406,10 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
         P.check(P.pitn_backward(bt.system, bt.B, params, x0, h, N, d, traj, None, gN, 1024, gx0, gp, opt),
                 "pitn_backward")
 
+    P.pitn_tune_enable(not args.no_tune)
     for _ in range(args.warmup):
         step()
+    P.pitn_tune_enable(False)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
@@ -473,9 +487,10 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
     p1, p3 = SMALL_FLOPS["vdp"]
     flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
     ach = flops / (fwd_ms / 1e3 / nk) / 1e12 if fwd_ms > 0 else 0.0
+    shape = P.pitn_tune_get(f"batch:{bt.system}:{d}:{M.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}")
     roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "batch solve graph (forward solve)",
+                "kernel": "forward solve: " + batch_kernel_name(shape),
                 "kernel_launches_per_step": fwd_n / nk, "kernel_ms_per_launch": fwd_ms / max(fwd_n, 1),
                 "note": "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -483,7 +498,7 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": spec["desc"], "B": bt.B, "sum_N": M, "d": d, "tol": spec["tol"],
                        "converged_ivps": int(ok.sum()), "mean_newton_updates": float(it_h.mean()),
-                       "forward_ms_per_step": fwd_ms / nk,
+                       "forward_ms_per_step": fwd_ms / nk, "launch_shape": shape,
                        "adjoint_ms_per_step": adj_ms / nk,
                        "step_ms": [round(x, 3) for x in times], "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}

@@ -59,7 +59,8 @@ struct BatchArgs {
     double* agg;            // [G][E]
     double* texcl;          // [G*block][E]
     IvpState* st;           // [B]
-    unsigned* running;      // [0] IVPs still running after the iteration, [1] iterations run
+    unsigned* running;      // [0] IVPs still running after the iteration, [1] iterations run,
+                            // [2] next IVP of the per-IVP queue
     long long B, M, chunk;
     double tol;
     unsigned long long cap_bits;
@@ -472,6 +473,252 @@ __global__ void batch_end_kernel(BatchArgs a) {
 }
 
 // ---- init / finalize --------------------------------------------------------
+// ---- per-IVP solve ----------------------------------------------------------
+// Exclusive scan of the CTA's per-thread elements in thread order (later on
+// the left): Kogge-Stone within each warp, then over the warp totals.
+template <int D>
+__device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D * D + D], double* tP,
+                                           double* tc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        double uP[D * D], uc[D];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) uP[i] = __shfl_up_sync(0xffffffffu, P[i], off);
+#pragma unroll
+        for (int i = 0; i < D; ++i) uc[i] = __shfl_up_sync(0xffffffffu, c[i], off);
+        if (lane >= off) b_compose<D>(P, c, uP, uc, P, c);
+    }
+    double eP[D * D], ec[D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) eP[i] = __shfl_up_sync(0xffffffffu, P[i], 1);
+#pragma unroll
+    for (int i = 0; i < D; ++i) ec[i] = __shfl_up_sync(0xffffffffu, c[i], 1);
+    if (lane == 0) {
+        b_identity<D>(eP);
+#pragma unroll
+        for (int i = 0; i < D; ++i) ec[i] = 0.0;
+    }
+    __syncthreads();   // s_w may still be read from the previous scan
+    if (lane == 31) {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) s_w[warp][i] = P[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) s_w[warp][D * D + i] = c[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double wP[D * D], wc[D];
+        if (lane < nwarps) {
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) wP[i] = s_w[lane][i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) wc[i] = s_w[lane][D * D + i];
+        } else {
+            b_identity<D>(wP);
+#pragma unroll
+            for (int i = 0; i < D; ++i) wc[i] = 0.0;
+        }
+#pragma unroll
+        for (int off = 1; off < kBWarps; off <<= 1) {
+            if (off >= nwarps) break;
+            double uP[D * D], uc[D];
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) uP[i] = __shfl_up_sync(0xffffffffu, wP[i], off);
+#pragma unroll
+            for (int i = 0; i < D; ++i) uc[i] = __shfl_up_sync(0xffffffffu, wc[i], off);
+            if (lane >= off) b_compose<D>(wP, wc, uP, uc, wP, wc);
+        }
+        double xP[D * D], xc[D];
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) xP[i] = __shfl_up_sync(0xffffffffu, wP[i], 1);
+#pragma unroll
+        for (int i = 0; i < D; ++i) xc[i] = __shfl_up_sync(0xffffffffu, wc[i], 1);
+        __syncwarp();
+        if (lane < nwarps) {
+            if (lane == 0) {
+                b_identity<D>(xP);
+#pragma unroll
+                for (int i = 0; i < D; ++i) xc[i] = 0.0;
+            }
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) s_w[lane][i] = xP[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) s_w[lane][D * D + i] = xc[i];
+        }
+    }
+    __syncthreads();
+    b_compose<D>(eP, ec, s_w[warp], s_w[warp] + D * D, tP, tc);
+}
+
+// One CTA solves whole IVPs, taken from a queue in the host's order (longest
+// first): the Newton loop of each IVP runs with CTA-level scans only, so no
+// IVP waits on another and nothing synchronises the grid.  Per iteration:
+// residuals, compact Jacobians and thread folds over contiguous chunks
+// (eqs. 3.8, 3.9, 3.4), the CTA scan (eq. 3.3), the decision on ||r||_inf,
+// the replay of the Newton step (eq. 3.13) into the other buffer with the
+// guard's first cut.  The IVP's record is left as the graph path leaves it.
+template <class Sys>
+__global__ void __launch_bounds__(256) batch_ivp_kernel(BatchArgs a, const long long* __restrict__ order,
+                                                        unsigned* __restrict__ queue) {
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
+    __shared__ double s_w[kBWarps][E];
+    __shared__ long long s_b;
+    __shared__ unsigned long long s_res, s_q;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned i = atomicAdd(queue, 1u);
+            s_b = (i < (unsigned long long)a.B) ? order[i] : -1;
+        }
+        __syncthreads();
+        const long long b = s_b;
+        if (b < 0) break;
+        const long long base = a.off[b], n = a.off[b + 1] - base;
+        Sys sys;
+        sys.init(a.params + b * Sys::P, a.h[b]);
+        const double* x0 = a.x0 + b * D;
+        double* Xb[2] = {a.X0 + base * D, a.X1 + base * D};
+        double* scr = a.scratch + base * W;
+        const long long C = (n + blockDim.x - 1) / blockDim.x;
+        const long long k0 = min(n, (long long)threadIdx.x * C), k1 = min(n, k0 + C);
+        int cur = 0, it = 0, status = PITN_NOT_CONVERGED;
+        long long q = 0, last_cut = n;
+        double final_res = 0.0;
+        auto state = [&](const double* X, long long j, double* o) {
+            const double* src;
+            if (j < 0) src = x0;
+            else if (j < q) src = X + j * D;
+            else if (q > 0) src = X + (q - 1) * D;
+            else src = x0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) o[i] = src[i];
+        };
+        for (;; ++it) {
+            const double* Xc = Xb[cur];
+            double* Xn = Xb[cur ^ 1];
+            if (threadIdx.x == 0) { s_res = 0ull; s_q = 0ull; }
+            // residuals, Jacobians and the thread fold
+            double P[D * D], c[D];
+            b_identity<D>(P);
+#pragma unroll
+            for (int i = 0; i < D; ++i) c[i] = 0.0;
+            unsigned long long mres = 0ull;
+            if (k0 < k1) {
+                double xp[D];
+                state(Xc, k0 - 1, xp);
+                for (long long k = k0; k < k1; ++k) {
+                    double x[D], r[D], jv[JN];
+                    state(Xc, k, x);
+                    sys.eval(xp, x, r, jv);
+#pragma unroll
+                    for (int i = 0; i < JN; ++i) scr[k * W + i] = jv[i];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        scr[k * W + JN + i] = r[i];
+                        const unsigned long long bits = abs_bits(r[i]);
+                        mres = bits > mres ? bits : mres;
+                    }
+                    if (k == 0) {
+#pragma unroll
+                        for (int i = 0; i < D * D; ++i) P[i] = 0.0;
+#pragma unroll
+                        for (int i = 0; i < D; ++i) c[i] = -r[i];
+                    } else {
+                        double tP[D * D], tc[D];
+                        sys.jmul(jv, P, tP);
+                        sys.jvec_sub(jv, c, r, tc);
+#pragma unroll
+                        for (int i = 0; i < D * D; ++i) P[i] = tP[i];
+#pragma unroll
+                        for (int i = 0; i < D; ++i) c[i] = tc[i];
+                    }
+#pragma unroll
+                    for (int i = 0; i < D; ++i) xp[i] = x[i];
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, mres, off);
+                mres = o > mres ? o : mres;
+            }
+            double tP[D * D], tc[D];
+            b_cta_scan<D>(P, c, s_w, tP, tc);   // (its barriers also order s_res's reset)
+            if (lane == 0 && mres) atomicMax(&s_res, mres);
+            __syncthreads();
+            const unsigned long long rb = s_res;
+            final_res = __longlong_as_double((long long)rb);
+            if (rb >= kInf) { status = PITN_NONFINITE; break; }
+            if (final_res <= a.tol) { status = PITN_OK; break; }
+            if (it >= a.max_iter) { status = PITN_NOT_CONVERGED; break; }
+            // replay of the Newton step from the thread's incoming vector (the
+            // element of step 0 has matrix 0, so the prefix's vector is it)
+            unsigned long long my_q = 0ull;
+            if (k0 < k1) {
+                double z[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) z[i] = tc[i];
+                bool found = false;
+                for (long long k = k0; k < k1; ++k) {
+                    double jv[JN], r[D], x[D];
+#pragma unroll
+                    for (int i = 0; i < JN; ++i) jv[i] = scr[k * W + i];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) r[i] = scr[k * W + JN + i];
+                    state(Xc, k, x);
+                    if (k == 0) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) z[i] = -r[i];
+                    } else {
+                        double tz[D];
+                        sys.jvec_sub(jv, z, r, tz);
+#pragma unroll
+                        for (int i = 0; i < D; ++i) z[i] = tz[i];
+                    }
+                    unsigned long long zb = 0ull;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        Xn[k * D + i] = x[i] + z[i];
+                        const unsigned long long bits = abs_bits(z[i]);
+                        zb = bits > zb ? bits : zb;
+                    }
+                    if (!found && zb > a.cap_bits) {
+                        found = true;
+                        my_q = ~(unsigned long long)k;
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+                my_q = o > my_q ? o : my_q;
+            }
+            if (lane == 0 && my_q) atomicMax(&s_q, my_q);
+            __syncthreads();
+            const unsigned long long qe = s_q;
+            const long long cut = qe ? (long long)(~qe) : n;
+            __syncthreads();   // s_res / s_q are reset at the top of the next iteration
+            if (!a.guarded && cut < n) { status = PITN_NONFINITE; break; }
+            q = a.guarded ? cut : n;
+            cur ^= 1;
+            last_cut = cut;
+        }
+        if (threadIdx.x == 0) {
+            IvpState s = a.st[b];
+            s.cur = cur;
+            s.q = q;
+            s.iters = it;
+            s.status = status;
+            s.final_res = final_res;
+            s.guard_index = last_cut;
+            s.active = 0;
+            s.stepping = 0;
+            a.st[b] = s;
+        }
+        __syncthreads();   // s_b is overwritten by the next pick
+    }
+}
+
 __global__ void batch_init_kernel(BatchArgs a) {
     for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < a.B;
          b += (long long)gridDim.x * blockDim.x) {
@@ -523,6 +770,33 @@ namespace {
 __global__ void batch_loop_kernel(BatchArgs a, cudaGraphConditionalHandle h) {
     const unsigned n = ++a.running[1];
     cudaGraphSetConditional(h, (a.running[0] != 0u && n <= (unsigned)a.max_iter) ? 1u : 0u);
+}
+
+// The per-IVP path: a persistent grid of CTAs takes IVPs from the queue
+// (longest first) and solves each one whole.  `iterations` reports the
+// launch count of the Newton loop (one).
+template <class Sys>
+int batch_run_ivp(BatchArgs& a, int block, cudaStream_t st, const long long* order, double* out,
+                  int* iters_out, int* status_out, double* res_out, long long* off_out, int* iterations) {
+    const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
+    batch_init_kernel<<<eg, 256, 0, st>>>(a);
+    count_launch(1);
+    if (cudaMemsetAsync(a.running + 2, 0, sizeof(unsigned), st) != cudaSuccess) return PITN_ECUDA;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ivp_kernel<Sys>, block, 0) != cudaSuccess)
+        return PITN_ECUDA;
+    if (per_sm < 1) return PITN_EUNSUPPORTED;
+    const long long grid = std::min<long long>((long long)per_sm * props().multiProcessorCount, a.B);
+    auto tok = timed_begin("batch", st);
+    batch_ivp_kernel<Sys><<<(unsigned)grid, block, 0, st>>>(a, order, a.running + 2);
+    timed_end(tok, st);
+    count_launch(1);
+    if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;
+    *iterations = 1;
+    batch_finalize_kernel<Sys::D><<<2048, 256, 0, st>>>(a, out, iters_out, status_out, res_out, off_out);
+    count_launch(1);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return PITN_ECUDA;
+    return PITN_OK;
 }
 
 template <class Sys>
@@ -651,11 +925,25 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         chunk = tc;
     } else if (o.tile_elems <= 0 && tune_enabled()) {
         tune_now = true;
+    } else if (o.tile_elems <= 0) {
+        // untuned default: the per-IVP path when no IVP is longer than one
+        // CTA's share of the steps (about four 128-thread CTAs per SM), so
+        // longest-first list scheduling keeps every CTA busy to the end
+        const long long maxN = *std::max_element(hN.begin(), hN.end());
+        const long long ctas = 4LL * props().multiProcessorCount;
+        if (maxN * ctas <= M) {
+            block = 128;
+            chunk = 0;
+        }
     }
-    static const int kShapes[][2] = {{256, 8}, {256, 16}, {256, 32}, {256, 64}, {128, 16}, {128, 32}};
-    const long long min_chunk = tune_now ? 8 : chunk;
+    // (threads per CTA, steps per thread) of the segmented-scan path; chunk 0:
+    // the per-IVP path with that many threads per CTA
+    static const int kShapes[][2] = {{256, 8}, {256, 16}, {256, 32}, {256, 64}, {128, 16}, {128, 32},
+                                     {256, 0}, {128, 0}};
+    const long long chunk_g = chunk > 0 ? chunk : 32;   // buffer sizing for the segmented path
+    const long long min_chunk = tune_now ? 8 : chunk_g;
     const long long max_threads = (M + min_chunk - 1) / min_chunk + 256;
-    const long long grid = (M + (long long)block * chunk - 1) / ((long long)block * chunk);
+    const long long grid = (M + (long long)block * chunk_g - 1) / ((long long)block * chunk_g);
     const long long grid_cap = (max_threads + 127) / 128 + 1;  // CTA count bound over all shapes
     const int JN = (system_id == PITN_LORENZ63) ? Lorenz63::JN
                    : (system_id == PITN_VDP ? VanDerPol::JN : LinearOsc::JN);
@@ -669,6 +957,7 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
                  o_st = take(sizeof(IvpState) * B), o_run = take(16),
                  o_it = take(sizeof(int) * B), o_stat = take(sizeof(int) * B),
                  o_res = take(sizeof(double) * B), o_offo = take(sizeof(long long) * (B + 1)),
+                 o_ord = take(sizeof(long long) * B),
                  o_out = out_dev ? 0 : take(sizeof(double) * (size_t)M * d);
     char* small = (char*)workspace(off, kSlotStage);
     double* X1 = (double*)workspace(sizeof(double) * (size_t)M * d, kSlotX1);
@@ -683,6 +972,14 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         return cudaMemcpyAsync(small + o2, src, bytes, kind, st) == cudaSuccess;
     };
+    // the per-IVP path's queue order: longest IVP first (list scheduling of
+    // unequal jobs on the CTAs), ties in index order
+    std::vector<long long> hord((size_t)B);
+    for (int64_t b = 0; b < B; ++b) hord[b] = b;
+    std::stable_sort(hord.begin(), hord.end(), [&](long long x, long long y) { return hN[x] > hN[y]; });
+    if (cudaMemcpyAsync(small + o_ord, hord.data(), sizeof(long long) * B, cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return PITN_ECUDA;
     if (!put(o_par, params, sizeof(double) * P * B) || !put(o_x0, x0, sizeof(double) * d * B) ||
         cudaMemcpyAsync(small + o_h, hh.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(small + o_off, hoff.data(), sizeof(long long) * (B + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
@@ -717,7 +1014,19 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     double* res_d = res_out ? (is_device_ptr(res_out) ? res_out : (double*)(small + o_res)) : nullptr;
     long long* offo_d = is_device_ptr(offsets_out) ? (long long*)offsets_out : (long long*)(small + o_offo);
 
+    const long long* ord_d = (const long long*)(small + o_ord);
+    // a shape with chunk 0 is the per-IVP path with `blk` threads per CTA
     auto run_shape = [&](int blk, long long ch, int* iters_run) -> int {
+        if (ch == 0) {
+            switch (system_id) {
+            case PITN_LORENZ63:
+                return batch_run_ivp<Lorenz63>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+            case PITN_VDP:
+                return batch_run_ivp<VanDerPol>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+            default:
+                return batch_run_ivp<LinearOsc>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d, iters_run);
+            }
+        }
         a.chunk = ch;
         const long long g = (M + (long long)blk * ch - 1) / ((long long)blk * ch);
         switch (system_id) {
@@ -730,7 +1039,7 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         }
     };
     if (tune_now) {
-        // time each shape on this batch; the cost per Newton iteration decides
+        // time each shape on this batch; the whole solve's time decides
         double best = 1e300;
         for (const auto& shp : kShapes) {
             cudaEvent_t e0, e1;
@@ -746,7 +1055,8 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (rc1 != PITN_OK) continue;
-            const double per = ms / std::max(1, its);
+            const double per = ms;
+            (void)its;
             if (per < best) {
                 best = per;
                 block = shp[0];

@@ -66,3 +66,9 @@ def test_cpu_baseline_leg(monkeypatch):
     cb = bench.cpu_baseline(spec, bench.oracle_passes("lorenz", 63), 3)
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] > 0 and cb["unit"] == bench.UNIT
     assert "residual evaluations" in cb["sample"]
+
+
+def test_batch_kernel_name():
+    assert bench.batch_kernel_name([128, 0]).startswith("batch_ivp_kernel")
+    assert "graph" in bench.batch_kernel_name([256, 32])
+    assert "default" in bench.batch_kernel_name(None)

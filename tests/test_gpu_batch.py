@@ -136,3 +136,51 @@ def test_batch_argument_errors(pk):
                             np.zeros(4, dtype=np.int64), np.zeros(3, dtype=np.int32),
                             np.zeros(3, dtype=np.int32), None, None)
     assert rc == P.PITN_EINVAL
+
+
+@pytest.mark.parametrize("block", [256, 128])
+@pytest.mark.parametrize("kind", ["vdp_plain", "lorenz_guard"])
+def test_per_ivp_path(pk, block, kind):
+    """The per-IVP path (one CTA solves each IVP whole, taken longest first)
+    pinned through the tuner's cache: the same parity bar as the segmented
+    path, lengths from 1 step to many steps per thread."""
+    from paper_2511_01465_gb300 import pitn as P
+    if kind == "vdp_plain":
+        # plain Newton on van der Pol stays rounding-robust up to ~3000 steps
+        # (longer IVPs can diverge on one side of a rounding difference)
+        rng = np.random.default_rng(5)
+        B = 24
+        bt = W.Batch("vdp", W.VDP, rng.uniform(0.5, 2.0, (B, 1)), rng.uniform(-2, 2, (B, 2)),
+                     np.full(B, 1e-3), rng.integers(1, 3000, B).astype(np.int64))
+        bt.N[:4] = [1, 2, 3, 257]
+        tol, it, gb = 1e-10, 60, 0.0
+    else:
+        bt = W.lorenz_batch(B=40, seed=3, n_min=1, n_max=3000)
+        tol, it, gb = 1e-10, 50, 100.0
+    M = int(bt.N.sum())
+    key = f"batch:{bt.system}:{bt.d}:{M.bit_length() - 1}:{1 if gb > 0 else 0}"
+    P.pitn_tune_clear()
+    P.pitn_tune_set(key, block, 0)
+    try:
+        out = run_batch(pk, bt, tol, it, gb)
+    finally:
+        P.pitn_tune_clear()
+    compare(bt, out, tol, it, gb)
+
+
+def test_default_shape_takes_per_ivp_path(pk):
+    """Untuned, a batch whose longest IVP is at most one CTA's share of the
+    steps runs on the per-IVP path (three launches: init, the persistent
+    solve, finalize) and matches the oracle IVP by IVP."""
+    from paper_2511_01465_gb300 import pitn as P
+    rng = np.random.default_rng(21)
+    B = 1500
+    bt = W.Batch("vdp", W.VDP, rng.uniform(0.5, 2.0, (B, 1)), rng.uniform(-2, 2, (B, 2)),
+                 np.full(B, 1e-3), rng.integers(40, 160, B).astype(np.int64))
+    bt.N[:3] = [1, 2, 3]
+    P.pitn_tune_clear()
+    P.pitn_tune_enable(False)
+    l0 = pk.pitn_launch_count()
+    out = run_batch(pk, bt, 1e-10, 60, 0.0)
+    assert pk.pitn_launch_count() - l0 == 3
+    compare(bt, out, 1e-10, 60, 0.0)
