@@ -153,12 +153,17 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
                   pitn_result* result);
 
 /*
- * Solve B independent IVPs of one system and uneven lengths N[b] in one
- * segmented scan per Newton iteration (not in the paper: its experiments run
- * one IVP at a time).  Each IVP runs its own Newton iteration with its own
- * stopping test; an IVP that has stopped is frozen (neither its trajectory
- * nor its count changes), and the launch sequence ends when every IVP has
- * stopped or max_iter is reached.
+ * Solve B independent IVPs of one system and uneven lengths N[b] in one call
+ * (not in the paper: its experiments run one IVP at a time).  Each IVP runs
+ * its own Newton iteration (Sec. 3) with its own stopping test; an IVP that
+ * has stopped is frozen (neither its trajectory nor its count changes), and
+ * the solve ends when every IVP has stopped or max_iter is reached.  Two
+ * device paths compute the same iteration: one segmented scan over all IVPs
+ * per Newton iteration, or one CTA per IVP running that IVP's whole loop
+ * (IVPs taken longest first).  The autotuner, or with it off the lengths
+ * (the per-IVP path when no IVP is longer than one CTA's share of the
+ * steps), choose; tile_elems > 0 forces the segmented path with that many
+ * steps per thread.
  *   params     [B][P], x0 [B][d], h [B], N [B] (each >= 1)
  *   traj_out   [sum N][d]: IVP b occupies rows offsets[b] .. offsets[b+1]-1
  *   offsets_out [B+1]: exclusive prefix sum of N (int64)
@@ -254,9 +259,10 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
  * of a configuration class -- (entry point, system, d, floor(log2 size),
  * guard on/off) -- times each candidate launch shape (threads per CTA and
  * CTAs per SM for pitn_solve; threads per CTA and steps per thread for
- * pitn_solve_batch) on the call's own inputs, keeps the fastest per Newton
- * pass in a process-wide cache, and then returns the result computed with
- * it; later solves of that class use the cached shape.  With the environment
+ * pitn_solve_batch, where 0 steps per thread is the per-IVP path) on the
+ * call's own inputs, keeps the fastest in a process-wide cache, and then
+ * returns the result computed with it; later solves of that class use the
+ * cached shape.  With the environment
  * variable PITN_TUNE_CACHE naming a file, the cache is loaded from and saved
  * to that file.  A user guess is saved and put back around the trials.
  * Different shapes associate the scan differently, so results may differ in
