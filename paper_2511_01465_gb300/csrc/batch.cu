@@ -60,7 +60,7 @@ struct BatchArgs {
     double* texcl;          // [G*block][E]
     IvpState* st;           // [B]
     unsigned* running;      // [0] IVPs still running after the iteration, [1] iterations run,
-                            // [2] next IVP of the per-IVP queue
+                            // [2..3] next IVP of the per-IVP queue (64-bit)
     long long B, M, chunk;
     double tol;
     unsigned long long cap_bits;
@@ -560,7 +560,7 @@ __device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D
 // guard's first cut.  The IVP's record is left as the graph path leaves it.
 template <class Sys>
 __global__ void __launch_bounds__(256) batch_ivp_kernel(BatchArgs a, const long long* __restrict__ order,
-                                                        unsigned* __restrict__ queue) {
+                                                        unsigned long long* __restrict__ queue) {
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
     __shared__ double s_w[kBWarps][E];
     __shared__ long long s_b;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(256) batch_ivp_kernel(BatchArgs a, const long 
     const int lane = threadIdx.x & 31;
     for (;;) {
         if (threadIdx.x == 0) {
-            const unsigned i = atomicAdd(queue, 1u);
+            const unsigned long long i = atomicAdd(queue, 1ull);
             s_b = (i < (unsigned long long)a.B) ? order[i] : -1;
         }
         __syncthreads();
@@ -781,14 +781,16 @@ int batch_run_ivp(BatchArgs& a, int block, cudaStream_t st, const long long* ord
     const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
     batch_init_kernel<<<eg, 256, 0, st>>>(a);
     count_launch(1);
-    if (cudaMemsetAsync(a.running + 2, 0, sizeof(unsigned), st) != cudaSuccess) return PITN_ECUDA;
+    // the queue counter: 64 bits at byte 8 of the 16-byte `running` slot
+    unsigned long long* queue = reinterpret_cast<unsigned long long*>(a.running + 2);
+    if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return PITN_ECUDA;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ivp_kernel<Sys>, block, 0) != cudaSuccess)
         return PITN_ECUDA;
     if (per_sm < 1) return PITN_EUNSUPPORTED;
     const long long grid = std::min<long long>((long long)per_sm * props().multiProcessorCount, a.B);
     auto tok = timed_begin("batch", st);
-    batch_ivp_kernel<Sys><<<(unsigned)grid, block, 0, st>>>(a, order, a.running + 2);
+    batch_ivp_kernel<Sys><<<(unsigned)grid, block, 0, st>>>(a, order, queue);
     timed_end(tok, st);
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;
