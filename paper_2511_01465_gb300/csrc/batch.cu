@@ -69,6 +69,7 @@ struct BatchArgs {
 
 constexpr unsigned long long kInf = 0x7ff0000000000000ull;
 constexpr int kBWarps = 8;
+constexpr int kIvpWarps = 16;   // per-IVP path: up to 512 threads per CTA
 
 template <int D>
 __device__ __forceinline__ void b_identity(double* P) {
@@ -520,7 +521,7 @@ __device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D
             for (int i = 0; i < D; ++i) wc[i] = 0.0;
         }
 #pragma unroll
-        for (int off = 1; off < kBWarps; off <<= 1) {
+        for (int off = 1; off < kIvpWarps; off <<= 1) {
             if (off >= nwarps) break;
             double uP[D * D], uc[D];
 #pragma unroll
@@ -559,10 +560,10 @@ __device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D
 // the replay of the Newton step (eq. 3.13) into the other buffer with the
 // guard's first cut.  The IVP's record is left as the graph path leaves it.
 template <class Sys>
-__global__ void __launch_bounds__(256) batch_ivp_kernel(BatchArgs a, const long long* __restrict__ order,
+__global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long long* __restrict__ order,
                                                         unsigned long long* __restrict__ queue) {
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
-    __shared__ double s_w[kBWarps][E];
+    __shared__ double s_w[kIvpWarps][E];
     __shared__ long long s_b;
     __shared__ unsigned long long s_res, s_q;
     const int lane = threadIdx.x & 31;
@@ -941,7 +942,7 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     // (threads per CTA, steps per thread) of the segmented-scan path; chunk 0:
     // the per-IVP path with that many threads per CTA
     static const int kShapes[][2] = {{256, 8}, {256, 16}, {256, 32}, {256, 64}, {128, 16}, {128, 32},
-                                     {256, 0}, {128, 0}};
+                                     {512, 0}, {256, 0}, {128, 0}, {64, 0}};
     const long long chunk_g = chunk > 0 ? chunk : 32;   // buffer sizing for the segmented path
     const long long min_chunk = tune_now ? 8 : chunk_g;
     const long long max_threads = (M + min_chunk - 1) / min_chunk + 256;

@@ -138,7 +138,7 @@ def test_batch_argument_errors(pk):
     assert rc == P.PITN_EINVAL
 
 
-@pytest.mark.parametrize("block", [256, 128])
+@pytest.mark.parametrize("block", [512, 256, 128, 64])
 @pytest.mark.parametrize("kind", ["vdp_plain", "lorenz_guard"])
 def test_per_ivp_path(pk, block, kind):
     """The per-IVP path (one CTA solves each IVP whole, taken longest first)
