@@ -141,25 +141,48 @@ constexpr uint32_t kLoadChunk = 16384;  // bytes per bulk copy
 
 // One compose by a CTA of 128 or 256 threads (with 256, two threads share a
 // row in the epilogue, each taking 64 columns).  Returns false if the MMA
-// completion wait timed out.
+// completion wait timed out.  `phase` is the parity of this CTA's MMA
+// completions so far (and of its bulk loads: bulk loads only in the CTA's
+// first compose).  bulk = false reads the inputs with L2 loads instead, for
+// inputs that other CTAs of the same launch wrote (ordered by the caller's
+// acquire).
 __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restrict__ S2,
                                            const float* __restrict__ b2, const float* __restrict__ S1,
                                            const float* __restrict__ b1, float* __restrict__ So,
-                                           float* __restrict__ bo, uint32_t phase) {
+                                           float* __restrict__ bo, uint32_t phase, bool bulk = true) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    // both inputs by bulk copies; b1 by plain loads meanwhile
-    if (tid == 0) {
-        mbar_expect_tx(&sm.mbar_ld, 2 * kMatBytes);
-        for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk) {
-            bulk_load(reinterpret_cast<uint8_t*>(sm.S2f) + o, reinterpret_cast<const uint8_t*>(S2) + o,
-                      kLoadChunk, &sm.mbar_ld);
-            bulk_load(reinterpret_cast<uint8_t*>(sm.S1f) + o, reinterpret_cast<const uint8_t*>(S1) + o,
-                      kLoadChunk, &sm.mbar_ld);
+    bool ok = true;
+    if (bulk) {
+        // both inputs by bulk copies; b1 by plain loads meanwhile
+        if (tid == 0) {
+            mbar_expect_tx(&sm.mbar_ld, 2 * kMatBytes);
+            for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk) {
+                bulk_load(reinterpret_cast<uint8_t*>(sm.S2f) + o, reinterpret_cast<const uint8_t*>(S2) + o,
+                          kLoadChunk, &sm.mbar_ld);
+                bulk_load(reinterpret_cast<uint8_t*>(sm.S1f) + o, reinterpret_cast<const uint8_t*>(S1) + o,
+                          kLoadChunk, &sm.mbar_ld);
+            }
         }
+        if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
+        ok = mbar_wait(&sm.mbar_ld, phase);
+        if (!ok) (void)mbar_wait(&sm.mbar_ld, phase);  // give the copies a second bounded wait; still a failure
+    } else {
+        // 16-byte asynchronous copies through L2, all in flight at once
+        const float4* s2 = reinterpret_cast<const float4*>(S2);
+        const float4* s1 = reinterpret_cast<const float4*>(S1);
+        float4* d2 = reinterpret_cast<float4*>(sm.S2f);
+        float4* d1 = reinterpret_cast<float4*>(sm.S1f);
+        for (int i = tid; i < kDim * kDim / 4; i += blockDim.x) {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"(smem_addr(d2 + i)), "l"(s2 + i) : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"(smem_addr(d1 + i)), "l"(s1 + i) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
     }
-    if (tid < kDim) sm.b1[tid] = b1[tid];
-    bool ok = mbar_wait(&sm.mbar_ld, phase);
-    if (!ok) (void)mbar_wait(&sm.mbar_ld, phase);  // give the copies a second bounded wait; still a failure
     // A(m, k) = S2[m][k] = S2 column-major [k][m]: thread gathers 8 consecutive
     // k of one row m (conflict-free across the warp) into one 16-byte core row
     for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
@@ -223,7 +246,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
     if (tid < kDim) {
         // S2 b1 from the staged BF16 row of S2 (the same operand the product
         // used), FP32 accumulation
-        float s = b2[m] + sm.b1[m];
+        float s = __ldcg(b2 + m) + sm.b1[m];
 #pragma unroll 4
         for (int kc = 0; kc < kDim; kc += 8) {
             const uint4 pk = *reinterpret_cast<const uint4*>(sm.A + core_off(m, kc));

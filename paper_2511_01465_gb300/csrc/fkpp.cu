@@ -40,6 +40,7 @@ namespace pitn {
 
 constexpr int FD = 128;  // padded state dimension
 constexpr int FK_TS = 64;  // elements per tile
+constexpr int kFkMaxLevels = 40;  // tree levels (2^40 tiles: far above the step limit)
 
 struct FkParams {
     const double* X;   // current iterate [N][d]
@@ -62,6 +63,9 @@ struct FkParams {
     unsigned long long* res_bits;  // this iteration's slot
     int* nonfinite;
     unsigned long long* qenc;
+    unsigned* cnt;     // up-sweep arrival counters, one per tree node (zero between passes)
+    int L;             // levels of the aggregate tree above the tiles
+    long long toff[kFkMaxLevels + 1];  // node offset of each level in S / b (level 0: the tiles)
 };
 
 __device__ __forceinline__ double fk_x(const FkParams& p, long long k, int i) {
@@ -432,49 +436,143 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     if (warp == 0) tc::tmem_dealloc(sm.tmem, FD);
 }
 
+// The whole up-sweep of the mixed-precision tree in one launch: one CTA per
+// level-1 node.  A CTA composes its node, then climbs: it counts itself in
+// the parent's arrival counter, and the second of the two children to
+// arrive composes the parent (a lone child's CTA climbs without counting).
+// The first to arrive leaves, so no CTA ever waits on another.  Inputs that
+// another CTA wrote are read through L2 after the counter's acquire; the
+// second arrival resets the counter for the next pass.  The climb stops
+// below the root, whose aggregate nothing reads.
+struct UpArgs {
+    float* S;
+    float* b;
+    long long off[kFkMaxLevels + 1];
+    long long n[kFkMaxLevels + 1];
+    int L;
+    unsigned* cnt;   // one arrival counter per node, indexed like S / b
+    int* err;
+    const int* stop;
+};
+
+__global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    tc::ComposeSmem& sm =
+        *reinterpret_cast<tc::ComposeSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    __shared__ int s_go;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const size_t MM = (size_t)FD * FD;
+    if (*a.stop) return;
+    if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
+    if (tid == 0) {
+        tc::mbar_init(&sm.mbar, 1);
+        tc::mbar_init(&sm.mbar_ld, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    long long m = blockIdx.x;
+    unsigned composes = 0;
+    for (int lv = 1; lv < a.L; ++lv) {
+        const long long n_in = a.n[lv - 1];
+        const float* Sin = a.S + (size_t)a.off[lv - 1] * MM;
+        const float* bin = a.b + (size_t)a.off[lv - 1] * FD;
+        float* So = a.S + (size_t)(a.off[lv] + m) * MM;
+        float* bo = a.b + (size_t)(a.off[lv] + m) * FD;
+        if ((n_in & 1) && m == n_in / 2) {
+            // lone earlier child (written by an earlier launch or by this CTA)
+            const float4* __restrict__ src = reinterpret_cast<const float4*>(Sin + (size_t)(2 * m) * MM);
+            float4* __restrict__ dst = reinterpret_cast<float4*>(So);
+            constexpr int U = 4;   // loads in flight per thread
+            for (int i0 = tid; i0 < (int)(MM / 4); i0 += U * blockDim.x) {
+                float4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < (int)(MM / 4)) v[u] = __ldcg(src + i);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < (int)(MM / 4)) dst[i] = v[u];
+                }
+            }
+            if (tid < FD) bo[tid] = __ldcg(bin + (2 * m) * FD + tid);
+        } else {
+            const bool ok = tc::compose_tc(sm, Sin + (size_t)(2 * m + 1) * MM, bin + (2 * m + 1) * FD,
+                                           Sin + (size_t)(2 * m) * MM, bin + (2 * m) * FD, So, bo,
+                                           composes & 1u, lv == 1);
+            ++composes;
+            if (!ok && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
+        }
+        if (lv + 1 >= a.L) break;
+        // release this node, then climb if both children of the parent are done
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            int go = 1;
+            const long long n_here = a.n[lv];
+            if (!((n_here & 1) && m == n_here - 1)) {
+                unsigned* c = a.cnt + a.off[lv + 1] + m / 2;
+                go = (atomicAdd(c, 1u) == 1u) ? 1 : 0;
+                if (go) {
+                    *c = 0u;
+                    __threadfence();
+                }
+            }
+            s_go = go;
+        }
+        __syncthreads();
+        if (!s_go) break;
+        m >>= 1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(sm.tmem, FD);
+}
+
 // ---------------------------------------------------------------------------
-// B2. down-sweep: z(child 2m) = z(m); z(child 2m+1) = z(m) + S_{2m} z(m) + b_{2m}.
-// kDownParts threads share a row: part p sums k in [p FD/kDownParts, ...) with
-// its own loads in flight, the parts meet in shared memory.
+// B2. down-sweep, inside the replay: the incoming vector of tile t follows the
+// path from the root to the leaf.  The root's is -r_0 (dx_1 = -h_1, the head
+// element a_0 = (0, -r_0)); going down to a left child keeps it, going down to
+// a right child c applies the left sibling's aggregate:
+// z <- z + S_{c-1} z + b_{c-1} (the operator of eq. 3.3 in the delta form).
+// Each of the FD threads owns one row; the row's dot product runs as
+// kDownParts partial chains over quarters of k, added in order, so the
+// result does not depend on which tile computes a node's vector.
 // ---------------------------------------------------------------------------
 constexpr int kDownParts = 4;
-constexpr int kDownThreads = FD * kDownParts;
 
 template <typename Real>
-__global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __restrict__ S_child,
-                                                               const Real* __restrict__ b_child,
-                                                               const Real* __restrict__ z_parent,
-                                                               Real* __restrict__ z_child, long long n_child,
-                                                               const double* __restrict__ r0, int d,
-                                                               const int* __restrict__ stop) {
-    if (*stop) return;
-    __shared__ Real zs[FD];
-    __shared__ Real part[kDownParts][FD];
-    const long long m = blockIdx.x;
-    const int i = threadIdx.x % FD, pt = threadIdx.x / FD;
-    if (pt == 0) {
-        Real zi;
-        if (r0) zi = (i < d) ? (Real)(-r0[i]) : (Real)0.0;  // root: dx_1 = -h_1
-        else zi = z_parent[m * FD + i];
-        zs[i] = zi;
-        z_child[(2 * m) * FD + i] = zi;
-    }
-    __syncthreads();
-    if (2 * m + 1 < n_child) {
-        const Real* S = S_child + (size_t)(2 * m) * FD * FD;
-        constexpr int KP = FD / kDownParts;
-        Real s = 0;
-#pragma unroll 8
-        for (int k = pt * KP; k < (pt + 1) * KP; ++k) s = fma(S[(size_t)k * FD + i], zs[k], s);
-        part[pt][i] = s;
+__device__ __forceinline__ Real fk_tile_z(const FkParams& p, const Real* __restrict__ S,
+                                          const Real* __restrict__ b, long long t, int row, Real* zs) {
+    Real z = (row < p.d) ? (Real)(-p.r[row]) : (Real)0.0;
+    for (int lv = p.L; lv >= 1; --lv) {
+        const long long c = t >> (lv - 1);
+        if (!(c & 1)) continue;
+        const long long node = p.toff[lv - 1] + c - 1;
+        const Real* Sn = S + (size_t)node * FD * FD;
+        __syncthreads();   // zs may still be read from the previous right turn
+        zs[row] = z;
         __syncthreads();
-        if (pt == 0) {
-            Real t = zs[i] + b_child[(2 * m) * FD + i];
+        constexpr int KP = FD / kDownParts;
+        Real part[kDownParts];
 #pragma unroll
-            for (int q = 0; q < kDownParts; ++q) t += part[q][i];
-            z_child[(2 * m + 1) * FD + i] = t;
+        for (int pt = 0; pt < kDownParts; ++pt) part[pt] = 0;
+#pragma unroll 8
+        for (int k = 0; k < KP; ++k) {
+#pragma unroll
+            for (int pt = 0; pt < kDownParts; ++pt)
+                part[pt] = fma(Sn[(size_t)(pt * KP + k) * FD + row], zs[pt * KP + k], part[pt]);
         }
+        Real tz = z + b[(size_t)node * FD + row];
+#pragma unroll
+        for (int pt = 0; pt < kDownParts; ++pt) tz += part[pt];
+        z = tz;
     }
+    return z;
 }
 
 // ---------------------------------------------------------------------------
@@ -485,9 +583,11 @@ __global__ void __launch_bounds__(kDownThreads) fk_down_kernel(const Real* __res
 // FP64 instruction streams in flight as one warp per tile would.
 // ---------------------------------------------------------------------------
 template <typename Real>
-__global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* __restrict__ z_tiles) {
+__global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* __restrict__ S,
+                                                       const Real* __restrict__ b) {
     if (*p.stop) return;
     __shared__ double s_edge[2][2][4];   // [parity][first / last lane][warp]
+    __shared__ Real s_z[FD];
     const int row = threadIdx.x, warp = row >> 5, lane = row & 31;
     const long long t = blockIdx.x;
     const int d = p.d;
@@ -495,7 +595,8 @@ __global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* _
     const long long k0 = 1 + t * p.TS;
     const long long k1 = min(p.N, k0 + p.TS);
     unsigned long long my_q = 0ull;
-    double z = live ? (double)z_tiles[t * FD + row] : 0.0;
+    const Real zt = fk_tile_z<Real>(p, S, b, t, row, s_z);
+    double z = live ? (double)zt : 0.0;
     double xprev = live ? fk_x(p, k0 - 1, row) : 0.0;
     if (t == 0 && live) {
         // element 0: dx_1 = -r_0 (already the incoming vector of tile 0)
@@ -606,7 +707,7 @@ Tree make_tree(long long T) {
 }
 
 template <typename Real>
-int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* abuf, bool mixed,
+int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, bool mixed,
                   int* err, cudaStream_t st, bool residual_only) {
     const size_t smemA = fold_smem_bytes<Real>(p.TS);
     {
@@ -626,33 +727,37 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
         timed_end(tok, st);
         count_launch(1);
     }
-    // up-sweep
-    for (size_t lv = 1; lv < tr.n.size(); ++lv) {
-        LevelArgs la;
-        la.S_in = S + (size_t)tr.off[lv - 1] * FD * FD;
-        la.b_in = b + (size_t)tr.off[lv - 1] * FD;
-        la.S_out = S + (size_t)tr.off[lv] * FD * FD;
-        la.b_out = b + (size_t)tr.off[lv] * FD;
-        la.n_in = tr.n[lv - 1];
-        la.stop = p.stop;
-        auto tok = timed_begin("fkpp_compose", st);
-        if (mixed) {
-            CombineArgs ca;
-            const float* Sin = (const float*)la.S_in;
-            const float* bin = (const float*)la.b_in;
-            ca.S1 = Sin;
-            ca.b1 = bin;
-            ca.S2 = Sin + (size_t)FD * FD;
-            ca.b2 = bin + FD;
-            ca.S = (float*)la.S_out;
-            ca.b = (float*)la.b_out;
-            ca.n = tr.n[lv];
-            ca.stride_in = 2;
-            ca.n_lone = (la.n_in & 1) ? la.n_in / 2 : -1;
-            ca.err = err;
-            ca.stop = p.stop;
-            fk_compose_tc_kernel<<<(unsigned)tr.n[lv], 256, kTcSmem, st>>>(ca);
-        } else {
+    // up-sweep, levels 1 .. L-1 (the root's aggregate is never read: the
+    // replay's walk applies only left siblings)
+    const int L = (int)tr.n.size() - 1;
+    if (mixed) {
+        if (L >= 2) {
+            UpArgs ua;
+            ua.S = reinterpret_cast<float*>(S);
+            ua.b = reinterpret_cast<float*>(b);
+            for (int lv = 0; lv <= L; ++lv) {
+                ua.off[lv] = tr.off[lv];
+                ua.n[lv] = tr.n[lv];
+            }
+            ua.L = L;
+            ua.cnt = p.cnt;
+            ua.err = err;
+            ua.stop = p.stop;
+            auto tok = timed_begin("fkpp_compose", st);
+            fk_upsweep_tc_kernel<<<(unsigned)tr.n[1], 256, kTcSmem, st>>>(ua);
+            timed_end(tok, st);
+            count_launch(1);
+        }
+    } else {
+        for (int lv = 1; lv < L; ++lv) {
+            LevelArgs la;
+            la.S_in = S + (size_t)tr.off[lv - 1] * FD * FD;
+            la.b_in = b + (size_t)tr.off[lv - 1] * FD;
+            la.S_out = S + (size_t)tr.off[lv] * FD * FD;
+            la.b_out = b + (size_t)tr.off[lv] * FD;
+            la.n_in = tr.n[lv - 1];
+            la.stop = p.stop;
+            auto tok = timed_begin("fkpp_compose", st);
             // column block per CTA: enough CTAs for two per SM where the level allows
             const long long nodes = tr.n[lv];
             const int cpt = nodes >= 76 ? 4 : (nodes >= 19 ? 2 : 1);
@@ -661,31 +766,13 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* z, Real* 
             if (cpt == 4) fk_compose_f64<4><<<grid, 256, sm, st>>>(la);
             else if (cpt == 2) fk_compose_f64<2><<<grid, 256, sm, st>>>(la);
             else fk_compose_f64<1><<<grid, 256, sm, st>>>(la);
+            timed_end(tok, st);
+            count_launch(1);
         }
-        timed_end(tok, st);
-        count_launch(1);
-    }
-    // down-sweep
-    const int L = (int)tr.n.size() - 1;
-    if (L == 0) {
-        auto tok = timed_begin("fkpp_down", st);
-        fk_down_kernel<Real><<<1, kDownThreads, 0, st>>>(S, b, z, z, 1, p.r, p.d, p.stop);  // z(tile 0) = -r_0
-        timed_end(tok, st);
-        count_launch(1);
-    }
-    for (int lv = L; lv >= 1; --lv) {
-        const Real* zpar = z + (size_t)tr.off[lv] * FD;
-        Real* zch = z + (size_t)tr.off[lv - 1] * FD;
-        auto tok = timed_begin("fkpp_down", st);
-        fk_down_kernel<Real><<<(unsigned)tr.n[lv], kDownThreads, 0, st>>>(
-            S + (size_t)tr.off[lv - 1] * FD * FD, b + (size_t)tr.off[lv - 1] * FD, zpar, zch,
-            tr.n[lv - 1], lv == L ? p.r : nullptr, p.d, p.stop);
-        timed_end(tok, st);
-        count_launch(1);
     }
     {
         auto tok = timed_begin("fkpp_replay", st);
-        fk_replay_kernel<Real><<<(unsigned)p.T, FD, 0, st>>>(p, z);
+        fk_replay_kernel<Real><<<(unsigned)p.T, FD, 0, st>>>(p, S, b);
         timed_end(tok, st);
         count_launch(1);
     }
@@ -698,19 +785,19 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     const int TS = FK_TS;
     const long long T = std::max(1LL, (long long)((N - 1 + TS - 1) / TS));
     Tree tr = make_tree(T);
-    // scratch: X1 | r ; aggregates S | b | z ; control
+    // scratch: X1 | r ; aggregates S | b ; control
     const size_t nd = (size_t)N * d;
     double* X1 = (double*)workspace(nd * sizeof(double) * 2, kSlotX1);
     if (!X1) return PITN_ENOMEM;
     double* r = X1 + nd;
-    const size_t aggBytes = (size_t)tr.total * FD * FD * sizeof(Real) +
-                            2 * (size_t)tr.total * FD * sizeof(Real);
+    const size_t aggBytes = (size_t)tr.total * FD * FD * sizeof(Real) + (size_t)tr.total * FD * sizeof(Real);
     Real* S = (Real*)workspace(aggBytes, kSlotAux);
     Real* abuf = (Real*)workspace((size_t)N * FD * sizeof(Real), kSlotAux2);
     if (!S || !abuf) return PITN_ENOMEM;
     Real* b = S + (size_t)tr.total * FD * FD;
-    Real* z = b + (size_t)tr.total * FD;
-    const size_t ctrlBytes = (size_t)(max_iter + 1) * (8 + 8 + 4) + 64;   // + stop flag and error word
+    // per-pass slots | up-sweep arrival counters | stop flag and error word
+    const size_t cntOff = ((size_t)(max_iter + 1) * (8 + 8 + 4) + 15) & ~(size_t)15;
+    const size_t ctrlBytes = cntOff + (((size_t)tr.total * sizeof(unsigned) + 15) & ~(size_t)15) + 64;
     char* ctrl = (char*)workspace(ctrlBytes, kSlotCtrl);
     if (!ctrl) return PITN_ENOMEM;
     unsigned long long* res_bits = (unsigned long long*)ctrl;
@@ -733,6 +820,8 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         cudaFuncSetAttribute(fk_compose_f64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((FD * FD + 8 * FD) * sizeof(double)));
         cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmem);
+        cudaFuncSetAttribute(fk_upsweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTcSmem);
     }
 
@@ -762,7 +851,11 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     p.cap = guarded ? o.guard_B : DBL_MAX;
     p.tol = tol;
     p.stop = stop_d;
+    p.cnt = (unsigned*)(ctrl + cntOff);
     std::memcpy(&p.cap_bits, &p.cap, sizeof(p.cap));
+    if ((int)tr.n.size() - 1 > kFkMaxLevels) return PITN_EINVAL;
+    p.L = (int)tr.n.size() - 1;
+    for (int lv = 0; lv <= p.L; ++lv) p.toff[lv] = tr.off[lv];
     double* bufs[2] = {io.traj_dev, X1};
     int cur = 0;
     long long q = io.have_guess ? N : 0;
@@ -777,7 +870,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         p.res_bits = res_bits + it;
         p.qenc = qenc + it;
         p.nonfinite = nonfinite + it;
-        int rc = run_iteration<Real>(p, tr, S, b, z, abuf, mixed, err_d, st, it == max_iter);
+        int rc = run_iteration<Real>(p, tr, S, b, abuf, mixed, err_d, st, it == max_iter);
         if (rc != PITN_OK) return rc;
         if (cudaMemcpyAsync(&hc->res, res_bits + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&hc->q, qenc + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
