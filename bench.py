@@ -637,6 +637,29 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def fk_tiles(N, sms=152, per_sm=1):
+    """Tiles of the FKPP scan, as the library picks them: 64 steps, shortened
+    once there is a full wave so that the count is a whole number of waves of
+    the fold (one 1024-thread FP32 or 512-thread FP64 CTA per SM)."""
+    ts = 64
+    t0 = (N - 1 + 63) // 64
+    slots = sms * per_sm
+    if t0 >= slots:
+        tw = (t0 + slots - 1) // slots * slots
+        ts = (N - 1 + tw - 1) // tw
+    return max(1, (N - 1 + ts - 1) // ts)
+
+
+def fk_composes(T):
+    """Dense composes of one up-sweep over T tiles: every level below the root
+    pairs its nodes (a lone last node is copied); the root is not composed."""
+    n, total = T, 0
+    while n > 2:
+        total += n // 2
+        n = (n + 1) // 2
+    return total
+
+
 def roofline_for(name, spec, wl, res, ktimes, steps):
     """Roofline of the kernel family with the largest device time."""
     kern = max(ktimes, key=lambda k: ktimes[k][0])
@@ -696,8 +719,7 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
                 "; peak from unit counts and clocks")
     elif kern == "fkpp_compose":
         mixed = spec.get("precision", 0) == 1
-        T = (wl.N - 1 + 63) // 64
-        flops = (T - 1) * FK_COMPOSE_FLOPS * res.iters
+        flops = fk_composes(fk_tiles(wl.N)) * FK_COMPOSE_FLOPS * res.iters
         if mixed:
             _, bf16, _, src = load_peaks()
             peak, bound, unit = bf16, "tensor", "TFLOP/s"

@@ -782,7 +782,27 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, boo
 template <typename Real>
 int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int max_iter,
                  const pitn_options& o, cudaStream_t st, SolveOutcome* out, bool mixed) {
-    const int TS = FK_TS;
+    // Tile length: FK_TS steps, shortened once there is at least one full wave
+    // of tiles so that the tile count is a whole number of waves of the fold
+    // (one CTA per tile; the replay has one per tile too).
+    int TS = FK_TS;
+    {
+        const int smem0 = (int)fold_smem_bytes<Real>(FK_TS);
+        int per_sm = 0;
+        if (cudaFuncSetAttribute(fk_fold_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem0) ==
+                cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk_fold_kernel<Real>,
+                                                          FoldTraits<Real>::THREADS, smem0) == cudaSuccess &&
+            per_sm > 0) {
+            const long long slots = (long long)per_sm * props().multiProcessorCount;
+            const long long T0 = (N - 1 + FK_TS - 1) / FK_TS;
+            if (T0 >= slots) {
+                const long long Tw = (T0 + slots - 1) / slots * slots;
+                TS = (int)((N - 1 + Tw - 1) / Tw);
+            }
+        }
+        cudaGetLastError();
+    }
     const long long T = std::max(1LL, (long long)((N - 1 + TS - 1) / TS));
     Tree tr = make_tree(T);
     // scratch: X1 | r ; aggregates S | b ; control

@@ -72,3 +72,16 @@ def test_batch_kernel_name():
     assert bench.batch_kernel_name([128, 0]).startswith("batch_ivp_kernel")
     assert "graph" in bench.batch_kernel_name([256, 32])
     assert "default" in bench.batch_kernel_name(None)
+
+
+def test_fkpp_tree_counts():
+    # 2^15 steps: 512 tiles of 64 make 3.4 waves on 152 SMs; 607 tiles of 54 make 4
+    assert bench.fk_tiles(1 << 15) == 607
+    assert bench.fk_tiles(65) == 1 and bench.fk_tiles(130) == 3
+    # below one wave the tiles stay at 64 steps
+    assert bench.fk_tiles(64 * 100 + 1) == 100
+    # composes: levels below the root pair their nodes; the root is not composed
+    assert bench.fk_composes(1) == 0 and bench.fk_composes(2) == 0
+    assert bench.fk_composes(3) == 1       # 3 -> 2 (one compose + a lone copy) -> root
+    assert bench.fk_composes(8) == 4 + 2   # 8 -> 4 -> 2 -> root
+    assert bench.fk_composes(512) == 256 + 128 + 64 + 32 + 16 + 8 + 4 + 2
