@@ -282,7 +282,7 @@ int pitn_tune_set(const char* key, int a, int b);
  * library is bracketed by CUDA events on its stream; pitn_timing_get returns
  * the summed device time and launch count of one kernel family since the
  * last reset (names: "newton_small", "fkpp_residual", "fkpp_fold", "fkpp_compose",
- * "fkpp_down", "fkpp_replay", "batch", "adjoint").  Timing adds two event
+ * "fkpp_replay", "batch", "adjoint").  Timing adds two event
  * records per launch; it is off by default. */
 int pitn_timing_enable(int on);
 int pitn_timing_reset(void);

@@ -839,8 +839,6 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
                              (int)((FD * FD + 16 * FD) * sizeof(double)));
         cudaFuncSetAttribute(fk_compose_f64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((FD * FD + 8 * FD) * sizeof(double)));
-        cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmem);
         cudaFuncSetAttribute(fk_upsweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTcSmem);
     }
