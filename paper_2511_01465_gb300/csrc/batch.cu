@@ -1042,6 +1042,15 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         }
     };
     if (tune_now) {
+        // one untimed solve on each path first: a kernel's first launch also
+        // loads its code (lazy module loading), which must not count against
+        // the first shape of a path
+        {
+            int its = 0;
+            (void)run_shape(kShapes[0][0], kShapes[0][1], &its);
+            (void)run_shape(128, 0, &its);
+            if (cudaStreamSynchronize(st) != cudaSuccess) return PITN_ECUDA;
+        }
         // time each shape on this batch; the whole solve's time decides
         double best = 1e300;
         for (const auto& shp : kShapes) {
