@@ -862,10 +862,13 @@ def run_reference(args):
         v = statistics.median(r["value"] for r in runs)
         cb = runs[-1]
         bt = spec["bt"]
+        # a step is a sample of the batch; ms_per_step projects the whole batch at its rate
+        ms = float(bt.N.sum()) / v * 1e3 if v > 0 else None
         return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": spec["desc"], "B": bt.B},
+                "config": {"workload": spec["desc"], "B": bt.B,
+                           "ms_per_step": "the whole batch (all steps) at the sampled rate"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                                  "sample": cb["sample"]},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -85,3 +85,18 @@ def test_fkpp_tree_counts():
     assert bench.fk_composes(3) == 1       # 3 -> 2 (one compose + a lone copy) -> root
     assert bench.fk_composes(8) == 4 + 2   # 8 -> 4 -> 2 -> root
     assert bench.fk_composes(512) == 256 + 128 + 64 + 32 + 16 + 8 + 4 + 2
+
+
+def test_reference_arm_batch_line(monkeypatch):
+    # the batch reference line carries every contract key, ms_per_step included
+    fake = {"value": 2.0e6, "unit": bench.UNIT, "cores": 4, "kind": "oracle", "sample": "fake sample"}
+    monkeypatch.setattr(bench, "cpu_baseline_batch_pool", lambda spec: dict(fake))
+    args = SimpleNamespace(workload="batch_small", steps=2, warmup=3)
+    line = bench.run_reference(args)
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] == 2.0e6
+    bt = bench.workload("batch_small")["bt"]
+    assert line["ms_per_step"] == pytest.approx(float(bt.N.sum()) / 2.0e6 * 1e3)
+    assert line["cpu_baseline"]["cores"] == 4 and line["e2e"]["h2d_bytes_per_step"] == 0
