@@ -19,7 +19,8 @@
  *     A pointer may be device memory of the current CUDA device or host
  *     memory (pageable or pinned); the library detects which with
  *     cudaPointerGetAttributes and stages host arrays through device memory.
- *     All array arguments of one call should live on the same side.
+ *     All array arguments of one call should live on the same side.  Device
+ *     memory of a GPU other than the current one is refused (PITN_EINVAL).
  *   - Ownership: the caller owns every array.  The library never frees or
  *     keeps a pointer after the call returns.  Scratch memory comes from a
  *     per-device cache that grows on demand; pitn_release_workspace frees it.
@@ -127,6 +128,13 @@ typedef struct {
     double* res_history;    /* NULL or host array of max_iter + 1 doubles:
                                ||h||_inf at every residual evaluation */
     int32_t method;         /* PITN_STEP_*; default explicit Euler */
+    int64_t* cut_history;   /* NULL or host array of max_iter + 1 int64 (not in the
+                               paper): entry k receives the guard cut q of
+                               Newton step k, N when nothing was cut, for every
+                               step computed -- the `iters` accepted steps and,
+                               when a plain solve ends NONFINITE on a
+                               correction, the rejected last one; the
+                               remaining entries receive -1 */
 } pitn_options;
 
 /*
@@ -246,13 +254,28 @@ int64_t pitn_launch_count(void);
  * the previous call's contents; each call clears what must start at zero.
  * Calls that overlapped on the GPU would race on the array, so the entry
  * point holds a process-wide lock until its results are back on the host.
- * Results equal pitn_solve_ex's for the same arguments.
+ * Results equal pitn_solve_ex's for the same arguments when no tuned or
+ * pinned launch shape exists for the configuration (see pitn_tune_set):
+ * this entry point always takes the default launch shape, and a different
+ * shape associates the scan differently (last bits, and the iteration count
+ * of a borderline solve, may then differ).  params, x0 and traj_out must not
+ * be another GPU's memory (PITN_EINVAL).
  */
 #define PITN_NOALLOC_MAX_STEPS 65536
 #define PITN_NOALLOC_MAX_ITER 1024
 int pitn_solve_noalloc(int system_id, const double* params, const double* x0, double h, int64_t N,
                        int d, double tol, int max_iter, double guard_B, double* traj_out,
                        pitn_result* result);
+
+/*
+ * Measured FMA issue rate of the current device (not in the paper; the
+ * benchmark's ALU roofline denominators): kind 0 = FP64 (DFMA), 1 = FP32
+ * (FFMA).  A register-only kernel runs 8 independent FMA chains per thread on
+ * 8 blocks of 256 threads per SM; the best of three timed launches (after one
+ * untimed) gives *fma_per_s, thread-level FMAs per second (one FMA = 2 flops).
+ * Returns PITN_OK, PITN_EINVAL (unknown kind, NULL output) or PITN_ECUDA.
+ */
+int pitn_probe_fma_rate(int kind, double* fma_per_s);
 
 /*
  * Launch-shape autotuner (not in the paper).  While enabled, the first solve

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -22,6 +23,22 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
+_variant_libs = {}
+
+# Rounding variants of the same C file (test builds only): each computes the
+# same mathematics in another rounding order.  They measure how far rounding
+# alone moves results whose decisions compare rounded values (the guard's cut
+# index and with it the Newton count of a guarded solve).
+_FMA = ["-ffp-contract=fast"] + (["-mfma"] if platform.machine() in ("x86_64", "AMD64") else [])
+VARIANTS = {
+    "fma": _FMA,                                        # every a*b + c contracted
+    "rev": ["-DORACLE_SUM_REVERSED"],                   # matrix-vector sums last index first
+    "diff": ["-DORACLE_RESID_DIFF_FIRST"],              # residual (x_n - x_{n-1}) - h f
+    "blk4": ["-DORACLE_BLOCK=4"],                       # recursion bracketed in blocks of 4
+    "blk64": ["-DORACLE_BLOCK=64"],                     # ... of 64
+    "fma_rev_diff_blk64": _FMA + ["-DORACLE_SUM_REVERSED", "-DORACLE_RESID_DIFF_FIRST",
+                                  "-DORACLE_BLOCK=64"],
+}
 
 # identifiers understood by the C oracle
 LORENZ63, VDP, LINEAR_OSC, FKPP, LOGISTIC, DAHLQUIST, ROBERTSON = 1, 2, 3, 4, 5, 6, 7
@@ -33,45 +50,55 @@ _i64p = ctypes.POINTER(ctypes.c_int64)
 _i32p = ctypes.POINTER(ctypes.c_int32)
 
 
-def build(force: bool = False) -> str:
-    """Compile the C oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no FP contraction)."""
+def build(force: bool = False, variant: str | None = None) -> str:
+    """Compile the C oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no FP
+    contraction), or one of its rounding VARIANTS into liboracle_<variant>.so."""
+    lib_path = _LIB if variant is None else os.path.join(_BUILD, f"liboracle_{variant}.so")
+    flags = ["-ffp-contract=off"] if variant is None else (
+        (["-ffp-contract=off"] if "-ffp-contract=fast" not in VARIANTS[variant] else []) + VARIANTS[variant])
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
+        if (not force and os.path.exists(lib_path)
+                and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):
+            return lib_path
         os.makedirs(_BUILD, exist_ok=True)
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+        tmp = lib_path + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11"] + flags + ["-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+        os.replace(tmp, lib_path)
+        return lib_path
 
 
-def _load():
+def _load(variant: str | None = None):
     global _lib
+    if variant is not None:
+        if variant not in _variant_libs:
+            _variant_libs[variant] = _declare(ctypes.CDLL(build(variant=variant)))
+        return _variant_libs[variant]
     if _lib is None:
-        path = build()
-        lib = ctypes.CDLL(path)
-        c_int, c_i64, c_d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
-        lib.oracle_nparams.argtypes = [c_int]
-        lib.oracle_rhs.argtypes = [c_int, _dp, c_int, _dp, _dp]
-        lib.oracle_rhs_jac.argtypes = [c_int, _dp, c_int, _dp, _dp]
-        lib.oracle_rhs_dparam.argtypes = [c_int, _dp, c_int, _dp, _dp]
-        lib.oracle_step.argtypes = [c_int, c_int, _dp, c_int, c_d, _dp, _dp, _dp, _dp]
-        lib.oracle_sequential.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp]
-        lib.oracle_residual.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp, _dp, _dp,
-                                        ctypes.POINTER(c_int)]
-        lib.oracle_combine.argtypes = [c_int, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.oracle_affine_scan.argtypes = [c_i64, c_int, _dp, _dp, _dp]
-        lib.oracle_newton.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, c_d, c_int, c_d,
-                                      _dp, _dp, _dp, _i32p, _i32p, _i64p]
-        lib.oracle_newton_batch.argtypes = [c_int, c_int, c_i64, _dp, _dp, _dp, _i64p, c_int, c_d,
-                                            c_int, c_d, _dp, _i64p, _i32p, _i32p, _dp]
-        lib.oracle_adjoint.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp, _dp, _dp,
-                                       _dp, _dp]
-        _lib = lib
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _declare(lib):
+    """Argument types of the oracle's C entry points."""
+    c_int, c_i64, c_d = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.oracle_nparams.argtypes = [c_int]
+    lib.oracle_rhs.argtypes = [c_int, _dp, c_int, _dp, _dp]
+    lib.oracle_rhs_jac.argtypes = [c_int, _dp, c_int, _dp, _dp]
+    lib.oracle_rhs_dparam.argtypes = [c_int, _dp, c_int, _dp, _dp]
+    lib.oracle_step.argtypes = [c_int, c_int, _dp, c_int, c_d, _dp, _dp, _dp, _dp]
+    lib.oracle_sequential.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp]
+    lib.oracle_residual.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp, _dp, _dp,
+                                    ctypes.POINTER(c_int)]
+    lib.oracle_combine.argtypes = [c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.oracle_affine_scan.argtypes = [c_i64, c_int, _dp, _dp, _dp]
+    lib.oracle_newton.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, c_d, c_int, c_d,
+                                  _dp, _dp, _dp, _i32p, _i32p, _i64p, _i64p]
+    lib.oracle_newton_batch.argtypes = [c_int, c_int, c_i64, _dp, _dp, _dp, _i64p, c_int, c_d,
+                                        c_int, c_d, _dp, _i64p, _i32p, _i32p, _dp]
+    lib.oracle_adjoint.argtypes = [c_int, c_int, _dp, _dp, c_d, c_i64, c_int, _dp, _dp, _dp,
+                                   _dp, _dp]
+    return lib
 
 
 def _f64(a):
@@ -180,22 +207,28 @@ def affine_scan(A, c):
     return z
 
 
-def newton(sys, p, x0, h, N, tol, max_iter, guard_B=0.0, guess=None, method=EULER):
-    """Returns dict(traj, res_hist, iters, status, guard_index)."""
+def newton(sys, p, x0, h, N, tol, max_iter, guard_B=0.0, guess=None, method=EULER, variant=None):
+    """Returns dict(traj, res_hist, iters, status, guard_index, cuts).
+
+    cuts[k] is the guard cut q of Newton step k (N when nothing was cut).
+    variant: None for the oracle itself, or a key of VARIANTS (a rounding
+    variant, test use only)."""
     p, x0 = _f64(p), _f64(x0)
     _need(p, nparams(sys), "p")
     d = x0.size
     traj = np.empty((int(N), d))
     hist = np.full(max_iter + 1, np.nan)
+    cuts = np.full(max_iter + 1, -1, dtype=np.int64)
     iters, status, gi = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     g = None
     if guess is not None:   # a scalar or d-vector fills every step; else one row per step
         g = _f64(np.broadcast_to(_f64(guess), (int(N), d)))
-    _check(_load().oracle_newton(sys, method, _ptr(p), _ptr(x0), float(h), int(N), d, float(tol),
-                                 int(max_iter), float(guard_B), _ptr(g), _ptr(traj), _ptr(hist),
-                                 ctypes.byref(iters), ctypes.byref(status), ctypes.byref(gi)))
+    _check(_load(variant).oracle_newton(sys, method, _ptr(p), _ptr(x0), float(h), int(N), d, float(tol),
+                                        int(max_iter), float(guard_B), _ptr(g), _ptr(traj), _ptr(hist),
+                                        ctypes.byref(iters), ctypes.byref(status), ctypes.byref(gi),
+                                        cuts.ctypes.data_as(_i64p)))
     return dict(traj=traj, res_hist=hist[: iters.value + 1], iters=iters.value,
-                status=status.value, guard_index=gi.value)
+                status=status.value, guard_index=gi.value, cuts=cuts[cuts >= 0])
 
 
 def newton_batch(sys, params, x0, h, N, tol, max_iter, guard_B=0.0, method=EULER):

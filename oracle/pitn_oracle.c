@@ -44,6 +44,24 @@
  *                               same affine structure, for gradients of a
  *                               loss of the trajectory.
  *
+ * Rounding variants (test builds only; the default build defines none of
+ * these and computes exactly as described above).  Each variant is the same
+ * mathematics in another rounding order; the tests build them to measure how
+ * far rounding alone moves an iteration count whose decisions compare
+ * rounded values (the guard's cut, reading R8):
+ *   ORACLE_SUM_REVERSED       the sums of the Newton recursion's matrix-vector
+ *                             products run from the last index to the first;
+ *   ORACLE_RESID_DIFF_FIRST   the explicit Euler residual is grouped as
+ *                             (x_n - x_{n-1}) - h f(x_{n-1}) instead of
+ *                             x_n - (x_{n-1} + h f(x_{n-1}));
+ *   ORACLE_BLOCK=C            the recursion of eq. (3.13) is bracketed in
+ *                             blocks of C elements: block aggregates folded
+ *                             with eq. (3.3), carried from block to block,
+ *                             each block replayed from its incoming vector
+ *                             (the same Newton step in exact arithmetic, by
+ *                             the associativity of Lemma 3.1);
+ *   and, through the compiler, FMA contraction of every a*b + c.
+ *
  * Readings of the paper that this file takes (the paper is silent on them):
  *   - K in the paper counts residual evaluations; `iters` here counts Newton
  *     updates actually applied (paper K - 1).
@@ -517,6 +535,21 @@ int oracle_residual(int sys, int method, const double *p, const double *x0, doub
     int saw_nan = 0, nf = 0;
     for (int64_t n = 0; n < N; ++n) {
         const double *prev = (n == 0) ? x0 : traj + (size_t)(n - 1) * d;
+#ifdef ORACLE_RESID_DIFF_FIRST
+        if (method == OR_EULER) {
+            /* rounding variant: h_n = (x_n - x_{n-1}) - h f(x_{n-1}) */
+            oracle_rhs(sys, p, d, prev, phi);
+            for (int c = 0; c < d; ++c) {
+                double v = (traj[(size_t)n * d + c] - prev[c]) - h * phi[c];
+                if (r) r[(size_t)n * d + c] = v;
+                double a = fabs(v);
+                if (!isfinite(v)) nf = 1;
+                if (a != a) saw_nan = 1;
+                else if (a > m) m = a;
+            }
+            continue;
+        }
+#endif
         if (is_implicit(method)) {
             /* implicit rule: the residual h_n of eq. 3.15 preconditioned by
              * (I - dg/dx_n)^{-1}, the quantity the paper's implicit residual
@@ -594,6 +627,90 @@ int oracle_affine_scan(int64_t N, int d, const double *A, const double *c, doubl
 /* Newton's method, eqs. (3.8)-(3.13).                                       */
 /* ------------------------------------------------------------------------ */
 
+/* Sum of row . v over d entries, in the order the build selects (index order
+ * by default; from the last index to the first in the ORACLE_SUM_REVERSED
+ * rounding variant). */
+static double row_dot(const double *row, const double *v, int d)
+{
+    double s = 0.0;
+#ifdef ORACLE_SUM_REVERSED
+    for (int j = d - 1; j >= 0; --j) s += row[j] * v[j];
+#else
+    for (int j = 0; j < d; ++j) s += row[j] * v[j];
+#endif
+    return s;
+}
+
+#if defined(ORACLE_BLOCK) && ORACLE_BLOCK > 0
+/*
+ * Rounding variant (test builds only): the explicit recursion of eq. (3.13),
+ *   dx[0] = -r[0],  dx[n] = J(x_n) dx[n-1] - r[n]   (0-based buffer index),
+ * bracketed in blocks of ORACLE_BLOCK elements.  Element n is (F_n, c_n) with
+ * F_0 = 0 (eq. 3.4), F_n = J(x_n) and c_n = -r[n]; each block's aggregate is
+ * folded with eq. (3.3), the aggregates carry the correction from block to
+ * block, and each block is replayed from its incoming vector.  By the
+ * associativity of eq. (3.3) (Lemma 3.1) this is the same Newton step in
+ * exact arithmetic.
+ */
+static int recursion_blocked(int sys, int method, const double *p, int d, double h, int64_t N,
+                             const double *traj, const double *r, double *dx)
+{
+    const int64_t C = ORACLE_BLOCK;
+    size_t dd = (size_t)d * d;
+    double *P = (double *)malloc(sizeof(double) * dd), *tP = (double *)malloc(sizeof(double) * dd);
+    double *F = (double *)malloc(sizeof(double) * dd), *phi = (double *)malloc(sizeof(double) * d);
+    double *c = (double *)malloc(sizeof(double) * d), *tc = (double *)malloc(sizeof(double) * d);
+    double *z = (double *)malloc(sizeof(double) * d), *v = (double *)malloc(sizeof(double) * d);
+    double *tv = (double *)malloc(sizeof(double) * d);
+    if (!P || !tP || !F || !phi || !c || !tc || !z || !v || !tv) {
+        free(P); free(tP); free(F); free(phi); free(c); free(tc); free(z); free(v); free(tv);
+        return OR_ENOMEM;
+    }
+    for (int i = 0; i < d; ++i) z[i] = 0.0;
+    for (int64_t s0 = 0; s0 < N; s0 += C) {
+        int64_t e0 = (s0 + C < N) ? s0 + C : N;
+        /* aggregate of the block: (P, c) <- (F_n, c_n) o (P, c) */
+        for (size_t i = 0; i < dd; ++i) P[i] = 0.0;
+        for (int i = 0; i < d; ++i) { P[(size_t)i * d + i] = 1.0; c[i] = 0.0; }
+        for (int64_t n = s0; n < e0; ++n) {
+            if (n == 0) {
+                for (size_t i = 0; i < dd; ++i) P[i] = 0.0;
+                for (int i = 0; i < d; ++i) c[i] = -r[i];
+                continue;
+            }
+            oracle_step(sys, method, p, d, h, traj + (size_t)(n - 1) * d, phi, F, NULL);
+            for (int i = 0; i < d; ++i) {
+                for (int j = 0; j < d; ++j) {
+                    double sacc = 0.0;
+                    for (int l = 0; l < d; ++l) sacc += F[(size_t)i * d + l] * P[(size_t)l * d + j];
+                    tP[(size_t)i * d + j] = sacc;
+                }
+                tc[i] = row_dot(F + (size_t)i * d, c, d) - r[(size_t)n * d + i];
+            }
+            memcpy(P, tP, sizeof(double) * dd);
+            memcpy(c, tc, sizeof(double) * d);
+        }
+        /* replay of the block from its incoming vector z */
+        memcpy(v, z, sizeof(double) * d);
+        for (int64_t n = s0; n < e0; ++n) {
+            if (n == 0) {
+                for (int i = 0; i < d; ++i) v[i] = -r[i];
+            } else {
+                oracle_step(sys, method, p, d, h, traj + (size_t)(n - 1) * d, phi, F, NULL);
+                for (int i = 0; i < d; ++i) tv[i] = row_dot(F + (size_t)i * d, v, d) - r[(size_t)n * d + i];
+                memcpy(v, tv, sizeof(double) * d);
+            }
+            memcpy(dx + (size_t)n * d, v, sizeof(double) * d);
+        }
+        /* incoming vector of the next block: the aggregate applied to z */
+        for (int i = 0; i < d; ++i) tv[i] = row_dot(P + (size_t)i * d, z, d) + c[i];
+        memcpy(z, tv, sizeof(double) * d);
+    }
+    free(P); free(tP); free(F); free(phi); free(c); free(tc); free(z); free(v); free(tv);
+    return OR_OK;
+}
+#endif
+
 /*
  * Solves h(xi) = 0 for xi = [x_1 .. x_N] (traj, [N][d]).
  *   guess     NULL: x_n = x0 for all n (constant guess); else the guess [N][d].
@@ -603,6 +720,9 @@ int oracle_affine_scan(int64_t N, int d, const double *A, const double *c, doubl
  *             residual evaluation.
  *   iters     Newton updates applied; status OR_OK / OR_NOT_CONVERGED /
  *             OR_NONFINITE; guard_index = q of the last update (N if none cut).
+ *   cut_hist  NULL or room for max_iter + 1 values: entry k receives the q of
+ *             Newton step k (N if nothing was cut), for every step computed
+ *             (including a plain solve's last, rejected step).
  * Each iteration:
  *   1. r = h(xi), res = ||r||_inf (eq. 3.8, Sec. 4 stopping quantity);
  *   2. non-finite residual -> NONFINITE; res <= tol -> OK;
@@ -615,7 +735,7 @@ int oracle_affine_scan(int64_t N, int d, const double *A, const double *c, doubl
 int oracle_newton(int sys, int method, const double *p, const double *x0, double h, int64_t N,
                   int d, double tol, int max_iter, double guard_B, const double *guess,
                   double *traj, double *res_hist, int32_t *iters, int32_t *status,
-                  int64_t *guard_index)
+                  int64_t *guard_index, int64_t *cut_hist)
 {
     if (!dim_ok(sys, d) || N < 1 || max_iter < 0 || !(tol >= 0.0) || !traj || !x0 || !p)
         return OR_EINVAL;
@@ -665,21 +785,27 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
                 for (int i = 0; i < d; ++i) dx[(size_t)n * d + i] = phi[i] - r[(size_t)n * d + i];
             }
         } else {
+#if defined(ORACLE_BLOCK) && ORACLE_BLOCK > 0
+            if (recursion_blocked(sys, method, p, d, h, N, traj, r, dx) != OR_OK) {
+                free(r); free(dx); free(J); free(Bm); free(phi);
+                return OR_ENOMEM;
+            }
+#else
             for (int64_t n = 1; n < (int64_t)N; ++n) {
                 const double *xn = traj + (size_t)(n - 1) * d;   /* x_n, state n (1-based) */
                 oracle_step(sys, method, p, d, h, xn, phi, J, NULL);
-                for (int i = 0; i < d; ++i) {
-                    double s = 0.0;
-                    for (int j = 0; j < d; ++j) s += J[(size_t)i * d + j] * dx[(size_t)(n - 1) * d + j];
-                    dx[(size_t)n * d + i] = s - r[(size_t)n * d + i];
-                }
+                for (int i = 0; i < d; ++i)
+                    dx[(size_t)n * d + i] = row_dot(J + (size_t)i * d, dx + (size_t)(n - 1) * d, d) -
+                                            r[(size_t)n * d + i];
             }
+#endif
         }
         /* first correction that is not finite (or exceeds the guard bound) */
         int64_t q = N;
         for (int64_t n = 0; n < N && q == N; ++n)
             for (int i = 0; i < d; ++i)
                 if (!(fabs(dx[(size_t)n * d + i]) <= cap)) { q = n; break; }
+        if (cut_hist) cut_hist[it] = q;
         if (!guarded && q < N) { st = OR_NONFINITE; break; }
 
         /* update, eq. (3.11) */
@@ -721,7 +847,7 @@ int oracle_newton_batch(int sys, int method, int64_t B, const double *params, co
         int64_t gi;
         int rc = oracle_newton(sys, method, params + (size_t)b * P, x0 + (size_t)b * d, h[b], N[b],
                                d, tol, max_iter, guard_B, NULL, traj + (size_t)off * d, hist,
-                               iters + b, status + b, &gi);
+                               iters + b, status + b, &gi, NULL);
         if (rc) { free(hist); return rc; }
         if (res_out) res_out[b] = hist[iters[b]];
         off += N[b];

@@ -38,7 +38,8 @@ def solve(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, precision=P.P
 
     info: iters (Newton updates), status (PITN_OK / NOT_CONVERGED / NONFINITE),
     final_res, guard_index and, with history=True, res_history (||h||_inf per
-    residual evaluation).  Raises PitnError on a negative return code.
+    residual evaluation) and cut_history (the guard cut of every computed
+    Newton step).  Raises PitnError on a negative return code.
     """
     torch = _torch()
     x0_t = _as_f64(x0, device)
@@ -47,14 +48,17 @@ def solve(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, precision=P.P
     traj = out if out is not None else torch.empty((int(N), d), dtype=torch.float64, device=device)
     g = _as_f64(guess, device) if guess is not None else None
     hist = np.full(max_iter + 1, np.nan) if history else None
+    cuts = np.full(max_iter + 1, -1, dtype=np.int64) if history else None
     opt = P.make_options(precision=precision, tile_elems=tile_elems, guard_B=guard_B, guess=g,
-                         stream=_stream_ptr(stream, device), res_history=hist, method=method)
+                         stream=_stream_ptr(stream, device), res_history=hist, method=method,
+                         cut_history=cuts)
     rc, res = P.pitn_solve_ex(system, p_t, x0_t, h, N, d, tol, max_iter, traj, opt)
     P.check(rc, "pitn_solve_ex")
     info = dict(iters=res.iters, status=res.status, final_res=res.final_res,
                 guard_index=res.guard_index, code=rc)
     if history:
         info["res_history"] = hist[: res.iters + 1].copy()
+        info["cut_history"] = cuts[cuts >= 0].copy()
     return traj, info
 
 

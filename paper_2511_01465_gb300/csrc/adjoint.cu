@@ -369,6 +369,8 @@ extern "C" int pitn_backward(int system_id, int64_t B, const double* params, con
         return PITN_EINVAL;
     if (B < 1 || !params || !x0 || !h || !N || !traj || !grad_x0_out || !grad_params_out) return PITN_EINVAL;
     if (ckpt_every < 0) return PITN_EINVAL;
+    if (any_foreign({params, x0, h, N, traj, grad_traj, grad_xN, grad_x0_out, grad_params_out}))
+        return PITN_EINVAL;
     if (o.method != PITN_STEP_EULER) return PITN_EUNSUPPORTED;
     const int P = num_params(system_id);
     std::lock_guard<std::recursive_mutex> lk(api_mutex());

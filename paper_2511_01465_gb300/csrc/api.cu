@@ -151,6 +151,29 @@ bool is_device_ptr(const void* p) {
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+// Device memory that belongs to a GPU other than the current one.  The
+// kernels run on the current device and would load or store through such a
+// pointer as a peer access (or fault), so the entry points refuse it.
+// Managed memory migrates to whichever device touches it and is accepted.
+bool is_foreign_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (attr.type != cudaMemoryTypeDevice) return false;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return true;
+    return attr.device != dev;
+}
+
+bool any_foreign(std::initializer_list<const void*> ptrs) {
+    for (const void* p : ptrs)
+        if (is_foreign_device_ptr(p)) return true;
+    return false;
+}
+
 int system_dim_ok(int sys, int d) {
     switch (sys) {
     case PITN_LORENZ63: return d == 3;
@@ -317,6 +340,7 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
     if (o.method < PITN_STEP_EULER || o.method > PITN_STEP_TRAPEZOID) return PITN_EINVAL;
+    if (any_foreign({params, x0, traj_out, o.guess})) return PITN_EINVAL;
     if (o.method == PITN_STEP_RK4 && system_id != PITN_VDP && system_id != PITN_LOGISTIC)
         return PITN_EUNSUPPORTED;
     if ((o.method == PITN_STEP_BACKWARD_EULER || o.method == PITN_STEP_TRAPEZOID) &&
@@ -341,6 +365,10 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
     if (rc != PITN_OK) return rc;
     if (o.res_history) {
         for (int k = 0; k <= out.iters && k <= max_iter; ++k) o.res_history[k] = out.history[k];
+    }
+    if (o.cut_history) {
+        for (int k = 0; k <= max_iter; ++k)
+            o.cut_history[k] = (size_t)k < out.cuts.size() ? (int64_t)out.cuts[k] : (int64_t)-1;
     }
     if (result) {
         result->iters = out.iters;

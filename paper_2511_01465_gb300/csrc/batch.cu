@@ -892,6 +892,8 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         o.method != PITN_STEP_EULER)
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
+    if (any_foreign({params, x0, h, N, traj_out, offsets_out, iters_out, status_out, res_out}))
+        return PITN_EINVAL;
     const int P = num_params(system_id);
 
     std::lock_guard<std::recursive_mutex> lk(api_mutex());

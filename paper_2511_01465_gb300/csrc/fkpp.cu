@@ -5,22 +5,33 @@
 // + u_i (1 - u_i), so the Jacobian of every leaf element is tridiagonal:
 //   J_k = I + S_k,  S_k = h (D L/dx^2 + diag(1 - 2 u_k)),
 // diagonal a_i = 1 + h (1 - 2 u_i) - 2 o and off-diagonals o = h D / dx^2.
-// The Newton step (eq. 3.13) is solved as a reduce-then-scan:
-//   A. fold:   one CTA per tile of TS consecutive elements computes the
-//              residuals (eq. 3.8, with ||r||_inf) and folds the tile's leaves
-//              P <- J_k P, b <- J_k b - r_k into a dense tile aggregate
-//              (P = I + S, b); the tridiagonal leaf is applied as a stencil,
-//              so the fold costs 3 d^2 per element instead of 2 d^3;
-//   B. tree:   an up-sweep composes pairs of aggregates (eq. 3.3),
+// One Newton pass is a host loop of launches on one stream:
+//   A0. residual: fk_residual_kernel evaluates r_k (eq. 3.8) in FP64 with
+//              ||r||_inf and the leaf diagonals; fk_stop_kernel then sets a
+//              device flag when the pass has converged (or is not finite),
+//              and every later kernel of the pass returns at once;
+//   A.  fold:  fk_fold_kernel, one CTA per tile of TS consecutive elements,
+//              folds the tile's leaves P <- J_k P, b <- J_k b - r_k into a
+//              dense tile aggregate (P = I + S, b); the tridiagonal leaf is
+//              applied as a stencil in registers (halo rows by warp
+//              shuffles), 3 d^2 per element instead of 2 d^3;
+//   B.  up-sweep: pairs of aggregates are composed level by level (eq. 3.3),
 //              (I + S2)(I + S1) = I + (S2 + S1 + S2 S1),  b = b2 + b1 + S2 b1,
-//              the dense S2 S1 product in FP64 on CUDA cores, or in mixed
-//              precision on tensor cores (BF16 operands, FP32 accumulation,
-//              sums in FP32; the delta form keeps the identity exact); a
-//              down-sweep then pushes the prefix vector dx (the root starts
-//              at dx_1 = -r_0) to the start of every tile with matrix-vector
-//              products only (every prefix from element 0 has matrix 0);
-//   C. replay: one warp per tile re-runs the tile's leaves in FP64 from its
-//              incoming vector with the exact Jacobians, writes x + dx and
+//              up to the level below the root (the root aggregate is never
+//              read).  FP64: fk_compose_f64, one launch per level on CUDA
+//              cores.  Mixed precision: fk_upsweep_tc_kernel, one launch per
+//              pass, S2 S1 on tensor cores (tcgen05.mma, TMEM accumulator,
+//              FP32 accumulation), sums in FP32; a CTA composes its level-1
+//              node and climbs while it is the second child to arrive at the
+//              parent's counter;
+//   C.  replay: fk_replay_kernel, one 128-thread CTA per tile, one row per
+//              thread.  Each tile first walks the tree from the root to its
+//              leaf: the walk starts from dx_1 = -r_0 and, at each right
+//              turn, applies the left sibling's aggregate to the vector
+//              (every prefix from element 0 has matrix 0, so only vectors
+//              are needed); this is the down-sweep, folded into the replay.
+//              The tile then re-runs its leaves in FP64 from that vector
+//              with the exact tridiagonal Jacobians, writes x + dx and
 //              records the guard index.
 // Aggregates are stored padded to 128 x 128, column-major (S[col][row]).
 #include <cuda_bf16.h>
@@ -881,6 +892,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     int it = 0, status = PITN_NOT_CONVERGED;
     double final_res = 0.0;
     out->history.clear();
+    out->cuts.clear();
     for (;;) {
         p.X = bufs[cur];
         p.Xn = bufs[cur ^ 1];
@@ -905,6 +917,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         if (hc->nf) { status = PITN_NONFINITE; break; }
         if (res <= tol) { status = PITN_OK; break; }
         if (it == max_iter) { status = PITN_NOT_CONVERGED; break; }
+        out->cuts.push_back(cut);
         if (!guarded && cut < N) { status = PITN_NONFINITE; break; }
         cur ^= 1;
         q = guarded ? cut : N;
@@ -952,6 +965,7 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
         !is_device_ptr(S) || !is_device_ptr(b))
         return PITN_EINVAL;
     if (((uintptr_t)S2 | (uintptr_t)S1 | (uintptr_t)S) & 15) return PITN_EINVAL;
+    if (any_foreign({S2, b2, S1, b1, S, b})) return PITN_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(api_mutex());
     cudaStream_t st = (cudaStream_t)stream;
     int* err = (int*)workspace(64, kSlotCtrl);

@@ -1,28 +1,33 @@
 // newton_small.cu -- the whole Newton solve for small state dimension
-// (d = 2, 3) in ONE persistent cooperative kernel.
+// (d = 1, 2, 3) in ONE persistent cooperative kernel.
 //
-// Per Newton iteration every CTA walks its tiles of BLOCK*C consecutive steps
-// and, in a single pass over the trajectory:
-//   1. loads x_{k-1}, x_k (lazy fill of the guard, see below) and evaluates
-//      the residual r_k = x_{k+1} - phi(x_k) (eq. 3.8) and the compact
-//      Jacobian J_k = dphi/dx(x_k) into registers; accumulates ||r||_inf and a
-//      non-finite flag;
-//   2. folds its C affine elements (J_k, -r_k) (eq. 3.4; element 0 has matrix
-//      0) into a thread aggregate (P, c) with the operator of eq. 3.3;
-//   3. scans the thread aggregates: Kogge-Stone over the warp with shuffles,
-//      then over the warps through shared memory;
-//   4. publishes the tile aggregate and resolves its incoming prefix by a
-//      decoupled look-back over the preceding tiles' published aggregates /
-//      inclusive prefixes (only the vector part of an inclusive prefix is
-//      needed: every prefix that starts at element 0 has matrix 0);
-//   5. replays its C elements from the incoming vector: dx_{k+1} = J_k dx_k -
-//      r_k (eq. 3.13) and writes x_k + dx_k into the other trajectory buffer,
+// Thread g of the grid owns a contiguous range of steps.  Per Newton
+// iteration the three-phase kernel (newton_small.cuh) runs:
+//   1. phase 1: loads x_{k-1}, x_k (lazy fill of the guard, see below),
+//      evaluates the residual r_k = x_{k+1} - phi(x_k) (eq. 3.8) and the
+//      compact Jacobian J_k = dphi/dx(x_k), stores both to scratch, keeps
+//      ||r||_inf (an integer max of the bit patterns) and folds its affine
+//      elements (J_k, -r_k) (eq. 3.4; element 0 has matrix 0) into a thread
+//      aggregate with the operator of eq. 3.3, as two interleaved chains;
+//   2. scans the thread aggregates: Kogge-Stone over the warp with shuffles,
+//      then over the warps through shared memory, and writes the CTA
+//      aggregate to its slot of a global array;
+//   3. grid barrier: every CTA's aggregate and the iteration's ||r||_inf are
+//      visible; every CTA takes the same stop/continue decision;
+//   4. every CTA scans the CTA aggregates in one fixed order to find its own
+//      incoming correction vector (only the vector part is needed: every
+//      prefix that starts at element 0 has matrix 0).  The order does not
+//      depend on timing, so results are reproducible run to run;
+//   5. phase 3: replays its steps from the incoming vector,
+//      dx_{k+1} = J_k dx_k - r_k (eq. 3.13), with J_k and r_k read back from
+//      scratch, and writes x_k + dx_k into the other trajectory buffer,
 //      recording the first index whose correction is not finite or exceeds
-//      the guard bound.
-// A grid barrier then makes the iteration's ||r||_inf, non-finite flag and
-// guard index visible to all CTAs, which take the same stop/continue
-// decision.  The guard's fill (states from q on set to state q-1) is never
-// written during the loop: the next pass reads x_k for k >= q as x_{q-1}.
+//      the guard bound;
+//   6. grid barrier: the iteration's guard index is visible to all CTAs.
+// Every CTA writes its aggregate slot before the first barrier of each
+// iteration, so the aggregate array never needs clearing between solves.
+// The guard's fill (states from q on set to state q-1) is never written
+// during the loop: the next pass reads x_k for k >= q as x_{q-1}.
 //
 // The decision order per iteration is the oracle's: non-finite residual ->
 // NONFINITE; ||r|| <= tol -> OK; max_iter updates -> NOT_CONVERGED; plain
@@ -125,8 +130,8 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     size_t off_rec = off_err + 16;
     size_t total = off_rec + sizeof(SolveRecord);
     char* ctrl = (char*)workspace(total, kSlotCtrl);
-    // host mirror: err | record | history
-    size_t hbytes = 16 + sizeof(SolveRecord) + sizeof(double) * (size_t)(max_iter + 1);
+    // host mirror: err | record | history | cut codes
+    size_t hbytes = 16 + sizeof(SolveRecord) + 2 * sizeof(double) * (size_t)(max_iter + 1);
     char* hbuf = (char*)pinned(hbytes);
     if (!X1 || !scratch || !ctrl || !hbuf) return PITN_ENOMEM;
 
@@ -162,9 +167,13 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     int* h_err = (int*)hbuf;
     SolveRecord* h_rec = (SolveRecord*)(hbuf + 16);
     unsigned long long* h_hist = (unsigned long long*)(hbuf + 16 + sizeof(SolveRecord));
+    unsigned long long* h_q = h_hist + (max_iter + 1);
+    // the residual history and the cut codes are adjacent in the control block
     if (cudaMemcpyAsync(h_err, ctrl + off_err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(h_rec, ctrl + off_rec, sizeof(SolveRecord), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(h_hist, ctrl + off_res, sizeof(unsigned long long) * (max_iter + 1),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(h_q, ctrl + off_q, sizeof(unsigned long long) * (max_iter + 1),
                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return PITN_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return PITN_ECUDA; }
@@ -180,6 +189,12 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
         std::memcpy(&v, &b, sizeof(v));
         out->history[k] = v;
     }
+    // cut of every computed Newton step (the code is ~q, 0 when nothing was
+    // cut); a step at index iters was computed only if it was rejected, which
+    // a plain solve does on a cut (a non-finite correction)
+    out->cuts.clear();
+    for (int k = 0; k < out->iters; ++k) out->cuts.push_back(h_q[k] ? (long long)~h_q[k] : (long long)N);
+    if (out->iters <= max_iter && h_q[out->iters]) out->cuts.push_back((long long)~h_q[out->iters]);
     return PITN_OK;
 }
 
@@ -311,6 +326,8 @@ constexpr int kNaMaxCtas = 1024;              // CTA aggregates
 constexpr size_t kNaX1 = 0;                                            // [N][3]
 constexpr size_t kNaScratch = kNaX1 + (size_t)kNaMaxSteps * 3;         // [6][lcap][threads]
 constexpr size_t kNaScratchDoubles = (size_t)kNaMaxSteps * 6 * 2;      // >= 6 (N + 2 threads)
+// CTA aggregates: never cleared, since every CTA writes its own slot before
+// the grid barrier after which any CTA reads it
 constexpr size_t kNaAgg = kNaScratch + kNaScratchDoubles;               // [CTAs][12]
 constexpr size_t kNaRes = kNaAgg + (size_t)kNaMaxCtas * 12;            // [iter+1] bits
 constexpr size_t kNaQ = kNaRes + (size_t)(kNaMaxIter + 1);             // [iter+1] bits
@@ -338,6 +355,8 @@ extern "C" int pitn_solve_noalloc(int system_id, const double* params, const dou
     if (!std::isfinite(h) || !(h > 0.0) || !std::isfinite(tol) || !(tol >= 0.0) || std::isnan(guard_B))
         return PITN_EINVAL;
     if (!is_device_ptr(traj_out)) return PITN_EINVAL;  // nowhere to stage a host trajectory
+    // the kernel runs on the current device: another GPU's memory is refused
+    if (any_foreign({params, x0, traj_out})) return PITN_EINVAL;
 
     std::lock_guard<std::mutex> lk(g_na_mu);
     int dev = 0;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <initializer_list>
 #include <mutex>
 #include <vector>
 
@@ -33,6 +34,8 @@ void release_all();
 void count_launch(int64_t n);
 const cudaDeviceProp& props();
 bool is_device_ptr(const void* p);
+bool is_foreign_device_ptr(const void* p);
+bool any_foreign(std::initializer_list<const void*> ptrs);
 int system_dim_ok(int sys, int d);
 int num_params(int sys);
 int fetch_to_host(const double* src, size_t n, double* dst);
@@ -63,6 +66,7 @@ struct SolveOutcome {
     double final_res = 0.0;
     int64_t guard_index = 0;
     std::vector<double> history;  // ||h||_inf per residual evaluation
+    std::vector<long long> cuts;  // guard cut q of every Newton step computed
 };
 
 int stage_inputs(int system_id, const double* params, const double* x0, int64_t N, int d,

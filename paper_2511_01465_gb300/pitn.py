@@ -39,7 +39,7 @@ class pitn_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("tile_elems", ctypes.c_int32),
                 ("guard_B", ctypes.c_double), ("guess", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p), ("res_history", ctypes.c_void_p),
-                ("method", ctypes.c_int32)]
+                ("method", ctypes.c_int32), ("cut_history", ctypes.c_void_p)]
 
 
 _lib = None
@@ -78,6 +78,8 @@ def lib():
         L.pitn_release_workspace.restype = c_int
         L.pitn_launch_count.argtypes = []
         L.pitn_launch_count.restype = i64
+        L.pitn_probe_fma_rate.argtypes = [c_int, ctypes.POINTER(d)]
+        L.pitn_probe_fma_rate.restype = c_int
         L.pitn_solve_noalloc.argtypes = [c_int, vp, vp, d, i64, c_int, d, c_int, d, vp,
                                           ctypes.POINTER(pitn_result)]
         L.pitn_solve_noalloc.restype = c_int
@@ -123,7 +125,7 @@ def _ptr(a, dtype=np.float64):
 
 
 def make_options(precision=PITN_PREC_FP64, tile_elems=0, guard_B=0.0, guess=None, stream=None,
-                 res_history=None, method=PITN_STEP_EULER):
+                 res_history=None, method=PITN_STEP_EULER, cut_history=None):
     o = pitn_options()
     o.method = int(method)
     o.precision = int(precision)
@@ -132,7 +134,8 @@ def make_options(precision=PITN_PREC_FP64, tile_elems=0, guard_B=0.0, guess=None
     o.guess = _ptr(guess)
     o.stream = ctypes.c_void_p(int(stream)) if stream is not None else None
     o.res_history = _ptr(res_history)
-    o._keep = (guess, res_history)
+    o.cut_history = _ptr(cut_history)
+    o._keep = (guess, res_history, cut_history)
     return o
 
 
@@ -259,3 +262,11 @@ def check(code, what="pitn"):
     if code < 0:
         raise PitnError(code, what)
     return code
+
+
+def pitn_probe_fma_rate(kind):
+    """Measured FMA rate of the current device (kind 0: FP64, 1: FP32), in
+    thread FMAs per second."""
+    v = ctypes.c_double()
+    check(lib().pitn_probe_fma_rate(int(kind), ctypes.byref(v)), "pitn_probe_fma_rate")
+    return v.value

@@ -1,0 +1,73 @@
+"""Rounding spread of guarded Newton solves, measured on the oracle.
+
+With the divergence guard (reading R8, not in the paper) every Newton step
+cuts the trajectory at the first correction that exceeds the bound B.
+Beyond the converged prefix the corrections grow exponentially, so where the
+cut falls depends on how the step was rounded, and with it the number of
+Newton updates a guarded solve takes.  Rounding alone is measured here: the
+oracle (oracle/pitn_oracle.c) is built in rounding variants of the same
+mathematics -- FMA contraction, reversed summation order, a regrouped
+residual, blocked bracketings of the recursion of eq. 3.13 (exact in real
+arithmetic by the associativity of Lemma 3.1) and all of these at once --
+and every variant solves the same problem.  What they agree on is fixed by
+the mathematics and FP64 rounding; what they spread over is not.
+
+The GPU parity bar for a guarded solve is then:
+  - the status equals the oracle's;
+  - the Newton count is within the variants' spread of the oracle's,
+    window = max over variants of |iters_variant - iters_oracle|
+    (0: the count must be equal);
+  - the cut of every Newton step before the first step at which any variant
+    cut elsewhere than the oracle is equal to the oracle's, and so is the
+    residual history up to and including that step.
+Only the oracle's code runs here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+
+VARIANTS = list(O.VARIANTS)
+
+
+def runs(wl, tol, max_iter, guard_B, method=O.EULER, guess=None):
+    """The oracle and each rounding variant on one problem: {None: ..., name: ...}."""
+    out = {}
+    for v in [None] + VARIANTS:
+        out[v] = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, tol, max_iter, guard_B=guard_B,
+                          guess=guess, method=method, variant=v)
+    return out
+
+
+def first_difference(a, b):
+    """First index at which two cut sequences differ (the shorter length if none)."""
+    m = min(len(a), len(b))
+    for i in range(m):
+        if int(a[i]) != int(b[i]):
+            return i
+    return m
+
+
+def spread(rs):
+    """(window, first_div) of a runs() result: the largest count difference of
+    a variant from the oracle, and the first Newton step at which a variant's
+    cut differs from the oracle's."""
+    ref = rs[None]
+    window = max(abs(r["iters"] - ref["iters"]) for r in rs.values())
+    first_div = min(first_difference(ref["cuts"], r["cuts"]) for r in rs.values())
+    return int(window), int(first_div)
+
+
+def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div):
+    """Asserts the GPU outcome of a guarded solve against the oracle's `ref`
+    (a dict with status, iters, cuts, res_hist) under the measured spread."""
+    assert gpu_status == ref["status"], (gpu_status, ref["status"])
+    assert abs(int(gpu_iters) - int(ref["iters"])) <= window, (gpu_iters, ref["iters"], window)
+    k = min(first_div, len(ref["cuts"]))
+    gc = np.asarray(gpu_cuts[:k], dtype=np.int64)
+    rc = np.asarray(ref["cuts"][:k], dtype=np.int64)
+    assert len(gc) == k and np.array_equal(gc, rc), (first_difference(gc, rc), k)
+    h = min(first_div + 1, len(ref["res_hist"]), len(gpu_hist))
+    np.testing.assert_allclose(np.asarray(gpu_hist[:h]), np.asarray(ref["res_hist"][:h]),
+                               rtol=1e-6, atol=1e-13)

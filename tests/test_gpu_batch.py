@@ -3,13 +3,15 @@
 Integer outputs (offsets, Newton counts, statuses) are compared bit-exactly
 where the solve is in the rounding-robust regime (plain Newton, or guarded
 runs whose guard never cut); guarded runs whose guard cut are checked for
-what is unique (status, root, prefix invariant, fill), as in the
-single-IVP tests.
+what is unique (status, root, prefix invariant, fill) and for a Newton count
+within the spread that rounding alone produces on the oracle's rounding
+variants (tests/rounding.py).
 """
 import numpy as np
 import pytest
 
 import oracle as O
+import rounding as R
 from paper_2511_01465_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
@@ -54,7 +56,11 @@ def compare(bt, out, tol, max_iter, guard_B, sample=None):
             if o["status"] != O.NONFINITE:
                 assert res[b] == pytest.approx(o["res_hist"][o["iters"]], rel=1e-6, abs=1e-13)
         elif o["status"] == O.OK:
-            assert abs(iters[b] - o["iters"]) <= max(3, 0.35 * o["iters"])
+            # the guard cut: the count may move by what rounding alone moves it,
+            # measured on the oracle's rounding variants for this IVP
+            wl = W.Single("ivp", bt.system, bt.params[b], bt.x0[b], float(bt.h[b]), int(bt.N[b]))
+            window, _ = R.spread(R.runs(wl, tol, max_iter, guard_B))
+            assert abs(int(iters[b]) - o["iters"]) <= window, (b, iters[b], o["iters"], window)
             seq = O.sequential(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b])
             assert relerr(g, seq) <= TOL_REL
         else:

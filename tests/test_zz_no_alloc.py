@@ -22,6 +22,10 @@ def P():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2511_01465_gb300 import pitn
+    # the allocation-free solve always takes the default launch shape: make
+    # the workspace-backed solve take it too, whatever ran before
+    pitn.pitn_tune_enable(False)
+    pitn.pitn_tune_clear()
     return pitn
 
 
@@ -59,6 +63,26 @@ def test_noalloc_matches_workspace_solve_twice(P):
             assert (r.iters, r.status, r.guard_index) == (r_ref.iters, r_ref.status, r_ref.guard_index)
             assert r.final_res == pytest.approx(r_ref.final_res, rel=1e-12, abs=0.0)
             assert relerr(out, ref) <= TOL_REL
+
+
+def check_same(P, case):
+    (rc_ref, r_ref, ref), (rc, r, out) = both(P, *case)
+    assert rc == rc_ref
+    assert (r.iters, r.status, r.guard_index) == (r_ref.iters, r_ref.status, r_ref.guard_index)
+    assert r.final_res == pytest.approx(r_ref.final_res, rel=1e-12, abs=0.0)
+    assert relerr(out, ref) <= TOL_REL
+    return r
+
+
+def test_noalloc_full_iteration_budget_then_a_fresh_solve(P):
+    """A solve that uses all of the array's per-iteration records (max_iter =
+    1024 with tol = 0 never meets the tolerance), then a normal solve at once:
+    the second call must start clean although the array holds the first
+    call's barrier words, error word, record and residual history."""
+    r = check_same(P, (W.lorenz(N=2048), 0.0, 1024, 100.0))
+    assert r.status == P.PITN_NOT_CONVERGED and r.iters == 1024
+    check_same(P, (W.vdp(N=30001, h=1e-3), 1e-10, 60, 0.0))
+    check_same(P, (W.lorenz(N=777), 1e-10, 40, 0.0))
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(P):
