@@ -134,7 +134,7 @@ def make_options(precision=PITN_PREC_FP64, tile_elems=0, guard_B=0.0, guess=None
     o.guess = _ptr(guess)
     o.stream = ctypes.c_void_p(int(stream)) if stream is not None else None
     o.res_history = _ptr(res_history)
-    o.cut_history = _ptr(cut_history)
+    o.cut_history = _ptr(cut_history, np.int64)
     o._keep = (guess, res_history, cut_history)
     return o
 

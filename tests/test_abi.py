@@ -72,6 +72,10 @@ def test_argument_errors_are_detected_on_the_host(lib):
     assert P.pitn_solve(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, None) == E
     assert P.pitn_solve(P.PITN_FKPP, np.ones(1), np.ones(200), 1e-3, 10, 200, 1e-10, 5,
                         np.zeros((10, 200))) == E                                        # d > 128
+    # the option arrays marshal (residual and cut histories), the host check still fires
+    opt = P.make_options(res_history=np.zeros(6), cut_history=np.zeros(6, dtype=np.int64))
+    rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 0, 3, 1e-10, 5, out, opt)
+    assert rc == E
     opt = P.make_options(precision=P.PITN_PREC_MIXED_BF16)
     rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
     assert rc == E                                                                       # mixed needs d >= 64
