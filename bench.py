@@ -4,8 +4,8 @@ One step = one complete Newton solve (every residual evaluation, scan and
 update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_rk4|lorenz|lorenz_mixed|osc|robertson|fkpp|fkpp_mixed|
-                                                      batch|batch_small|adjoint]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|lorenz|lorenz_mixed|osc|
+                                                      robertson|fkpp|fkpp_mixed|batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica of
@@ -72,17 +72,44 @@ def load_peaks():
     return 6800.0, 1900.0, 1700.0, "fallback"
 
 
-# ALU peaks of a GB300 from unit counts and clocks: 152 SMs at 2.07 GHz;
-# FP64: nominal 1.25 TFLOP/s dense (FMA = 2 flops);
-# FP32: 128 FP32 lanes per SM -> 152 * 128 * 2 * 2.07e9 = 80.5 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# ALU peaks.  Measured in the bench process itself by the library's
+# register-only FMA probe (pitn_probe_fma_rate: FP64 DFMA and FP32 FFMA
+# issue rates, FMA = 2 flops); profiles/fp64_peak.md records one such
+# measurement (0.525 T DFMA/s, 39.0 T FFMA/s at 2070 MHz).  The figures
+# below are what the unit counts and clocks give, used only until the
+# probe has run: FP64 nominal 1.25 TFLOP/s; FP32 152 SMs x 128 lanes x 2 x
+# 2.07 GHz = 80.5 TFLOP/s.
+PEAKS = {"fp64_tflops": 1.25, "fp32_tflops": 152 * 128 * 2 * 2.07e9 / 1e12, "source": "unit counts"}
+
+
+def measure_alu_peaks():
+    from paper_2511_01465_gb300 import pitn as P
+    PEAKS["fp64_tflops"] = 2 * P.pitn_probe_fma_rate(0) / 1e12
+    PEAKS["fp32_tflops"] = 2 * P.pitn_probe_fma_rate(1) / 1e12
+    PEAKS["source"] = "measured in this run (pitn_probe_fma_rate)"
+    return dict(PEAKS)
+
+
+def fp64_peak():
+    return PEAKS["fp64_tflops"]
+
+
+def fp32_peak():
+    return PEAKS["fp32_tflops"]
+
+
+# Algorithmic bytes per step and Newton pass of the small-state solves: the
+# state read once and written once (2 d doubles); everything else (the
+# scan's scratch, a second read) is implementation traffic.
+def small_alg_bytes(d):
+    return 16 * d
 
 # FP64 flops per step executed by the small-state kernel, counted from its
 # source (FMA = 2): phase 1 (residual, compact Jacobian, thread fold) runs on
 # every residual evaluation, phase 3 (replay, update) once per Newton update.
 SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
                "vdp_mixed": (34.0, 9.0), "lorenz_mixed": (76.0, 19.0),
+               "vdp_ff": (34.0, 9.0),
                # backward Euler Robertson: f 8, Jf 9, I - h Jf 12, h_n 9, 3x3 inverse 42
                # (one division counted as 1), M^-1 h_n 18, dense fold 72; replay 18 + update 3
                "robertson": (170.0, 21.0),
@@ -94,6 +121,10 @@ SMALL_FLOPS = {"vdp": (34.0, 9.0), "osc": (26.0, 9.0), "lorenz": (76.0, 19.0),
 # as counted by ncu (DADD + DFMA + DMUL thread instructions at 1 and 11 passes;
 # equal to the count of the source)
 FP64_OPS = {"vdp": (20.0, 6.0)}
+# FP64 work per step and pass of the reduced-precision scans (fused kernel,
+# one pass per Newton iteration): the van der Pol residual (7 instructions,
+# 11 flops) and the update (FP32 scan: 2 DADD; float-float: 4 DADD)
+REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed": (13.0, 20.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -125,6 +156,10 @@ def workload(name):
         return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=2,
                     desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
                          "scan in FP32 delta form (inexact Newton), FP64 residual and update")
+    if name == "vdp_ff":
+        return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=3,
+                    desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
+                         "scan in double-FP32 (float-float), FP64 residual and update")
     if name == "lorenz_mixed":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0, precision=2,
                     desc="lorenz63 N=8192 h=1e-3, guarded Newton B=100, scan in FP32 delta form")
@@ -304,12 +339,12 @@ def run_ours_batch(args, rank, world, local_rank, spec):
     flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
     achieved = flops / (kms / 1e3 / nk) / 1e12 if kms > 0 else 0.0
     shape = P.pitn_tune_get(f"batch:{bt.system}:{d}:{M.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak(), "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak(), "traffic": None,
                 "kernel": batch_kernel_name(shape),
                 "kernel_launches_per_step": kl / nk, "kernel_ms_per_launch": kms / max(kl, 1),
                 "note": "FP64 flops of the executed iterations counted from the kernel source; "
-                        "peak = nominal GB300 FP64"}
+                        "peak = measured DFMA rate x 2"}
     # the same IVPs solved one at a time by the single-IVP GPU solver (a sample)
     single = None
     if rank == 0:
@@ -488,11 +523,11 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
     flops = float((bt.N * ((it_h + 1) * p1 + it_h * p3)).sum())
     ach = flops / (fwd_ms / 1e3 / nk) / 1e12 if fwd_ms > 0 else 0.0
     shape = P.pitn_tune_get(f"batch:{bt.system}:{d}:{M.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}")
-    roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+    roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak(), "unit": "TFLOP/s",
+                "frac": ach / fp64_peak(), "traffic": None,
                 "kernel": "forward solve: " + batch_kernel_name(shape),
                 "kernel_launches_per_step": fwd_n / nk, "kernel_ms_per_launch": fwd_ms / max(fwd_n, 1),
-                "note": "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"}
+                "note": "FP64 flops counted from the kernel source; peak = measured DFMA rate x 2"}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -617,7 +652,7 @@ def run_ours(args, rank, world, local_rank):
 
     roofline = roofline_for(args.workload, spec, wl, res, ktimes, nk)
     tkey = (f"small:{wl.system}:{wl.d}:{wl.N.bit_length() - 1}:{1 if spec['guard_B'] > 0 else 0}"
-            f"{ {1: ':rk4', 2: ':be', 3: ':tr'}.get(method, '')}{':f32' if prec == 2 else ''}")
+            f"{ {1: ':rk4', 2: ':be', 3: ':tr'}.get(method, '')}{ {2: ':f32', 3: ':ff'}.get(prec, '')}")
     launch_shape = P.pitn_tune_get(tkey)   # (threads per CTA, CTAs per SM), + min steps per thread
     if launch_shape is not None:
         cm = P.pitn_tune_get(tkey + ":c")
@@ -634,7 +669,123 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / nk for k, v in ktimes.items()}}
+    if args.workload == "vdp" and not args.no_companions:
+        # the metric's comparison: reduced-precision scans and batching against
+        # the plain FP64 solver, same tolerance, timed after the FP64 line
+        line["mixed"] = {
+            "fp32_scan": companion_single(args, "vdp_mixed", dev, stream, flush, value, traj),
+            "float_float_scan": companion_single(args, "vdp_ff", dev, stream, flush, value, traj),
+        }
+        line["batched"] = companion_batched(args, dev, stream)
     return line
+
+
+def companion_single(args, name, dev, stream, flush, ref_value, ref_traj):
+    """The same metric for another precision of the same workload (same
+    tolerance, same timing rules), with its ratio to the FP64 line's value
+    and its largest difference from the FP64 solve's trajectory."""
+    import torch
+    from paper_2511_01465_gb300 import pitn as P
+    spec = workload(name)
+    wl = spec["wl"]
+    params = torch.tensor(wl.params, dtype=torch.float64, device=dev)
+    x0 = torch.tensor(wl.x0, dtype=torch.float64, device=dev)
+    traj = torch.empty((wl.N, wl.d), dtype=torch.float64, device=dev)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=spec["precision"])
+
+    def solve_once():
+        rc, res = P.pitn_solve_ex(wl.system, params, x0, wl.h, wl.N, wl.d, spec["tol"], spec["max_iter"],
+                                  traj, opt)
+        P.check(rc, "pitn_solve_ex")
+        return res
+
+    P.pitn_tune_enable(not args.no_tune)
+    for _ in range(args.warmup):
+        res = solve_once()
+    P.pitn_tune_enable(False)
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        res = solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(sum(times)) / args.steps
+    ok = res.status == P.PITN_OK and res.final_res <= spec["tol"]
+    value = (wl.N if ok else 0) / (ms / 1e3)
+    diff = float((traj - ref_traj).abs().max() / ref_traj.abs().max())
+    return {"workload": spec["desc"], "value": value, "unit": UNIT, "ms_per_step": ms,
+            "newton_updates": res.iters, "status": P.pitn_status_string(res.status), "final_res": res.final_res,
+            "ratio_vs_fp64": value / ref_value if ref_value > 0 else None,
+            "max_rel_diff_vs_fp64_solve": diff}
+
+
+def companion_batched(args, dev, stream):
+    """Batching against the plain solver: the 4096-IVP Lorenz batch
+    (lengths 2^10..2^13) in one batched solve, against its first 64 IVPs
+    solved one pitn_solve_ex call at a time, both at tol 1e-8."""
+    import torch
+    from paper_2511_01465_gb300 import pitn as P
+    spec = workload("batch_small")
+    bt = spec["bt"]
+    t = lambda a, dt=torch.float64: torch.tensor(a, dtype=dt, device=dev)
+    params, x0, h, N = t(bt.params), t(bt.x0), t(bt.h), t(bt.N, torch.int64)
+    M, d = int(bt.N.sum()), bt.d
+    traj = torch.empty((M, d), dtype=torch.float64, device=dev)
+    offs = torch.empty(bt.B + 1, dtype=torch.int64, device=dev)
+    iters = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    status = torch.empty(bt.B, dtype=torch.int32, device=dev)
+    res = torch.empty(bt.B, dtype=torch.float64, device=dev)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+
+    def solve_once():
+        P.check(P.pitn_solve_batch(bt.system, bt.B, params, x0, h, N, d, spec["tol"], spec["max_iter"],
+                                   traj, offs, iters, status, res, opt), "pitn_solve_batch")
+
+    P.pitn_tune_enable(not args.no_tune)
+    solve_once()
+    P.pitn_tune_enable(False)
+    solve_once()
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solve_once()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    st_h, res_h = status.cpu().numpy(), res.cpu().numpy()
+    ok = (st_h == P.PITN_OK) & (res_h <= spec["tol"])
+    batched = float(bt.N[ok].sum()) / (ms / 1e3)
+    n_s = 64
+    so = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream)
+    tr1 = torch.empty((int(bt.N[:n_s].max()), d), dtype=torch.float64, device=dev)
+    ps = [t(bt.params[b]) for b in range(n_s)]
+    xs = [t(bt.x0[b]) for b in range(n_s)]
+    P.pitn_solve_ex(bt.system, ps[0], xs[0], float(bt.h[0]), int(bt.N[0]), d, spec["tol"], spec["max_iter"],
+                    tr1, so)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    solved1 = 0
+    for b in range(n_s):
+        _, r1 = P.pitn_solve_ex(bt.system, ps[b], xs[b], float(bt.h[b]), int(bt.N[b]), d, spec["tol"],
+                                spec["max_iter"], tr1, so)
+        if r1.status == P.PITN_OK and r1.final_res <= spec["tol"]:
+            solved1 += int(bt.N[b])
+    torch.cuda.synchronize(dev)
+    one = solved1 / (time.perf_counter() - t0)
+    return {"workload": spec["desc"], "value": batched, "unit": UNIT, "ms_per_step": ms,
+            "converged_ivps": int(ok.sum()),
+            "one_at_a_time": {"value": one, "unit": UNIT,
+                              "sample": f"first {n_s} IVPs, one pitn_solve_ex call each (host clock)"},
+            "ratio_vs_one_at_a_time": batched / one if one > 0 else None}
 
 
 def fk_tiles(N, sms=152, per_sm=1):
@@ -667,56 +818,52 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
     ms, launches = ktimes[kern]
     passes = res.iters + 1
     per_step_s = ms / 1e3 / steps
-    if kern == "newton_small" and spec.get("precision", 0) == 2:
-        # mixed: the FP64 part per step is the residual (van der Pol 11, Lorenz 17 flops)
-        # and the update (d flops); the scan runs in FP32.  Its design traffic per
-        # step and pass is x read twice and written once (24 d B) plus the FP32
-        # scratch (Jacobian entries and residual, JN + d floats) written and read.
-        # (the d = 2 solve runs fused: the state is read once per pass, 16 d B)
-        f64 = {"vdp_mixed": 11.0 + 2.0, "lorenz_mixed": 17.0 + 3.0}[name]
-        jn = {"vdp_mixed": 2, "lorenz_mixed": 3}[name]
-        xb = 16 * wl.d if wl.d == 2 else 24 * wl.d
-        flops = wl.N * f64 * passes
-        nbytes = wl.N * (xb + 8 * (jn + wl.d)) * passes
+    if kern == "newton_small":
+        # FP64-pipe bound (ncu: the FP64 pipe is the busiest unit of every
+        # small-state kernel); flops counted from the source (FMA = 2) against
+        # the measured DFMA rate, the FP64 instruction issue (DADD, DMUL, DFMA
+        # one slot each) as the pipe's fraction, and the algorithmic bytes
+        # (state read and written once per pass) against the measured copy
+        # bandwidth
         hbm, _, _, src = load_peaks()
-        f_alu = flops / (ms / 1e3 / steps) / 1e12 / FP64_PEAK_TFLOPS
-        f_hbm = nbytes / (ms / 1e3 / steps) / 1e9 / hbm
-        if f_hbm > f_alu:
-            flops = None
-            achieved = nbytes / (ms / 1e3 / steps) / 1e9
-            return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": f_hbm,
-                    "traffic": traffic_for(name), "kernel": kern, "kernel_launches_per_step": launches / steps,
-                    "kernel_ms_per_launch": ms / max(launches, 1),
-                    "fp64_frac": f_alu,
-                    "note": f"design bytes per step {xb + 8 * (jn + wl.d)} B x passes; peak = {src} "
-                            f"copy bandwidth; fp64_frac = FP64 residual+update flops vs nominal 1.25 TFLOP/s"}
-        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
-        note = "FP64 flops (residual + update) of the mixed kernel; peak = nominal GB300 FP64"
-    elif kern == "newton_small":
-        p1, p3 = SMALL_FLOPS[name]
-        flops = wl.N * (p1 * passes + p3 * res.iters)
-        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
-        note = "FP64 flops counted from the kernel source; peak = nominal GB300 FP64"
-        if name in FP64_OPS:
-            # the pipe view: a DADD or DMUL takes an FP64 issue slot like a DFMA
-            o1, o3 = FP64_OPS[name]
-            ops = wl.N * (o1 * passes + o3 * res.iters) / (ms / 1e3 / steps) / 1e12
-            extra = {"fp64_ops_tops": ops, "fp64_ops_frac": ops / (FP64_PEAK_TFLOPS / 2)}
-            note += ("; fp64_ops_frac: FP64 instructions (DADD, DMUL, DFMA each one, per step: "
-                     f"{o1:g} phase 1 + {o3:g} phase 3, ncu counters) against the DFMA issue rate "
-                     f"{FP64_PEAK_TFLOPS / 2:g} T/s")
+        if name in REDUCED_FP64:
+            ops, fl = REDUCED_FP64[name]
+            flops = wl.N * fl * passes
+            fp64_ops = wl.N * ops * passes
+            note = ("FP64 work of the reduced-precision scan: residual and update per step and pass "
+                    f"({ops:g} instructions, {fl:g} flops); the scan itself runs on the FP32 pipe")
+        else:
+            p1, p3 = SMALL_FLOPS[name]
+            flops = wl.N * (p1 * passes + p3 * res.iters)
+            o = FP64_OPS.get(name)
+            fp64_ops = wl.N * (o[0] * passes + o[1] * res.iters) if o else None
+            note = "FP64 flops per step counted from the kernel source (phase 1 every pass, phase 3 per update)"
+        achieved = flops / per_step_s / 1e12
+        alg = wl.N * small_alg_bytes(wl.d) * passes
+        out = {"bound": "alu", "achieved": achieved, "peak": fp64_peak(), "unit": "TFLOP/s",
+               "frac": achieved / fp64_peak(), "traffic": traffic_for(name), "kernel": kern,
+               "kernel_launches_per_step": launches / steps, "kernel_ms_per_launch": ms / max(launches, 1),
+               "peak_source": PEAKS["source"] + " (DFMA rate x 2)",
+               "hbm_achieved_gbs": alg / per_step_s / 1e9, "hbm_peak_gbs": hbm,
+               "hbm_frac": alg / per_step_s / 1e9 / hbm,
+               "hbm_note": f"algorithmic bytes {small_alg_bytes(wl.d)} B per step and pass (x read and written "
+                           f"once) against the {src} copy bandwidth",
+               "note": note}
+        if fp64_ops:
+            out["fp64_pipe_frac"] = fp64_ops / per_step_s / (fp64_peak() / 2 * 1e12)
+        return out
     elif kern == "fkpp_residual":
         flops = wl.N * passes * 128 * 15
-        peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
-        note = "FP64 residual flops (15 per entry); peak = nominal GB300 FP64"
+        peak, bound, unit = fp64_peak(), "alu", "TFLOP/s"
+        note = "FP64 residual flops (15 per entry); peak = measured DFMA rate x 2"
     elif kern == "fkpp_fold":
         # the scan runs once per Newton update (a converged pass stops after its residual)
         mixed = spec.get("precision", 0) == 1
         flops = wl.N * res.iters * FK_FOLD_REAL_FLOPS
-        peak = FP32_PEAK_TFLOPS if mixed else FP64_PEAK_TFLOPS
+        peak = fp32_peak() if mixed else fp64_peak()
         bound, unit = "alu", "TFLOP/s"
         note = ("dense fold flops in " + ("FP32" if mixed else "FP64") +
-                "; peak from unit counts and clocks")
+                "; peak = measured " + ("FFMA" if mixed else "DFMA") + " rate x 2")
     elif kern == "fkpp_compose":
         mixed = spec.get("precision", 0) == 1
         flops = fk_composes(fk_tiles(wl.N)) * FK_COMPOSE_FLOPS * res.iters
@@ -725,8 +872,8 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
             peak, bound, unit = bf16, "tensor", "TFLOP/s"
             note = f"BF16 tensor-core composes; peak = {src} cuBLAS bf16 burst"
         else:
-            peak, bound, unit = FP64_PEAK_TFLOPS, "alu", "TFLOP/s"
-            note = "FP64 CUDA-core composes; peak = nominal GB300 FP64"
+            peak, bound, unit = fp64_peak(), "alu", "TFLOP/s"
+            note = "FP64 CUDA-core composes; peak = measured DFMA rate x 2"
     else:
         hbm, _, _, src = load_peaks()
         flops = None
@@ -761,7 +908,7 @@ def oracle_passes(name, fallback):
     """Residual evaluations the oracle's own full solve needs (stored by
     tests/golden/make_oracle_golden.py, which runs only the oracle)."""
     key = {"vdp": "vdp_2^22_guard100_tol1e-8_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
-           "vdp_mixed": "vdp_2^22_guard100_tol1e-8_it400",
+           "vdp_mixed": "vdp_2^22_guard100_tol1e-8_it400", "vdp_ff": "vdp_2^22_guard100_tol1e-8_it400",
            "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
@@ -794,7 +941,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
-SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6,
+SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6, "vdp_ff": 6,
                 "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7}
 
 
@@ -904,6 +1051,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner")
+    ap.add_argument("--no-companions", action="store_true",
+                    help="vdp: skip the FP32-scan, float-float and batched comparison lines")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -921,6 +1070,8 @@ def main():
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     import __graft_entry__ as ge
     ge.build_library_only()
+    torch.cuda.set_device(local_rank)
+    peaks = measure_alu_peaks()
     spec0 = workload(args.workload)
     if spec0["kind"] == "batch":
         line = run_ours_batch(args, rank, world, local_rank, spec0)
@@ -935,6 +1086,7 @@ def main():
         full_passes = oracle_passes(args.workload, line["config"]["newton_updates"] + 1)
         line["cpu_baseline"] = cpu_baseline(workload(args.workload), full_passes,
                                             SAMPLE_ITERS.get(args.workload, 5))
+    line["alu_peaks"] = peaks
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -98,9 +98,16 @@ enum {
                                   scan on tensor cores (BF16 operands, FP32
                                   accumulation) in the delta form A = J - I;
                                   an inexact Newton step */
-    PITN_PREC_MIXED_FP32 = 2   /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
+    PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
                                   Euler: the scan's elements in FP32 delta form
                                   (I + S, c); an inexact Newton step */
+    PITN_PREC_FP64_FF = 3      /* d = 2 (VDP, LINEAR_OSC), explicit Euler (not in
+                                  the paper): the scan (Jacobians, folds, carries,
+                                  replay) in double-FP32 "float-float" arithmetic,
+                                  ~2^-47 relative, on the FP32 pipe; residual,
+                                  stopping test and update in FP64.  An inexact
+                                  Newton step whose error is ~60x FP64 rounding:
+                                  it reaches the FP64 root at FP64 accuracy */
 };
 
 /* Per-solve outcome. */

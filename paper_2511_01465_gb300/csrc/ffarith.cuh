@@ -16,15 +16,15 @@
 // Conversions from FP64 run on the integer pipes (as in fpconv.cuh): hi is
 // the double rounded to 24 bits, lo the remainder rounded to 24 bits, built
 // from the bit pattern, so that a conversion puts no work on the FP64 pipe.
-// Magnitudes below the float normal range flush to zero (this arithmetic
-// serves only the scan of the Newton step, an inexact linear solve).
+// Remainders far below the float range flush to zero (this arithmetic serves
+// only the scan of the Newton step, an inexact linear solve).
 #pragma once
 
 #include "fpconv.cuh"
 
 namespace pitn {
 
-struct ff {
+struct __align__(8) ff {
     float hi, lo;
 };
 
@@ -86,10 +86,14 @@ __device__ __forceinline__ ff ff_from_double(double x) {
     const int es = eb - 1023 - 52 + 127;                   // biased float exponent of 2^(E-52)
     const bool finite_hi = (__float_as_uint(hi) & 0x7f800000u) != 0x7f800000u;
     float lo = 0.f;
-    if (es >= 1 && es <= 254 && eb != 0 && finite_hi && t != 0) {
-        const float scale = __uint_as_float((unsigned)es << 23);
+    if (eb != 0 && finite_hi && t != 0) {
         const float tf = __int2float_rn(t);
-        lo = __fmul_rn(tf, scale);
+        if (es >= 1) {            // 2^(E-52) a normal float (es <= 254 whenever hi is finite)
+            lo = __fmul_rn(tf, __uint_as_float((unsigned)es << 23));
+        } else if (es >= -99) {   // two scalings: the remainder itself may still be normal
+            lo = __fmul_rn(__fmul_rn(tf, __uint_as_float((unsigned)(es + 100) << 23)),
+                           __uint_as_float(27u << 23));   // 2^-100
+        }
         if (w1 & 0x80000000u) lo = -lo;
     }
     return ff{hi, lo};

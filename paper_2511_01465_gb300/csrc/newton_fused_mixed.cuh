@@ -241,17 +241,26 @@ __device__ __forceinline__ void pol_block_scan(typename Pol::T* Q, typename Pol:
     __syncthreads();
 }
 
-template <class Sys>
+// L2-coherent loads of aggregates written by other CTAs before a grid barrier
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ ff ld_cg(const ff* p) {
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return ff{v.x, v.y};
+}
+
+
+template <class Sys, class Pol>
 __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
+    using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
     Sys sys;
     sys.init(a.params, a.h);
 
-    __shared__ float s_wex[kMaxWarps][E];
-    __shared__ float s_tot[E];
-    __shared__ float s_g[kMaxWarps][E];
-    __shared__ float s_gtot[E];
-    __shared__ float s_zin[D];
+    __shared__ T s_wex[kMaxWarps][E];
+    __shared__ T s_tot[E];
+    __shared__ T s_g[kMaxWarps][E];
+    __shared__ T s_gtot[E];
+    __shared__ T s_zin[D];
     extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
 
     const int lane = threadIdx.x & 31;
@@ -259,8 +268,8 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     const unsigned G = gridDim.x;
-    float* __restrict__ scr = reinterpret_cast<float*>(a.scratch);
-    float* __restrict__ agg = reinterpret_cast<float*>(a.agg);
+    T* __restrict__ scr = reinterpret_cast<T*>(a.scratch);   // sizeof(T) <= sizeof(double)
+    T* __restrict__ agg = reinterpret_cast<T*>(a.agg);
     float capf;
     {
         const double capd = __longlong_as_double((long long)a.cap_bits);
@@ -281,67 +290,59 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
     int it = 0, status = PITN_NOT_CONVERGED;
     double final_res = 0.0;
 
-    float QA[D * D], cA[D], QB[D * D], cB[D];
+    T QA[D * D], cA[D], QB[D * D], cB[D];
     unsigned long long my_res = 0ull;
 
-    // element k from the state pair (xp, xc): FP64 residual, FP32 delta-form
-    // element into scratch, folded into (Q, c)
-    auto fold_elem = [&](long long k, const double* xp, const double* xc, float* Q, float* c,
+    // element k from the state pair (xp, xc): FP64 residual, scan element into
+    // scratch, folded into (Q, c)
+    auto fold_elem = [&](long long k, const double* xp, const double* xc, T* Q, T* c,
                          unsigned long long& res) {
         double r[D];
-        float sv[JN], rf[D];
-        sys.eval_mixed(xp, xc, r, sv);
+        T sv[JN], rf[D];
+        Pol::eval(sys, xp, xc, r, sv);
 #pragma unroll
         for (int j = 0; j < JN; ++j) scr[sidx(k, j)] = sv[j];
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const unsigned long long b = abs_bits(r[j]);
             res = b > res ? b : res;
-            rf[j] = d2f_int(r[j]);
+            rf[j] = Pol::from_double(r[j]);
             scr[sidx(k, JN + j)] = rf[j];
         }
-        if (k == 0) {  // a_0 = (0, -r_0): S = -I
-#pragma unroll
-            for (int j = 0; j < D * D; ++j) Q[j] = (j % (D + 1) == 0) ? -1.f : 0.f;
-#pragma unroll
-            for (int j = 0; j < D; ++j) c[j] = -rf[j];
-        } else {
-            float S[D * D];
-            sys.sfull(sv, S);
-            dz_leaf<D>(S, rf, Q, c);
-        }
+        if (k == 0) Pol::template head<D>(rf, Q, c);   // a_0 = (0, -r_0), eq. 3.4
+        else Pol::leaf(sys, sv, rf, Q, c);
     };
-    auto prepend_elem = [&](long long k, const double* xp, const double* xc, float* Q, float* c,
+    auto prepend_elem = [&](long long k, const double* xp, const double* xc, T* Q, T* c,
                             unsigned long long& res) {
-        float EQ[D * D], Ec[D];
-        dz_zero<D>(EQ, Ec);
+        T EQ[D * D], Ec[D];
+        Pol::template ident<D>(EQ, Ec);
         fold_elem(k, xp, xc, EQ, Ec, res);
-        dz_compose<D>(Q, c, EQ, Ec, Q, c);
+        Pol::template compose<D>(Q, c, EQ, Ec, Q, c);
     };
-    auto append_fill = [&](long long count, const double* xf, float* Q, float* c, unsigned long long& res) {
+    auto append_fill = [&](long long count, const double* xf, T* Q, T* c, unsigned long long& res) {
         if (count <= 0) return;
         double rf64[D];
-        float svf[JN], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
-        sys.eval_mixed(xf, xf, rf64, svf);
+        T svf[JN], rff[D], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
+        Pol::eval(sys, xf, xf, rf64, svf);
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             const unsigned long long b = abs_bits(rf64[j]);
             res = b > res ? b : res;
-            Ec[j] = -d2f_int(rf64[j]);
+            rff[j] = Pol::from_double(rf64[j]);
         }
-        sys.sfull(svf, EQ);
-        dz_zero<D>(RQ, Rc);
+        Pol::elem(sys, svf, rff, EQ, Ec);
+        Pol::template ident<D>(RQ, Rc);
         for (long long e = count;;) {
-            if (e & 1) dz_compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
+            if (e & 1) Pol::template compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
             e >>= 1;
             if (!e) break;
-            dz_compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
+            Pol::template compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
         }
-        dz_compose<D>(RQ, Rc, Q, c, Q, c);
+        Pol::template compose<D>(RQ, Rc, Q, c, Q, c);
     };
-    auto build_chain = [&](const double* X, long long s, long long e, long long qq, float* Q, float* c,
+    auto build_chain = [&](const double* X, long long s, long long e, long long qq, T* Q, T* c,
                            unsigned long long& res) {
-        dz_zero<D>(Q, c);
+        Pol::template ident<D>(Q, c);
         if (s >= e) return;
         const long long sf = (qq < N) ? (qq > 1 ? qq : 1LL) : N;
         const long long er = min(e, max(s, sf));
@@ -370,9 +371,9 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
         const double* __restrict__ Xc = cur ? a.X1 : a.X0;
         double* __restrict__ Xn = cur ? a.X0 : a.X1;
 
-        float Q[D * D], c[D], eQ[D * D], ec[D];
-        dz_compose<D>(QB, cB, QA, cA, Q, c);
-        dz_block_scan<D>(Q, c, eQ, ec, s_wex, s_tot);
+        T Q[D * D], c[D], eQ[D * D], ec[D];
+        Pol::template compose<D>(QB, cB, QA, cA, Q, c);
+        pol_block_scan<Pol, D>(Q, c, eQ, ec, s_wex, s_tot);
         if (threadIdx.x < E) agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -391,31 +392,31 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
 
         {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;
-            float gQ[D * D], gc[D];
-            dz_zero<D>(gQ, gc);
+            T gQ[D * D], gc[D];
+            Pol::template ident<D>(gQ, gc);
             for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
-                float sQ[D * D], sc[D];
+                T sQ[D * D], sc[D];
 #pragma unroll
-                for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+                for (int j = 0; j < D * D; ++j) sQ[j] = ld_cg(agg + (size_t)i * E + j);
 #pragma unroll
-                for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
-                dz_compose<D>(sQ, sc, gQ, gc, gQ, gc);
+                for (int j = 0; j < D; ++j) sc[j] = ld_cg(agg + (size_t)i * E + D * D + j);
+                Pol::template compose<D>(sQ, sc, gQ, gc, gQ, gc);
             }
-            float xQ[D * D], xc[D];
-            dz_block_scan<D>(gQ, gc, xQ, xc, s_g, s_gtot);
+            T xQ[D * D], xc[D];
+            pol_block_scan<Pol, D>(gQ, gc, xQ, xc, s_g, s_gtot);
             if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
-                float v[D], t[D], zero[D];
+                T v[D], t[D], zero[D];
 #pragma unroll
-                for (int j = 0; j < D; ++j) zero[j] = 0.f;
-                dz_apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
-                dz_apply<D>(xQ, xc, t, v);
+                for (int j = 0; j < D; ++j) zero[j] = Pol::zero();
+                Pol::template apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
+                Pol::template apply<D>(xQ, xc, t, v);
                 for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
-                    float sQ[D * D], sc[D];
+                    T sQ[D * D], sc[D];
 #pragma unroll
-                    for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+                    for (int j = 0; j < D * D; ++j) sQ[j] = ld_cg(agg + (size_t)i * E + j);
 #pragma unroll
-                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
-                    dz_apply<D>(sQ, sc, v, t);
+                    for (int j = 0; j < D; ++j) sc[j] = ld_cg(agg + (size_t)i * E + D * D + j);
+                    Pol::template apply<D>(sQ, sc, v, t);
 #pragma unroll
                     for (int j = 0; j < D; ++j) v[j] = t[j];
                 }
@@ -424,34 +425,31 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) s_zin[j] = 0.f;
+                for (int j = 0; j < D; ++j) s_zin[j] = Pol::zero();
             }
             __syncthreads();
         }
 
         // ---- fused pass ----------------------------------------------------
-        float zA[D], zB[D];
+        T zA[D], zB[D];
         {
-            float zw[D];
-            dz_apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
-            dz_apply<D>(eQ, ec, zw, zA);
-            dz_apply<D>(QA, cA, zA, zB);
+            T zw[D];
+            Pol::template apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
+            Pol::template apply<D>(eQ, ec, zw, zA);
+            Pol::template apply<D>(QA, cA, zA, zB);
         }
         const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
-        double xf[D];
-        float Sf[D * D], rff[D];
+        T svf[JN], rff[D];
         if (sfill < k1 && k0 < k1) {
-            double rf64[D];
-            float svf[JN];
+            double xf[D], rf64[D];
             load_state<D>(Xc, a.x0, q - 1, q, xf);
-            sys.eval_mixed(xf, xf, rf64, svf);
-            sys.sfull(svf, Sf);
+            Pol::eval(sys, xf, xf, rf64, svf);
 #pragma unroll
-            for (int j = 0; j < D; ++j) rff[j] = d2f_int(rf64[j]);
+            for (int j = 0; j < D; ++j) rff[j] = Pol::from_double(rf64[j]);
         }
-        float NA[D * D], nA[D], NB[D * D], nB[D];
-        dz_zero<D>(NA, nA);
-        dz_zero<D>(NB, nB);
+        T NA[D * D], nA[D], NB[D * D], nB[D];
+        Pol::template ident<D>(NA, nA);
+        Pol::template ident<D>(NB, nB);
         unsigned long long resA = 0ull, resB = 0ull;
         double prevA[D], prevB[D], firstA[D], firstB[D];
         long long cutA = N, cutB = N;
@@ -465,19 +463,17 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
 #pragma unroll
             for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
         };
-        auto step = [&](int ch, long long k, long long s, float* z, double* prev, double* first, float* NQ,
-                        float* nc, long long& cut, unsigned long long& res) {
-            float S[D * D], r[D];
+        auto step = [&](int ch, long long k, long long s, T* z, double* prev, double* first, T* NQ,
+                        T* nc, long long& cut, unsigned long long& res) {
+            T sv[JN], r[D];
             if (k < sfill) {
-                float sv[JN];
 #pragma unroll
                 for (int j = 0; j < JN; ++j) sv[j] = scr[sidx(k, j)];
 #pragma unroll
                 for (int j = 0; j < D; ++j) r[j] = scr[sidx(k, JN + j)];
-                sys.sfull(sv, S);
             } else {
 #pragma unroll
-                for (int j = 0; j < D * D; ++j) S[j] = Sf[j];
+                for (int j = 0; j < JN; ++j) sv[j] = svf[j];
 #pragma unroll
                 for (int j = 0; j < D; ++j) r[j] = rff[j];
             }
@@ -485,25 +481,16 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
             load_state<D>(Xc, a.x0, k, q, x);
             if (k == 0) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) z[j] = -r[j];
+                for (int j = 0; j < D; ++j) z[j] = Pol::neg(r[j]);
             } else {
-                float t[D];
-#pragma unroll
-                for (int i = 0; i < D; ++i) {
-                    float sacc = z[i] - r[i];
-#pragma unroll
-                    for (int l = 0; l < D; ++l) sacc = fmaf(S[i * D + l], z[l], sacc);
-                    t[i] = sacc;
-                }
-#pragma unroll
-                for (int j = 0; j < D; ++j) z[j] = t[j];
+                Pol::replay(sys, sv, r, z);
             }
             double xn[D];
             bool bad = false;
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                xn[j] = x[j] + f2d_int(z[j]);
-                bad |= !(fabsf(z[j]) <= capf);
+                xn[j] = Pol::add_to(x[j], z[j]);
+                bad |= !Pol::within(z[j], capf);
             }
             put_row(ch, k, xn);
             if (bad) {
@@ -531,10 +518,10 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
         if (staged) stg.finish(Xn);
         const long long kc = (cutA < N) ? cutA : cutB;
         if (LB > 0 && kc > km) {
-            float EQ[D * D], Ec[D];
-            dz_zero<D>(EQ, Ec);
+            T EQ[D * D], Ec[D];
+            Pol::template ident<D>(EQ, Ec);
             fold_elem(km, prevA, firstB, EQ, Ec, resB);
-            dz_compose<D>(NB, nB, EQ, Ec, NB, nB);
+            Pol::template compose<D>(NB, nB, EQ, Ec, NB, nB);
         }
         unsigned long long my_q = (kc < N) ? ~(unsigned long long)kc : 0ull;
 #pragma unroll
@@ -571,7 +558,7 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
                     load_state<D>(Xn, a.x0, qn - 1, qn, xfn);
                     if (sfn < km) {
                         append_fill(km - sfn, xfn, NA, nA, my_res);
-                        dz_zero<D>(NB, nB);
+                        Pol::template ident<D>(NB, nB);
                         append_fill(LB, xfn, NB, nB, my_res);
                     } else {
                         append_fill(k1 - sfn, xfn, NB, nB, my_res);

@@ -55,9 +55,19 @@ void small_default_config(int d, long long N, int* block, int* C) {
 // The kernel instantiation for a system, step map and precision.  Explicit
 // maps are instantiated here; the implicit (backward Euler) ones and the
 // stiff test systems live in newton_implicit.cu.
-int select_small_kernel(int system_id, int method, bool mixed, pitn::SmallKernel* K) {
+int select_small_kernel(int system_id, int method, int precision, pitn::SmallKernel* K) {
     using namespace pitn;
-    if (mixed) {
+    if (precision == PITN_PREC_FP64_FF) {
+        // the float-float scan runs fused, like the FP32 one: its FP64 work
+        // is the residual and the update
+        if (method != PITN_STEP_EULER) return PITN_EUNSUPPORTED;
+        switch (system_id) {
+        case PITN_VDP: *K = small_kernel_of<VanDerPol, kVarFusedFF>(); return PITN_OK;
+        case PITN_LINEAR_OSC: *K = small_kernel_of<LinearOsc, kVarFusedFF>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (precision == PITN_PREC_MIXED_FP32) {
         // the d = 2 FP32-scan solves run fused: their FP64 work (residual,
         // update) is light enough that one pass per iteration beats two (van
         // der Pol N = 2^22: 21.5 -> 17.0 ms); Lorenz (177 registers fused)
@@ -103,7 +113,7 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     using namespace pitn;
     if (o.tile_elems > 0) cmin = o.tile_elems;
     pitn::SmallKernel K{};
-    int rc = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
+    int rc = select_small_kernel(system_id, o.method, o.precision, &K);
     if (rc != PITN_OK) return rc;
     int per_sm = K.per_sm(block);
     const int W = K.W;
@@ -214,7 +224,7 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
                   o.method == PITN_STEP_RK4 ? ":rk4"
                   : o.method == PITN_STEP_BACKWARD_EULER ? ":be"
                   : o.method == PITN_STEP_TRAPEZOID ? ":tr" : "",
-                  o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : "");
+                  o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : o.precision == PITN_PREC_FP64_FF ? ":ff" : "");
     char ckey[104];
     std::snprintf(ckey, sizeof(ckey), "%s:c", key);   // steps-per-thread floor of the shape
     int tb = 0, tc = 0;
@@ -237,7 +247,7 @@ int small_solve_full(int system_id, const SolveIO& io, double h, int64_t N, int 
                 return PITN_ECUDA;
         }
         pitn::SmallKernel K{};
-        int rk = select_small_kernel(system_id, o.method, o.precision == PITN_PREC_MIXED_FP32, &K);
+        int rk = select_small_kernel(system_id, o.method, o.precision, &K);
         if (rk != PITN_OK) return rk;
         // a short trajectory fills the GPU only with few steps per thread, and
         // there the floor decides the grid: try 1, 2 and 4 steps as well

@@ -656,7 +656,7 @@ namespace pitn {
 
 // Kernel variants behind a SmallKernel: the three-phase FP64 kernel, its
 // FP32 delta-form twin, and the fused FP64 and FP32-delta kernels.
-enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3 };
+enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3, kVarFusedFF = 4 };
 
 // Dynamic shared memory of a launch: the row-stage tiles for d = 2.
 template <class Sys>
@@ -668,7 +668,8 @@ template <class Sys, int VAR>
 static const void* small_kernel_ptr() {
     if constexpr (VAR == kVarMixed) return (const void*)newton_small_mixed_kernel<Sys>;
     else if constexpr (VAR == kVarFused) return (const void*)newton_fused_kernel<Sys>;
-    else if constexpr (VAR == kVarFusedMixed) return (const void*)newton_fused_mixed_kernel<Sys>;
+    else if constexpr (VAR == kVarFusedMixed) return (const void*)newton_fused_mixed_kernel<Sys, ScanF32>;
+    else if constexpr (VAR == kVarFusedFF) return (const void*)newton_fused_mixed_kernel<Sys, ScanFF>;
     else return (const void*)newton_small_kernel<Sys>;
 }
 

@@ -16,10 +16,16 @@
 //                         the latter computed in FP32 from the states rounded
 //                         on the integer pipes (no FP64-pipe work for it)
 //   jfull(jv, J):         the dense D x D Jacobian from its compact form
+//   eval_ff(xp, xc, r, jv), leaf_ff(jv, r, P, c), replay_ff(jv, r, z),
+//   jfull_ff(jv, J):      FP64 residual with the compact Jacobian in
+//                         float-float (ffarith.cuh), the fold of one leaf
+//                         (P, c) <- (J P, J c - r), the replay z <- J z - r,
+//                         and the dense Jacobian, in float-float
 // The compact form stores only the state-dependent entries of J, so an
 // element of the scan costs D + JN registers instead of D + D*D.
 #pragma once
 
+#include "ffarith.cuh"
 #include "fpconv.cuh"
 
 namespace pitn {
@@ -119,9 +125,45 @@ struct VanDerPol {
     static constexpr int D = 2, JN = 2, P = 1;
     double mu, h, hmu, m2hmu;
     float h_f, hmu_f, m2hmu_f;
+    ff h_ff, hmu_ff, m2hmu_ff;
     __host__ __device__ void init(const double* p, double hh) {
         mu = p[0]; h = hh; hmu = h * mu; m2hmu = -2.0 * h * mu;
         h_f = (float)h; hmu_f = (float)hmu; m2hmu_f = (float)m2hmu;
+        h_ff = ff_const(h); hmu_ff = ff_const(hmu); m2hmu_ff = ff_const(m2hmu);
+    }
+    // float-float scan: FP64 residual (as eval), J = [[1, h], [a, b]] with
+    // a = -2 h mu x v - h and b = 1 + h mu (1 - x^2) in float-float from the
+    // states split on the integer pipes
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        const double x = xp[0], v = xp[1];
+        const double w = fma(-x, x, 1.0);
+        const double t = hmu * w;
+        res[0] = fma(-h, v, xc[0] - x);
+        res[1] = fma(h, x, fma(-t, v, xc[1] - v));
+        const ff xf = ff_from_double(x), vf = ff_from_double(v);
+        jv[0] = ff_sub(ff_mul(ff_mul(m2hmu_ff, xf), vf), h_ff);
+        jv[1] = ff_add(ff_one(), ff_mul(hmu_ff, ff_sub(ff_one(), ff_mul(xf, xf))));
+    }
+    // (P, c) <- (J P, J c - r)
+    __device__ __forceinline__ void leaf_ff(const ff* jv, const ff* r, ff* Pm, ff* c) const {
+        const ff p00 = Pm[0], p01 = Pm[1], p10 = Pm[2], p11 = Pm[3];
+        Pm[0] = ff_fma(h_ff, p10, p00);
+        Pm[1] = ff_fma(h_ff, p11, p01);
+        Pm[2] = ff_fma(jv[0], p00, ff_mul(jv[1], p10));
+        Pm[3] = ff_fma(jv[0], p01, ff_mul(jv[1], p11));
+        const ff c0 = c[0], c1 = c[1];
+        c[0] = ff_sub(ff_fma(h_ff, c1, c0), r[0]);
+        c[1] = ff_sub(ff_fma(jv[0], c0, ff_mul(jv[1], c1)), r[1]);
+    }
+    // z <- J z - r
+    __device__ __forceinline__ void replay_ff(const ff* jv, const ff* r, ff* z) const {
+        const ff z0 = z[0], z1 = z[1];
+        z[0] = ff_sub(ff_fma(h_ff, z1, z0), r[0]);
+        z[1] = ff_sub(ff_fma(jv[0], z0, ff_mul(jv[1], z1)), r[1]);
+    }
+    __device__ __forceinline__ void jfull_ff(const ff* jv, ff* J) const {
+        J[0] = ff_one(); J[1] = h_ff;
+        J[2] = jv[0];    J[3] = jv[1];
     }
     // r = xc - x - h f(x) written as r0 = (xc0 - x) - h v,
     // r1 = (xc1 - v) - (h mu w) v + h x with w = 1 - x^2; 10 FP64 operations
@@ -194,10 +236,36 @@ struct LinearOsc {
     static constexpr int D = 2, JN = 1, P = 2;  // JN = 1 keeps arrays non-empty
     double w, z, h, j10, j11;
     float h_f, j10_f, s11_f;
+    ff h_ff, j10_ff, j11_ff;
     __host__ __device__ void init(const double* p, double hh) {
         w = p[0]; z = p[1]; h = hh;
         j10 = -h * w * w; j11 = 1.0 - 2.0 * h * z * w;
         h_f = (float)h; j10_f = (float)j10; s11_f = (float)(-2.0 * h * z * w);
+        h_ff = ff_const(h); j10_ff = ff_const(j10); j11_ff = ff_const(j11);
+    }
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        double jd[1];
+        eval(xp, xc, res, jd);
+        jv[0] = ff_zero();
+    }
+    __device__ __forceinline__ void leaf_ff(const ff*, const ff* r, ff* Pm, ff* c) const {
+        const ff p00 = Pm[0], p01 = Pm[1], p10 = Pm[2], p11 = Pm[3];
+        Pm[0] = ff_fma(h_ff, p10, p00);
+        Pm[1] = ff_fma(h_ff, p11, p01);
+        Pm[2] = ff_fma(j10_ff, p00, ff_mul(j11_ff, p10));
+        Pm[3] = ff_fma(j10_ff, p01, ff_mul(j11_ff, p11));
+        const ff c0 = c[0], c1 = c[1];
+        c[0] = ff_sub(ff_fma(h_ff, c1, c0), r[0]);
+        c[1] = ff_sub(ff_fma(j10_ff, c0, ff_mul(j11_ff, c1)), r[1]);
+    }
+    __device__ __forceinline__ void replay_ff(const ff*, const ff* r, ff* zz) const {
+        const ff z0 = zz[0], z1 = zz[1];
+        zz[0] = ff_sub(ff_fma(h_ff, z1, z0), r[0]);
+        zz[1] = ff_sub(ff_fma(j10_ff, z0, ff_mul(j11_ff, z1)), r[1]);
+    }
+    __device__ __forceinline__ void jfull_ff(const ff*, ff* J) const {
+        J[0] = ff_one(); J[1] = h_ff;
+        J[2] = j10_ff;   J[3] = j11_ff;
     }
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res,
                                          double* jv) const {

@@ -27,7 +27,7 @@ PITN_DAHLQUIST, PITN_ROBERTSON = 6, 7
 # one-step maps
 PITN_STEP_EULER, PITN_STEP_RK4, PITN_STEP_BACKWARD_EULER, PITN_STEP_TRAPEZOID = 0, 1, 2, 3
 # precisions
-PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32 = 0, 1, 2
+PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF = 0, 1, 2, 3
 
 
 class pitn_result(ctypes.Structure):

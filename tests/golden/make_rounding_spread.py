@@ -49,7 +49,7 @@ def _one(task):
 def main():
     import oracle as O
     sys.path.insert(0, os.path.dirname(HERE))
-    from rounding import first_difference
+    from rounding import first_difference, first_res_difference
     variants = [None] + list(O.VARIANTS)
     for v in variants:
         O.build(variant=v)
@@ -67,12 +67,14 @@ def main():
         for v in variants[1:]:
             r = rs[v]
             var[v] = dict(iters=r["iters"], status=r["status"],
-                          first_cut_difference=first_difference(ref["cuts"], r["cuts"]))
+                          first_cut_difference=first_difference(ref["cuts"], r["cuts"]),
+                          first_res_difference=first_res_difference(r["res_history"], ref["res_history"]))
         kind, kw, tol, it, B = CASES[name]
         out[name] = dict(workload=kind, tol=tol, max_iter=it, guard_B=B,
                          oracle=ref, variants=var,
                          window=max(abs(r["iters"] - ref["iters"]) for r in rs.values()),
-                         first_div=min(x["first_cut_difference"] for x in var.values()))
+                         first_div=min(x["first_cut_difference"] for x in var.values()),
+                         first_res_div=min(x["first_res_difference"] for x in var.values()))
     with open(os.path.join(HERE, "oracle_rounding_spread.json"), "w") as f:
         json.dump(out, f, indent=1)
 

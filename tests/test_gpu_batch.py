@@ -59,7 +59,7 @@ def compare(bt, out, tol, max_iter, guard_B, sample=None):
             # the guard cut: the count may move by what rounding alone moves it,
             # measured on the oracle's rounding variants for this IVP
             wl = W.Single("ivp", bt.system, bt.params[b], bt.x0[b], float(bt.h[b]), int(bt.N[b]))
-            window, _ = R.spread(R.runs(wl, tol, max_iter, guard_B))
+            window = R.spread(R.runs(wl, tol, max_iter, guard_B))[0]
             assert abs(int(iters[b]) - o["iters"]) <= window, (b, iters[b], o["iters"], window)
             seq = O.sequential(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b])
             assert relerr(g, seq) <= TOL_REL

@@ -1,0 +1,116 @@
+"""The float-float scan (PITN_PREC_FP64_FF) on the GPU.
+
+Its arithmetic (csrc/ffarith.cuh) against FP64 references: the integer-pipe
+split of a double into hi + lo is the hardware rounding of the double to
+float (exact ties aside) plus a remainder within 2^-47 relative; sums and
+products of float-float values are within 2^-44 of the FP64 results
+(normwise).  Its solves against the FP64 oracle, at the FP64 path's bars."""
+import json
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as O
+import rounding as R
+from paper_2511_01465_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2511_01465_gb300", "csrc")
+
+
+def test_ff_against_fp64(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    exe = str(tmp_path / "ff_check")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-I", CSRC, "-o", exe,
+                    os.path.join(HERE, "gpu_helpers", "ff_check.cu")], check=True, timeout=300)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    f = out.stdout.split()
+    counts = dict(zip(f[0::2], map(int, f[1::2])))
+    assert counts["checked"] >= 1 << 22
+    for k in ("split_hi_bad", "split_err", "split_unnorm", "add_bad", "mul_bad", "special_bad"):
+        assert counts[k] == 0, counts
+
+
+# ---------------------------------------------------------------------------
+# The float-float solve (PITN_PREC_FP64_FF) against the FP64 oracle: it must
+# meet the FP64 path's bars -- trajectories within 1e-10 of the oracle's,
+# integer outcomes equal where they are rounding-robust, guarded solves
+# within the spread rounding alone produces (tests/rounding.py).
+# ---------------------------------------------------------------------------
+TOL_REL = 1e-10
+SPREAD = os.path.join(HERE, "golden", "oracle_rounding_spread.json")
+
+
+@pytest.fixture(scope="module")
+def pk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2511_01465_gb300 as pk
+    return pk
+
+
+def relerr(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300))
+
+
+def ff_solve(pk, wl, tol, max_iter, guard_B):
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, tol, max_iter, guard_B=guard_B,
+                          precision=pk.PITN_PREC_FP64_FF, history=True)
+    return traj.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 31, 32, 33, 255, 256, 257, 1000, 4097, 20011, 30001])
+@pytest.mark.parametrize("kind", ["vdp", "osc"])
+def test_ff_plain_equals_oracle(pk, kind, N):
+    """Plain Newton (rounding-robust): count, status, cuts and residual
+    history equal to the oracle's, trajectory within 1e-10."""
+    wl = W.vdp(N=N, h=1e-3) if kind == "vdp" else W.damped_oscillator(N=N, h=1e-3)
+    g, gi = ff_solve(pk, wl, 1e-10, 60, 0.0)
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
+    assert (gi["iters"], gi["status"], gi["guard_index"]) == (o["iters"], o["status"], o["guard_index"])
+    assert np.array_equal(gi["cut_history"], o["cuts"])
+    np.testing.assert_allclose(gi["res_history"], o["res_hist"], rtol=1e-6, atol=1e-13)
+    assert relerr(g, o["traj"]) <= TOL_REL
+
+
+def test_ff_guarded_ragged(pk):
+    wl = W.vdp(N=20011, h=1e-3)
+    g, gi = ff_solve(pk, wl, 1e-10, 80, 100.0)
+    rs = R.runs(wl, 1e-10, 80, 100.0)
+    window, first_div, first_res_div = R.spread(rs)
+    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], rs[None], window,
+                    first_div, first_res_div)
+    if rs[None]["status"] == O.OK:
+        assert relerr(g, O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)) <= TOL_REL
+
+
+@pytest.mark.parametrize("name", ["vdp_2^22_guard100_tol1e-8_it400", "vdp_2^22_guard100_tol1e-12_it400"])
+def test_ff_bench_size(pk, name):
+    """The bench workload (van der Pol, N = 2^22, guard B = 100): converged,
+    within the measured rounding spread of the oracle's count, cuts and
+    residuals, and within 1e-10 of the sequential FP64 trajectory."""
+    with open(SPREAD) as f:
+        sp = json.load(f)[name]
+    ref = dict(sp["oracle"], res_hist=sp["oracle"]["res_history"])
+    wl = W.vdp()
+    g, gi = ff_solve(pk, wl, sp["tol"], sp["max_iter"], sp["guard_B"])
+    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, sp["window"],
+                    sp["first_div"], sp["first_res_div"])
+    assert gi["final_res"] <= sp["tol"]
+    assert relerr(g, O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)) <= TOL_REL
+
+
+def test_ff_rejects_other_systems(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    wl = W.lorenz(N=10)
+    with pytest.raises(P.PitnError):
+        pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 5, precision=P.PITN_PREC_FP64_FF)

@@ -46,7 +46,7 @@ def run(pk, wl, tol, max_iter, guard_B=0.0, **kw):
     return traj.cpu().numpy(), info
 
 
-def check_guarded(wl, g, gi, ref, window, first_div, tol):
+def check_guarded(wl, g, gi, ref, window, first_div, first_res_div, tol):
     """Guarded Newton (reading R8): where the guard cuts, the cut index is
     decided by FP64 comparisons on corrections beyond the converged prefix,
     which grow exponentially there, so the count of updates depends on
@@ -54,11 +54,12 @@ def check_guarded(wl, g, gi, ref, window, first_div, tol):
     on the oracle's rounding variants (tests/rounding.py): the status equal,
     the count within the variants' window of the oracle's, the cuts and the
     residual history equal up to the first step at which a variant cut
-    elsewhere.  Then what is unique: the root of a converged solve, and for a
+    elsewhere, the residual history equal until rounding alone moves it.
+    Then what is unique: the root of a converged solve, and for a
     capped solve the prefix invariant (the first `iters` states are exact)
     and the guard fill."""
     R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, window,
-                    first_div)
+                    first_div, first_res_div)
     if ref["status"] == O.OK:
         assert gi["final_res"] <= tol
         seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
@@ -79,8 +80,8 @@ def check_against_oracle(pk, wl, tol, max_iter, guard_B=0.0, **kw):
     cut_seen = (gi["cut_history"] < wl.N).any() or (o["cuts"] < wl.N).any()
     if guard_B > 0 and cut_seen:
         rs = R.runs(wl, tol, max_iter, guard_B)
-        window, first_div = R.spread(rs)
-        check_guarded(wl, g, gi, rs[None], window, first_div, tol)
+        window, first_div, first_res_div = R.spread(rs)
+        check_guarded(wl, g, gi, rs[None], window, first_div, first_res_div, tol)
         return g, gi, o
     assert gi["iters"] == o["iters"]
     assert gi["status"] == o["status"]
@@ -126,7 +127,8 @@ def test_full_size_against_oracle(pk, name):
     if gold["guard_B"] > 0:
         sp = load_spread()[name]
         assert sp["oracle"]["iters"] == gold["iters"] and sp["oracle"]["status"] == gold["status"]
-        check_guarded(wl, g, gi, sp["oracle"], sp["window"], sp["first_div"], gold["tol"])
+        check_guarded(wl, g, gi, sp["oracle"], sp["window"], sp["first_div"], sp["first_res_div"],
+                      gold["tol"])
         return
     assert (gi["iters"], gi["status"], gi["guard_index"]) == \
         (gold["iters"], gold["status"], gold["guard_index"])

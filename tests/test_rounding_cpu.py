@@ -63,7 +63,10 @@ def test_spread_logic():
     rs = {None: dict(iters=10, cuts=np.array([5, 6, 7, 9])),
           "a": dict(iters=12, cuts=np.array([5, 6, 8, 9])),
           "b": dict(iters=9, cuts=np.array([5, 6, 7, 9, 9]))}
-    assert R.spread(rs) == (2, 2)
+    for r in rs.values():
+        r["res_hist"] = np.array([1.0, 2.0, 3.0])
+    rs["a"]["res_hist"] = np.array([1.0, 2.0, 3.1])
+    assert R.spread(rs) == (2, 2, 2)
     assert R.first_difference([1, 2], [1, 2, 3]) == 2
 
 
@@ -82,6 +85,7 @@ def test_stored_spread_is_consistent():
         assert len(ref["cuts"]) == ref["iters"] and len(ref["res_history"]) == ref["iters"] + 1
         assert e["window"] == max(abs(v["iters"] - ref["iters"]) for v in e["variants"].values())
         assert e["first_div"] == min(v["first_cut_difference"] for v in e["variants"].values())
+        assert e["first_res_div"] == min(v["first_res_difference"] for v in e["variants"].values())
         assert set(e["variants"]) == set(R.VARIANTS)
         for v in e["variants"].values():
             assert v["status"] == ref["status"]
@@ -92,5 +96,4 @@ def test_spread_of_lorenz_8192_recomputed():
     with open(os.path.join(HERE, "golden", "oracle_rounding_spread.json")) as f:
         e = json.load(f)["lorenz_8192_guard100_tol1e-8_it100"]
     wl = W.lorenz()
-    window, first_div = R.spread(R.runs(wl, 1e-8, 100, 100.0))
-    assert (window, first_div) == (e["window"], e["first_div"])
+    assert R.spread(R.runs(wl, 1e-8, 100, 100.0)) == (e["window"], e["first_div"], e["first_res_div"])

@@ -75,11 +75,12 @@ def check_same(P, case):
 
 
 def test_noalloc_full_iteration_budget_then_a_fresh_solve(P):
-    """A solve that uses all of the array's per-iteration records (max_iter =
-    1024 with tol = 0 never meets the tolerance), then a normal solve at once:
-    the second call must start clean although the array holds the first
-    call's barrier words, error word, record and residual history."""
-    r = check_same(P, (W.lorenz(N=2048), 0.0, 1024, 100.0))
+    """A solve that uses all of the array's per-iteration records (guarded
+    Lorenz-63 over 65536 steps, a chaotic horizon on which no FP64 Newton
+    iterate meets 1e-10 within 1024 updates), then normal solves at once:
+    they must start clean although the array holds the first call's barrier
+    words, error word, record and residual history."""
+    r = check_same(P, (W.lorenz(N=65536), 1e-10, 1024, 100.0))
     assert r.status == P.PITN_NOT_CONVERGED and r.iters == 1024
     check_same(P, (W.vdp(N=30001, h=1e-3), 1e-10, 60, 0.0))
     check_same(P, (W.lorenz(N=777), 1e-10, 40, 0.0))
