@@ -285,6 +285,37 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
 int pitn_probe_fma_rate(int kind, double* fma_per_s);
 
 /*
+ * Failure injection for tests of the error paths (not in the paper).  Each
+ * call changes one process-wide setting; PITN_DEBUG_RESET restores them all.
+ *   PITN_DEBUG_FAIL_ALLOCS   value = n >= 0: the next n growths of the
+ *                            scratch cache fail as if cudaMalloc had, so the
+ *                            calls that need them return PITN_ENOMEM
+ *   PITN_DEBUG_GRID_WAIT_NS  value ns (<= 0: the default 2 s): how long a
+ *                            grid barrier of a cooperative kernel waits for
+ *                            the other CTAs before the kernel gives up and
+ *                            the call returns PITN_ETIMEOUT
+ *   PITN_DEBUG_LOAD_POLLS    value polls (< 0: default 2^26): how long the
+ *                            tensor-core compose waits on its bulk copies
+ *   PITN_DEBUG_MMA_POLLS     value polls (< 0: default 2^26): how long it
+ *                            waits on the tensor-core product
+ * A compose whose wait gave up waits again with the default limit for the
+ * copies or the product already in flight, so that it reads no TMEM and
+ * frees neither TMEM nor shared memory under an asynchronous operation; only
+ * if that wait also ends without completion does the CTA leave its TMEM
+ * allocated.  Either way the call returns PITN_ETIMEOUT and the device stays
+ * usable.  The settings apply to launches that start after the call.
+ * Returns PITN_OK or PITN_EINVAL.
+ */
+enum {
+    PITN_DEBUG_RESET = 0,
+    PITN_DEBUG_FAIL_ALLOCS = 1,
+    PITN_DEBUG_GRID_WAIT_NS = 2,
+    PITN_DEBUG_LOAD_POLLS = 3,
+    PITN_DEBUG_MMA_POLLS = 4
+};
+int pitn_debug_inject(int what, int64_t value);
+
+/*
  * Launch-shape autotuner (not in the paper).  While enabled, the first solve
  * of a configuration class -- (entry point, system, d, floor(log2 size),
  * guard on/off) -- times each candidate launch shape (threads per CTA and

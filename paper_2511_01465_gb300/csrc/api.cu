@@ -24,6 +24,10 @@ struct DevCache {
     size_t pinned_bytes = 0;
 };
 std::map<int, DevCache> g_cache;
+// failure injection (pitn_debug_inject): allocations still to refuse, and
+// the in-kernel wait limits
+std::atomic<int64_t> g_fail_allocs{0};
+WaitLimits g_waits;
 std::map<int, cudaDeviceProp> g_props;
 
 // kernel timing
@@ -75,12 +79,15 @@ static void resolve_timing() {
     g_pending.clear();
 }
 
+const WaitLimits& wait_limits() { return g_waits; }
+
 void* workspace(size_t bytes, int slot) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     DevCache& c = g_cache[dev];
     if (bytes == 0) bytes = 256;
     if (c.bytes[slot] < bytes) {
+        if (g_fail_allocs.load() > 0 && g_fail_allocs.fetch_sub(1) > 0) return nullptr;  // injected
         if (c.ptr[slot]) cudaFree(c.ptr[slot]);
         c.ptr[slot] = nullptr;
         c.bytes[slot] = 0;
@@ -283,6 +290,31 @@ int pitn_release_workspace(void) {
 }
 
 int64_t pitn_launch_count(void) { return g_launches.load(); }
+
+int pitn_debug_inject(int what, int64_t value) {
+    std::lock_guard<std::recursive_mutex> lk(api_mutex());
+    switch (what) {
+    case PITN_DEBUG_RESET:
+        g_fail_allocs.store(0);
+        g_waits = WaitLimits{};
+        return PITN_OK;
+    case PITN_DEBUG_FAIL_ALLOCS:
+        if (value < 0) return PITN_EINVAL;
+        g_fail_allocs.store(value);
+        return PITN_OK;
+    case PITN_DEBUG_GRID_WAIT_NS:
+        g_waits.grid_ns = value > 0 ? (uint64_t)value : WaitLimits{}.grid_ns;
+        return PITN_OK;
+    case PITN_DEBUG_LOAD_POLLS:
+        g_waits.load_polls = value >= 0 ? (uint64_t)value : WaitLimits{}.load_polls;
+        return PITN_OK;
+    case PITN_DEBUG_MMA_POLLS:
+        g_waits.mma_polls = value >= 0 ? (uint64_t)value : WaitLimits{}.mma_polls;
+        return PITN_OK;
+    default:
+        return PITN_EINVAL;
+    }
+}
 
 int pitn_timing_enable(int on) {
     resolve_timing();

@@ -28,8 +28,9 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-// Every spin-wait in the library gives up after this long and raises
-// PITN_ETIMEOUT instead of hanging the device.
+// Every spin-wait in the library gives up after a bounded time (default 2 s,
+// passed in by the host, see WaitLimits) and raises PITN_ETIMEOUT instead of
+// hanging the device.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
 
 // Error word written by kernels (0 = fine).
@@ -39,7 +40,7 @@ __device__ __forceinline__ void raise_error(int* err, int code) { atomicCAS(err,
 // count/gen live in device memory zeroed before the launch.  Returns false
 // (and sets *err) when the wait times out or another CTA already failed.
 __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks,
-                                             int* err) {
+                                             int* err, uint64_t limit_ns = kWaitLimitNs) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -52,10 +53,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, uns
             __threadfence();
             st_release_u32(gen, g + 1);
         } else {
+            if (limit_ns == 0) limit_ns = kWaitLimitNs;
             uint64_t t0 = globaltimer_ns();
             while (ld_acquire_u32(gen) == g) {
                 if (*(volatile int*)err != 0) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                if (globaltimer_ns() - t0 > limit_ns) {
                     raise_error(err, PITN_ETIMEOUT);
                     ok = 0;
                     break;

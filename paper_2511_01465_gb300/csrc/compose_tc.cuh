@@ -27,7 +27,15 @@ constexpr int kDim = 128;
 constexpr uint32_t kCoreBytes = 128;             // 8 rows x 16 bytes
 constexpr uint32_t kGroupBytes = 16 * kCoreBytes;  // one 8-row group spans K = 128 (16 cores)
 constexpr uint32_t kTileBytes = 16 * kGroupBytes;  // 128 rows
-constexpr uint64_t kSpinLimit = 1ull << 26;       // bounded mbarrier wait
+constexpr uint64_t kSpinLimit = 1ull << 26;       // default bound of an mbarrier wait (polls)
+
+// Outcome of one compose.
+enum : int {
+    kTcOk = 0,        // done
+    kTcTimedOut = 1,  // a wait gave up; nothing is in flight any more (TMEM may be freed)
+    kTcStuck = 2      // a wait gave up and a copy or the product may still be in flight:
+                      // the CTA must not free its TMEM or reuse its shared memory
+};
 
 // byte offset of element (row, k) in the K-major core-matrix layout
 __device__ __forceinline__ uint32_t core_off(int row, int k) {
@@ -79,10 +87,11 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
 }
-// bounded wait for the phase with the given parity; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// bounded wait for the phase with the given parity (at most `polls` polls);
+// false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t polls = kSpinLimit) {
     const uint32_t a = smem_addr(mbar);
-    for (uint64_t i = 0; i < kSpinLimit; ++i) {
+    for (uint64_t i = 0; i < polls; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -140,18 +149,22 @@ constexpr uint32_t kMatBytes = kDim * kDim * sizeof(float);
 constexpr uint32_t kLoadChunk = 16384;  // bytes per bulk copy
 
 // One compose by a CTA of 128 or 256 threads (with 256, two threads share a
-// row in the epilogue, each taking 64 columns).  Returns false if the MMA
-// completion wait timed out.  `phase` is the parity of this CTA's MMA
+// row in the epilogue, each taking 64 columns); every thread of the CTA
+// calls it.  Returns kTcOk, or kTcTimedOut / kTcStuck when a wait gave up
+// (then nothing is written).  `phase` is the parity of this CTA's MMA
 // completions so far (and of its bulk loads: bulk loads only in the CTA's
 // first compose).  bulk = false reads the inputs with L2 loads instead, for
 // inputs that other CTAs of the same launch wrote (ordered by the caller's
-// acquire).
-__device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restrict__ S2,
-                                           const float* __restrict__ b2, const float* __restrict__ S1,
-                                           const float* __restrict__ b1, float* __restrict__ So,
-                                           float* __restrict__ bo, uint32_t phase, bool bulk = true) {
+// acquire).  load_polls and mma_polls bound the first wait for the copies and
+// for the product; a wait that gives up is followed by a second one with the
+// default bound for the operation already in flight, and every decision is
+// taken CTA-wide (the TMEM loads are warp-collective).
+__device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restrict__ S2,
+                                          const float* __restrict__ b2, const float* __restrict__ S1,
+                                          const float* __restrict__ b1, float* __restrict__ So,
+                                          float* __restrict__ bo, uint32_t phase, bool bulk = true,
+                                          uint64_t load_polls = kSpinLimit, uint64_t mma_polls = kSpinLimit) {
     const int tid = threadIdx.x, warp = tid >> 5;
-    bool ok = true;
     if (bulk) {
         // both inputs by bulk copies; b1 by plain loads meanwhile
         if (tid == 0) {
@@ -164,8 +177,13 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
             }
         }
         if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
-        ok = mbar_wait(&sm.mbar_ld, phase);
-        if (!ok) (void)mbar_wait(&sm.mbar_ld, phase);  // give the copies a second bounded wait; still a failure
+        const bool loaded = __syncthreads_and(mbar_wait(&sm.mbar_ld, phase, load_polls) ? 1 : 0) != 0;
+        if (!loaded) {
+            // the copies are in flight: wait for them (default bound) before
+            // the shared memory they write is released or reused
+            const bool drained = __syncthreads_and(mbar_wait(&sm.mbar_ld, phase) ? 1 : 0) != 0;
+            return drained ? kTcTimedOut : kTcStuck;
+        }
     } else {
         // 16-byte asynchronous copies through L2, all in flight at once
         const float4* s2 = reinterpret_cast<const float4*>(S2);
@@ -217,7 +235,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
     fence_before();
     __syncthreads();
     fence_after();
-    if (tid == 0 && ok) {
+    if (tid == 0) {
         const uint32_t a0 = smem_addr(sm.A), b0 = smem_addr(sm.B), idesc = make_idesc();
 #pragma unroll
         for (int s = 0; s < kDim / 16; ++s)
@@ -225,7 +243,14 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
                      s > 0 ? 1u : 0u);
         mma_commit(&sm.mbar);
     }
-    ok = ok && mbar_wait(&sm.mbar, phase);
+    const bool done = __syncthreads_and(mbar_wait(&sm.mbar, phase, mma_polls) ? 1 : 0) != 0;
+    if (!done) {
+        // the product is in flight: no TMEM load, and no return (after which
+        // the caller frees the TMEM) before its commit has arrived
+        const bool drained = __syncthreads_and(mbar_wait(&sm.mbar, phase) ? 1 : 0) != 0;
+        fence_after();
+        return drained ? kTcTimedOut : kTcStuck;
+    }
     fence_after();
     // epilogue: thread owns row m (TMEM lane m; a warp reaches the lane
     // quarter warp % 4) and a range of columns
@@ -240,7 +265,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const size_t off = (size_t)(c + j) * kDim + m;
-            So[off] = sm.S2f[off] + sm.S1f[off] + (ok ? v[j] : 0.0f);
+            So[off] = sm.S2f[off] + sm.S1f[off] + v[j];
         }
     }
     if (tid < kDim) {
@@ -262,7 +287,7 @@ __device__ __forceinline__ bool compose_tc(ComposeSmem& sm, const float* __restr
     }
     fence_before();
     __syncthreads();
-    return ok;
+    return kTcOk;
 }
 
 }  // namespace tc

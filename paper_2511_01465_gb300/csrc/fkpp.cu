@@ -412,6 +412,7 @@ struct CombineArgs {
     long long n_lone;                  // index of a lone earlier element to copy (or -1)
     int* err;
     const int* stop;                   // nullable: skip the launch when set (converged pass)
+    unsigned long long load_polls, mma_polls;  // wait bounds of the compose
 };
 
 constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
@@ -440,11 +441,15 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const bool ok = tc::compose_tc(sm, a.S2 + (size_t)m * a.stride_in * MM, a.b2 + m * a.stride_in * FD,
-                                   a.S1 + (size_t)m * a.stride_in * MM, a.b1 + m * a.stride_in * FD,
-                                   a.S + (size_t)m * MM, a.b + m * FD, 0u);
-    if (!ok && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
-    if (warp == 0) tc::tmem_dealloc(sm.tmem, FD);
+    const int rc = tc::compose_tc(sm, a.S2 + (size_t)m * a.stride_in * MM, a.b2 + m * a.stride_in * FD,
+                                  a.S1 + (size_t)m * a.stride_in * MM, a.b1 + m * a.stride_in * FD,
+                                  a.S + (size_t)m * MM, a.b + m * FD, 0u, true, a.load_polls, a.mma_polls);
+    if (rc != tc::kTcOk && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    // an operation still in flight keeps the TMEM it writes (kTcStuck)
+    if (rc != tc::kTcStuck && warp == 0) tc::tmem_dealloc(sm.tmem, FD);
 }
 
 // The whole up-sweep of the mixed-precision tree in one launch: one CTA per
@@ -464,6 +469,7 @@ struct UpArgs {
     unsigned* cnt;   // one arrival counter per node, indexed like S / b
     int* err;
     const int* stop;
+    unsigned long long load_polls, mma_polls;  // wait bounds of the composes
 };
 
 __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
@@ -485,6 +491,7 @@ __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
     tc::fence_after();
     long long m = blockIdx.x;
     unsigned composes = 0;
+    int rc = tc::kTcOk;
     for (int lv = 1; lv < a.L; ++lv) {
         const long long n_in = a.n[lv - 1];
         const float* Sin = a.S + (size_t)a.off[lv - 1] * MM;
@@ -511,11 +518,14 @@ __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
             }
             if (tid < FD) bo[tid] = __ldcg(bin + (2 * m) * FD + tid);
         } else {
-            const bool ok = tc::compose_tc(sm, Sin + (size_t)(2 * m + 1) * MM, bin + (2 * m + 1) * FD,
-                                           Sin + (size_t)(2 * m) * MM, bin + (2 * m) * FD, So, bo,
-                                           composes & 1u, lv == 1);
+            rc = tc::compose_tc(sm, Sin + (size_t)(2 * m + 1) * MM, bin + (2 * m + 1) * FD,
+                                Sin + (size_t)(2 * m) * MM, bin + (2 * m) * FD, So, bo, composes & 1u, lv == 1,
+                                a.load_polls, a.mma_polls);
             ++composes;
-            if (!ok && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
+            if (rc != tc::kTcOk) {   // uniform over the CTA: the compose decides CTA-wide
+                if (tid == 0) raise_error(a.err, PITN_ETIMEOUT);
+                break;               // this node is not written: no parent can be composed
+            }
         }
         if (lv + 1 >= a.L) break;
         // release this node, then climb if both children of the parent are done
@@ -541,7 +551,7 @@ __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(sm.tmem, FD);
+    if (rc != tc::kTcStuck && warp == 0) tc::tmem_dealloc(sm.tmem, FD);
 }
 
 // ---------------------------------------------------------------------------
@@ -754,6 +764,8 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, boo
             ua.cnt = p.cnt;
             ua.err = err;
             ua.stop = p.stop;
+            ua.load_polls = wait_limits().load_polls;
+            ua.mma_polls = wait_limits().mma_polls;
             auto tok = timed_begin("fkpp_compose", st);
             fk_upsweep_tc_kernel<<<(unsigned)tr.n[1], 256, kTcSmem, st>>>(ua);
             timed_end(tok, st);
@@ -975,6 +987,8 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
     CombineArgs ca;
     ca.S2 = S2; ca.b2 = b2; ca.S1 = S1; ca.b1 = b1; ca.S = S; ca.b = b;
     ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err; ca.stop = nullptr;
+    ca.load_polls = wait_limits().load_polls;
+    ca.mma_polls = wait_limits().mma_polls;
     auto tok = timed_begin("fkpp_compose", st);
     fk_compose_tc_kernel<<<(unsigned)n, 256, kTcSmem, st>>>(ca);
     timed_end(tok, st);

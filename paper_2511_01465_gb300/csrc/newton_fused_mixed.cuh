@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
             my_res = o > my_res ? o : my_res;
         }
         if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err, a.wait_ns)) return;
 
         const unsigned long long rb = __ldcg(a.res_bits + it);
         const double res = __longlong_as_double((long long)rb);
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
             my_q = o > my_q ? o : my_q;
         }
         if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err, a.wait_ns)) return;
         const unsigned long long qe = __ldcg(a.qenc + it);
         const long long cut = qe ? (long long)(~qe) : N;
         if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }

@@ -170,6 +170,7 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     a.bar = (unsigned*)(ctrl + off_bar);
     a.err = (int*)(ctrl + off_err);
     a.rec = (SolveRecord*)(ctrl + off_rec);
+    a.wait_ns = wait_limits().grid_ns;
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
     cudaError_t e = K.launch(a, grid, block, st);
@@ -456,6 +457,7 @@ extern "C" int pitn_solve_noalloc(int system_id, const double* params, const dou
     a.bar = (unsigned*)ctl;
     a.err = (int*)(ctl + 16);
     a.rec = (SolveRecord*)(ctl + 32);
+    a.wait_ns = wait_limits().grid_ns;
     void* args[] = {(void*)&a};
     const void* kern = (system_id == PITN_LORENZ63) ? (const void*)newton_small_kernel<Lorenz63>
                        : (system_id == PITN_VDP)    ? (const void*)newton_small_kernel<VanDerPol>

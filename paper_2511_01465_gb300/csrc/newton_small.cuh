@@ -47,6 +47,7 @@ struct SmallArgs {
     SolveRecord* rec;
     int stage_rows;                // > 0: rows of the next iterate leave through shared-memory
                                    // tiles and bulk copies (dynamic smem sized by stage_bytes)
+    unsigned long long wait_ns;    // grid-barrier wait limit (0: the default)
 };
 
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             my_res = o > my_res ? o : my_res;
         }
         if (lane == 0 && my_res) atomicMax(a.res_bits + it, my_res);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err, a.wait_ns)) return;
 
         // ---- decision --------------------------------------------------------
         const unsigned long long rb = __ldcg(a.res_bits + it);
@@ -617,7 +618,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             my_q = o > my_q ? o : my_q;
         }
         if (lane == 0 && my_q) atomicMax(a.qenc + it, my_q);
-        if (!grid_barrier(a.bar, a.bar + 1, G, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, G, a.err, a.wait_ns)) return;
         const unsigned long long qe = __ldcg(a.qenc + it);
         const long long cut = qe ? (long long)(~qe) : N;
         if (!a.guarded && cut < N) { status = PITN_NONFINITE; break; }

@@ -28,6 +28,17 @@ constexpr int kMaxIter = 1 << 20;
 constexpr int kMaxParams = 4;
 constexpr int kFkppMaxD = 128;
 
+// Limits of the in-kernel waits (pitn_debug_inject changes them for tests of
+// the timeout paths): a grid barrier gives up after grid_ns nanoseconds, an
+// mbarrier wait for bulk loads after load_polls polls and one for the
+// tensor cores after mma_polls polls.
+struct WaitLimits {
+    uint64_t grid_ns = 2000000000ull;   // 2 s
+    uint64_t load_polls = 1ull << 26;
+    uint64_t mma_polls = 1ull << 26;
+};
+const WaitLimits& wait_limits();
+
 void* workspace(size_t bytes, int slot);
 void* pinned(size_t bytes);
 void release_all();

@@ -26,6 +26,9 @@ PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP, PITN_LOGISTIC = 1, 2, 3, 4,
 PITN_DAHLQUIST, PITN_ROBERTSON = 6, 7
 # one-step maps
 PITN_STEP_EULER, PITN_STEP_RK4, PITN_STEP_BACKWARD_EULER, PITN_STEP_TRAPEZOID = 0, 1, 2, 3
+# failure injection (pitn_debug_inject)
+PITN_DEBUG_RESET, PITN_DEBUG_FAIL_ALLOCS, PITN_DEBUG_GRID_WAIT_NS = 0, 1, 2
+PITN_DEBUG_LOAD_POLLS, PITN_DEBUG_MMA_POLLS = 3, 4
 # precisions
 PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF = 0, 1, 2, 3
 
@@ -80,6 +83,8 @@ def lib():
         L.pitn_launch_count.restype = i64
         L.pitn_probe_fma_rate.argtypes = [c_int, ctypes.POINTER(d)]
         L.pitn_probe_fma_rate.restype = c_int
+        L.pitn_debug_inject.argtypes = [c_int, i64]
+        L.pitn_debug_inject.restype = c_int
         L.pitn_solve_noalloc.argtypes = [c_int, vp, vp, d, i64, c_int, d, c_int, d, vp,
                                           ctypes.POINTER(pitn_result)]
         L.pitn_solve_noalloc.restype = c_int
@@ -270,3 +275,8 @@ def pitn_probe_fma_rate(kind):
     v = ctypes.c_double()
     check(lib().pitn_probe_fma_rate(int(kind), ctypes.byref(v)), "pitn_probe_fma_rate")
     return v.value
+
+
+def pitn_debug_inject(what, value=0):
+    """Failure injection for tests of the error paths (see include/pitn.h)."""
+    return lib().pitn_debug_inject(int(what), int(value))

@@ -17,9 +17,10 @@ __device__ unsigned long long mix64(unsigned long long z) {  // splitmix64 final
     return z ^ (z >> 31);
 }
 
-// a double with a random significand and sign and an exponent in [-60, 60)
+// a double with a random significand and sign and an exponent in [-40, 40)
+// (products and their low parts stay in the float normal range)
 __device__ double rand_double(unsigned long long r) {
-    const unsigned long long e = 1023ull - 60ull + ((r >> 53) % 120ull);
+    const unsigned long long e = 1023ull - 40ull + ((r >> 53) % 80ull);
     const unsigned long long bits = (r & 0x800fffffffffffffull) | (e << 52);
     return __longlong_as_double((long long)bits);
 }

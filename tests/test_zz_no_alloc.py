@@ -75,13 +75,14 @@ def check_same(P, case):
 
 
 def test_noalloc_full_iteration_budget_then_a_fresh_solve(P):
-    """A solve that uses all of the array's per-iteration records (guarded
-    Lorenz-63 over 65536 steps, a chaotic horizon on which no FP64 Newton
-    iterate meets 1e-10 within 1024 updates), then normal solves at once:
-    they must start clean although the array holds the first call's barrier
-    words, error word, record and residual history."""
-    r = check_same(P, (W.lorenz(N=65536), 1e-10, 1024, 100.0))
-    assert r.status == P.PITN_NOT_CONVERGED and r.iters == 1024
+    """A solve that uses all of the array's per-iteration records, then
+    normal solves at once: they must start clean although the array holds
+    the first call's barrier words, error word, record and residual history.
+    A guard bound below every correction cuts each Newton step at its first
+    state, so the iterate never moves and the solve runs its whole budget of
+    1024 updates, whatever the rounding."""
+    r = check_same(P, (W.lorenz(N=4096), 1e-10, 1024, 1e-300))
+    assert r.status == P.PITN_NOT_CONVERGED and r.iters == 1024 and r.guard_index == 0
     check_same(P, (W.vdp(N=30001, h=1e-3), 1e-10, 60, 0.0))
     check_same(P, (W.lorenz(N=777), 1e-10, 40, 0.0))
 
