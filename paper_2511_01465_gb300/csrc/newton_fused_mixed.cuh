@@ -21,6 +21,7 @@ namespace pitn {
 // FP32 delta form: the existing mixed-precision arithmetic.
 struct ScanF32 {
     using T = float;
+    static constexpr int kMinBlocks = 0;   // no occupancy request: the compiler's own register choice
     template <int D>
     static __device__ __forceinline__ void ident(T* Q, T* c) { dz_zero<D>(Q, c); }
     template <int D>
@@ -37,6 +38,8 @@ struct ScanF32 {
 #pragma unroll
         for (int j = 0; j < D; ++j) c[j] = -r[j];
     }
+    template <class Sys>
+    static __device__ __forceinline__ void setup(Sys&, const SmallArgs&) {}
     template <class Sys>
     static __device__ __forceinline__ void eval(const Sys& sys, const double* xp, const double* xc, double* r,
                                                 T* sv) {
@@ -83,6 +86,7 @@ struct ScanF32 {
 // float-float, plain form (J, c).
 struct ScanFF {
     using T = ff;
+    static constexpr int kMinBlocks = 2;   // 128 registers: two 256-thread CTAs per SM
     template <int D>
     static __device__ __forceinline__ void ident(T* P, T* c) {
 #pragma unroll
@@ -135,6 +139,9 @@ struct ScanFF {
 #pragma unroll
         for (int j = 0; j < D; ++j) c[j] = ff_neg(r[j]);
     }
+    // constants from the host (see SmallArgs::fc, dc)
+    template <class Sys>
+    static __device__ __forceinline__ void setup(Sys& sys, const SmallArgs& a) { sys.init_ff(a.fc, a.dc); }
     template <class Sys>
     static __device__ __forceinline__ void eval(const Sys& sys, const double* xp, const double* xc, double* r,
                                                 T* jv) {
@@ -250,11 +257,12 @@ __device__ __forceinline__ ff ld_cg(const ff* p) {
 
 
 template <class Sys, class Pol>
-__global__ void __launch_bounds__(256) newton_fused_mixed_kernel(SmallArgs a) {
+__global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kernel(SmallArgs a) {
     using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
     Sys sys;
     sys.init(a.params, a.h);
+    Pol::setup(sys, a);
 
     __shared__ T s_wex[kMaxWarps][E];
     __shared__ T s_tot[E];

@@ -173,6 +173,7 @@ int small_launch(int system_id, const SolveIO& io, double h, int64_t N, int d, d
     a.wait_ns = wait_limits().grid_ns;
 
     if (cudaMemsetAsync(ctrl, 0, total, st) != cudaSuccess) return PITN_ECUDA;
+    if (K.consts) K.consts(io.params, h, a.fc, a.dc);
     cudaError_t e = K.launch(a, grid, block, st);
     if (e != cudaSuccess) { cudaGetLastError(); return PITN_ECUDA; }
     int* h_err = (int*)hbuf;

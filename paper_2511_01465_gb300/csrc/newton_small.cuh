@@ -48,6 +48,11 @@ struct SmallArgs {
     int stage_rows;                // > 0: rows of the next iterate leave through shared-memory
                                    // tiles and bulk copies (dynamic smem sized by stage_bytes)
     unsigned long long wait_ns;    // grid-barrier wait limit (0: the default)
+    // system constants precomputed on the host for the float-float scan
+    // (kernel parameters live in the constant bank, so the compiler reloads
+    // them instead of recomputing them with FP64 instructions inside the loop)
+    float fc[8];
+    double dc[4];
 };
 
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
@@ -709,11 +714,14 @@ struct SmallKernel {
     cudaError_t (*launch)(SmallArgs&, int, int, cudaStream_t);
     int (*per_sm)(int);
     int W;
+    void (*consts)(const double* p, double h, float* fc, double* dc);  // nullable
 };
 
 template <class Sys, int VAR = kVarPlain>
 static SmallKernel small_kernel_of() {
-    return SmallKernel{&launch_small<Sys, VAR>, &max_blocks_per_sm<Sys, VAR>, Sys::JN + Sys::D};
+    SmallKernel k{&launch_small<Sys, VAR>, &max_blocks_per_sm<Sys, VAR>, Sys::JN + Sys::D, nullptr};
+    if constexpr (VAR == kVarFusedFF) k.consts = &Sys::host_ff_consts;
+    return k;
 }
 
 }  // namespace pitn

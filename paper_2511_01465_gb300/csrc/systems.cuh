@@ -131,6 +131,25 @@ struct VanDerPol {
         h_f = (float)h; hmu_f = (float)hmu; m2hmu_f = (float)m2hmu;
         h_ff = ff_const(h); hmu_ff = ff_const(hmu); m2hmu_ff = ff_const(m2hmu);
     }
+    // float-float constants, split on the host: fc = (h, h mu, -2 h mu) as
+    // hi/lo pairs, dc = (h mu, -2 h mu)
+    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+        const double c[3] = {hh, hh * p[0], -2.0 * hh * p[0]};
+        for (int i = 0; i < 3; ++i) {
+            const ff v = ff_const(c[i]);
+            fc[2 * i] = v.hi;
+            fc[2 * i + 1] = v.lo;
+        }
+        dc[0] = c[1];
+        dc[1] = c[2];
+    }
+    __device__ __forceinline__ void init_ff(const float* fc, const double* dc) {
+        h_ff = ff{fc[0], fc[1]};
+        hmu_ff = ff{fc[2], fc[3]};
+        m2hmu_ff = ff{fc[4], fc[5]};
+        hmu = dc[0];
+        m2hmu = dc[1];
+    }
     // float-float scan: FP64 residual (as eval), J = [[1, h], [a, b]] with
     // a = -2 h mu x v - h and b = 1 + h mu (1 - x^2) in float-float from the
     // states split on the integer pipes
@@ -234,7 +253,7 @@ struct VanDerPol {
 // Damped linear oscillator, state (x, v): f = (v, -w^2 x - 2 z w v); J is constant.
 struct LinearOsc {
     static constexpr int D = 2, JN = 1, P = 2;  // JN = 1 keeps arrays non-empty
-    double w, z, h, j10, j11;
+    double w, z, h, j10, j11, ww, zw2;
     float h_f, j10_f, s11_f;
     ff h_ff, j10_ff, j11_ff;
     __host__ __device__ void init(const double* p, double hh) {
@@ -242,10 +261,32 @@ struct LinearOsc {
         j10 = -h * w * w; j11 = 1.0 - 2.0 * h * z * w;
         h_f = (float)h; j10_f = (float)j10; s11_f = (float)(-2.0 * h * z * w);
         h_ff = ff_const(h); j10_ff = ff_const(j10); j11_ff = ff_const(j11);
+        ww = w * w; zw2 = 2.0 * z * w;
     }
+    // float-float constants, split on the host: fc = (h, j10, j11) as hi/lo
+    // pairs, dc = (w^2, 2 z w)
+    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+        const double c[3] = {hh, -hh * p[0] * p[0], 1.0 - 2.0 * hh * p[1] * p[0]};
+        for (int i = 0; i < 3; ++i) {
+            const ff v = ff_const(c[i]);
+            fc[2 * i] = v.hi;
+            fc[2 * i + 1] = v.lo;
+        }
+        dc[0] = p[0] * p[0];
+        dc[1] = 2.0 * p[1] * p[0];
+    }
+    __device__ __forceinline__ void init_ff(const float* fc, const double* dc) {
+        h_ff = ff{fc[0], fc[1]};
+        j10_ff = ff{fc[2], fc[3]};
+        j11_ff = ff{fc[4], fc[5]};
+        ww = dc[0];
+        zw2 = dc[1];
+    }
+    // FP64 residual r = xc - (x + h f(x)), f = (v, -w^2 x - 2 z w v)
     __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
-        double jd[1];
-        eval(xp, xc, res, jd);
+        const double f1 = fma(-ww, xp[0], -zw2 * xp[1]);
+        res[0] = xc[0] - fma(h, xp[1], xp[0]);
+        res[1] = xc[1] - fma(h, f1, xp[1]);
         jv[0] = ff_zero();
     }
     __device__ __forceinline__ void leaf_ff(const ff*, const ff* r, ff* Pm, ff* c) const {
