@@ -37,13 +37,13 @@ UNIT = "steps/s"
 # under profiles/), keyed by workload and tagged with a hash of the kernel
 # sources they were taken on: a changed kernel reports traffic null.
 SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "newton_fused.cuh",
-             "newton_fused_mixed.cuh", "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "common.cuh"]
+             "newton_fused_mixed.cuh", "newton_implicit.cu", "systems.cuh", "fpconv.cuh", "ffarith.cuh",
+             "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28926442752 + 24175795200, "f256e3c44be6de8f"),        # 147 passes
-    "vdp_mixed": (13101624320 + 15198681600, "f256e3c44be6de8f"),  # 137 passes (fused kernel)
-    "vdp_rk4": (29213696 + 347228928, "f256e3c44be6de8f"),         # 8 passes; the 16 MB state stays in L2
-    "robertson": (13364147456 + 13725263360, "f256e3c44be6de8f"),  # 22 passes
+    "vdp": (28944568320 + 24172590848, "0abc2b5fa25dcbad"),        # 147 passes
+    "vdp_ff": (25518999808 + 27638631680, "0abc2b5fa25dcbad"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13094423552 + 15200515584, "0abc2b5fa25dcbad"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
