@@ -275,6 +275,54 @@ int pitn_solve_noalloc(int system_id, const double* params, const double* x0, do
                        pitn_result* result);
 
 /*
+ * Time-sharded solve of one IVP over several GPUs (not in the paper, which
+ * runs on one GPU; the split is the paper's own scan split at the level of
+ * devices).  A shard owns the contiguous steps [s, s + n) of one IVP of
+ * PITN_LORENZ63, PITN_VDP or PITN_LINEAR_OSC (explicit Euler, FP64).  Per
+ * Newton iteration a driver exchanges, between the shards, the state before
+ * each shard (halo), the shard aggregates ((d^2 + d) doubles each, eq. 3.3),
+ * the largest residual and the first guard cut; the shard-local work runs in
+ * these calls:
+ *   pitn_shard_create   a plan for n local steps (owns its device scratch);
+ *                       guard_B as in pitn_options; stream nullable
+ *   pitn_shard_pass     x_prev [d]: the state before the shard (x0 for the
+ *                       shard holding step 0; the guard's fill state for a
+ *                       shard wholly beyond the cut); holds_first: the shard
+ *                       holds step 0 (its first element is (0, -r_0),
+ *                       eq. 3.4); X [n][d]: the current iterate, whose states
+ *                       from q_local on are read as the state before them
+ *                       (lazy guard fill); writes the shard aggregate
+ *                       agg_out [d^2 + d] (matrix row-major, then vector) and
+ *                       the bit pattern of max |r| (eq. 3.8) to res_bits_out
+ *                       [1] (non-negative doubles order like their bits; NaN
+ *                       above +inf, so the driver reduces them as integers)
+ *   pitn_shard_carry    the incoming correction of shard r: aggs [r][d^2 + d]
+ *                       (the aggregates of shards 0 .. r-1 in order) composed
+ *                       from the zero correction; z_out [d]
+ *   pitn_shard_update   the replay of eq. 3.13 from z_in [d] over the elements
+ *                       of the last pass, the next iterate into Xn [n][d], and
+ *                       the local index of the first correction that is not
+ *                       finite or exceeds guard_B, or n, into cut_out [1]
+ *                       (int64)
+ *   pitn_shard_finalize the iterate with its lazy fill written out: out [n][d]
+ *   pitn_shard_destroy  frees the plan
+ * Every array is device memory of the current device; each call blocks
+ * until its outputs are written.  paper_2511_01465_gb300/timeshard.py is the
+ * driver (torch.distributed, or shards emulated on one GPU).  Returns
+ * PITN_OK, PITN_EINVAL (bad argument, update without a pass), PITN_ENOMEM or
+ * PITN_ECUDA.
+ */
+typedef struct pitn_shard pitn_shard;
+int pitn_shard_create(int system_id, const double* params, double h, int64_t n, int d, double guard_B,
+                      void* stream, pitn_shard** out);
+int pitn_shard_pass(pitn_shard* s, const double* x_prev, int holds_first, const double* X, int64_t q_local,
+                    double* agg_out, int64_t* res_bits_out);
+int pitn_shard_carry(pitn_shard* s, int64_t r, const double* aggs, double* z_out);
+int pitn_shard_update(pitn_shard* s, const double* z_in, double* Xn, int64_t* cut_out);
+int pitn_shard_finalize(pitn_shard* s, const double* X, const double* x_prev, int64_t q_local, double* out);
+int pitn_shard_destroy(pitn_shard* s);
+
+/*
  * Measured FMA issue rate of the current device (not in the paper; the
  * benchmark's ALU roofline denominators): kind 0 = FP64 (DFMA), 1 = FP32
  * (FFMA).  A register-only kernel runs 8 independent FMA chains per thread on

@@ -85,6 +85,18 @@ def lib():
         L.pitn_probe_fma_rate.restype = c_int
         L.pitn_debug_inject.argtypes = [c_int, i64]
         L.pitn_debug_inject.restype = c_int
+        L.pitn_shard_create.argtypes = [c_int, vp, d, i64, c_int, d, vp, ctypes.POINTER(vp)]
+        L.pitn_shard_create.restype = c_int
+        L.pitn_shard_pass.argtypes = [vp, vp, c_int, vp, i64, vp, vp]
+        L.pitn_shard_pass.restype = c_int
+        L.pitn_shard_carry.argtypes = [vp, i64, vp, vp]
+        L.pitn_shard_carry.restype = c_int
+        L.pitn_shard_update.argtypes = [vp, vp, vp, vp]
+        L.pitn_shard_update.restype = c_int
+        L.pitn_shard_finalize.argtypes = [vp, vp, vp, i64, vp]
+        L.pitn_shard_finalize.restype = c_int
+        L.pitn_shard_destroy.argtypes = [vp]
+        L.pitn_shard_destroy.restype = c_int
         L.pitn_solve_noalloc.argtypes = [c_int, vp, vp, d, i64, c_int, d, c_int, d, vp,
                                           ctypes.POINTER(pitn_result)]
         L.pitn_solve_noalloc.restype = c_int
@@ -280,3 +292,12 @@ def pitn_probe_fma_rate(kind):
 def pitn_debug_inject(what, value=0):
     """Failure injection for tests of the error paths (see include/pitn.h)."""
     return lib().pitn_debug_inject(int(what), int(value))
+
+
+def shard_create(system, params, h, n, d, guard_B=0.0, stream=None):
+    """A time-shard plan (see include/pitn.h); params on the device or host."""
+    plan = ctypes.c_void_p()
+    st = ctypes.c_void_p(int(stream)) if stream is not None else None
+    check(lib().pitn_shard_create(int(system), _ptr(params), float(h), int(n), int(d), float(guard_B), st,
+                                  ctypes.byref(plan)), "pitn_shard_create")
+    return plan
