@@ -77,6 +77,17 @@ def spread(rs):
     return int(window), int(first_div), int(first_res_div)
 
 
+def rejected_cut_window(rs):
+    """For a plain solve that ends on a non-finite correction: the largest
+    distance of a variant's index of that rejected correction from the
+    oracle's (where a diverging correction leaves the FP64 range moves with
+    rounding), or 0 when the solve does not end that way."""
+    ref = rs[None]
+    if len(ref["cuts"]) <= ref["iters"]:
+        return 0
+    return max(abs(int(r["cuts"][-1]) - int(ref["cuts"][-1])) for r in rs.values())
+
+
 def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div, first_res_div):
     """Asserts the GPU outcome of a guarded solve against the oracle's `ref`
     (a dict with status, iters, cuts, res_hist) under the measured spread."""
