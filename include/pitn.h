@@ -101,13 +101,16 @@ enum {
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
                                   Euler: the scan's elements in FP32 delta form
                                   (I + S, c); an inexact Newton step */
-    PITN_PREC_FP64_FF = 3      /* d = 2 (VDP, LINEAR_OSC), explicit Euler (not in
+    PITN_PREC_FP64_FF = 3,     /* d = 2 (VDP, LINEAR_OSC), explicit Euler (not in
                                   the paper): the scan (Jacobians, folds, carries,
                                   replay) in double-FP32 "float-float" arithmetic,
                                   ~2^-47 relative, on the FP32 pipe; residual,
                                   stopping test and update in FP64.  An inexact
                                   Newton step whose error is ~60x FP64 rounding:
                                   it reaches the FP64 root at FP64 accuracy */
+    PITN_PREC_MIXED_TF32 = 4   /* PITN_FKPP with d >= 64: as PITN_PREC_MIXED_BF16
+                                  with TF32 operands (tcgen05 kind::tf32: the FP32
+                                  aggregates as they stand, 10 mantissa bits) */
 };
 
 /* Per-solve outcome. */
@@ -224,6 +227,13 @@ int pitn_backward(int system_id, int64_t B, const double* params, const double* 
  */
 int pitn_affine_combine_delta(int64_t n, const float* S2, const float* b2, const float* S1,
                               const float* b1, float* S, float* b, void* stream);
+
+/* The same combine with TF32 operands (tcgen05.mma kind::tf32, FP32
+ * accumulation): the FP32 inputs are the operands as they stand, of which
+ * the tensor core uses the TF32 part; the vector part uses the FP32 rows of
+ * S2.  Same arguments, layouts and return codes. */
+int pitn_affine_combine_delta_tf32(int64_t n, const float* S2, const float* b2, const float* S1,
+                                   const float* b1, float* S, float* b, void* stream);
 
 /* Number of parameters of a system, or -1 for an unknown id. */
 int pitn_num_params(int system_id);

@@ -21,7 +21,7 @@ from .pitn import (  # noqa: F401
     PITN_ETIMEOUT, PITN_EUNSUPPORTED, PITN_LORENZ63, PITN_VDP, PITN_LINEAR_OSC, PITN_FKPP,
     PITN_LOGISTIC, PITN_DAHLQUIST, PITN_ROBERTSON, PITN_STEP_EULER, PITN_STEP_RK4,
     PITN_STEP_BACKWARD_EULER, PITN_STEP_TRAPEZOID,
-    PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF, PitnError, pitn_solve, pitn_solve_ex, pitn_solve_batch,
+    PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF, PITN_PREC_MIXED_TF32, PitnError, pitn_solve, pitn_solve_ex, pitn_solve_batch,
     pitn_backward, pitn_status_string, pitn_release_workspace, pitn_launch_count, pitn_num_params,
 )
 from .api import solve, solve_batch, backward  # noqa: F401

@@ -363,8 +363,10 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
     if (max_iter < 0 || max_iter > kMaxIter) return PITN_EINVAL;
     if (std::isnan(o.guard_B)) return PITN_EINVAL;
     if (o.precision != PITN_PREC_FP64 && o.precision != PITN_PREC_MIXED_BF16 &&
-        o.precision != PITN_PREC_MIXED_FP32 && o.precision != PITN_PREC_FP64_FF)
+        o.precision != PITN_PREC_MIXED_FP32 && o.precision != PITN_PREC_FP64_FF &&
+        o.precision != PITN_PREC_MIXED_TF32)
         return PITN_EINVAL;
+    if (o.precision == PITN_PREC_MIXED_TF32 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.precision == PITN_PREC_FP64_FF &&
         ((system_id != PITN_VDP && system_id != PITN_LINEAR_OSC) || o.method != PITN_STEP_EULER))
         return PITN_EINVAL;

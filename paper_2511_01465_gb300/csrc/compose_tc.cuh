@@ -290,5 +290,135 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
     return kTcOk;
 }
 
+// ---------------------------------------------------------------------------
+// The same compose with TF32 operands (tcgen05.mma kind::tf32).  The FP32
+// aggregates are the operands as they stand: a 32-bit container per element,
+// of which the tensor core uses the TF32 part (10 explicit mantissa bits
+// against BF16's 7), accumulating in FP32.  Core matrices of the canonical
+// K-major layout hold 8 rows x 4 elements (16 bytes per row); one MMA takes
+// K = 8, so K = 128 is 16 MMAs.  The inputs come by L2 loads straight into
+// that layout (no FP32 staging tiles and no conversion: 128 KB of shared
+// memory for both operands); the epilogue re-reads S2 + S1 through L2 and
+// the vector part uses the FP32 rows of S2 from the A tile.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kGroupBytes32 = 32 * kCoreBytes;      // one 8-row group spans K = 128 (32 cores)
+constexpr uint32_t kTileBytes32 = 16 * kGroupBytes32;    // 128 rows, 64 KB
+
+__device__ __forceinline__ uint32_t core_off32(int row, int k) {
+    return (uint32_t)((row >> 3) * kGroupBytes32 + (k >> 2) * kCoreBytes + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t make_desc32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((kCoreBytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((kGroupBytes32 >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor of kind::tf32: D = F32, A = B = TF32 (format 2),
+// both K-major, N = 128, M = 128
+__device__ __forceinline__ uint32_t make_idesc_tf32() {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kDim >> 3) << 17) | ((uint32_t)(kDim >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate) : "memory");
+}
+
+struct __align__(1024) ComposeSmem32 {
+    uint8_t A[kTileBytes32];   // S2 (rows m, K-major), FP32 bits
+    uint8_t B[kTileBytes32];   // S1 (rows n = columns of S1, K-major), FP32 bits
+    float b1[kDim];
+    uint64_t mbar;             // MMA completion
+    uint64_t mbar_ld;          // unused (kept so both layouts share the set-up code)
+    uint32_t tmem;
+};
+
+// One TF32 compose by a CTA of 128 or 256 threads; every thread calls it.
+// Inputs by L2 loads (the caller orders them after their writers); returns
+// kTcOk, or kTcTimedOut / kTcStuck as compose_tc (then nothing is written).
+__device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __restrict__ S2,
+                                            const float* __restrict__ b2, const float* __restrict__ S1,
+                                            const float* __restrict__ b1, float* __restrict__ So,
+                                            float* __restrict__ bo, uint32_t phase,
+                                            uint64_t mma_polls = kSpinLimit) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // A(m, k) = S2[m][k], stored column-major at k * 128 + m: thread (m, kq)
+    // gathers k = 4 kq .. 4 kq + 3 (four coalesced warp loads) into one
+    // 16-byte core row; lanes run over m, so a phase of 8 lanes fills one
+    // 128-byte core matrix (no bank conflicts)
+    for (int idx = tid; idx < kDim * (kDim / 4); idx += blockDim.x) {
+        const int m = idx & (kDim - 1), k = (idx >> 7) * 4;
+        float4 v;
+        v.x = __ldcg(S2 + (size_t)k * kDim + m);
+        v.y = __ldcg(S2 + (size_t)(k + 1) * kDim + m);
+        v.z = __ldcg(S2 + (size_t)(k + 2) * kDim + m);
+        v.w = __ldcg(S2 + (size_t)(k + 3) * kDim + m);
+        *reinterpret_cast<float4*>(sm.A + core_off32(m, k)) = v;
+    }
+    // B(n, k) = S1[k][n], stored at n * 128 + k: 4 consecutive k are 16 contiguous bytes
+    for (int idx = tid; idx < kDim * (kDim / 4); idx += blockDim.x) {
+        const int n = idx & (kDim - 1), k = (idx >> 7) * 4;
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + k));
+        *reinterpret_cast<float4*>(sm.B + core_off32(n, k)) = v;
+    }
+    if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
+    fence_proxy_async();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (tid == 0) {
+        const uint32_t a0 = smem_addr(sm.A), b0 = smem_addr(sm.B), idesc = make_idesc_tf32();
+#pragma unroll
+        for (int s = 0; s < kDim / 8; ++s)
+            mma_tf32(sm.tmem, make_desc32(a0 + s * 2 * kCoreBytes), make_desc32(b0 + s * 2 * kCoreBytes), idesc,
+                     s > 0 ? 1u : 0u);
+        mma_commit(&sm.mbar);
+    }
+    const bool done = __syncthreads_and(mbar_wait(&sm.mbar, phase, mma_polls) ? 1 : 0) != 0;
+    if (!done) {
+        const bool drained = __syncthreads_and(mbar_wait(&sm.mbar, phase) ? 1 : 0) != 0;
+        fence_after();
+        return drained ? kTcTimedOut : kTcStuck;
+    }
+    fence_after();
+    const int m = tid & (kDim - 1);
+    const int halves = blockDim.x / kDim;  // 1 or 2
+    const int cols = kDim / halves, c0 = (tid / kDim) * cols;
+    const uint32_t trow = sm.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+#pragma unroll 1
+    for (int c = c0; c < c0 + cols; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const size_t off = (size_t)(c + j) * kDim + m;
+            So[off] = __ldcg(S2 + off) + __ldcg(S1 + off) + v[j];
+        }
+    }
+    if (tid < kDim) {
+        // S2 b1 from the FP32 row of S2 in the A tile, FP32 accumulation
+        float s = __ldcg(b2 + m) + sm.b1[m];
+#pragma unroll 4
+        for (int kc = 0; kc < kDim; kc += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(sm.A + core_off32(m, kc));
+            s = fmaf(a.x, sm.b1[kc], s);
+            s = fmaf(a.y, sm.b1[kc + 1], s);
+            s = fmaf(a.z, sm.b1[kc + 2], s);
+            s = fmaf(a.w, sm.b1[kc + 3], s);
+        }
+        bo[m] = s;
+    }
+    fence_before();
+    __syncthreads();
+    return kTcOk;
+}
+
 }  // namespace tc
 }  // namespace pitn

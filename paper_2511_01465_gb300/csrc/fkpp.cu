@@ -417,10 +417,32 @@ struct CombineArgs {
 
 constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
 
+// Operand precision of the tensor-core composes: BF16 (operands converted,
+// bulk copies for fresh inputs) or TF32 (FP32 aggregates as they stand).
+struct TcBf16 {
+    using Smem = tc::ComposeSmem;
+    static constexpr size_t kSmem = sizeof(Smem) + 1024;
+    static __device__ __forceinline__ int compose(Smem& sm, const float* S2, const float* b2, const float* S1,
+                                                  const float* b1, float* So, float* bo, uint32_t phase,
+                                                  bool bulk, uint64_t lp, uint64_t mp) {
+        return tc::compose_tc(sm, S2, b2, S1, b1, So, bo, phase, bulk, lp, mp);
+    }
+};
+struct TcTf32 {
+    using Smem = tc::ComposeSmem32;
+    static constexpr size_t kSmem = sizeof(Smem) + 1024;
+    static __device__ __forceinline__ int compose(Smem& sm, const float* S2, const float* b2, const float* S1,
+                                                  const float* b1, float* So, float* bo, uint32_t phase, bool,
+                                                  uint64_t, uint64_t mp) {
+        return tc::compose_tc32(sm, S2, b2, S1, b1, So, bo, phase, mp);
+    }
+};
+
+template <class Op>
 __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    tc::ComposeSmem& sm =
-        *reinterpret_cast<tc::ComposeSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    typename Op::Smem& sm =
+        *reinterpret_cast<typename Op::Smem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     const long long m = blockIdx.x;
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t MM = (size_t)FD * FD;
@@ -441,9 +463,9 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    const int rc = tc::compose_tc(sm, a.S2 + (size_t)m * a.stride_in * MM, a.b2 + m * a.stride_in * FD,
-                                  a.S1 + (size_t)m * a.stride_in * MM, a.b1 + m * a.stride_in * FD,
-                                  a.S + (size_t)m * MM, a.b + m * FD, 0u, true, a.load_polls, a.mma_polls);
+    const int rc = Op::compose(sm, a.S2 + (size_t)m * a.stride_in * MM, a.b2 + m * a.stride_in * FD,
+                               a.S1 + (size_t)m * a.stride_in * MM, a.b1 + m * a.stride_in * FD,
+                               a.S + (size_t)m * MM, a.b + m * FD, 0u, true, a.load_polls, a.mma_polls);
     if (rc != tc::kTcOk && tid == 0) raise_error(a.err, PITN_ETIMEOUT);
     tc::fence_before();
     __syncthreads();
@@ -472,10 +494,11 @@ struct UpArgs {
     unsigned long long load_polls, mma_polls;  // wait bounds of the composes
 };
 
+template <class Op>
 __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    tc::ComposeSmem& sm =
-        *reinterpret_cast<tc::ComposeSmem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
+    typename Op::Smem& sm =
+        *reinterpret_cast<typename Op::Smem*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~(uintptr_t)1023);
     __shared__ int s_go;
     const int tid = threadIdx.x, warp = tid >> 5;
     const size_t MM = (size_t)FD * FD;
@@ -518,9 +541,9 @@ __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
             }
             if (tid < FD) bo[tid] = __ldcg(bin + (2 * m) * FD + tid);
         } else {
-            rc = tc::compose_tc(sm, Sin + (size_t)(2 * m + 1) * MM, bin + (2 * m + 1) * FD,
-                                Sin + (size_t)(2 * m) * MM, bin + (2 * m) * FD, So, bo, composes & 1u, lv == 1,
-                                a.load_polls, a.mma_polls);
+            rc = Op::compose(sm, Sin + (size_t)(2 * m + 1) * MM, bin + (2 * m + 1) * FD,
+                             Sin + (size_t)(2 * m) * MM, bin + (2 * m) * FD, So, bo, composes & 1u, lv == 1,
+                             a.load_polls, a.mma_polls);
             ++composes;
             if (rc != tc::kTcOk) {   // uniform over the CTA: the compose decides CTA-wide
                 if (tid == 0) raise_error(a.err, PITN_ETIMEOUT);
@@ -729,7 +752,7 @@ Tree make_tree(long long T) {
 
 template <typename Real>
 int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, bool mixed,
-                  int* err, cudaStream_t st, bool residual_only) {
+                  int* err, cudaStream_t st, bool residual_only, bool tf32) {
     const size_t smemA = fold_smem_bytes<Real>(p.TS);
     {
         auto tok = timed_begin("fkpp_residual", st);
@@ -767,7 +790,8 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, boo
             ua.load_polls = wait_limits().load_polls;
             ua.mma_polls = wait_limits().mma_polls;
             auto tok = timed_begin("fkpp_compose", st);
-            fk_upsweep_tc_kernel<<<(unsigned)tr.n[1], 256, kTcSmem, st>>>(ua);
+            if (tf32) fk_upsweep_tc_kernel<TcTf32><<<(unsigned)tr.n[1], 256, TcTf32::kSmem, st>>>(ua);
+            else fk_upsweep_tc_kernel<TcBf16><<<(unsigned)tr.n[1], 256, TcBf16::kSmem, st>>>(ua);
             timed_end(tok, st);
             count_launch(1);
         }
@@ -862,8 +886,10 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
                              (int)((FD * FD + 16 * FD) * sizeof(double)));
         cudaFuncSetAttribute(fk_compose_f64<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((FD * FD + 8 * FD) * sizeof(double)));
-        cudaFuncSetAttribute(fk_upsweep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmem);
+        cudaFuncSetAttribute(fk_upsweep_tc_kernel<TcBf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcBf16::kSmem);
+        cudaFuncSetAttribute(fk_upsweep_tc_kernel<TcTf32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcTf32::kSmem);
     }
 
     const bool guarded = o.guard_B > 0.0 && std::isfinite(o.guard_B);
@@ -912,7 +938,8 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
         p.res_bits = res_bits + it;
         p.qenc = qenc + it;
         p.nonfinite = nonfinite + it;
-        int rc = run_iteration<Real>(p, tr, S, b, abuf, mixed, err_d, st, it == max_iter);
+        int rc = run_iteration<Real>(p, tr, S, b, abuf, mixed, err_d, st, it == max_iter,
+                                     o.precision == PITN_PREC_MIXED_TF32);
         if (rc != PITN_OK) return rc;
         if (cudaMemcpyAsync(&hc->res, res_bits + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&hc->q, qenc + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -956,7 +983,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
 int fkpp_solve(const SolveIO& io, double h, int64_t N, int d, double tol, int max_iter,
                const pitn_options& o, cudaStream_t st, SolveOutcome* out) {
     if (d > FD) return PITN_EINVAL;
-    if (o.precision == PITN_PREC_MIXED_BF16) {
+    if (o.precision == PITN_PREC_MIXED_BF16 || o.precision == PITN_PREC_MIXED_TF32) {
         if (d < 64) return PITN_EINVAL;
         return fkpp_solve_t<float>(io, h, N, d, tol, max_iter, o, st, out, true);
     }
@@ -968,8 +995,10 @@ int fkpp_solve(const SolveIO& io, double h, int64_t N, int d, double tol, int ma
 // ---------------------------------------------------------------------------
 // C-ABI primitive: n independent dense delta-form combines on tensor cores.
 // ---------------------------------------------------------------------------
-extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float* b2, const float* S1,
-                                         const float* b1, float* S, float* b, void* stream) {
+namespace {
+template <class Op>
+int combine_delta(int64_t n, const float* S2, const float* b2, const float* S1, const float* b1, float* S,
+                  float* b, void* stream) {
     using namespace pitn;
     using namespace pitn_host;
     if (n < 1 || !S2 || !b2 || !S1 || !b1 || !S || !b) return PITN_EINVAL;
@@ -983,14 +1012,14 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
     int* err = (int*)workspace(64, kSlotCtrl);
     if (!err) return PITN_ENOMEM;
     if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return PITN_ECUDA;
-    cudaFuncSetAttribute(fk_compose_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    cudaFuncSetAttribute(fk_compose_tc_kernel<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Op::kSmem);
     CombineArgs ca;
     ca.S2 = S2; ca.b2 = b2; ca.S1 = S1; ca.b1 = b1; ca.S = S; ca.b = b;
     ca.n = n; ca.stride_in = 1; ca.n_lone = -1; ca.err = err; ca.stop = nullptr;
     ca.load_polls = wait_limits().load_polls;
     ca.mma_polls = wait_limits().mma_polls;
     auto tok = timed_begin("fkpp_compose", st);
-    fk_compose_tc_kernel<<<(unsigned)n, 256, kTcSmem, st>>>(ca);
+    fk_compose_tc_kernel<Op><<<(unsigned)n, 256, Op::kSmem, st>>>(ca);
     timed_end(tok, st);
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;
@@ -999,4 +1028,15 @@ extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float
         cudaStreamSynchronize(st) != cudaSuccess)
         return PITN_ECUDA;
     return h_err ? h_err : PITN_OK;
+}
+}  // namespace
+
+extern "C" int pitn_affine_combine_delta(int64_t n, const float* S2, const float* b2, const float* S1,
+                                         const float* b1, float* S, float* b, void* stream) {
+    return combine_delta<pitn::TcBf16>(n, S2, b2, S1, b1, S, b, stream);
+}
+
+extern "C" int pitn_affine_combine_delta_tf32(int64_t n, const float* S2, const float* b2, const float* S1,
+                                              const float* b1, float* S, float* b, void* stream) {
+    return combine_delta<pitn::TcTf32>(n, S2, b2, S1, b1, S, b, stream);
 }

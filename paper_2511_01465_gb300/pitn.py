@@ -30,7 +30,7 @@ PITN_STEP_EULER, PITN_STEP_RK4, PITN_STEP_BACKWARD_EULER, PITN_STEP_TRAPEZOID = 
 PITN_DEBUG_RESET, PITN_DEBUG_FAIL_ALLOCS, PITN_DEBUG_GRID_WAIT_NS = 0, 1, 2
 PITN_DEBUG_LOAD_POLLS, PITN_DEBUG_MMA_POLLS = 3, 4
 # precisions
-PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF = 0, 1, 2, 3
+PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_FP32, PITN_PREC_FP64_FF, PITN_PREC_MIXED_TF32 = 0, 1, 2, 3, 4
 
 
 class pitn_result(ctypes.Structure):
@@ -102,6 +102,8 @@ def lib():
         L.pitn_solve_noalloc.restype = c_int
         L.pitn_affine_combine_delta.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         L.pitn_affine_combine_delta.restype = c_int
+        L.pitn_affine_combine_delta_tf32.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
+        L.pitn_affine_combine_delta_tf32.restype = c_int
         L.pitn_tune_enable.argtypes = [c_int]
         L.pitn_tune_enable.restype = c_int
         L.pitn_tune_clear.argtypes = []
@@ -205,7 +207,12 @@ def pitn_solve_noalloc(system_id, params, x0, h, N, d, tol, max_iter, guard_B, t
     return rc, res
 
 
-def pitn_affine_combine_delta(n, S2, b2, S1, b1, S, b, stream=None):
+def pitn_affine_combine_delta_tf32(n, S2, b2, S1, b1, S, b, stream=None):
+    """pitn_affine_combine_delta with TF32 operands."""
+    return pitn_affine_combine_delta(n, S2, b2, S1, b1, S, b, stream, _fn="pitn_affine_combine_delta_tf32")
+
+
+def pitn_affine_combine_delta(n, S2, b2, S1, b1, S, b, stream=None, _fn="pitn_affine_combine_delta"):
     """n dense delta-form combines (float32 CUDA tensors, matrices [n][128][128] column-major)."""
     import torch
     def fp(t):
@@ -213,7 +220,7 @@ def pitn_affine_combine_delta(n, S2, b2, S1, b1, S, b, stream=None):
             raise TypeError("float32 contiguous tensors expected")
         return ctypes.c_void_p(t.data_ptr())
     st = ctypes.c_void_p(int(stream)) if stream is not None else None
-    return lib().pitn_affine_combine_delta(int(n), fp(S2), fp(b2), fp(S1), fp(b1), fp(S), fp(b), st)
+    return getattr(lib(), _fn)(int(n), fp(S2), fp(b2), fp(S1), fp(b1), fp(S), fp(b), st)
 
 
 def pitn_num_params(system_id):
