@@ -5,7 +5,7 @@ update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|lorenz|lorenz_mixed|osc|
-                                                      robertson|fkpp|fkpp_mixed|batch|batch_small|adjoint]
+                                                      robertson|fkpp|fkpp_mixed|fkpp_tf32|batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica of
@@ -174,6 +174,10 @@ def workload(name):
     if name == "fkpp_mixed":
         return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=1,
                     desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, BF16 tensor-core "
+                         "composes (FP32 accumulate), FP64 residual and update")
+    if name == "fkpp_tf32":
+        return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=4,
+                    desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, TF32 tensor-core "
                          "composes (FP32 accumulate), FP64 residual and update")
     if name == "batch":
         return dict(kind="batch", bt=W.lorenz_batch(), tol=1e-8, max_iter=50, guard_B=100.0,
@@ -858,16 +862,21 @@ def roofline_for(name, spec, wl, res, ktimes, steps):
         note = "FP64 residual flops (15 per entry); peak = measured DFMA rate x 2"
     elif kern == "fkpp_fold":
         # the scan runs once per Newton update (a converged pass stops after its residual)
-        mixed = spec.get("precision", 0) == 1
+        mixed = spec.get("precision", 0) in (1, 4)
         flops = wl.N * res.iters * FK_FOLD_REAL_FLOPS
         peak = fp32_peak() if mixed else fp64_peak()
         bound, unit = "alu", "TFLOP/s"
         note = ("dense fold flops in " + ("FP32" if mixed else "FP64") +
                 "; peak = measured " + ("FFMA" if mixed else "DFMA") + " rate x 2")
     elif kern == "fkpp_compose":
-        mixed = spec.get("precision", 0) == 1
+        mixed = spec.get("precision", 0) in (1, 4)
         flops = fk_composes(fk_tiles(wl.N)) * FK_COMPOSE_FLOPS * res.iters
-        if mixed:
+        if mixed and spec.get("precision") == 4:
+            _, bf16, _, src = load_peaks()
+            peak, bound, unit = bf16 * 1.1 / 2.25, "tensor", "TFLOP/s"
+            note = (f"TF32 tensor-core composes; peak = {src} cuBLAS bf16 burst x 1.1/2.25 "
+                    "(nominal dense TF32 / BF16)")
+        elif mixed:
             _, bf16, _, src = load_peaks()
             peak, bound, unit = bf16, "tensor", "TFLOP/s"
             note = f"BF16 tensor-core composes; peak = {src} cuBLAS bf16 burst"
@@ -912,6 +921,7 @@ def oracle_passes(name, fallback):
            "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
+           "fkpp_tf32": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     try:
@@ -941,7 +951,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
-SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "vdp_mixed": 6, "vdp_ff": 6,
+SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6,
                 "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7}
 
 

@@ -353,20 +353,43 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
     // gathers k = 4 kq .. 4 kq + 3 (four coalesced warp loads) into one
     // 16-byte core row; lanes run over m, so a phase of 8 lanes fills one
     // 128-byte core matrix (no bank conflicts)
-    for (int idx = tid; idx < kDim * (kDim / 4); idx += blockDim.x) {
-        const int m = idx & (kDim - 1), k = (idx >> 7) * 4;
-        float4 v;
-        v.x = __ldcg(S2 + (size_t)k * kDim + m);
-        v.y = __ldcg(S2 + (size_t)(k + 1) * kDim + m);
-        v.z = __ldcg(S2 + (size_t)(k + 2) * kDim + m);
-        v.w = __ldcg(S2 + (size_t)(k + 3) * kDim + m);
-        *reinterpret_cast<float4*>(sm.A + core_off32(m, k)) = v;
+    // (kU core rows per thread and batch: all their loads are issued before
+    // any of their stores, so that many L2 requests are in flight at once)
+    constexpr int kU = 8;
+    constexpr int kRows = kDim * (kDim / 4);
+    for (int base = tid; base < kRows; base += kU * blockDim.x) {
+        float4 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < kRows) {
+                const int m = idx & (kDim - 1), k = (idx >> 7) * 4;
+                v[u].x = __ldcg(S2 + (size_t)k * kDim + m);
+                v[u].y = __ldcg(S2 + (size_t)(k + 1) * kDim + m);
+                v[u].z = __ldcg(S2 + (size_t)(k + 2) * kDim + m);
+                v[u].w = __ldcg(S2 + (size_t)(k + 3) * kDim + m);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < kRows) *reinterpret_cast<float4*>(sm.A + core_off32(idx & (kDim - 1), (idx >> 7) * 4)) = v[u];
+        }
     }
     // B(n, k) = S1[k][n], stored at n * 128 + k: 4 consecutive k are 16 contiguous bytes
-    for (int idx = tid; idx < kDim * (kDim / 4); idx += blockDim.x) {
-        const int n = idx & (kDim - 1), k = (idx >> 7) * 4;
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(S1 + (size_t)n * kDim + k));
-        *reinterpret_cast<float4*>(sm.B + core_off32(n, k)) = v;
+    for (int base = tid; base < kRows; base += kU * blockDim.x) {
+        float4 v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < kRows)
+                v[u] = __ldcg(reinterpret_cast<const float4*>(S1 + (size_t)(idx & (kDim - 1)) * kDim + (idx >> 7) * 4));
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int idx = base + u * blockDim.x;
+            if (idx < kRows) *reinterpret_cast<float4*>(sm.B + core_off32(idx & (kDim - 1), (idx >> 7) * 4)) = v[u];
+        }
     }
     if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
     fence_proxy_async();

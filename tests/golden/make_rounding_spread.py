@@ -29,6 +29,8 @@ CASES = {
     "lorenz_8192_guard100_tol1e-8_it100": ("lorenz", {}, 1e-8, 100, 100.0),
     "vdp_2^22_guard100_tol1e-12_it400": ("vdp", {}, 1e-12, 400, 100.0),
     "vdp_2^22_guard100_tol1e-8_it400": ("vdp", {}, 1e-8, 400, 100.0),
+    # plain Newton that diverges: the index at which the rejected correction overflows
+    "vdp_30001_h1e-3_plain_tol1e-10_it60": ("vdp", {"N": 30001, "h": 1e-3}, 1e-10, 60, 0.0),
 }
 
 
@@ -70,7 +72,10 @@ def main():
                           first_cut_difference=first_difference(ref["cuts"], r["cuts"]),
                           first_res_difference=first_res_difference(r["res_history"], ref["res_history"]))
         kind, kw, tol, it, B = CASES[name]
-        out[name] = dict(workload=kind, tol=tol, max_iter=it, guard_B=B,
+        rej = 0
+        if len(ref["cuts"]) > ref["iters"]:
+            rej = max(abs(r["cuts"][-1] - ref["cuts"][-1]) for r in rs.values())
+        out[name] = dict(workload=kind, kwargs=kw, tol=tol, max_iter=it, guard_B=B, rejected_cut_window=rej,
                          oracle=ref, variants=var,
                          window=max(abs(r["iters"] - ref["iters"]) for r in rs.values()),
                          first_div=min(x["first_cut_difference"] for x in var.values()),

@@ -36,17 +36,20 @@ def test_sharded_plain_equals_oracle(T, kind, shards):
     wl = {"vdp": W.vdp(N=30001, h=1e-3), "lorenz_plain": W.lorenz(N=4099),
           "osc": W.damped_oscillator(N=65537, h=1e-3)}[kind]
     traj, info = T.solve_sharded_on_one_gpu(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60, shards)
-    rs = R.runs(wl, 1e-10, 60, 0.0)
-    o = rs[None]
+    o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
     assert (info["iters"], info["status"], info["guard_index"]) == (o["iters"], o["status"], o["guard_index"])
     # the accepted steps' cuts exactly; where plain Newton diverges, the index
     # at which the rejected correction overflows within the oracle's rounding
-    # variants' spread of it (van der Pol, 30001 steps: 11026 and 11027)
+    # variants' spread of it (van der Pol, 30001 steps: 11026 and 11027,
+    # stored by tests/golden/make_rounding_spread.py)
     k = o["iters"]
     assert len(info["cut_history"]) == len(o["cuts"])
     assert np.array_equal(info["cut_history"][:k], o["cuts"][:k])
     if len(o["cuts"]) > k:
-        assert abs(int(info["cut_history"][k]) - int(o["cuts"][k])) <= R.rejected_cut_window(rs)
+        with open(os.path.join(HERE, "golden", "oracle_rounding_spread.json")) as f:
+            win = json.load(f)["vdp_30001_h1e-3_plain_tol1e-10_it60"]["rejected_cut_window"] \
+                if kind == "vdp" else 0
+        assert abs(int(info["cut_history"][k]) - int(o["cuts"][k])) <= win
     np.testing.assert_allclose(info["res_history"], o["res_hist"], rtol=1e-6, atol=1e-13)
     assert relerr(traj.cpu().numpy(), o["traj"]) <= 1e-10
 
