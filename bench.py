@@ -4,7 +4,7 @@ One step = one complete Newton solve (every residual evaluation, scan and
 update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|lorenz|lorenz_mixed|osc|
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|lorenz|lorenz_mixed|lorenz_ff|osc|
                                                       robertson|fkpp|fkpp_mixed|fkpp_tf32|batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
@@ -124,7 +124,8 @@ FP64_OPS = {"vdp": (20.0, 6.0)}
 # FP64 work per step and pass of the reduced-precision scans (fused kernel,
 # one pass per Newton iteration): the van der Pol residual (7 instructions,
 # 11 flops) and the update (FP32 scan: 2 DADD; float-float: 4 DADD)
-REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed": (13.0, 20.0)}
+REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed": (13.0, 20.0),
+                "lorenz_ff": (20.0, 23.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -160,6 +161,9 @@ def workload(name):
         return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=3,
                     desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
                          "scan in double-FP32 (float-float), FP64 residual and update")
+    if name == "lorenz_ff":
+        return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0, precision=3,
+                    desc="lorenz63 N=8192 h=1e-3, guarded Newton B=100, scan in double-FP32 (float-float)")
     if name == "lorenz_mixed":
         return dict(kind="single", wl=W.lorenz(), tol=1e-8, max_iter=100, guard_B=100.0, precision=2,
                     desc="lorenz63 N=8192 h=1e-3, guarded Newton B=100, scan in FP32 delta form")
@@ -918,7 +922,7 @@ def oracle_passes(name, fallback):
     tests/golden/make_oracle_golden.py, which runs only the oracle)."""
     key = {"vdp": "vdp_2^22_guard100_tol1e-8_it400", "osc": "osc_2^22_plain_tol1e-8_it10",
            "vdp_mixed": "vdp_2^22_guard100_tol1e-8_it400", "vdp_ff": "vdp_2^22_guard100_tol1e-8_it400",
-           "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100",
+           "lorenz_mixed": "lorenz_8192_guard100_tol1e-8_it100", "lorenz_ff": "lorenz_8192_guard100_tol1e-8_it100",
            "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "fkpp_tf32": "fkpp_d128_2^15_plain_tol1e-8_it50",
@@ -951,7 +955,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
-SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6,
+SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6, "lorenz_ff": 62,
                 "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7}
 
 

@@ -64,6 +64,8 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
         switch (system_id) {
         case PITN_VDP: *K = small_kernel_of<VanDerPol, kVarFusedFF>(); return PITN_OK;
         case PITN_LINEAR_OSC: *K = small_kernel_of<LinearOsc, kVarFusedFF>(); return PITN_OK;
+        // d = 3 keeps the three-phase structure, as its FP32 twin (registers)
+        case PITN_LORENZ63: *K = small_kernel_of<Lorenz63, kVarMixedFF>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }
     }

@@ -51,7 +51,7 @@ struct SmallArgs {
     // system constants precomputed on the host for the float-float scan
     // (kernel parameters live in the constant bank, so the compiler reloads
     // them instead of recomputing them with FP64 instructions inside the loop)
-    float fc[8];
+    float fc[16];
     double dc[4];
 };
 
@@ -661,8 +661,10 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
 namespace pitn {
 
 // Kernel variants behind a SmallKernel: the three-phase FP64 kernel, its
-// FP32 delta-form twin, and the fused FP64 and FP32-delta kernels.
-enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3, kVarFusedFF = 4 };
+// reduced-precision twins (FP32 delta form, float-float), and the fused FP64
+// and reduced-precision kernels.
+enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3, kVarFusedFF = 4,
+                    kVarMixedFF = 5 };
 
 // Dynamic shared memory of a launch: the row-stage tiles for d = 2.
 template <class Sys>
@@ -672,7 +674,8 @@ static size_t small_dyn_smem(int block) {
 
 template <class Sys, int VAR>
 static const void* small_kernel_ptr() {
-    if constexpr (VAR == kVarMixed) return (const void*)newton_small_mixed_kernel<Sys>;
+    if constexpr (VAR == kVarMixed) return (const void*)newton_small_mixed_kernel<Sys, ScanF32>;
+    else if constexpr (VAR == kVarMixedFF) return (const void*)newton_small_mixed_kernel<Sys, ScanFF>;
     else if constexpr (VAR == kVarFused) return (const void*)newton_fused_kernel<Sys>;
     else if constexpr (VAR == kVarFusedMixed) return (const void*)newton_fused_mixed_kernel<Sys, ScanF32>;
     else if constexpr (VAR == kVarFusedFF) return (const void*)newton_fused_mixed_kernel<Sys, ScanFF>;
@@ -720,7 +723,7 @@ struct SmallKernel {
 template <class Sys, int VAR = kVarPlain>
 static SmallKernel small_kernel_of() {
     SmallKernel k{&launch_small<Sys, VAR>, &max_blocks_per_sm<Sys, VAR>, Sys::JN + Sys::D, nullptr};
-    if constexpr (VAR == kVarFusedFF) k.consts = &Sys::host_ff_consts;
+    if constexpr (VAR == kVarFusedFF || VAR == kVarMixedFF) k.consts = &Sys::host_ff_consts;
     return k;
 }
 

@@ -167,17 +167,25 @@ __device__ __forceinline__ void dz_leaf(const float* S, const float* r, float* Q
     for (int i = 0; i < D; ++i) c[i] = tc[i];
 }
 
-template <class Sys>
+}  // namespace pitn
+
+#include "scan_policy.cuh"
+
+namespace pitn {
+
+template <class Sys, class Pol>
 __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
+    using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
     Sys sys;
     sys.init(a.params, a.h);
+    Pol::setup(sys, a);
 
-    __shared__ float s_wex[kMaxWarps][E];
-    __shared__ float s_tot[E];
-    __shared__ float s_g[kMaxWarps][E];
-    __shared__ float s_gtot[E];
-    __shared__ float s_zin[D];
+    __shared__ T s_wex[kMaxWarps][E];
+    __shared__ T s_tot[E];
+    __shared__ T s_g[kMaxWarps][E];
+    __shared__ T s_gtot[E];
+    __shared__ T s_zin[D];
     extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
 
     const int lane = threadIdx.x & 31;
@@ -185,8 +193,8 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthreads = (long long)gridDim.x * blockDim.x;
     const unsigned G = gridDim.x;
-    float* __restrict__ scr = reinterpret_cast<float*>(a.scratch);
-    float* __restrict__ agg = reinterpret_cast<float*>(a.agg);
+    T* __restrict__ scr = reinterpret_cast<T*>(a.scratch);   // sizeof(T) <= sizeof(double)
+    T* __restrict__ agg = reinterpret_cast<T*>(a.agg);
     double capd;
     {
         const unsigned long long cb = a.cap_bits;
@@ -226,10 +234,10 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
         unsigned long long my_res = 0ull;
         const long long Lr = kreg - k0;
         const long long LA = (Lr + 1) / 2, LB = Lr - LA, km = k0 + LA;
-        float QA[D * D], cA[D], QB[D * D], cB[D];
+        T QA[D * D], cA[D], QB[D * D], cB[D];
         double xpA[D], xpB[D];
-        dz_zero<D>(QA, cA);
-        dz_zero<D>(QB, cB);
+        Pol::template ident<D>(QA, cA);
+        Pol::template ident<D>(QB, cB);
         // x of each half's next step is loaded one step ahead
         double xnA[D], xnB[D];
         if (LA > 0) {
@@ -240,32 +248,24 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             load_state<D>(Xc, a.x0, km - 1, q, xpB);
             load_state<D>(Xc, a.x0, km, q, xnB);
         }
-        auto fold_step = [&](long long k, bool more, double* xp, double* xn, float* Q, float* c) {
+        auto fold_step = [&](long long k, bool more, double* xp, double* xn, T* Q, T* c) {
             double x[D], r[D];
-            float sv[JN], rf[D];
+            T sv[JN], rf[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) x[j] = xn[j];
             if (more) load_state<D>(Xc, a.x0, k + 1, q, xn);
-            sys.eval_mixed(xp, x, r, sv);
+            Pol::eval(sys, xp, x, r, sv);
 #pragma unroll
             for (int j = 0; j < JN; ++j) scr[sidx(k - k0, j)] = sv[j];
 #pragma unroll
             for (int j = 0; j < D; ++j) {
-                rf[j] = d2f_int(r[j]);
+                rf[j] = Pol::from_double(r[j]);
                 scr[sidx(k - k0, JN + j)] = rf[j];
                 const unsigned long long b = abs_bits(r[j]);
                 my_res = b > my_res ? b : my_res;
             }
-            if (k == 0) {  // a_0 = (0, -r_0): S = -I
-#pragma unroll
-                for (int j = 0; j < D * D; ++j) Q[j] = (j % (D + 1) == 0) ? -1.f : 0.f;
-#pragma unroll
-                for (int j = 0; j < D; ++j) c[j] = -rf[j];
-            } else {
-                float S[D * D];
-                sys.sfull(sv, S);
-                dz_leaf<D>(S, rf, Q, c);
-            }
+            if (k == 0) Pol::template head<D>(rf, Q, c);   // a_0 = (0, -r_0), eq. 3.4
+            else Pol::leaf(sys, sv, rf, Q, c);
 #pragma unroll
             for (int j = 0; j < D; ++j) xp[j] = x[j];
         };
@@ -273,31 +273,31 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             fold_step(k0 + i, i + 1 < LA, xpA, xnA, QA, cA);
             if (i < LB) fold_step(km + i, i + 1 < LB, xpB, xnB, QB, cB);
         }
-        float Q[D * D], c[D];
-        dz_compose<D>(QB, cB, QA, cA, Q, c);
+        T Q[D * D], c[D];
+        Pol::template compose<D>(QB, cB, QA, cA, Q, c);
         if (kreg < k1) {  // fill region: identical elements, binary powering
             double xf[D], rf64[D];
-            float svf[JN], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
+            T svf[JN], rff[D], EQ[D * D], Ec[D], RQ[D * D], Rc[D];
             load_state<D>(Xc, a.x0, q - 1, q, xf);
-            sys.eval_mixed(xf, xf, rf64, svf);
+            Pol::eval(sys, xf, xf, rf64, svf);
 #pragma unroll
             for (int j = 0; j < D; ++j) {
                 const unsigned long long b = abs_bits(rf64[j]);
                 my_res = b > my_res ? b : my_res;
-                Ec[j] = -(float)rf64[j];
+                rff[j] = Pol::from_double(rf64[j]);
             }
-            sys.sfull(svf, EQ);
-            dz_zero<D>(RQ, Rc);
+            Pol::elem(sys, svf, rff, EQ, Ec);
+            Pol::template ident<D>(RQ, Rc);
             for (long long e = k1 - kreg;;) {
-                if (e & 1) dz_compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
+                if (e & 1) Pol::template compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
                 e >>= 1;
                 if (!e) break;
-                dz_compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
+                Pol::template compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
             }
-            dz_compose<D>(RQ, Rc, Q, c, Q, c);
+            Pol::template compose<D>(RQ, Rc, Q, c, Q, c);
         }
-        float eQ[D * D], ec[D];
-        dz_block_scan<D>(Q, c, eQ, ec, s_wex, s_tot);
+        T eQ[D * D], ec[D];
+        pol_block_scan<Pol, D>(Q, c, eQ, ec, s_wex, s_tot);
         if (threadIdx.x < E) agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -317,31 +317,31 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
         // ---- incoming prefix: fixed-order scan of the CTA aggregates ----
         {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;
-            float gQ[D * D], gc[D];
-            dz_zero<D>(gQ, gc);
+            T gQ[D * D], gc[D];
+            Pol::template ident<D>(gQ, gc);
             for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
-                float sQ[D * D], sc[D];
+                T sQ[D * D], sc[D];
 #pragma unroll
-                for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+                for (int j = 0; j < D * D; ++j) sQ[j] = ld_cg(agg + (size_t)i * E + j);
 #pragma unroll
-                for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
-                dz_compose<D>(sQ, sc, gQ, gc, gQ, gc);
+                for (int j = 0; j < D; ++j) sc[j] = ld_cg(agg + (size_t)i * E + D * D + j);
+                Pol::template compose<D>(sQ, sc, gQ, gc, gQ, gc);
             }
-            float xQ[D * D], xc[D];
-            dz_block_scan<D>(gQ, gc, xQ, xc, s_g, s_gtot);
+            T xQ[D * D], xc[D];
+            pol_block_scan<Pol, D>(gQ, gc, xQ, xc, s_g, s_gtot);
             if (blockIdx.x > 0 && threadIdx.x == (blockIdx.x - 1) / m) {
-                float v[D], t[D], zero[D];
+                T v[D], t[D], zero[D];
 #pragma unroll
-                for (int j = 0; j < D; ++j) zero[j] = 0.f;
-                dz_apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
-                dz_apply<D>(xQ, xc, t, v);
+                for (int j = 0; j < D; ++j) zero[j] = Pol::zero();
+                Pol::template apply<D>(s_g[threadIdx.x >> 5], s_g[threadIdx.x >> 5] + D * D, zero, t);
+                Pol::template apply<D>(xQ, xc, t, v);
                 for (unsigned i = threadIdx.x * m; i <= blockIdx.x - 1; ++i) {
-                    float sQ[D * D], sc[D];
+                    T sQ[D * D], sc[D];
 #pragma unroll
-                    for (int j = 0; j < D * D; ++j) sQ[j] = __ldcg(agg + (size_t)i * E + j);
+                    for (int j = 0; j < D * D; ++j) sQ[j] = ld_cg(agg + (size_t)i * E + j);
 #pragma unroll
-                    for (int j = 0; j < D; ++j) sc[j] = __ldcg(agg + (size_t)i * E + D * D + j);
-                    dz_apply<D>(sQ, sc, v, t);
+                    for (int j = 0; j < D; ++j) sc[j] = ld_cg(agg + (size_t)i * E + D * D + j);
+                    Pol::template apply<D>(sQ, sc, v, t);
 #pragma unroll
                     for (int j = 0; j < D; ++j) v[j] = t[j];
                 }
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             }
             if (blockIdx.x == 0 && threadIdx.x == 0) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) s_zin[j] = 0.f;
+                for (int j = 0; j < D; ++j) s_zin[j] = Pol::zero();
             }
             __syncthreads();
         }
@@ -358,16 +358,16 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
         // ---- phase 3: FP32 replay, FP64 update ----
         unsigned long long my_q = 0ull;
         {
-            float zw[D], zA[D], zB[D];
-            dz_apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
-            dz_apply<D>(eQ, ec, zw, zA);
-            dz_apply<D>(QA, cA, zA, zB);
+            T zw[D], zA[D], zB[D];
+            Pol::template apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, s_zin, zw);
+            Pol::template apply<D>(eQ, ec, zw, zA);
+            Pol::template apply<D>(QA, cA, zA, zB);
             bool foundA = false, foundB = false;
             long long firstA = 0, firstB = 0;
             // each half's next (S entries, r, x) is loaded one step ahead
-            float fsA[W], fsB[W];
+            T fsA[W], fsB[W];
             double fxA[D], fxB[D];
-            auto fetch = [&](long long k, float* fs, double* fx) {
+            auto fetch = [&](long long k, T* fs, double* fx) {
 #pragma unroll
                 for (int j = 0; j < W; ++j) fs[j] = scr[sidx(k - k0, j)];   // this thread's phase-1 writes
                 load_state<D>(Xc, a.x0, k, q, fx);
@@ -384,8 +384,8 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
 #pragma unroll
                 for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
             };
-            auto replay_step = [&](int c, long long k, bool more, float* fs, double* fx, float* z) -> bool {
-                float sv[JN], rf[D], S[D * D];
+            auto replay_step = [&](int c, long long k, bool more, T* fs, double* fx, T* z) -> bool {
+                T sv[JN], rf[D];
                 double x[D];
 #pragma unroll
                 for (int j = 0; j < JN; ++j) sv[j] = fs[j];
@@ -397,26 +397,16 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
                 if (more) fetch(k + 1, fs, fx);
                 if (k == 0) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = -rf[j];
+                    for (int j = 0; j < D; ++j) z[j] = Pol::neg(rf[j]);
                 } else {
-                    sys.sfull(sv, S);
-                    float t[D];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        float s = z[i] - rf[i];
-#pragma unroll
-                        for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], z[l], s);
-                        t[i] = s;
-                    }
-#pragma unroll
-                    for (int j = 0; j < D; ++j) z[j] = t[j];
+                    Pol::replay(sys, sv, rf, z);
                 }
                 bool bad = false;
                 double xn[D];
 #pragma unroll
                 for (int j = 0; j < D; ++j) {
-                    xn[j] = x[j] + f2d_int(z[j]);
-                    bad |= !(fabsf(z[j]) <= capf);
+                    xn[j] = Pol::add_to(x[j], z[j]);
+                    bad |= !Pol::within(z[j], capf);
                 }
                 put_row(c, k, xn);
                 return bad;
@@ -430,33 +420,24 @@ __global__ void __launch_bounds__(256) newton_small_mixed_kernel(SmallArgs a) {
             }
             const bool found = foundA || foundB;
             if (found) my_q = ~(unsigned long long)(foundA ? firstA : firstB);
-            float z[D];
+            T z[D];
 #pragma unroll
             for (int j = 0; j < D; ++j) z[j] = (LB > 0) ? zB[j] : zA[j];
             if (!found && kreg < k1) {
                 double xf[D], rf64[D];
-                float svf[JN], S[D * D], rfl[D];
+                T svf[JN], rfl[D];
                 load_state<D>(Xc, a.x0, q - 1, q, xf);
-                sys.eval_mixed(xf, xf, rf64, svf);
-                sys.sfull(svf, S);
+                Pol::eval(sys, xf, xf, rf64, svf);
 #pragma unroll
-                for (int j = 0; j < D; ++j) rfl[j] = (float)rf64[j];
+                for (int j = 0; j < D; ++j) rfl[j] = Pol::from_double(rf64[j]);
                 for (long long k = kreg; k < k1; ++k) {
-                    float t[D];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) {
-                        float s = z[i] - rfl[i];
-#pragma unroll
-                        for (int l = 0; l < D; ++l) s = fmaf(S[i * D + l], z[l], s);
-                        t[i] = s;
-                    }
+                    Pol::replay(sys, svf, rfl, z);
                     bool bad = false;
                     double xn[D];
 #pragma unroll
                     for (int j = 0; j < D; ++j) {
-                        z[j] = t[j];
-                        xn[j] = xf[j] + f2d_int(z[j]);
-                        bad |= !(fabsf(z[j]) <= capf);
+                        xn[j] = Pol::add_to(xf[j], z[j]);
+                        bad |= !Pol::within(z[j], capf);
                     }
                     put_row(1, k, xn);
                     if (bad) {

@@ -107,6 +107,73 @@ struct Lorenz63 {
         J[3] = jv[0]; J[4] = j11;   J[5] = -jv[1];
         J[6] = jv[2]; J[7] = jv[1]; J[8] = j22;
     }
+    // float-float scan: constants split on the host, fc = (h, h rho, 1 - h sigma,
+    // h sigma, 1 - h, 1 - h beta) as hi/lo pairs
+    ff h_ff, hr_ff, j00_ff, j01_ff, j11_ff, j22_ff;
+    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+        const double c[6] = {hh, hh * p[1], 1.0 - hh * p[0], hh * p[0], 1.0 - hh, 1.0 - hh * p[2]};
+        for (int i = 0; i < 6; ++i) {
+            const ff v = ff_const(c[i]);
+            fc[2 * i] = v.hi;
+            fc[2 * i + 1] = v.lo;
+        }
+        (void)dc;
+    }
+    __device__ __forceinline__ void init_ff(const float* fc, const double*) {
+        h_ff = ff{fc[0], fc[1]};
+        hr_ff = ff{fc[2], fc[3]};
+        j00_ff = ff{fc[4], fc[5]};
+        j01_ff = ff{fc[6], fc[7]};
+        j11_ff = ff{fc[8], fc[9]};
+        j22_ff = ff{fc[10], fc[11]};
+    }
+    // FP64 residual (as eval); compact Jacobian jv = (h (rho - z), h x, h y)
+    // in float-float from the states split on the integer pipes
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        const double f0 = s * (xp[1] - xp[0]);
+        const double f1 = xp[0] * (r - xp[2]) - xp[1];
+        const double f2 = xp[0] * xp[1] - b * xp[2];
+        res[0] = xc[0] - (xp[0] + h * f0);
+        res[1] = xc[1] - (xp[1] + h * f1);
+        res[2] = xc[2] - (xp[2] + h * f2);
+        const ff xf = ff_from_double(xp[0]), yf = ff_from_double(xp[1]), zf = ff_from_double(xp[2]);
+        jv[0] = ff_sub(hr_ff, ff_mul(h_ff, zf));
+        jv[1] = ff_mul(h_ff, xf);
+        jv[2] = ff_mul(h_ff, yf);
+    }
+    // o = J v, J = [[j00, j01, 0], [jv0, j11, -jv1], [jv2, jv1, j22]]
+    __device__ __forceinline__ void jvec_ff(const ff* jv, const ff* v, ff* o) const {
+        const ff v0 = v[0], v1 = v[1], v2 = v[2];
+        o[0] = ff_fma(j00_ff, v0, ff_mul(j01_ff, v1));
+        o[1] = ff_fma(jv[0], v0, ff_fma(j11_ff, v1, ff_neg(ff_mul(jv[1], v2))));
+        o[2] = ff_fma(jv[2], v0, ff_fma(jv[1], v1, ff_mul(j22_ff, v2)));
+    }
+    __device__ __forceinline__ void leaf_ff(const ff* jv, const ff* rr, ff* Pm, ff* c) const {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const ff col[3] = {Pm[j], Pm[3 + j], Pm[6 + j]};
+            ff o[3];
+            jvec_ff(jv, col, o);
+            Pm[j] = o[0];
+            Pm[3 + j] = o[1];
+            Pm[6 + j] = o[2];
+        }
+        ff o[3];
+        jvec_ff(jv, c, o);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c[i] = ff_sub(o[i], rr[i]);
+    }
+    __device__ __forceinline__ void replay_ff(const ff* jv, const ff* rr, ff* z) const {
+        ff o[3];
+        jvec_ff(jv, z, o);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) z[i] = ff_sub(o[i], rr[i]);
+    }
+    __device__ __forceinline__ void jfull_ff(const ff* jv, ff* J) const {
+        J[0] = j00_ff; J[1] = j01_ff; J[2] = ff_zero();
+        J[3] = jv[0];  J[4] = j11_ff; J[5] = ff_neg(jv[1]);
+        J[6] = jv[2];  J[7] = jv[1];  J[8] = j22_ff;
+    }
     __device__ __forceinline__ void jac(const double* xp, double* jv) const {
         jv[0] = h * (r - xp[2]);
         jv[1] = h * xp[0];

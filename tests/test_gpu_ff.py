@@ -69,7 +69,7 @@ def ff_solve(pk, wl, tol, max_iter, guard_B):
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 31, 32, 33, 255, 256, 257, 1000, 4097, 20011, 30001])
-@pytest.mark.parametrize("kind", ["vdp", "osc"])
+@pytest.mark.parametrize("kind", ["vdp", "osc", "lorenz"])
 def test_ff_plain_equals_oracle(pk, kind, N):
     """Plain Newton: count, status, the cuts of the accepted steps and the
     residual history equal to the oracle's, trajectory within 1e-10.  (Where
@@ -77,7 +77,8 @@ def test_ff_plain_equals_oracle(pk, kind, N):
     overflows is where noise of the size of the scan's rounding, grown
     exponentially beyond the converged prefix, reaches the FP64 range: it
     moves with the scan's precision and is not compared.)"""
-    wl = W.vdp(N=N, h=1e-3) if kind == "vdp" else W.damped_oscillator(N=N, h=1e-3)
+    wl = {"vdp": lambda: W.vdp(N=N, h=1e-3), "osc": lambda: W.damped_oscillator(N=N, h=1e-3),
+          "lorenz": lambda: W.lorenz(N=N)}[kind]()
     g, gi = ff_solve(pk, wl, 1e-10, 60, 0.0)
     o = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
     assert (gi["iters"], gi["status"], gi["guard_index"]) == (o["iters"], o["status"], o["guard_index"])
@@ -123,8 +124,28 @@ def test_ff_bench_size(pk, name):
         assert relerr(g, O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)) <= TOL_REL
 
 
+@pytest.mark.parametrize("name", ["lorenz_8192_guard100_tol1e-12_it100", "lorenz_8192_guard100_tol1e-10_it50"])
+def test_ff_lorenz_guarded_8192(pk, name):
+    """Lorenz-63 (d = 3, the three-phase float-float kernel) at N = 8192,
+    guarded: within the measured rounding spread of the oracle; converged,
+    the root to 1e-10; capped, the prefix invariant."""
+    with open(SPREAD) as f:
+        sp = json.load(f)[name]
+    ref = dict(sp["oracle"], res_hist=sp["oracle"]["res_history"])
+    wl = W.lorenz()
+    g, gi = ff_solve(pk, wl, sp["tol"], sp["max_iter"], sp["guard_B"])
+    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, sp["window"],
+                    sp["first_div"], sp["first_res_div"])
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
+    if gi["status"] == O.OK:
+        assert relerr(g, seq) <= TOL_REL
+    else:
+        k = gi["iters"]
+        assert relerr(g[:k], seq[:k]) <= TOL_REL
+
+
 def test_ff_rejects_other_systems(pk):
     from paper_2511_01465_gb300 import pitn as P
-    wl = W.lorenz(N=10)
+    wl = W.robertson(h=1e-3)
     with pytest.raises(P.PitnError):
         pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 5, precision=P.PITN_PREC_FP64_FF)
