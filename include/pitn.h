@@ -101,13 +101,16 @@ enum {
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
                                   Euler: the scan's elements in FP32 delta form
                                   (I + S, c); an inexact Newton step */
-    PITN_PREC_FP64_FF = 3,     /* d = 2 (VDP, LINEAR_OSC), explicit Euler (not in
-                                  the paper): the scan (Jacobians, folds, carries,
-                                  replay) in double-FP32 "float-float" arithmetic,
-                                  ~2^-47 relative, on the FP32 pipe; residual,
-                                  stopping test and update in FP64.  An inexact
-                                  Newton step whose error is ~60x FP64 rounding:
-                                  it reaches the FP64 root at FP64 accuracy */
+    PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63), explicit Euler
+                                  (not in the paper): the scan (Jacobians, folds,
+                                  carries, replay) in double-FP32 "float-float"
+                                  arithmetic, ~2^-47 relative, on the FP32 pipe;
+                                  residual, stopping test and update in FP64.  An
+                                  inexact Newton step whose error is ~64x FP64
+                                  rounding: it reaches the FP64 root at FP64
+                                  accuracy.  Its range is the float range: a
+                                  correction beyond 3.4e38 counts as not finite
+                                  (FP64: 1.8e308) */
     PITN_PREC_MIXED_TF32 = 4   /* PITN_FKPP with d >= 64: as PITN_PREC_MIXED_BF16
                                   with TF32 operands (tcgen05 kind::tf32: the FP32
                                   aggregates as they stand, 10 mantissa bits) */

@@ -88,12 +88,15 @@ def rejected_cut_window(rs):
     return max(abs(int(r["cuts"][-1]) - int(ref["cuts"][-1])) for r in rs.values())
 
 
-def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div, first_res_div):
+def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div, first_res_div,
+                  compare_cuts=True):
     """Asserts the GPU outcome of a guarded solve against the oracle's `ref`
-    (a dict with status, iters, cuts, res_hist) under the measured spread."""
+    (a dict with status, iters, cuts, res_hist) under the measured spread.
+    compare_cuts=False leaves out the per-step cuts (for a scan whose own
+    rounding is coarser than the FP64 variants')."""
     assert gpu_status == ref["status"], (gpu_status, ref["status"])
     assert abs(int(gpu_iters) - int(ref["iters"])) <= window, (gpu_iters, ref["iters"], window)
-    k = min(first_div, len(ref["cuts"]))
+    k = min(first_div, len(ref["cuts"])) if compare_cuts else 0
     gc = np.asarray(gpu_cuts[:k], dtype=np.int64)
     rc = np.asarray(ref["cuts"][:k], dtype=np.int64)
     assert len(gc) == k and np.array_equal(gc, rc), (first_difference(gc, rc), k)
