@@ -98,5 +98,8 @@ def test_reference_arm_batch_line(monkeypatch):
         assert k in line, k
     assert line["impl"] == "reference" and line["value"] == 2.0e6
     bt = bench.workload("batch_small")["bt"]
-    assert line["ms_per_step"] == pytest.approx(float(bt.N.sum()) / 2.0e6 * 1e3)
+    # ms_per_step is the measured wall time of a step (one bounded sample);
+    # the whole batch at the sampled rate is reported beside it
+    assert 0 < line["ms_per_step"] < 1e3
+    assert line["config"]["projected_ms_per_solve"] == pytest.approx(float(bt.N.sum()) / 2.0e6 * 1e3)
     assert line["cpu_baseline"]["cores"] == 4 and line["e2e"]["h2d_bytes_per_step"] == 0
