@@ -42,9 +42,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28944568320 + 24172590848, "0abc2b5fa25dcbad"),        # 147 passes
-    "vdp_ff": (25518999808 + 27638631680, "0abc2b5fa25dcbad"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13094423552 + 15200515584, "0abc2b5fa25dcbad"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28943938304 + 24171237376, "13d733b96a425115"),        # 147 passes
+    "vdp_ff": (25517492736 + 27637988096, "13d733b96a425115"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13092923392 + 15200302336, "13d733b96a425115"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
