@@ -39,6 +39,12 @@ VARIANTS = {
     "fma_rev_diff_blk64": _FMA + ["-DORACLE_SUM_REVERSED", "-DORACLE_RESID_DIFF_FIRST",
                                   "-DORACLE_BLOCK=64"],
 }
+# A reduced-precision variant (test builds only): the recursion of eq. 3.13
+# carried in a 48-bit significand, the precision of a scan in pairs of 24-bit
+# floats; kept apart from VARIANTS, which are FP64 rounding orders only.
+SCAN_VARIANTS = {
+    "s48": ["-DORACLE_SCAN_BITS=48"],
+}
 
 # identifiers understood by the C oracle
 LORENZ63, VDP, LINEAR_OSC, FKPP, LOGISTIC, DAHLQUIST, ROBERTSON = 1, 2, 3, 4, 5, 6, 7
@@ -52,10 +58,11 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 
 def build(force: bool = False, variant: str | None = None) -> str:
     """Compile the C oracle into ``oracle/_build/liboracle.so`` (gcc, -O2, no FP
-    contraction), or one of its rounding VARIANTS into liboracle_<variant>.so."""
+    contraction), or one of its rounding VARIANTS (or SCAN_VARIANTS) into
+    liboracle_<variant>.so."""
     lib_path = _LIB if variant is None else os.path.join(_BUILD, f"liboracle_{variant}.so")
-    flags = ["-ffp-contract=off"] if variant is None else (
-        (["-ffp-contract=off"] if "-ffp-contract=fast" not in VARIANTS[variant] else []) + VARIANTS[variant])
+    vflags = [] if variant is None else {**VARIANTS, **SCAN_VARIANTS}[variant]
+    flags = (["-ffp-contract=off"] if "-ffp-contract=fast" not in vflags else []) + vflags
     with _lock:
         if (not force and os.path.exists(lib_path)
                 and os.path.getmtime(lib_path) >= os.path.getmtime(_SRC)):

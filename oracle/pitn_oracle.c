@@ -60,6 +60,12 @@
  *                             each block replayed from its incoming vector
  *                             (the same Newton step in exact arithmetic, by
  *                             the associativity of Lemma 3.1);
+ *   ORACLE_SCAN_BITS=b        the explicit recursion of eq. (3.13) is carried
+ *                             in a b-bit significand: the Jacobian entries,
+ *                             the residual entries and every correction are
+ *                             rounded to b significant bits (to nearest) as
+ *                             they enter or leave the recursion (b = 48: a
+ *                             scan in pairs of 24-bit floats);
  *   and, through the compiler, FMA contraction of every a*b + c.
  *
  * Readings of the paper that this file takes (the paper is silent on them):
@@ -641,6 +647,20 @@ static double row_dot(const double *row, const double *v, int d)
     return s;
 }
 
+#if defined(ORACLE_SCAN_BITS) && ORACLE_SCAN_BITS > 0
+/* v rounded to ORACLE_SCAN_BITS significant bits, to nearest (ties to even
+ * in the default rounding mode); zero, infinities and NaN unchanged.
+ * v = m 2^e with 0.5 <= |m| < 1, so m 2^b holds the b leading bits in its
+ * integer part. */
+static double scan_round(double v)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    double m = frexp(v, &e);
+    return ldexp(nearbyint(ldexp(m, ORACLE_SCAN_BITS)), e - ORACLE_SCAN_BITS);
+}
+#endif
+
 #if defined(ORACLE_BLOCK) && ORACLE_BLOCK > 0
 /*
  * Rounding variant (test builds only): the explicit recursion of eq. (3.13),
@@ -789,6 +809,17 @@ int oracle_newton(int sys, int method, const double *p, const double *x0, double
             if (recursion_blocked(sys, method, p, d, h, N, traj, r, dx) != OR_OK) {
                 free(r); free(dx); free(J); free(Bm); free(phi);
                 return OR_ENOMEM;
+            }
+#elif defined(ORACLE_SCAN_BITS) && ORACLE_SCAN_BITS > 0
+            for (int i = 0; i < d; ++i) dx[i] = scan_round(dx[i]);
+            for (int64_t n = 1; n < (int64_t)N; ++n) {
+                const double *xn = traj + (size_t)(n - 1) * d;
+                oracle_step(sys, method, p, d, h, xn, phi, J, NULL);
+                for (size_t i = 0; i < dd; ++i) J[i] = scan_round(J[i]);
+                for (int i = 0; i < d; ++i)
+                    dx[(size_t)n * d + i] =
+                        scan_round(row_dot(J + (size_t)i * d, dx + (size_t)(n - 1) * d, d) -
+                                   scan_round(r[(size_t)n * d + i]));
             }
 #else
             for (int64_t n = 1; n < (int64_t)N; ++n) {

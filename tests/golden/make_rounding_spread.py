@@ -8,7 +8,9 @@ Newton count, status, guard index, per-step cuts and residual history, every
 variant's count, status and first cut that differs from the oracle's, and
 the two figures the GPU parity tests use: ``window`` (the largest count
 difference of a variant from the oracle) and ``first_div`` (the first Newton
-step at which a variant cut elsewhere).
+step at which a variant cut elsewhere).  Under ``ff`` it stores the same three
+figures over the FP64 variants and the 48-bit-scan variant ``s48`` together:
+the bar of the float-float scan, whose corrections carry 48 significant bits.
 
     python tests/golden/make_rounding_spread.py
 """
@@ -52,7 +54,8 @@ def main():
     import oracle as O
     sys.path.insert(0, os.path.dirname(HERE))
     from rounding import first_difference, first_res_difference
-    variants = [None] + list(O.VARIANTS)
+    variants = [None] + list(O.VARIANTS) + list(O.SCAN_VARIANTS)
+    fp64 = list(O.VARIANTS)
     for v in variants:
         O.build(variant=v)
     tasks = [(n, v) for n in CASES for v in variants]
@@ -74,12 +77,14 @@ def main():
         kind, kw, tol, it, B = CASES[name]
         rej = 0
         if len(ref["cuts"]) > ref["iters"]:
-            rej = max(abs(r["cuts"][-1] - ref["cuts"][-1]) for r in rs.values())
+            rej = max(abs(rs[v]["cuts"][-1] - ref["cuts"][-1]) for v in [None] + fp64)
+
+        def figures(names):
+            return dict(window=max([abs(rs[v]["iters"] - ref["iters"]) for v in names] + [0]),
+                        first_div=min(var[v]["first_cut_difference"] for v in names),
+                        first_res_div=min(var[v]["first_res_difference"] for v in names))
         out[name] = dict(workload=kind, kwargs=kw, tol=tol, max_iter=it, guard_B=B, rejected_cut_window=rej,
-                         oracle=ref, variants=var,
-                         window=max(abs(r["iters"] - ref["iters"]) for r in rs.values()),
-                         first_div=min(x["first_cut_difference"] for x in var.values()),
-                         first_res_div=min(x["first_res_difference"] for x in var.values()))
+                         oracle=ref, variants=var, **figures(fp64), ff=figures(variants[1:]))
     with open(os.path.join(HERE, "oracle_rounding_spread.json"), "w") as f:
         json.dump(out, f, indent=1)
 

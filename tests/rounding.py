@@ -24,6 +24,11 @@ The GPU parity bar for a guarded solve is then:
     residual of a guarded iterate is largest next to the cut, where the
     corrections have grown exponentially, so it carries amplified rounding
     even while every variant cuts at the same step.
+A scan in reduced precision rounds the Newton step more coarsely than any
+FP64 order.  For the float-float scan (pairs of 24-bit floats, 48 significant
+bits) the spread also takes the oracle's 48-bit-scan variant (s48: the
+recursion's Jacobian entries, residuals and corrections rounded to 48 bits),
+which models that precision with the same mathematics.
 Only the oracle's code runs here.
 """
 from __future__ import annotations
@@ -35,10 +40,11 @@ import oracle as O
 VARIANTS = list(O.VARIANTS)
 
 
-def runs(wl, tol, max_iter, guard_B, method=O.EULER, guess=None):
-    """The oracle and each rounding variant on one problem: {None: ..., name: ...}."""
+def runs(wl, tol, max_iter, guard_B, method=O.EULER, guess=None, scan48=False):
+    """The oracle and each rounding variant on one problem: {None: ..., name: ...}
+    (with scan48, the 48-bit-scan variant as well)."""
     out = {}
-    for v in [None] + VARIANTS:
+    for v in [None] + VARIANTS + (list(O.SCAN_VARIANTS) if scan48 else []):
         out[v] = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, tol, max_iter, guard_B=guard_B,
                           guess=guess, method=method, variant=v)
     return out
@@ -88,15 +94,12 @@ def rejected_cut_window(rs):
     return max(abs(int(r["cuts"][-1]) - int(ref["cuts"][-1])) for r in rs.values())
 
 
-def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div, first_res_div,
-                  compare_cuts=True):
+def check_guarded(gpu_status, gpu_iters, gpu_cuts, gpu_hist, ref, window, first_div, first_res_div):
     """Asserts the GPU outcome of a guarded solve against the oracle's `ref`
-    (a dict with status, iters, cuts, res_hist) under the measured spread.
-    compare_cuts=False leaves out the per-step cuts (for a scan whose own
-    rounding is coarser than the FP64 variants')."""
+    (a dict with status, iters, cuts, res_hist) under the measured spread."""
     assert gpu_status == ref["status"], (gpu_status, ref["status"])
     assert abs(int(gpu_iters) - int(ref["iters"])) <= window, (gpu_iters, ref["iters"], window)
-    k = min(first_div, len(ref["cuts"])) if compare_cuts else 0
+    k = min(first_div, len(ref["cuts"]))
     gc = np.asarray(gpu_cuts[:k], dtype=np.int64)
     rc = np.asarray(ref["cuts"][:k], dtype=np.int64)
     assert len(gc) == k and np.array_equal(gc, rc), (first_difference(gc, rc), k)

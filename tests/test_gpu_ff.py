@@ -4,7 +4,9 @@ Its arithmetic (csrc/ffarith.cuh) against FP64 references: the integer-pipe
 split of a double into hi + lo is the hardware rounding of the double to
 float (exact ties aside) plus a remainder within 2^-47 relative; sums and
 products of float-float values are within 2^-44 of the FP64 results
-(normwise).  Its solves against the FP64 oracle, at the FP64 path's bars."""
+(normwise).  Its solves against the FP64 oracle, at the FP64 path's bars;
+where a guarded solve's cuts depend on rounding, within the spread of the
+FP64 rounding variants and the 48-bit-scan variant (tests/rounding.py)."""
 import json
 import os
 import shutil
@@ -43,7 +45,8 @@ def test_ff_against_fp64(tmp_path):
 # The float-float solve (PITN_PREC_FP64_FF) against the FP64 oracle: it must
 # meet the FP64 path's bars -- trajectories within 1e-10 of the oracle's,
 # integer outcomes equal where they are rounding-robust, guarded solves
-# within the spread rounding alone produces (tests/rounding.py).
+# within the spread rounding alone produces, the 48-bit scan's included
+# (tests/rounding.py).
 # ---------------------------------------------------------------------------
 TOL_REL = 1e-10
 SPREAD = os.path.join(HERE, "golden", "oracle_rounding_spread.json")
@@ -104,7 +107,7 @@ def test_ff_guarded_ragged(pk):
     is 3.9e-9 from the sequential trajectory)."""
     wl = W.vdp(N=20011, h=1e-3)
     g, gi = ff_solve(pk, wl, 1e-12, 80, 100.0)
-    rs = R.runs(wl, 1e-12, 80, 100.0)
+    rs = R.runs(wl, 1e-12, 80, 100.0, scan48=True)
     window, first_div, first_res_div = R.spread(rs)
     R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], rs[None], window,
                     first_div, first_res_div)
@@ -124,8 +127,9 @@ def test_ff_bench_size(pk, name):
     ref = dict(sp["oracle"], res_hist=sp["oracle"]["res_history"])
     wl = W.vdp()
     g, gi = ff_solve(pk, wl, sp["tol"], sp["max_iter"], sp["guard_B"])
-    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, sp["window"],
-                    sp["first_div"], sp["first_res_div"])
+    ff = sp["ff"]
+    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, ff["window"],
+                    ff["first_div"], ff["first_res_div"])
     assert gi["final_res"] <= sp["tol"]
     _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, g)
     assert not nf and res <= sp["tol"] * (1 + 1e-6)
@@ -136,18 +140,19 @@ def test_ff_bench_size(pk, name):
 @pytest.mark.parametrize("name", ["lorenz_8192_guard100_tol1e-12_it100", "lorenz_8192_guard100_tol1e-10_it50"])
 def test_ff_lorenz_guarded_8192(pk, name):
     """Lorenz-63 (d = 3, the three-phase float-float kernel) at N = 8192,
-    guarded: status, count and residual history within the measured rounding
-    spread of the oracle; converged, the root to 1e-10; capped, the prefix
-    invariant.  The per-step cuts are not compared: the float-float scan's
-    rounding (2^-47) is coarser than the FP64 variants', and on this chaotic
-    horizon its cut moves one step before theirs (step 40 against 41)."""
+    guarded: status, count, cuts and residual history within the rounding
+    spread of the oracle's FP64 variants and its 48-bit-scan variant (the
+    float-float scan's precision: on this chaotic horizon the 48-bit scan
+    cuts elsewhere from step 39, the FP64 orders from step 41); converged,
+    the root to 1e-10; capped, the prefix invariant."""
     with open(SPREAD) as f:
         sp = json.load(f)[name]
     ref = dict(sp["oracle"], res_hist=sp["oracle"]["res_history"])
     wl = W.lorenz()
     g, gi = ff_solve(pk, wl, sp["tol"], sp["max_iter"], sp["guard_B"])
-    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, sp["window"],
-                    sp["first_div"], sp["first_res_div"], compare_cuts=False)
+    ff = sp["ff"]
+    R.check_guarded(gi["status"], gi["iters"], gi["cut_history"], gi["res_history"], ref, ff["window"],
+                    ff["first_div"], ff["first_res_div"])
     seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
     if gi["status"] == O.OK:
         assert relerr(g, seq) <= TOL_REL

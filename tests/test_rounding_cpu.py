@@ -31,6 +31,28 @@ def test_variant_is_the_same_newton_iteration(variant):
         np.testing.assert_allclose(b["res_hist"], a["res_hist"], rtol=1e-6, atol=1e-14)
 
 
+def test_scan48_variant_is_the_newton_iteration_to_its_precision():
+    """The 48-bit-scan variant: plain Newton on Lorenz-63 (N = 500) and van
+    der Pol (N = 3000) takes the oracle's count, status and cuts, and its
+    root is the oracle's within 1e-12 (the residual and the update stay FP64,
+    so the root does not depend on the step's precision); an affine system
+    (the damped oscillator) still converges in one update, with a first
+    residual after it of the size of 48-bit rounding, not FP64 rounding."""
+    for wl in (W.lorenz(N=500), W.vdp(N=3000, h=1e-3)):
+        a = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60)
+        b = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-10, 60, variant="s48")
+        assert (a["iters"], a["status"], a["guard_index"]) == (b["iters"], b["status"], b["guard_index"])
+        assert np.array_equal(a["cuts"], b["cuts"])
+        assert np.abs(a["traj"] - b["traj"]).max() <= 1e-12 * np.abs(a["traj"]).max()
+    wl = W.damped_oscillator(N=4000, h=1e-3)
+    a = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 0.0, 1)
+    b = O.newton(wl.system, wl.params, wl.x0, wl.h, wl.N, 0.0, 1, variant="s48")
+    scale = np.abs(a["traj"]).max()
+    assert a["res_hist"][1] <= 1e-15 * scale
+    assert 1e-16 * scale < b["res_hist"][1] <= 2.0 ** -40 * scale
+    assert np.abs(a["traj"] - b["traj"]).max() <= 2.0 ** -40 * scale
+
+
 @pytest.mark.parametrize("variant", ["blk4", "blk64"])
 def test_blocked_bracketing_is_the_newton_step(variant):
     """One Newton step from a random guess bracketed in blocks equals the
@@ -86,10 +108,16 @@ def test_stored_spread_is_consistent():
         rejected = ref["status"] == O.NONFINITE and len(ref["cuts"]) > ref["iters"]
         assert len(ref["cuts"]) == ref["iters"] + (1 if rejected else 0)
         assert len(ref["res_history"]) == ref["iters"] + 1
-        assert e["window"] == max(abs(v["iters"] - ref["iters"]) for v in e["variants"].values())
-        assert e["first_div"] == min(v["first_cut_difference"] for v in e["variants"].values())
-        assert e["first_res_div"] == min(v["first_res_difference"] for v in e["variants"].values())
-        assert set(e["variants"]) == set(R.VARIANTS)
+        fp64 = {k: v for k, v in e["variants"].items() if k in R.VARIANTS}
+        assert e["window"] == max(abs(v["iters"] - ref["iters"]) for v in fp64.values())
+        assert e["first_div"] == min(v["first_cut_difference"] for v in fp64.values())
+        assert e["first_res_div"] == min(v["first_res_difference"] for v in fp64.values())
+        ff = e["ff"]   # the FP64 orders and the 48-bit scan together: a bar no tighter
+        assert ff["window"] == max(abs(v["iters"] - ref["iters"]) for v in e["variants"].values())
+        assert ff["first_div"] == min(v["first_cut_difference"] for v in e["variants"].values())
+        assert ff["first_res_div"] == min(v["first_res_difference"] for v in e["variants"].values())
+        assert ff["window"] >= e["window"] and ff["first_div"] <= e["first_div"]
+        assert set(e["variants"]) == set(R.VARIANTS) | set(O.SCAN_VARIANTS)
         for v in e["variants"].values():
             assert v["status"] == ref["status"]
 
@@ -99,4 +127,7 @@ def test_spread_of_lorenz_8192_recomputed():
     with open(os.path.join(HERE, "golden", "oracle_rounding_spread.json")) as f:
         e = json.load(f)["lorenz_8192_guard100_tol1e-8_it100"]
     wl = W.lorenz()
-    assert R.spread(R.runs(wl, 1e-8, 100, 100.0)) == (e["window"], e["first_div"], e["first_res_div"])
+    rs = R.runs(wl, 1e-8, 100, 100.0, scan48=True)
+    assert R.spread({k: v for k, v in rs.items() if k != "s48"}) == \
+        (e["window"], e["first_div"], e["first_res_div"])
+    assert R.spread(rs) == (e["ff"]["window"], e["ff"]["first_div"], e["ff"]["first_res_div"])
