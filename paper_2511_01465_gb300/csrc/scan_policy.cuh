@@ -18,6 +18,7 @@ namespace pitn {
 struct ScanF32 {
     using T = float;
     static constexpr int kMinBlocks = 0;   // no occupancy request: the compiler's own register choice
+    static constexpr bool kRollScans = false;
     template <int D>
     static __device__ __forceinline__ void ident(T* Q, T* c) { dz_zero<D>(Q, c); }
     template <int D>
@@ -83,6 +84,11 @@ struct ScanF32 {
 struct ScanFF {
     using T = ff;
     static constexpr int kMinBlocks = 2;   // 128 registers: two 256-thread CTAs per SM
+    // A float-float compose of 3 x 3 elements is ~400 instructions; for
+    // d >= 3 the scans' levels run as loops, so that the kernel's code stays
+    // within the instruction caches (unrolled, the d = 3 kernel's warps
+    // waited on instruction fetch more than on anything else).
+    static constexpr bool kRollScans = true;
     template <int D>
     static __device__ __forceinline__ void ident(T* P, T* c) {
 #pragma unroll
@@ -170,14 +176,20 @@ struct ScanFF {
 template <class Pol, int D>
 __device__ __forceinline__ void pol_warp_scan(typename Pol::T* Q, typename Pol::T* c, int lane) {
     using T = typename Pol::T;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    auto level = [&](int off) {
         T uQ[D * D], uc[D];
 #pragma unroll
         for (int j = 0; j < D * D; ++j) uQ[j] = Pol::shfl_up(Q[j], off);
 #pragma unroll
         for (int j = 0; j < D; ++j) uc[j] = Pol::shfl_up(c[j], off);
         if (lane >= off) Pol::template compose<D>(Q, c, uQ, uc, Q, c);
+    };
+    if constexpr (Pol::kRollScans && D >= 3) {
+#pragma unroll 1
+        for (int off = 1; off < 32; off <<= 1) level(off);
+    } else {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) level(off);
     }
 }
 
@@ -211,15 +223,24 @@ __device__ __forceinline__ void pol_block_scan(typename Pol::T* Q, typename Pol:
         } else {
             Pol::template ident<D>(wQ, wc);
         }
-#pragma unroll
-        for (int off = 1; off < kMaxWarps; off <<= 1) {
-            if (off >= nwarps) break;   // lanes from nwarps on hold identities
+        auto level = [&](int off) {
             T uQ[D * D], uc[D];
 #pragma unroll
             for (int j = 0; j < D * D; ++j) uQ[j] = Pol::shfl_up(wQ[j], off);
 #pragma unroll
             for (int j = 0; j < D; ++j) uc[j] = Pol::shfl_up(wc[j], off);
             if (lane >= off) Pol::template compose<D>(wQ, wc, uQ, uc, wQ, wc);
+        };
+        // lanes from nwarps on hold identities
+        if constexpr (Pol::kRollScans && D >= 3) {
+#pragma unroll 1
+            for (int off = 1; off < nwarps; off <<= 1) level(off);
+        } else {
+#pragma unroll
+            for (int off = 1; off < kMaxWarps; off <<= 1) {
+                if (off >= nwarps) break;
+                level(off);
+            }
         }
         T xQ[D * D], xc[D];
 #pragma unroll
