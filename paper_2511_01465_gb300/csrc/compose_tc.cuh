@@ -5,15 +5,17 @@
 //   S = S2 + S1 + S2 S1,   b = b2 + b1 + S2 b1                       (eq. 3.3)
 //
 // Both FP32 inputs arrive in shared memory by bulk copies (TMA, completion
-// counted on an mbarrier); S2 S1 is then one M = N = K = 128 product: BF16
+// counted on one mbarrier per input, so that S2's conversion starts while S1
+// is still in flight); S2 S1 is then one M = N = K = 128 product: BF16
 // operands converted into the canonical K-major core-matrix layout (8 rows x
 // 16 bytes per core matrix, no swizzle), eight tcgen05.mma (K = 16 each)
 // issued by one thread into a 128-lane x 128-column FP32 accumulator in TMEM,
-// completion signalled through a second mbarrier, and read back with
+// completion signalled through another mbarrier, and read back with
 // tcgen05.ld: TMEM lane m is row m of the product, so thread m of the CTA
-// owns row m in the epilogue, which adds S2 + S1 (FP32, from the staged
-// copies) and stores column-major (coalesced across the warp).
-// The vector part uses the same BF16 rows of S2 with FP32 accumulation.
+// owns row m in the epilogue, which adds S2 + S1 (FP32, summed in shared
+// memory while the product runs) and stores column-major (coalesced across
+// the warp).  The vector part uses the same BF16 rows of S2 with FP32
+// accumulation, also while the product runs.
 // Matrices are column-major FP32 (S[col][row]), 128 x 128.
 #pragma once
 
@@ -142,11 +144,32 @@ struct __align__(1024) ComposeSmem {
     float S1f[kDim * kDim];    // S1 column-major, as loaded
     float b1[kDim];
     uint64_t mbar;             // MMA completion
-    uint64_t mbar_ld;          // bulk-load completion
+    uint64_t mbar_ld;          // bulk copies of S2
+    uint64_t mbar_ld2;         // bulk copies of S1
     uint32_t tmem;
 };
 constexpr uint32_t kMatBytes = kDim * kDim * sizeof(float);
 constexpr uint32_t kLoadChunk = 16384;  // bytes per bulk copy
+
+// mbarrier set-up of a compose's shared memory (one thread), made visible to
+// the async proxy; the caller synchronises the CTA afterwards
+template <class Sm>
+__device__ __forceinline__ void init_barriers(Sm& sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.mbar, 1);
+        mbar_init(&sm.mbar_ld, 1);
+        mbar_init(&sm.mbar_ld2, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+}
+
+// After a copy wait gave up: wait (default bound) for both inputs' copies,
+// CTA-wide, before the shared memory they write is released or reused.
+__device__ __forceinline__ int drain_loads(ComposeSmem& sm, uint32_t phase) {
+    const bool drained =
+        __syncthreads_and((mbar_wait(&sm.mbar_ld, phase) && mbar_wait(&sm.mbar_ld2, phase)) ? 1 : 0) != 0;
+    return drained ? kTcTimedOut : kTcStuck;
+}
 
 // One compose by a CTA of 128 or 256 threads (with 256, two threads share a
 // row in the epilogue, each taking 64 columns); every thread of the CTA
@@ -166,39 +189,36 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
                                           uint64_t load_polls = kSpinLimit, uint64_t mma_polls = kSpinLimit) {
     const int tid = threadIdx.x, warp = tid >> 5;
     if (bulk) {
-        // both inputs by bulk copies; b1 by plain loads meanwhile
+        // each input by its own bulk copies and mbarrier; b1 by plain loads meanwhile
         if (tid == 0) {
-            mbar_expect_tx(&sm.mbar_ld, 2 * kMatBytes);
-            for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk) {
+            mbar_expect_tx(&sm.mbar_ld, kMatBytes);
+            mbar_expect_tx(&sm.mbar_ld2, kMatBytes);
+            for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk)
                 bulk_load(reinterpret_cast<uint8_t*>(sm.S2f) + o, reinterpret_cast<const uint8_t*>(S2) + o,
                           kLoadChunk, &sm.mbar_ld);
+            for (uint32_t o = 0; o < kMatBytes; o += kLoadChunk)
                 bulk_load(reinterpret_cast<uint8_t*>(sm.S1f) + o, reinterpret_cast<const uint8_t*>(S1) + o,
-                          kLoadChunk, &sm.mbar_ld);
-            }
+                          kLoadChunk, &sm.mbar_ld2);
         }
         if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
-        const bool loaded = __syncthreads_and(mbar_wait(&sm.mbar_ld, phase, load_polls) ? 1 : 0) != 0;
-        if (!loaded) {
-            // the copies are in flight: wait for them (default bound) before
-            // the shared memory they write is released or reused
-            const bool drained = __syncthreads_and(mbar_wait(&sm.mbar_ld, phase) ? 1 : 0) != 0;
-            return drained ? kTcTimedOut : kTcStuck;
-        }
+        if (__syncthreads_and(mbar_wait(&sm.mbar_ld, phase, load_polls) ? 1 : 0) == 0) return drain_loads(sm, phase);
     } else {
-        // 16-byte asynchronous copies through L2, all in flight at once
+        // 16-byte asynchronous copies through L2, all in flight at once: S2
+        // in the first commit group, S1 in the second
         const float4* s2 = reinterpret_cast<const float4*>(S2);
         const float4* s1 = reinterpret_cast<const float4*>(S1);
         float4* d2 = reinterpret_cast<float4*>(sm.S2f);
         float4* d1 = reinterpret_cast<float4*>(sm.S1f);
-        for (int i = tid; i < kDim * kDim / 4; i += blockDim.x) {
+        for (int i = tid; i < kDim * kDim / 4; i += blockDim.x)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
                          :: "r"(smem_addr(d2 + i)), "l"(s2 + i) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        for (int i = tid; i < kDim * kDim / 4; i += blockDim.x)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
                          :: "r"(smem_addr(d1 + i)), "l"(s1 + i) : "memory");
-        }
         asm volatile("cp.async.commit_group;" ::: "memory");
         if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
         __syncthreads();
     }
     // A(m, k) = S2[m][k] = S2 column-major [k][m]: thread gathers 8 consecutive
@@ -217,9 +237,19 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
         pk.w = *reinterpret_cast<uint32_t*>(&h3);
         *reinterpret_cast<uint4*>(sm.A + core_off(m, kc)) = pk;
     }
-    // B(n, k) = S1[k][n] = S1 column-major [n][k]: 8 consecutive k are contiguous
+    if (bulk) {
+        if (__syncthreads_and(mbar_wait(&sm.mbar_ld2, phase, load_polls) ? 1 : 0) == 0)
+            return drain_loads(sm, phase);
+    } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+    }
+    // B(n, k) = S1[k][n] = S1 column-major [n][k]: 8 consecutive k of one n are
+    // 32 contiguous bytes.  Consecutive threads take consecutive n, and chunk
+    // j + (n mod 8) of it: the 16-byte stores of 8 lanes fill one 128-byte
+    // core matrix row set (no bank conflicts), the loads meet at most 2-way.
     for (int idx = tid; idx < kDim * (kDim / 8); idx += blockDim.x) {
-        const int n = idx / (kDim / 8), kc = (idx % (kDim / 8)) * 8;
+        const int n = idx & (kDim - 1), kc = (((idx >> 7) + (n & 7)) & (kDim / 8 - 1)) * 8;
         const float4 lo = *reinterpret_cast<const float4*>(sm.S1f + n * kDim + kc);
         const float4 hi = *reinterpret_cast<const float4*>(sm.S1f + n * kDim + kc + 4);
         __nv_bfloat162 h0 = __floats2bfloat162_rn(lo.x, lo.y), h1 = __floats2bfloat162_rn(lo.z, lo.w);
@@ -243,6 +273,43 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
                      s > 0 ? 1u : 0u);
         mma_commit(&sm.mbar);
     }
+    // while the product runs (it reads only the A and B tiles): the vector
+    // part b = b2 + b1 + S2 b1 from the staged BF16 rows of S2 (the same
+    // operand the product uses), FP32 accumulation, kept in a register until
+    // the product is known to be done (threads 0 .. 127); and S1f <- S1 + S2
+    // for the epilogue (the other threads; with 128 threads, all of them
+    // after the vector part)
+    const int m = tid & (kDim - 1);
+    float bvec = 0.f;
+    if (tid < kDim) {
+        float sacc = __ldcg(b2 + m) + sm.b1[m];
+#pragma unroll 4
+        for (int kc = 0; kc < kDim; kc += 8) {
+            const uint4 pk = *reinterpret_cast<const uint4*>(sm.A + core_off(m, kc));
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float2 f = __bfloat1622float2(h[j]);
+                sacc = fmaf(f.x, sm.b1[kc + 2 * j], sacc);
+                sacc = fmaf(f.y, sm.b1[kc + 2 * j + 1], sacc);
+            }
+        }
+        bvec = sacc;
+    }
+    {
+        const int nadd = blockDim.x > kDim ? blockDim.x - kDim : blockDim.x;
+        const int t0 = blockDim.x > kDim ? tid - kDim : tid;
+        if (t0 >= 0) {
+            float4* s1 = reinterpret_cast<float4*>(sm.S1f);
+            const float4* s2 = reinterpret_cast<const float4*>(sm.S2f);
+            for (int i = t0; i < kDim * kDim / 4; i += nadd) {
+                float4 x = s2[i];
+                const float4 y = s1[i];
+                x.x += y.x; x.y += y.y; x.z += y.z; x.w += y.w;
+                s1[i] = x;
+            }
+        }
+    }
     const bool done = __syncthreads_and(mbar_wait(&sm.mbar, phase, mma_polls) ? 1 : 0) != 0;
     if (!done) {
         // the product is in flight: no TMEM load, and no return (after which
@@ -253,8 +320,8 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
     }
     fence_after();
     // epilogue: thread owns row m (TMEM lane m; a warp reaches the lane
-    // quarter warp % 4) and a range of columns
-    const int m = tid & (kDim - 1);
+    // quarter warp % 4) and a range of columns, and stores column-major
+    // (coalesced across the warp)
     const int halves = blockDim.x / kDim;  // 1 or 2
     const int cols = kDim / halves, c0 = (tid / kDim) * cols;
     const uint32_t trow = sm.tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -265,26 +332,10 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const size_t off = (size_t)(c + j) * kDim + m;
-            So[off] = sm.S2f[off] + sm.S1f[off] + v[j];
+            So[off] = sm.S1f[off] + v[j];
         }
     }
-    if (tid < kDim) {
-        // S2 b1 from the staged BF16 row of S2 (the same operand the product
-        // used), FP32 accumulation
-        float s = __ldcg(b2 + m) + sm.b1[m];
-#pragma unroll 4
-        for (int kc = 0; kc < kDim; kc += 8) {
-            const uint4 pk = *reinterpret_cast<const uint4*>(sm.A + core_off(m, kc));
-            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&pk);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float2 f = __bfloat1622float2(h[j]);
-                s = fmaf(f.x, sm.b1[kc + 2 * j], s);
-                s = fmaf(f.y, sm.b1[kc + 2 * j + 1], s);
-            }
-        }
-        bo[m] = s;
-    }
+    if (tid < kDim) bo[m] = bvec;
     fence_before();
     __syncthreads();
     return kTcOk;
@@ -296,10 +347,12 @@ __device__ __forceinline__ int compose_tc(ComposeSmem& sm, const float* __restri
 // of which the tensor core uses the TF32 part (10 explicit mantissa bits
 // against BF16's 7), accumulating in FP32.  Core matrices of the canonical
 // K-major layout hold 8 rows x 4 elements (16 bytes per row); one MMA takes
-// K = 8, so K = 128 is 16 MMAs.  The inputs come by L2 loads straight into
-// that layout (no FP32 staging tiles and no conversion: 128 KB of shared
-// memory for both operands); the epilogue re-reads S2 + S1 through L2 and
-// the vector part uses the FP32 rows of S2 from the A tile.
+// K = 8, so K = 128 is 16 MMAs.  S1 arrives column-major by asynchronous
+// copies into a staging tile, from which its operand tile is built in shared
+// memory; S2's operand tile is gathered from L2 meanwhile (its rows are
+// strided in memory).  The epilogue takes S2 from its operand tile and S1
+// from the staging tile; the vector part uses the FP32 rows of S2 while the
+// product runs.
 // ---------------------------------------------------------------------------
 constexpr uint32_t kGroupBytes32 = 32 * kCoreBytes;      // one 8-row group spans K = 128 (32 cores)
 constexpr uint32_t kTileBytes32 = 16 * kGroupBytes32;    // 128 rows, 64 KB
@@ -334,9 +387,10 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
 struct __align__(1024) ComposeSmem32 {
     uint8_t A[kTileBytes32];   // S2 (rows m, K-major), FP32 bits
     uint8_t B[kTileBytes32];   // S1 (rows n = columns of S1, K-major), FP32 bits
+    float S1f[kDim * kDim];    // S1 column-major as loaded; the result tile in the epilogue
     float b1[kDim];
     uint64_t mbar;             // MMA completion
-    uint64_t mbar_ld;          // unused (kept so both layouts share the set-up code)
+    uint64_t mbar_ld, mbar_ld2;  // unused (kept so both layouts share the set-up code)
     uint32_t tmem;
 };
 
@@ -349,6 +403,17 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
                                             float* __restrict__ bo, uint32_t phase,
                                             uint64_t mma_polls = kSpinLimit) {
     const int tid = threadIdx.x, warp = tid >> 5;
+    // S1 (column-major, contiguous) into the staging tile: 16-byte
+    // asynchronous copies through L2, all in flight while A is gathered
+    {
+        const float4* s1 = reinterpret_cast<const float4*>(S1);
+        float4* d1 = reinterpret_cast<float4*>(sm.S1f);
+        for (int i = tid; i < kDim * kDim / 4; i += blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                         :: "r"(smem_addr(d1 + i)), "l"(s1 + i) : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
     // A(m, k) = S2[m][k], stored column-major at k * 128 + m: thread (m, kq)
     // gathers k = 4 kq .. 4 kq + 3 (four coalesced warp loads) into one
     // 16-byte core row; lanes run over m, so a phase of 8 lanes fills one
@@ -376,22 +441,16 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
             if (idx < kRows) *reinterpret_cast<float4*>(sm.A + core_off32(idx & (kDim - 1), (idx >> 7) * 4)) = v[u];
         }
     }
-    // B(n, k) = S1[k][n], stored at n * 128 + k: 4 consecutive k are 16 contiguous bytes
-    for (int base = tid; base < kRows; base += kU * blockDim.x) {
-        float4 v[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int idx = base + u * blockDim.x;
-            if (idx < kRows)
-                v[u] = __ldcg(reinterpret_cast<const float4*>(S1 + (size_t)(idx & (kDim - 1)) * kDim + (idx >> 7) * 4));
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int idx = base + u * blockDim.x;
-            if (idx < kRows) *reinterpret_cast<float4*>(sm.B + core_off32(idx & (kDim - 1), (idx >> 7) * 4)) = v[u];
-        }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    // B(n, k) = S1[k][n] = S1f[n * 128 + k]: 4 consecutive k of one n are 16
+    // contiguous bytes.  Consecutive threads take consecutive n and k group
+    // j + (n mod 8): the 8 lanes of a phase store into one 128-byte core
+    // matrix and load from 8 distinct bank groups (no conflicts either way).
+    for (int idx = tid; idx < kRows; idx += blockDim.x) {
+        const int n = idx & (kDim - 1), k = (((idx >> 7) + (n & 7)) & (kDim / 4 - 1)) * 4;
+        *reinterpret_cast<float4*>(sm.B + core_off32(n, k)) = *reinterpret_cast<const float4*>(sm.S1f + n * kDim + k);
     }
-    if (tid < kDim) sm.b1[tid] = __ldcg(b1 + tid);
     fence_proxy_async();
     fence_before();
     __syncthreads();
@@ -404,6 +463,22 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
                      s > 0 ? 1u : 0u);
         mma_commit(&sm.mbar);
     }
+    // while the product runs: the vector part from the FP32 rows of S2 in the
+    // A tile, FP32 accumulation, kept in a register until the product is done
+    const int m = tid & (kDim - 1);
+    float bvec = 0.f;
+    if (tid < kDim) {
+        float sacc = __ldcg(b2 + m) + sm.b1[m];
+#pragma unroll 4
+        for (int kc = 0; kc < kDim; kc += 4) {
+            const float4 a = *reinterpret_cast<const float4*>(sm.A + core_off32(m, kc));
+            sacc = fmaf(a.x, sm.b1[kc], sacc);
+            sacc = fmaf(a.y, sm.b1[kc + 1], sacc);
+            sacc = fmaf(a.z, sm.b1[kc + 2], sacc);
+            sacc = fmaf(a.w, sm.b1[kc + 3], sacc);
+        }
+        bvec = sacc;
+    }
     const bool done = __syncthreads_and(mbar_wait(&sm.mbar, phase, mma_polls) ? 1 : 0) != 0;
     if (!done) {
         const bool drained = __syncthreads_and(mbar_wait(&sm.mbar, phase) ? 1 : 0) != 0;
@@ -411,7 +486,9 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
         return drained ? kTcTimedOut : kTcStuck;
     }
     fence_after();
-    const int m = tid & (kDim - 1);
+    // epilogue: row m, a range of columns; S2 (m, c..c+3) is one 16-byte core
+    // row of the A tile, S1 (m, c) the staging tile's column c; stores
+    // column-major (coalesced across the warp)
     const int halves = blockDim.x / kDim;  // 1 or 2
     const int cols = kDim / halves, c0 = (tid / kDim) * cols;
     const uint32_t trow = sm.tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -420,24 +497,18 @@ __device__ __forceinline__ int compose_tc32(ComposeSmem32& sm, const float* __re
         float v[16];
         tmem_ld16(trow + (uint32_t)c, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const size_t off = (size_t)(c + j) * kDim + m;
-            So[off] = __ldcg(S2 + off) + __ldcg(S1 + off) + v[j];
+        for (int q = 0; q < 4; ++q) {
+            const float4 a = *reinterpret_cast<const float4*>(sm.A + core_off32(m, c + 4 * q));
+            const float s2[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 4 * q + e;
+                const size_t off = (size_t)(c + j) * kDim + m;
+                So[off] = s2[e] + sm.S1f[off] + v[j];
+            }
         }
     }
-    if (tid < kDim) {
-        // S2 b1 from the FP32 row of S2 in the A tile, FP32 accumulation
-        float s = __ldcg(b2 + m) + sm.b1[m];
-#pragma unroll 4
-        for (int kc = 0; kc < kDim; kc += 4) {
-            const float4 a = *reinterpret_cast<const float4*>(sm.A + core_off32(m, kc));
-            s = fmaf(a.x, sm.b1[kc], s);
-            s = fmaf(a.y, sm.b1[kc + 1], s);
-            s = fmaf(a.z, sm.b1[kc + 2], s);
-            s = fmaf(a.w, sm.b1[kc + 3], s);
-        }
-        bo[m] = s;
-    }
+    if (tid < kDim) bo[m] = bvec;
     fence_before();
     __syncthreads();
     return kTcOk;

@@ -38,6 +38,7 @@
 
 #include <algorithm>
 #include <type_traits>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -58,6 +59,8 @@ struct FkParams {
     const double* x0;  // [d]
     double* Xn;        // next iterate [N][d]
     double* r;         // residuals [N][d]
+    float* rf;         // mixed precision: the residuals rounded to FP32 [N][d], the fold's and the
+                       // replay's input (null for the FP64 scan)
     long long N;
     int d;
     int TS;
@@ -123,8 +126,9 @@ __device__ __forceinline__ void fk_reduce_res(unsigned long long my_res, bool my
 
 // ---------------------------------------------------------------------------
 // A0. residual (FP64) and leaf diagonals (working precision), one thread per
-// entry, grid-stride: r_k = x_{k+1} - phi(x_k) (eq. 3.8) into p.r, the
-// diagonal 1 + e of J_k into a_out [N][128] (1 on padding rows), ||r||_inf.
+// entry, grid-stride: r_k = x_{k+1} - phi(x_k) (eq. 3.8) into p.r (and, for
+// the mixed-precision scan, rounded to FP32 into p.rf), the diagonal 1 + e of
+// J_k into a_out [N][128] (1 on padding rows), ||r||_inf.
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __restrict__ a_out) {
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(256) fk_residual_kernel(FkParams p, Real* __re
                 a = fma(-2.0 * p.h, u, p.a0);   // one FP64 instruction, as in the replay
             }
             p.r[k * d + i] = rr;
+            if constexpr (std::is_same<Real, float>::value) p.rf[k * d + i] = d2f_int(rr);
             const unsigned long long b = abs_bits(rr);
             my_res = b > my_res ? b : my_res;
             my_nf |= b >= kInfBitsAbs;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(FoldTraits<Real>::THREADS, 1)
             const long long k = k0 + s;
             a = a_in[k * FD + i];
             if (i < d) {
-                if constexpr (std::is_same<Real, float>::value) rr = d2f_int(p.r[k * d + i]);
+                if constexpr (std::is_same<Real, float>::value) rr = p.rf[k * d + i];
                 else rr = p.r[k * d + i];
             }
         }
@@ -415,8 +420,6 @@ struct CombineArgs {
     unsigned long long load_polls, mma_polls;  // wait bounds of the compose
 };
 
-constexpr size_t kTcSmem = sizeof(tc::ComposeSmem) + 1024;
-
 // Operand precision of the tensor-core composes: BF16 (operands converted,
 // bulk copies for fresh inputs) or TF32 (FP32 aggregates as they stand).
 struct TcBf16 {
@@ -455,11 +458,7 @@ __global__ void __launch_bounds__(256) fk_compose_tc_kernel(CombineArgs a) {
         return;
     }
     if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
-    if (tid == 0) {
-        tc::mbar_init(&sm.mbar, 1);
-        tc::mbar_init(&sm.mbar_ld, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    tc::init_barriers(sm);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -504,11 +503,7 @@ __global__ void __launch_bounds__(256) fk_upsweep_tc_kernel(UpArgs a) {
     const size_t MM = (size_t)FD * FD;
     if (*a.stop) return;
     if (warp == 0) tc::tmem_alloc(&sm.tmem, FD);
-    if (tid == 0) {
-        tc::mbar_init(&sm.mbar, 1);
-        tc::mbar_init(&sm.mbar_ld, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    tc::init_barriers(sm);
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
@@ -620,17 +615,25 @@ __device__ __forceinline__ Real fk_tile_z(const FkParams& p, const Real* __restr
 }
 
 // ---------------------------------------------------------------------------
-// C. replay: one CTA of 128 threads per tile, one row per thread, exact FP64
-// leaves.  Neighbour rows come from the same warp by shuffles and, at the
-// four warps' edges, through shared memory (a slot per step parity and one
-// block barrier per step).  Four warps per tile keep four times as many
-// FP64 instruction streams in flight as one warp per tile would.
+// C. replay: one CTA of 128 threads per tile, one row per thread.  Neighbour
+// rows come from the same warp by shuffles and, at the four warps' edges,
+// through shared memory (a slot per step parity and one block barrier per
+// step).  The recursion runs in the scan's working precision Real: FP64 for
+// the FP64 scan (exact leaves); FP32 for the mixed-precision scans, whose
+// composes already make the Newton step inexact -- there it takes the FP32
+// leaf diagonals and residuals the residual kernel wrote (the fold's inputs),
+// and the FP32 correction is added to the FP64 state exactly (the update
+// stays FP64).  A warp's FP64 instruction holds its FP64 unit for ~70 cycles
+// on this part: the FP64 recursion spends five per entry and step, the FP32
+// one a single addition.
 // ---------------------------------------------------------------------------
 template <typename Real>
 __global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* __restrict__ S,
-                                                       const Real* __restrict__ b) {
+                                                       const Real* __restrict__ b,
+                                                       const Real* __restrict__ a_in) {
     if (*p.stop) return;
-    __shared__ double s_edge[2][2][4];   // [parity][first / last lane][warp]
+    constexpr bool kF32 = std::is_same<Real, float>::value;
+    __shared__ Real s_edge[2][2][4];   // [parity][first / last lane][warp]
     __shared__ Real s_z[FD];
     const int row = threadIdx.x, warp = row >> 5, lane = row & 31;
     const long long t = blockIdx.x;
@@ -639,59 +642,80 @@ __global__ void __launch_bounds__(FD) fk_replay_kernel(FkParams p, const Real* _
     const long long k0 = 1 + t * p.TS;
     const long long k1 = min(p.N, k0 + p.TS);
     unsigned long long my_q = 0ull;
-    const Real zt = fk_tile_z<Real>(p, S, b, t, row, s_z);
-    double z = live ? (double)zt : 0.0;
+    // |dz| beyond the cut bound (or not finite) cuts the step; in FP32 the
+    // bound is at most the largest finite float, so an overflow to
+    // infinity is caught
+    const float capf = (float)fmin(p.cap, (double)FLT_MAX);
+    auto cut = [&](Real v) -> bool {
+        if constexpr (kF32) return !(fabsf(v) <= capf);
+        else return abs_bits(v) > p.cap_bits;
+    };
+    auto to_double = [](Real v) -> double {
+        if constexpr (kF32) return f2d_int(v);
+        else return v;
+    };
+    Real z = fk_tile_z<Real>(p, S, b, t, row, s_z);
+    if (!live) z = (Real)0;
     double xprev = live ? fk_x(p, k0 - 1, row) : 0.0;
     if (t == 0 && live) {
         // element 0: dx_1 = -r_0 (already the incoming vector of tile 0)
-        if (abs_bits(z) > p.cap_bits) my_q = ~0ull;  // ~0 = index 0
-        p.Xn[row] = xprev + z;
+        if (cut(z)) my_q = ~0ull;  // ~0 = index 0
+        p.Xn[row] = xprev + to_double(z);
     }
-    const double m2h = -2.0 * p.h;
+    const Real m2h = (Real)(-2.0 * p.h), a0 = (Real)p.a0, o = (Real)p.o;
     // steps in groups of G: the loads of a group are issued together so their
     // latency overlaps; the recurrence itself is serial in k
     constexpr int G = 4;
     int par = 0;
     for (long long kg = k0; kg < k1; kg += G) {
-        double xc[G], rk[G];
+        double xc[G];
+        Real rk[G], ak[G];
 #pragma unroll
         for (int gq = 0; gq < G; ++gq) {
             const long long k = kg + gq;
             const bool ld = (k < k1) && live;
             xc[gq] = ld ? fk_x(p, k, row) : 0.0;
-            rk[gq] = ld ? p.r[k * d + row] : 0.0;
+            if constexpr (kF32) {
+                rk[gq] = ld ? p.rf[k * d + row] : 0.f;
+                ak[gq] = ld ? a_in[k * FD + row] : 0.f;
+            } else {
+                rk[gq] = ld ? p.r[k * d + row] : 0.0;
+                ak[gq] = 0.0;
+            }
         }
 #pragma unroll
         for (int gq = 0; gq < G; ++gq) {
             const long long k = kg + gq;
             if (k >= k1) break;
-            // dz_{k+1} = J_k dz_k - r_k with J_k = diag(a0 - 2 h x_k) + o (sub + super):
-            // 4 FP64 instructions per entry
+            // dz_{k+1} = J_k dz_k - r_k with J_k = diag(a0 - 2 h x_k) + o (sub + super)
             if (lane == 0) s_edge[par][0][warp] = z;
             if (lane == 31) s_edge[par][1][warp] = z;
             __syncthreads();
-            double up = __shfl_up_sync(0xffffffffu, z, 1);
-            double dn = __shfl_down_sync(0xffffffffu, z, 1);
-            if (lane == 0) up = (warp > 0) ? s_edge[par][1][warp - 1] : 0.0;
-            if (lane == 31) dn = (warp < 3) ? s_edge[par][0][warp + 1] : 0.0;
+            Real up = __shfl_up_sync(0xffffffffu, z, 1);
+            Real dn = __shfl_down_sync(0xffffffffu, z, 1);
+            if (lane == 0) up = (warp > 0) ? s_edge[par][1][warp - 1] : (Real)0;
+            if (lane == 31) dn = (warp < 3) ? s_edge[par][0][warp + 1] : (Real)0;
             par ^= 1;
-            const double a = fma(m2h, xprev, p.a0);
-            const double nz = live ? fma(a, z, fma(p.o, up + dn, -rk[gq])) : 0.0;
+            // leaf diagonal a0 - 2 h x_k (FP64: from the state; FP32: as staged)
+            Real a;
+            if constexpr (kF32) a = ak[gq];
+            else a = fma(m2h, xprev, a0);
+            const Real nz = live ? fma(a, z, fma(o, up + dn, -rk[gq])) : (Real)0;
             z = nz;
             if (live) {
-                if (abs_bits(z) > p.cap_bits) {
+                if (cut(z)) {
                     const unsigned long long e = ~(unsigned long long)k;
                     my_q = e > my_q ? e : my_q;
                 }
-                p.Xn[k * d + row] = xc[gq] + z;
+                p.Xn[k * d + row] = xc[gq] + to_double(z);
             }
             xprev = xc[gq];
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
-        my_q = o > my_q ? o : my_q;
+        const unsigned long long o2 = __shfl_xor_sync(0xffffffffu, my_q, off);
+        my_q = o2 > my_q ? o2 : my_q;
     }
     if (lane == 0 && my_q) atomicMax(p.qenc, my_q);
 }
@@ -819,7 +843,7 @@ int run_iteration(FkParams& p, const Tree& tr, Real* S, Real* b, Real* abuf, boo
     }
     {
         auto tok = timed_begin("fkpp_replay", st);
-        fk_replay_kernel<Real><<<(unsigned)p.T, FD, 0, st>>>(p, S, b);
+        fk_replay_kernel<Real><<<(unsigned)p.T, FD, 0, st>>>(p, S, b, abuf);
         timed_end(tok, st);
         count_launch(1);
     }
@@ -859,7 +883,9 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     double* r = X1 + nd;
     const size_t aggBytes = (size_t)tr.total * FD * FD * sizeof(Real) + (size_t)tr.total * FD * sizeof(Real);
     Real* S = (Real*)workspace(aggBytes, kSlotAux);
-    Real* abuf = (Real*)workspace((size_t)N * FD * sizeof(Real), kSlotAux2);
+    // leaf diagonals [N][128] in the working precision, and for the mixed
+    // scan the FP32 residuals [N][d] after them
+    Real* abuf = (Real*)workspace((size_t)N * FD * sizeof(Real) + (mixed ? nd * sizeof(float) : 0), kSlotAux2);
     if (!S || !abuf) return PITN_ENOMEM;
     Real* b = S + (size_t)tr.total * FD * FD;
     // per-pass slots | up-sweep arrival counters | stop flag and error word
@@ -896,6 +922,7 @@ int fkpp_solve_t(const SolveIO& io, double h, int64_t N, int d, double tol, int 
     FkParams p{};
     p.x0 = io.x0_dev;
     p.r = r;
+    p.rf = mixed ? reinterpret_cast<float*>(abuf + (size_t)N * FD) : nullptr;
     p.N = N;
     p.d = d;
     p.TS = TS;

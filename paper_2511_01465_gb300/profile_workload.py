@@ -8,7 +8,7 @@ Workloads: vdp, lorenz, osc (single IVP; --precision 2 for the FP32 delta
 scan), vdp_rk4 (RK4 van der Pol on [0, 10], h = 10 / N, from the ones
 guess, or from the root with --from-root), robertson (backward Euler from
 the zero guess, h = 500 / N), fkpp,
-fkpp_mixed (d = 128),
+fkpp_mixed, fkpp_tf32 (d = 128; BF16 / TF32 tensor-core composes),
 batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]), adjoint
 (Van der Pol batch forward + backward).  Sizes default to the small cases
 used for full captures; prints the outcome of the last repetition.
@@ -40,7 +40,8 @@ def main():
     import torch
 
     from . import api, workloads as W
-    from .pitn import PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_STEP_BACKWARD_EULER, PITN_STEP_RK4
+    from .pitn import (PITN_PREC_FP64, PITN_PREC_MIXED_BF16, PITN_PREC_MIXED_TF32, PITN_STEP_BACKWARD_EULER,
+                       PITN_STEP_RK4)
 
     out = None
     root = None
@@ -68,9 +69,10 @@ def main():
             wl = W.robertson(h=500.0 / a.N)
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter,
                             guess=np.zeros((wl.N, wl.d)), method=PITN_STEP_BACKWARD_EULER)[1]
-        elif a.workload in ("fkpp", "fkpp_mixed"):
+        elif a.workload in ("fkpp", "fkpp_mixed", "fkpp_tf32"):
             wl = W.fkpp(N=a.N)
-            prec = PITN_PREC_MIXED_BF16 if a.workload == "fkpp_mixed" else PITN_PREC_FP64
+            prec = {"fkpp": PITN_PREC_FP64, "fkpp_mixed": PITN_PREC_MIXED_BF16,
+                    "fkpp_tf32": PITN_PREC_MIXED_TF32}[a.workload]
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, precision=prec)[1]
         elif a.workload == "batch":
             bt = W.lorenz_batch(B=a.B, n_min=a.nmin, n_max=a.nmax)
