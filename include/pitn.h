@@ -96,8 +96,10 @@ enum {
     PITN_PREC_FP64 = 0,        /* every operation in FP64 */
     PITN_PREC_MIXED_BF16 = 1,  /* PITN_FKPP with d >= 64: dense composes of the
                                   scan on tensor cores (BF16 operands, FP32
-                                  accumulation) in the delta form A = J - I;
-                                  an inexact Newton step */
+                                  accumulation) in the delta form A = J - I,
+                                  tile folds and replay in FP32; residual,
+                                  stopping test and update in FP64.  An
+                                  inexact Newton step */
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
                                   Euler: the scan's elements in FP32 delta form
                                   (I + S, c); an inexact Newton step */
