@@ -42,9 +42,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28943938304 + 24171237376, "13d733b96a425115"),        # 147 passes
-    "vdp_ff": (25517492736 + 27637988096, "13d733b96a425115"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13092923392 + 15200302336, "13d733b96a425115"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28952071424 + 24173547008, "75fe57d21d1d8b9f"),        # 147 passes
+    "vdp_ff": (25493814016 + 27627901184, "75fe57d21d1d8b9f"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13094215424 + 15203116800, "75fe57d21d1d8b9f"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
