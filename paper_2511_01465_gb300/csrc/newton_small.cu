@@ -406,9 +406,14 @@ extern "C" int pitn_solve_noalloc(int system_id, const double* params, const dou
     const int block = (int)b;
     int per_sm = 0;
     cudaError_t e = cudaSuccess;
+    // Lorenz-63's kernel takes the CTA-wide scan buffer, as in the workspace-backed solve
+    const size_t dyn = (system_id == PITN_LORENZ63) ? CtaScanLayout<3>::kBytes : 0;
+    if (dyn > 0 && cudaFuncSetAttribute((const void*)newton_small_kernel<Lorenz63>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
+        return PITN_ECUDA;
     switch (system_id) {
     case PITN_LORENZ63:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Lorenz63>, block, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<Lorenz63>, block, dyn);
         break;
     case PITN_VDP:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, newton_small_kernel<VanDerPol>, block, 0);
@@ -461,11 +466,12 @@ extern "C" int pitn_solve_noalloc(int system_id, const double* params, const dou
     a.err = (int*)(ctl + 16);
     a.rec = (SolveRecord*)(ctl + 32);
     a.wait_ns = wait_limits().grid_ns;
+    a.cta_scan = dyn > 0 ? 1 : 0;
     void* args[] = {(void*)&a};
     const void* kern = (system_id == PITN_LORENZ63) ? (const void*)newton_small_kernel<Lorenz63>
                        : (system_id == PITN_VDP)    ? (const void*)newton_small_kernel<VanDerPol>
                                                     : (const void*)newton_small_kernel<LinearOsc>;
-    if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, 0, st) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, dyn, st) != cudaSuccess) {
         cudaGetLastError();
         return PITN_ECUDA;
     }

@@ -47,6 +47,8 @@ struct SmallArgs {
     SolveRecord* rec;
     int stage_rows;                // > 0: rows of the next iterate leave through shared-memory
                                    // tiles and bulk copies (dynamic smem sized by stage_bytes)
+    int cta_scan;                  // d = 3 three-phase kernel: 1 when the launch gave it the
+                                   // CTA-wide scan buffer (dynamic smem, CtaScanLayout<3>::kBytes)
     unsigned long long wait_ns;    // grid-barrier wait limit (0: the default)
     // system constants precomputed on the host for the float-float scan
     // (kernel parameters live in the constant bank, so the compiler reloads
@@ -200,12 +202,71 @@ __device__ __forceinline__ void warp_scan(double* P, double* c, int lane) {
     }
 }
 
+// CTA-wide inclusive Kogge-Stone scan (eq. 3.3) of n <= kCtaScanMax elements
+// held in shared memory, for d = 3.  A warp's FP64 instruction holds its
+// sub-partition's FP64 unit for ~70 cycles on this part, so a level of a
+// scan that one warp runs alone (36 FP64 instructions for a 3 x 3 compose)
+// takes ~2.7 k cycles while the CTA's other sub-partitions idle.  Here each
+// level's composes are dealt out to all threads one output at a time
+// (element l, output o), so every sub-partition's FP64 unit shares the
+// level.  Each output is computed in compose<D>'s order: the results are
+// those of the warp scan.  buf holds two halves of kCtaScanMax elements of
+// EP doubles (E padded to an odd count: 8-byte accesses of consecutive
+// elements without bank conflicts); the elements start in the first half,
+// and the returned pointer is the half that holds the result.
+constexpr int kCtaScanMax = 128;
+template <int D>
+struct CtaScanLayout {
+    static constexpr int E = D * D + D;
+    static constexpr int EP = E | 1;
+    static constexpr size_t kBytes = 2 * (size_t)kCtaScanMax * EP * sizeof(double);
+};
+
+// output o of compose<D>(A, B) (A the later element), in compose<D>'s order
+template <int D>
+__device__ __forceinline__ double compose_out(const double* A, const double* B, int o) {
+    double v;
+    if (o < D * D) {
+        const int i = o / D, j = o - i * D;
+        v = A[i * D] * B[j];
+#pragma unroll
+        for (int k = 1; k < D; ++k) v = fma(A[i * D + k], B[k * D + j], v);
+    } else {
+        const int i = o - D * D;
+        v = A[D * D + i];
+#pragma unroll
+        for (int k = 0; k < D; ++k) v = fma(A[i * D + k], B[D * D + k], v);
+    }
+    return v;
+}
+
+template <int D>
+__device__ __forceinline__ double* cta_scan(double* buf, int n) {
+    constexpr int E = CtaScanLayout<D>::E, EP = CtaScanLayout<D>::EP;
+    double* src = buf;
+    double* dst = buf + kCtaScanMax * EP;
+    for (int off = 1; off < n; off <<= 1) {
+        for (int item = threadIdx.x; item < n * E; item += blockDim.x) {
+            const int l = item / E, o = item - l * E;
+            dst[l * EP + o] = (l >= off) ? compose_out<D>(src + l * EP, src + (l - off) * EP, o) : src[l * EP + o];
+        }
+        __syncthreads();
+        double* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
 // Exclusive block scan of per-thread elements.  On return (eP, ec) is the
 // lane-exclusive prefix within the warp, s_wex[warp] the warp-exclusive
 // prefix, and s_tot the block total.  All in a fixed order.
+// (d = 3 with a scan buffer: the scan over the warps runs CTA-wide, see
+// cta_scan, with the same results.)
 template <int D>
 __device__ __forceinline__ void block_scan(double* P, double* c, double* eP, double* ec,
-                                           double (*s_wex)[D * D + D], double* s_tot) {
+                                           double (*s_wex)[D * D + D], double* s_tot,
+                                           double* scan_buf = nullptr) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     warp_scan<D>(P, c, lane);
 #pragma unroll
@@ -218,6 +279,25 @@ __device__ __forceinline__ void block_scan(double* P, double* c, double* eP, dou
         for (int j = 0; j < D; ++j) ec[j] = 0.0;
     }
     __syncthreads();  // s_wex may still be read from a previous use
+    if (D == 3 && scan_buf != nullptr) {   // (the launchers pass a buffer for d = 3 only)
+        constexpr int E = D * D + D, EP = CtaScanLayout<D>::EP;
+        if (lane == 31) {
+#pragma unroll
+            for (int j = 0; j < D * D; ++j) scan_buf[warp * EP + j] = P[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) scan_buf[warp * EP + D * D + j] = c[j];
+        }
+        __syncthreads();
+        const double* inc = cta_scan<D>(scan_buf, nwarps);
+        // warp-exclusive prefixes (identity for warp 0) and the block total
+        for (int item = threadIdx.x; item < nwarps * E; item += blockDim.x) {
+            const int w = item / E, o = item - w * E;
+            s_wex[w][o] = (w > 0) ? inc[(w - 1) * EP + o] : ((o < D * D && o % (D + 1) == 0) ? 1.0 : 0.0);
+        }
+        if (threadIdx.x < E) s_tot[threadIdx.x] = inc[(nwarps - 1) * EP + threadIdx.x];
+        __syncthreads();
+        return;
+    }
     if (lane == 31) {
 #pragma unroll
         for (int j = 0; j < D * D; ++j) s_wex[warp][j] = P[j];
@@ -331,6 +411,70 @@ __device__ __forceinline__ void cta_incoming(const double* __restrict__ agg, uns
     __syncthreads();
 }
 
+// cta_incoming with its composes dealt out to the whole CTA (d = 3, G <= 64),
+// in the same order and so with the same results: each group's fold onto the
+// identity, aggregate by aggregate; the Kogge-Stone scan of the group
+// aggregates (cta_scan); then the owner of aggregate b - 1 (one thread)
+// applies its group's aggregates up to b - 1 to the group's incoming vector.
+// buf (CtaScanLayout<D>) holds the group aggregates in rows [0, 32) of its
+// halves and the CTA aggregates, read once through L2, in rows [64, 128) of
+// its first half.
+template <int D>
+__device__ __forceinline__ void cta_incoming_wide(const double* __restrict__ agg, unsigned G, double* s_zin,
+                                                  double* buf) {
+    constexpr int E = D * D + D, EP = CtaScanLayout<D>::EP;
+    const unsigned m = (G + 31) / 32;
+    const int ng = (int)((G + m - 1) / m);   // groups that hold aggregates
+    double* g = buf;                          // group aggregates (first half, rows [0, ng))
+    double* t = buf + kCtaScanMax * EP;       // second half: the folds' other buffer
+    double* A = buf + 64 * EP;                // the CTA aggregates (first half, rows [64, 64 + G))
+    for (int item = threadIdx.x; item < (int)G * E; item += blockDim.x) {
+        const int l = item / E, o = item - l * E;
+        A[l * EP + o] = __ldcg(agg + (size_t)l * E + o);
+    }
+    for (int item = threadIdx.x; item < ng * E; item += blockDim.x) {
+        const int o = item % E;
+        g[(item / E) * EP + o] = (o < D * D && o % (D + 1) == 0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (unsigned r = 0; r < m; ++r) {
+        // g_l <- aggregate (l m + r) o g_l, for every group that has one
+        for (int item = threadIdx.x; item < ng * E; item += blockDim.x) {
+            const int l = item / E, o = item - l * E;
+            const unsigned i = (unsigned)l * m + r;
+            t[l * EP + o] = (i < G) ? compose_out<D>(A + i * EP, g + l * EP, o) : g[l * EP + o];
+        }
+        __syncthreads();
+        for (int item = threadIdx.x; item < ng * E; item += blockDim.x) {
+            const int l = item / E, o = item - l * E;
+            g[l * EP + o] = t[l * EP + o];
+        }
+        __syncthreads();
+    }
+    const double* inc = cta_scan<D>(buf, ng);
+    if (threadIdx.x == 0) {
+        double v[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = 0.0;
+        if (blockIdx.x > 0) {
+            const unsigned lo = (blockIdx.x - 1) / m;   // the group that holds aggregate b - 1
+            if (lo > 0) {
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = inc[(lo - 1) * EP + D * D + j];
+            }
+            for (unsigned i = lo * m; i <= blockIdx.x - 1; ++i) {
+                double tv[D];
+                apply<D>(A + i * EP, A + i * EP + D * D, v, tv);
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = tv[j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < D; ++j) s_zin[j] = v[j];
+    }
+    __syncthreads();
+}
+
 // Deterministic three-phase Newton kernel (persistent, cooperative launch).
 // Thread g owns steps [g*chunk, (g+1)*chunk).  Per Newton iteration:
 //   phase 1: residuals + compact Jacobians (stored to scratch), thread fold,
@@ -351,7 +495,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
     __shared__ double s_g[kMaxWarps][E];
     __shared__ double s_gtot[E];
     __shared__ double s_zin[D];
-    extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
+    // row-stage tiles (D == 2, stage_rows > 0); the CTA-wide scan buffer (D == 3, cta_scan)
+    extern __shared__ __align__(16) double s_dyn[];
+    double* const scan_buf = (D == 3 && a.cta_scan) ? s_dyn : nullptr;
 
     const int lane = threadIdx.x & 31;
     const long long N = a.N;
@@ -465,7 +611,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             compose<D>(RP, Rc, P, c, P, c);
         }
         double eP[D * D], ec[D];
-        block_scan<D>(P, c, eP, ec, s_wex, s_tot);
+        block_scan<D>(P, c, eP, ec, s_wex, s_tot, scan_buf);
         if (threadIdx.x < E) a.agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -486,7 +632,9 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
         // ---- incoming prefix of this CTA: fixed-order scan of the aggregates ----
         // (a grid of at most 64 CTAs: warp 0 alone, its serial part stays short;
         // larger grids: every thread takes a share and the CTA scans)
-        if (G <= 64) {
+        if (G <= 64 && scan_buf != nullptr) {
+            cta_incoming_wide<D>(a.agg, G, s_zin, scan_buf);   // d = 3: dealt out to the CTA
+        } else if (G <= 64) {
             cta_incoming<D>(a.agg, G, s_zin);
         } else {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;   // aggregates per thread
@@ -503,7 +651,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                 compose<D>(sP, sc, gP, gc, gP, gc);
             }
             double xP[D * D], xc[D];
-            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot);
+            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot, scan_buf);
             // CTA b needs the prefix through aggregate b-1, held by thread (b-1)/m:
             // its exclusive prefix (warp part, then lane part) applied to the zero
             // vector -- every prefix from aggregate 0 has matrix 0 -- then the
@@ -666,10 +814,13 @@ namespace pitn {
 enum SmallVariant { kVarPlain = 0, kVarMixed = 1, kVarFused = 2, kVarFusedMixed = 3, kVarFusedFF = 4,
                     kVarMixedFF = 5 };
 
-// Dynamic shared memory of a launch: the row-stage tiles for d = 2.
-template <class Sys>
+// Dynamic shared memory of a launch: the row-stage tiles for d = 2; the
+// CTA-wide scan buffer of the three-phase FP64 kernel for d = 3.
+template <class Sys, int VAR>
 static size_t small_dyn_smem(int block) {
-    return Sys::D == 2 ? stage_bytes(block) : 0;
+    if constexpr (Sys::D == 2) return stage_bytes(block);
+    else if constexpr (Sys::D == 3 && VAR == kVarPlain) return CtaScanLayout<3>::kBytes;
+    else return 0;
 }
 
 template <class Sys, int VAR>
@@ -685,12 +836,13 @@ static const void* small_kernel_ptr() {
 template <class Sys, int VAR = kVarPlain>
 static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t st) {
     const void* kern = small_kernel_ptr<Sys, VAR>();
-    const size_t dyn = small_dyn_smem<Sys>(block);
+    const size_t dyn = small_dyn_smem<Sys, VAR>(block);
     if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return cudaErrorInvalidValue;
     // bulk copies need 16 B-aligned rows in both trajectory buffers
     const bool aligned = ((reinterpret_cast<uintptr_t>(a.X0) | reinterpret_cast<uintptr_t>(a.X1)) & 15) == 0;
-    a.stage_rows = (dyn > 0 && aligned) ? kStageT : 0;
+    a.stage_rows = (Sys::D == 2 && dyn > 0 && aligned) ? kStageT : 0;
+    a.cta_scan = (Sys::D == 3 && dyn > 0) ? 1 : 0;
     void* args[] = {(void*)&a};
     auto tok = pitn_host::timed_begin("newton_small", st);
     cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(block), args, dyn, st);
@@ -702,7 +854,7 @@ static cudaError_t launch_small(SmallArgs& a, int grid, int block, cudaStream_t 
 template <class Sys, int VAR = kVarPlain>
 static int max_blocks_per_sm(int block) {
     const void* kern = small_kernel_ptr<Sys, VAR>();
-    const size_t dyn = small_dyn_smem<Sys>(block);
+    const size_t dyn = small_dyn_smem<Sys, VAR>(block);
     if (dyn > 0 && cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return 0;
     int per_sm = 0;
