@@ -42,9 +42,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28952071424 + 24173547008, "75fe57d21d1d8b9f"),        # 147 passes
-    "vdp_ff": (25493814016 + 27627901184, "75fe57d21d1d8b9f"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13094215424 + 15203116800, "75fe57d21d1d8b9f"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28943195136 + 24171944960, "ef49663647be9ab1"),        # 147 passes
+    "vdp_ff": (25514931712 + 27637535744, "ef49663647be9ab1"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13093617152 + 15200926464, "ef49663647be9ab1"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
