@@ -23,6 +23,11 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
     __shared__ T s_g[kMaxWarps][E];
     __shared__ T s_gtot[E];
     __shared__ T s_zin[D];
+    // the fill element (the same for every thread) and each thread's first
+    // updated state per half, kept here rather than in registers through
+    // the pass's step loop
+    __shared__ T s_fill[JN + D];
+    __shared__ double s_first[2 * D][256];
     extern __shared__ __align__(16) double s_dyn[];   // row-stage tiles (D == 2, stage_rows > 0)
 
     const int lane = threadIdx.x & 31;
@@ -201,19 +206,22 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
             Pol::template apply<D>(QA, cA, zA, zB);
         }
         const long long sfill = (q < N) ? (q > 1 ? q : 1LL) : N;
-        T svf[JN], rff[D];
-        if (sfill < k1 && k0 < k1) {
+        if (sfill < N && threadIdx.x == 0) {
             double xf[D], rf64[D];
+            T svf[JN];
             load_state<D>(Xc, a.x0, q - 1, q, xf);
             Pol::eval(sys, xf, xf, rf64, svf);
 #pragma unroll
-            for (int j = 0; j < D; ++j) rff[j] = Pol::from_double(rf64[j]);
+            for (int j = 0; j < JN; ++j) s_fill[j] = svf[j];
+#pragma unroll
+            for (int j = 0; j < D; ++j) s_fill[JN + j] = Pol::from_double(rf64[j]);
         }
+        __syncthreads();
         T NA[D * D], nA[D], NB[D * D], nB[D];
         Pol::template ident<D>(NA, nA);
         Pol::template ident<D>(NB, nB);
         unsigned long long resA = 0ull, resB = 0ull;
-        double prevA[D], prevB[D], firstA[D], firstB[D];
+        double prevA[D], prevB[D];
         long long cutA = N, cutB = N;
         const bool staged = (D == 2) && a.stage_rows > 0;
         RowStage stg;
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
 #pragma unroll
             for (int j = 0; j < D; ++j) Xn[k * D + j] = v[j];
         };
-        auto step = [&](int ch, long long k, long long s, T* z, double* prev, double* first, T* NQ,
+        auto step = [&](int ch, long long k, long long s, T* z, double* prev, T* NQ,
                         T* nc, long long& cut, unsigned long long& res) {
             T sv[JN], r[D];
             if (k < sfill) {
@@ -235,9 +243,9 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
                 for (int j = 0; j < D; ++j) r[j] = scr[sidx(k, JN + j)];
             } else {
 #pragma unroll
-                for (int j = 0; j < JN; ++j) sv[j] = svf[j];
+                for (int j = 0; j < JN; ++j) sv[j] = s_fill[j];
 #pragma unroll
-                for (int j = 0; j < D; ++j) r[j] = rff[j];
+                for (int j = 0; j < D; ++j) r[j] = s_fill[JN + j];
             }
             double x[D];
             load_state<D>(Xc, a.x0, k, q, x);
@@ -262,7 +270,7 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
             if (k > s) fold_elem(k, prev, xn, NQ, nc, res);
             else {
 #pragma unroll
-                for (int j = 0; j < D; ++j) first[j] = xn[j];
+                for (int j = 0; j < D; ++j) s_first[ch * D + j][threadIdx.x] = xn[j];
             }
 #pragma unroll
             for (int j = 0; j < D; ++j) prev[j] = xn[j];
@@ -270,8 +278,8 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
         };
         bool liveA = LA > 0, liveB = LB > 0;
         for (long long i = 0; i < LA && liveA; ++i) {
-            liveA = step(0, k0 + i, k0, zA, prevA, firstA, NA, nA, cutA, resA);
-            if (liveB && i < LB) liveB = step(1, km + i, km, zB, prevB, firstB, NB, nB, cutB, resB);
+            liveA = step(0, k0 + i, k0, zA, prevA, NA, nA, cutA, resA);
+            if (liveB && i < LB) liveB = step(1, km + i, km, zB, prevB, NB, nB, cutB, resB);
         }
         if (cutA < N) {
             cutB = N;
@@ -282,6 +290,9 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
         if (LB > 0 && kc > km) {
             T EQ[D * D], Ec[D];
             Pol::template ident<D>(EQ, Ec);
+            double firstB[D];
+#pragma unroll
+            for (int j = 0; j < D; ++j) firstB[j] = s_first[D + j][threadIdx.x];
             fold_elem(km, prevA, firstB, EQ, Ec, resB);
             Pol::template compose<D>(NB, nB, EQ, Ec, NB, nB);
         }
@@ -310,7 +321,7 @@ __global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kerne
                 load_state<D>(Xn, a.x0, k0 - 1, qn, xp);
                 if (k0 < qn) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) xc0[j] = firstA[j];
+                    for (int j = 0; j < D; ++j) xc0[j] = s_first[j][threadIdx.x];
                 } else {
                     load_state<D>(Xn, a.x0, k0, qn, xc0);
                 }
