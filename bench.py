@@ -42,9 +42,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28943195136 + 24171944960, "ef49663647be9ab1"),        # 147 passes
-    "vdp_ff": (25514931712 + 27637535744, "ef49663647be9ab1"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13093617152 + 15200926464, "ef49663647be9ab1"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28952843776 + 24174319616, "2d2f8dc84fdaca9d"),        # 147 passes
+    "vdp_ff": (25450576640 + 27273824000, "2d2f8dc84fdaca9d"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13104614400 + 15208973056, "2d2f8dc84fdaca9d"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
