@@ -263,12 +263,14 @@ __device__ __forceinline__ double* cta_scan(double* buf, int n) {
 // prefix, and s_tot the block total.  All in a fixed order.
 // (d = 3 with a scan buffer: the scan over the warps runs CTA-wide, see
 // cta_scan, with the same results.)
+// live_warps: warps from live_warps on hold identities only and skip their
+// warp scan (which would leave the identities unchanged).
 template <int D>
 __device__ __forceinline__ void block_scan(double* P, double* c, double* eP, double* ec,
                                            double (*s_wex)[D * D + D], double* s_tot,
-                                           double* scan_buf = nullptr) {
+                                           double* scan_buf = nullptr, int live_warps = kMaxWarps) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    warp_scan<D>(P, c, lane);
+    if (warp < live_warps) warp_scan<D>(P, c, lane);
 #pragma unroll
     for (int j = 0; j < D * D; ++j) eP[j] = __shfl_up_sync(0xffffffffu, P[j], 1);
 #pragma unroll
@@ -638,11 +640,16 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
             cta_incoming<D>(a.agg, G, s_zin);
         } else {
             const unsigned m = (G + blockDim.x - 1) / blockDim.x;   // aggregates per thread
+            // only aggregates 0 .. b-1 reach CTA b's prefix: later groups stay
+            // the identity and warps holding none of them skip their scan
+            // (the prefixes this CTA reads are the same)
+            const unsigned need = blockIdx.x;
+            const int live_warps = (int)(((need + m - 1) / m + 31) / 32);
             double gP[D * D], gc[D];
             mat_identity<D>(gP);
 #pragma unroll
             for (int j = 0; j < D; ++j) gc[j] = 0.0;
-            for (unsigned i = threadIdx.x * m; i < min(G, (threadIdx.x + 1) * m); ++i) {
+            for (unsigned i = threadIdx.x * m; i < min(need, (threadIdx.x + 1) * m); ++i) {
                 double sP[D * D], sc[D];
 #pragma unroll
                 for (int j = 0; j < D * D; ++j) sP[j] = __ldcg(a.agg + (size_t)i * E + j);
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(256) newton_small_kernel(SmallArgs a) {
                 compose<D>(sP, sc, gP, gc, gP, gc);
             }
             double xP[D * D], xc[D];
-            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot, scan_buf);
+            block_scan<D>(gP, gc, xP, xc, s_g, s_gtot, scan_buf, live_warps);
             // CTA b needs the prefix through aggregate b-1, held by thread (b-1)/m:
             // its exclusive prefix (warp part, then lane part) applied to the zero
             // vector -- every prefix from aggregate 0 has matrix 0 -- then the
