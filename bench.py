@@ -678,9 +678,10 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / nk for k, v in ktimes.items()}}
-    if args.workload == "vdp" and not args.no_companions:
+    if args.workload == "vdp" and not args.no_companions and world == 1:
         # the metric's comparison: reduced-precision scans and batching against
-        # the plain FP64 solver, same tolerance, timed after the FP64 line
+        # the plain FP64 solver, same tolerance, timed after the FP64 line (on
+        # one GPU: with several, the replicas' line carries no comparison)
         line["mixed"] = {
             "fp32_scan": companion_single(args, "vdp_mixed", dev, stream, flush, value, traj),
             "float_float_scan": companion_single(args, "vdp_ff", dev, stream, flush, value, traj),
