@@ -42,9 +42,9 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28952843776 + 24174319616, "2d2f8dc84fdaca9d"),        # 147 passes
-    "vdp_ff": (25450576640 + 27273824000, "2d2f8dc84fdaca9d"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13104614400 + 15208973056, "2d2f8dc84fdaca9d"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28941035264 + 24169681408, "bb76b2b48a7d82ec"),        # 147 passes
+    "vdp_ff": (25447224576 + 27272660480, "bb76b2b48a7d82ec"),     # 151 passes (fused float-float kernel)
+    "vdp_mixed": (13103398656 + 15208973056, "bb76b2b48a7d82ec"),  # 137 passes (fused FP32-scan kernel)
 }
 
 
