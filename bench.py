@@ -126,7 +126,11 @@ FP64_OPS = {"vdp": (20.0, 6.0)}
 # one pass per Newton iteration): the van der Pol residual (7 instructions,
 # 11 flops) and the update (FP32 scan: 2 DADD; float-float: 4 DADD)
 REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed": (13.0, 20.0),
-                "lorenz_ff": (20.0, 23.0)}
+                "lorenz_ff": (20.0, 23.0),
+                # RK4 van der Pol, float-float Jacobian chain: the FP64 residual (four
+                # right-hand sides 4 x 3, stage states 6, weighted sums 8, residual 4,
+                # h/2 1) and the update (4 DADD)
+                "vdp_rk4_ff": (35.0, 57.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -154,6 +158,12 @@ def workload(name):
                     guess=1.0,
                     desc="van_der_pol mu=1 x0=(0,1) on [0,10], classical RK4 h=1e-5 N=1e6, plain Newton "
                          "from the ones guess (Sec. 4.1)")
+    if name == "vdp_rk4_ff":
+        return dict(kind="single", wl=W.vdp_paper(h=1e-5), tol=1e-8, max_iter=50, guard_B=0.0, method=1,
+                    guess=1.0, precision=3,
+                    desc="van_der_pol mu=1 x0=(0,1) on [0,10], classical RK4 h=1e-5 N=1e6, plain Newton "
+                         "from the ones guess (Sec. 4.1), Jacobian chain and scan in double-FP32 "
+                         "(float-float), FP64 residual and update")
     if name == "vdp_mixed":
         return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=2,
                     desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
@@ -928,7 +938,8 @@ def oracle_passes(name, fallback):
            "lorenz": "lorenz_8192_guard100_tol1e-8_it100",
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "fkpp_tf32": "fkpp_d128_2^15_plain_tol1e-8_it50",
-           "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50"}
+           "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50",
+           "vdp_rk4_ff": "vdp_rk4_1e6_ones_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     try:
         with open(p) as f:
@@ -958,7 +969,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6, "lorenz_ff": 62,
-                "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7}
+                "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7, "vdp_rk4_ff": 7}
 
 
 def cpu_baseline_batch(spec, n_ivps=96):

@@ -103,9 +103,10 @@ enum {
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
                                   Euler: the scan's elements in FP32 delta form
                                   (I + S, c); an inexact Newton step */
-    PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63), explicit Euler
-                                  (not in the paper): the scan (Jacobians, folds,
-                                  carries, replay) in double-FP32 "float-float"
+    PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63) with explicit
+                                  Euler, and VDP with RK4 (not in the paper): the
+                                  scan (Jacobians -- for RK4 the stage chain rule --,
+                                  folds, carries, replay) in double-FP32 "float-float"
                                   arithmetic, ~2^-47 relative, on the FP32 pipe;
                                   residual, stopping test and update in FP64.  An
                                   inexact Newton step whose error is ~64x FP64

@@ -11,7 +11,7 @@
 namespace pitn {
 
 template <class Sys, class Pol>
-__global__ void __launch_bounds__(256, Pol::kMinBlocks) newton_fused_mixed_kernel(SmallArgs a) {
+__global__ void __launch_bounds__(256, Pol::template min_blocks<Sys>()) newton_fused_mixed_kernel(SmallArgs a) {
     using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
     Sys sys;

@@ -60,6 +60,12 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
     if (precision == PITN_PREC_FP64_FF) {
         // the float-float scan runs fused, like the FP32 one: its FP64 work
         // is the residual and the update
+        if (method == PITN_STEP_RK4) {
+            // the RK4 map's stage chain rule in float-float, its residual in FP64
+            if (system_id != PITN_VDP) return PITN_EUNSUPPORTED;
+            *K = small_kernel_of<RK4Map<VdpRhs>, kVarFusedFF>();
+            return PITN_OK;
+        }
         if (method != PITN_STEP_EULER) return PITN_EUNSUPPORTED;
         switch (system_id) {
         case PITN_VDP: *K = small_kernel_of<VanDerPol, kVarFusedFF>(); return PITN_OK;

@@ -18,6 +18,8 @@ namespace pitn {
 struct ScanF32 {
     using T = float;
     static constexpr int kMinBlocks = 0;   // no occupancy request: the compiler's own register choice
+    template <class Sys>
+    static constexpr int min_blocks() { return 0; }
     static constexpr bool kRollScans = false;
     template <int D>
     static __device__ __forceinline__ void ident(T* Q, T* c) { dz_zero<D>(Q, c); }
@@ -84,6 +86,10 @@ struct ScanF32 {
 struct ScanFF {
     using T = ff;
     static constexpr int kMinBlocks = 2;   // 128 registers: two 256-thread CTAs per SM
+    // (a dense Jacobian -- the RK4 map's chain rule -- needs more registers
+    // than two CTAs per SM leave: one CTA per SM there)
+    template <class Sys>
+    static constexpr int min_blocks() { return Sys::JN > Sys::D ? 1 : kMinBlocks; }
     // A float-float compose of 3 x 3 elements is ~400 instructions; for
     // d >= 3 the scans' levels run as loops, so that the kernel's code stays
     // within the instruction caches (unrolled, the d = 3 kernel's warps

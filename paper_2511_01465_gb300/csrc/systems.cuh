@@ -478,6 +478,20 @@ struct VdpRhs {
         Ko[2] = fma(J[3], Y[2], J[2] * Y[0]);
         Ko[3] = fma(J[3], Y[3], J[2] * Y[1]);
     }
+    // float-float: the constants the Jacobian needs, (mu, -2 mu)
+    static void ff_params(const double* p, double* c) {
+        c[0] = p[0];
+        c[1] = -2.0 * p[0];
+    }
+    // Jf(y) Y in float-float, a = -2 mu y0 y1 - 1, b = mu (1 - y0^2); rc = (mu, -2 mu)
+    __device__ __forceinline__ void jf_times_ff(const ff* y, const ff* Y, ff* Ko, const ff* rc) const {
+        const ff a = ff_sub(ff_mul(ff_mul(rc[1], y[0]), y[1]), ff_one());
+        const ff b = ff_mul(rc[0], ff_sub(ff_one(), ff_mul(y[0], y[0])));
+        Ko[0] = Y[2];
+        Ko[1] = Y[3];
+        Ko[2] = ff_fma(b, Y[2], ff_mul(a, Y[0]));
+        Ko[3] = ff_fma(b, Y[3], ff_mul(a, Y[1]));
+    }
 };
 
 template <class Rhs>
@@ -527,6 +541,115 @@ struct RK4Map {
 #pragma unroll
         for (int i = 0; i < D * D; ++i) J[i] = jv[i];
     }
+
+    // ---- float-float scan (PITN_PREC_FP64_FF; right-hand sides with
+    // ff_params and jf_times_ff) ----
+    // The residual is the FP64 one above, operation for operation; the
+    // stage chain rule of the Jacobian runs in float-float from the FP64
+    // stage states.  Constants split on the host: (h, h/2, h/6) and the
+    // right-hand side's two.
+    ff h_ff, hh_ff, h6_ff, rc_ff[2];
+    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+        double rc[2];
+        Rhs::ff_params(p, rc);
+        const double c[5] = {hh, 0.5 * hh, hh / 6.0, rc[0], rc[1]};
+        for (int i = 0; i < 5; ++i) {
+            const ff v = ff_const(c[i]);
+            fc[2 * i] = v.hi;
+            fc[2 * i + 1] = v.lo;
+        }
+        (void)dc;
+    }
+    __device__ __forceinline__ void init_ff(const float* fc, const double*) {
+        h_ff = ff{fc[0], fc[1]};
+        hh_ff = ff{fc[2], fc[3]};
+        h6_ff = ff{fc[4], fc[5]};
+        rc_ff[0] = ff{fc[6], fc[7]};
+        rc_ff[1] = ff{fc[8], fc[9]};
+    }
+    // r = xc - phi(xp) in FP64; jv = dphi/dx(xp) in float-float (dense, row-major)
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        double k[D], ksum[D], y[D];
+        ff yf[D], Y[D * D], K[D * D], Ks[D * D];
+        const double a[4] = {0.0, 0.5, 0.5, 1.0};
+        const double w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        rhs.f(xp, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            ksum[i] = w[0] * k[i];
+            yf[i] = ff_from_double(xp[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) Y[i] = (i % (D + 1) == 0) ? ff_one() : ff_zero();
+        rhs.jf_times_ff(yf, Y, K, rc_ff);   // K_1 = Jf(x)
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) Ks[i] = K[i];
+#pragma unroll
+        for (int s = 1; s < 4; ++s) {
+            const double ha = h * a[s];
+            const ff hs = (s == 3) ? h_ff : hh_ff;
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = fma(ha, k[i], xp[i]);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) Y[i] = (i % (D + 1) == 0) ? ff_fma(hs, K[i], ff_one()) : ff_mul(hs, K[i]);
+            rhs.f(y, k);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                ksum[i] = fma(w[s], k[i], ksum[i]);
+                yf[i] = ff_from_double(y[i]);
+            }
+            rhs.jf_times_ff(yf, Y, K, rc_ff);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) {
+                const ff kk = (s == 3) ? K[i] : ff{2.f * K[i].hi, 2.f * K[i].lo};   // 2 K: exact
+                Ks[i] = ff_add(Ks[i], kk);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) res[i] = xc[i] - (xp[i] + h * ksum[i]);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) jv[i] = (i % (D + 1) == 0) ? ff_fma(h6_ff, Ks[i], ff_one()) : ff_mul(h6_ff, Ks[i]);
+    }
+    // (P, c) <- (J, -r) o (P, c), eq. 3.3
+    __device__ __forceinline__ void leaf_ff(const ff* jv, const ff* r, ff* Pm, ff* c) const {
+        ff tP[D * D], tc[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                ff sacc = ff_mul(jv[i * D], Pm[j]);
+#pragma unroll
+                for (int l = 1; l < D; ++l) sacc = ff_fma(jv[i * D + l], Pm[l * D + j], sacc);
+                tP[i * D + j] = sacc;
+            }
+            ff sacc = ff_neg(r[i]);
+#pragma unroll
+            for (int l = 0; l < D; ++l) sacc = ff_fma(jv[i * D + l], c[l], sacc);
+            tc[i] = sacc;
+        }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) Pm[i] = tP[i];
+#pragma unroll
+        for (int i = 0; i < D; ++i) c[i] = tc[i];
+    }
+    // z <- J z - r
+    __device__ __forceinline__ void replay_ff(const ff* jv, const ff* r, ff* z) const {
+        ff t[D];
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            ff sacc = ff_neg(r[i]);
+#pragma unroll
+            for (int l = 0; l < D; ++l) sacc = ff_fma(jv[i * D + l], z[l], sacc);
+            t[i] = sacc;
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) z[i] = t[i];
+    }
+    __device__ __forceinline__ void jfull_ff(const ff* jv, ff* J) const {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) J[i] = jv[i];
+    }
+
     __device__ __forceinline__ void jmul(const double* jv, const double* M, double* o) const {
 #pragma unroll
         for (int i = 0; i < D; ++i)

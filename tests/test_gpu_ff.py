@@ -166,3 +166,57 @@ def test_ff_rejects_other_systems(pk):
     wl = W.robertson(h=1e-3)
     with pytest.raises(P.PitnError):
         pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 5, precision=P.PITN_PREC_FP64_FF)
+
+
+# ---------------------------------------------------------------------------
+# The RK4 map (eq. 2.3) with the float-float scan: the stage chain rule of
+# the Jacobian in float-float, the residual the FP64 one.  The paper's
+# printed Sec. 4.1 trace for van der Pol, counts equal to the oracle's on
+# ragged sizes (plain Newton from the ones guess, rounding-robust), the root
+# to 1e-10, and the bench workload's outcome.
+# ---------------------------------------------------------------------------
+RK4_GOLD = os.path.join(HERE, "golden", "paper_residual_traces.json")
+
+
+def test_ff_rk4_reproduces_paper_trace(pk):
+    with open(RK4_GOLD) as f:
+        g = json.load(f)["van_der_pol"]
+    N, d = g["N"], len(g["x0"])
+    traj, info = pk.solve(2, g["params"], g["x0"], g["h"], N, 2e-14, 30, guess=np.full((N, d), g["guess"]),
+                          history=True, method=pk.PITN_STEP_RK4, precision=pk.PITN_PREC_FP64_FF)
+    paper = np.array(g["residuals"])
+    assert info["status"] == pk.PITN_OK
+    assert info["iters"] + 1 == g["K"] == len(paper)
+    for k, (a, b) in enumerate(zip(info["res_history"], paper)):
+        assert abs(a - b) <= 1e-8 * abs(b) + 1e-15, (k, a, b)
+
+
+@pytest.mark.parametrize("N", [1, 7, 1000, 20001])
+def test_ff_rk4_against_oracle(pk, N):
+    with open(RK4_GOLD) as f:
+        g = json.load(f)["van_der_pol"]
+    d = len(g["x0"])
+    guess = np.full((N, d), g["guess"])
+    traj, info = pk.solve(2, g["params"], g["x0"], g["h"], N, 1e-12, 40, history=True, guess=guess,
+                          method=pk.PITN_STEP_RK4, precision=pk.PITN_PREC_FP64_FF)
+    o = O.newton(2, g["params"], g["x0"], g["h"], N, 1e-12, 40, method=O.RK4, guess=guess)
+    assert (info["iters"], info["status"]) == (o["iters"], o["status"])
+    np.testing.assert_allclose(info["res_history"], o["res_hist"], rtol=1e-6, atol=1e-13)
+    assert relerr(traj.cpu().numpy(), o["traj"]) <= TOL_REL
+
+
+def test_ff_rk4_bench_size(pk):
+    """The RK4 bench workload (Sec. 4.1's van der Pol on [0, 10], h = 1e-5,
+    N = 1e6, guess ones, tol 1e-8): count and status equal the oracle's stored
+    outcome, residual history within 1e-6, the returned trajectory passing the
+    oracle's residual test."""
+    with open(os.path.join(HERE, "golden", "oracle_full_size.json")) as f:
+        gold = json.load(f)["vdp_rk4_1e6_ones_tol1e-8_it50"]
+    wl = W.vdp_paper(h=1e-5)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, gold["tol"], gold["max_iter"],
+                          guess=np.full((wl.N, wl.d), gold["guess"]), history=True,
+                          method=pk.PITN_STEP_RK4, precision=pk.PITN_PREC_FP64_FF)
+    assert (info["iters"], info["status"]) == (gold["iters"], gold["status"])
+    np.testing.assert_allclose(info["res_history"][:-1], gold["res_history"][:-1], rtol=1e-6, atol=1e-15)
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, traj.cpu().numpy(), method=O.RK4)
+    assert not nf and res <= gold["tol"]
