@@ -15,6 +15,7 @@ total over ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import datetime
 import hashlib
 import json
 import os
@@ -130,7 +131,9 @@ REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed"
                 # RK4 van der Pol, float-float Jacobian chain: the FP64 residual (four
                 # right-hand sides 4 x 3, stage states 6, weighted sums 8, residual 4,
                 # h/2 1) and the update (4 DADD)
-                "vdp_rk4_ff": (35.0, 57.0)}
+                "vdp_rk4_ff": (35.0, 57.0),
+                # the same residual with the FP32 scan's update (2 DADD)
+                "vdp_rk4_mixed": (33.0, 55.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -164,6 +167,12 @@ def workload(name):
                     desc="van_der_pol mu=1 x0=(0,1) on [0,10], classical RK4 h=1e-5 N=1e6, plain Newton "
                          "from the ones guess (Sec. 4.1), Jacobian chain and scan in double-FP32 "
                          "(float-float), FP64 residual and update")
+    if name == "vdp_rk4_mixed":
+        return dict(kind="single", wl=W.vdp_paper(h=1e-5), tol=1e-8, max_iter=50, guard_B=0.0, method=1,
+                    guess=1.0, precision=2,
+                    desc="van_der_pol mu=1 x0=(0,1) on [0,10], classical RK4 h=1e-5 N=1e6, plain Newton "
+                         "from the ones guess (Sec. 4.1), Jacobian chain and scan in FP32 delta form "
+                         "(inexact Newton), FP64 residual and update")
     if name == "vdp_mixed":
         return dict(kind="single", wl=W.vdp(), tol=1e-8, max_iter=400, guard_B=100.0, precision=2,
                     desc="van_der_pol mu=1 x0=(2,0) explicit Euler h=1e-4 N=2^22, guarded Newton B=100, "
@@ -214,7 +223,12 @@ def workload(name):
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi sampling every 200 ms from before the warm-up steps to the
+    end of the timed region.  The median SM clock and the throttle reasons
+    are those of the samples stamped inside the timed region; a timed region
+    shorter than the sampling interval may hold none, and then the samples
+    of the warm-up steps and the timed region are reported, marked so."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -223,6 +237,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.t_timed = None
 
     def start(self):
         try:
@@ -236,6 +251,10 @@ class ClockSampler:
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
 
+    def timed(self):
+        """Marks the start of the timed region."""
+        self.t_timed = datetime.datetime.now()
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
@@ -243,6 +262,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return None
+        t_end = datetime.datetime.now()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -250,29 +270,44 @@ class ClockSampler:
             self.proc.kill()
         if self.t:
             self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        run, timed = [], []
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                smp = (float(f[2]), float(f[3]), {n for n, v in zip(names, f[6:10]) if v.lower() == "active"})
             except ValueError:
                 continue
-            for n, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+            if ts > t_end:
+                continue
+            run.append(smp)
+            if self.t_timed is not None and ts >= self.t_timed:
+                timed.append(smp)
+        use = timed or run
+        if not use:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(x[0] for x in use), "sm_max_mhz": max(x[1] for x in use),
+                "reasons": sorted(set().union(*(x[2] for x in use))), "samples": len(use),
+                "window": "timed region" if timed else
+                          "warm-up and timed region (no sample fell inside the shorter timed region)"}
 
 
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def gpu_uuid(dev, local_rank):
+    """The nvidia-smi id of a torch device (its UUID; the local rank if the
+    UUID is not available)."""
+    import torch
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return str(local_rank)
+
+
 def batch_kernel_name(shape):
     """The batch solver's timed kernel for a (threads per CTA, steps per
     thread) launch shape: steps per thread 0 is the per-IVP path."""
@@ -311,6 +346,8 @@ def run_ours_batch(args, rank, world, local_rank, spec):
                                 traj, offs, iters, status, res, opt)
         P.check(rc, "pitn_solve_batch")
 
+    clocks = ClockSampler(gpu_uuid(dev, local_rank))
+    clocks.start()
     P.pitn_tune_enable(not args.no_tune)
     for _ in range(args.warmup):
         solve_once()
@@ -318,12 +355,7 @@ def run_ours_batch(args, rank, world, local_rank, spec):
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local_rank)
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
+    clocks.timed()
     launches0 = pk.pitn_launch_count()
     times = []
     for _ in range(args.steps):
@@ -460,6 +492,8 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
         P.check(P.pitn_backward(bt.system, bt.B, params, x0, h, N, d, traj, None, gN, 1024, gx0, gp, opt),
                 "pitn_backward")
 
+    clocks = ClockSampler(gpu_uuid(dev, local_rank))
+    clocks.start()
     P.pitn_tune_enable(not args.no_tune)
     for _ in range(args.warmup):
         step()
@@ -467,12 +501,7 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local_rank)
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
+    clocks.timed()
     launches0 = pk.pitn_launch_count()
     times = []
     for _ in range(args.steps):
@@ -586,6 +615,8 @@ def run_ours(args, rank, world, local_rank):
         P.check(rc, "pitn_solve_ex")
         return rc, res
 
+    clocks = ClockSampler(gpu_uuid(dev, local_rank))
+    clocks.start()
     P.pitn_tune_enable(not args.no_tune)  # the first warm-up solve picks the launch shape
     for _ in range(args.warmup):
         rc, res = solve_once()
@@ -594,12 +625,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
 
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local_rank)
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
+    clocks.timed()
     launches0 = pk.pitn_launch_count()
     times = []
     for _ in range(args.steps):
@@ -939,7 +965,7 @@ def oracle_passes(name, fallback):
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "fkpp_tf32": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50",
-           "vdp_rk4_ff": "vdp_rk4_1e6_ones_tol1e-8_it50"}
+           "vdp_rk4_ff": "vdp_rk4_1e6_ones_tol1e-8_it50", "vdp_rk4_mixed": "vdp_rk4_1e6_ones_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
     try:
         with open(p) as f:
@@ -969,7 +995,8 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6, "lorenz_ff": 62,
-                "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7, "vdp_rk4_ff": 7}
+                "lorenz_mixed": 62, "robertson": 9, "vdp_rk4": 7, "vdp_rk4_ff": 7,
+                "vdp_rk4_mixed": 7}
 
 
 def cpu_baseline_batch(spec, n_ivps=96):

@@ -100,9 +100,11 @@ enum {
                                   tile folds and replay in FP32; residual,
                                   stopping test and update in FP64.  An
                                   inexact Newton step */
-    PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC), explicit
-                                  Euler: the scan's elements in FP32 delta form
-                                  (I + S, c); an inexact Newton step */
+    PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC) with explicit
+                                  Euler, and VDP with RK4 (not in the paper; the
+                                  stage chain rule of S in FP32 from the FP64
+                                  stage states): the scan's elements in FP32
+                                  delta form (I + S, c); an inexact Newton step */
     PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63) with explicit
                                   Euler, and VDP with RK4 (not in the paper): the
                                   scan (Jacobians -- for RK4 the stage chain rule --,

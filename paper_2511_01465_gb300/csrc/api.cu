@@ -374,8 +374,9 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
         return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_FP32 &&
-        ((system_id != PITN_LORENZ63 && system_id != PITN_VDP && system_id != PITN_LINEAR_OSC) ||
-         o.method != PITN_STEP_EULER))
+        !(((system_id == PITN_LORENZ63 || system_id == PITN_VDP || system_id == PITN_LINEAR_OSC) &&
+           o.method == PITN_STEP_EULER) ||
+          (system_id == PITN_VDP && o.method == PITN_STEP_RK4)))
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
     if (o.method < PITN_STEP_EULER || o.method > PITN_STEP_TRAPEZOID) return PITN_EINVAL;

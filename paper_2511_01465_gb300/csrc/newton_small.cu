@@ -75,6 +75,12 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
         default: return PITN_EUNSUPPORTED;
         }
     }
+    if (precision == PITN_PREC_MIXED_FP32 && method == PITN_STEP_RK4) {
+        // the RK4 map's stage chain rule in FP32 (delta form), its residual in FP64
+        if (system_id != PITN_VDP) return PITN_EUNSUPPORTED;
+        *K = small_kernel_of<RK4Map<VdpRhs>, kVarFusedMixed>();
+        return PITN_OK;
+    }
     if (precision == PITN_PREC_MIXED_FP32) {
         // the d = 2 FP32-scan solves run fused: their FP64 work (residual,
         // update) is light enough that one pass per iteration beats two (van

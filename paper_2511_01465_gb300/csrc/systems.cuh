@@ -25,6 +25,8 @@
 // element of the scan costs D + JN registers instead of D + D*D.
 #pragma once
 
+#include <type_traits>
+
 #include "ffarith.cuh"
 #include "fpconv.cuh"
 
@@ -478,10 +480,22 @@ struct VdpRhs {
         Ko[2] = fma(J[3], Y[2], J[2] * Y[0]);
         Ko[3] = fma(J[3], Y[3], J[2] * Y[1]);
     }
+    // reduced-precision Jacobian chains of the RK4 map (RK4Map::eval_mixed,
+    // eval_ff) are provided
+    static constexpr bool kReducedJacobian = true;
     // float-float: the constants the Jacobian needs, (mu, -2 mu)
-    static void ff_params(const double* p, double* c) {
+    __host__ __device__ static void ff_params(const double* p, double* c) {
         c[0] = p[0];
         c[1] = -2.0 * p[0];
+    }
+    // Jf(y) Y in FP32 (the mixed scan), a = -2 mu y0 y1 - 1, b = mu (1 - y0^2); rc = (mu, -2 mu)
+    __device__ __forceinline__ void jf_times_f32(const float* y, const float* Y, float* Ko, const float* rc) const {
+        const float a = fmaf(rc[1] * y[0], y[1], -1.f);
+        const float b = rc[0] * fmaf(-y[0], y[0], 1.f);
+        Ko[0] = Y[2];
+        Ko[1] = Y[3];
+        Ko[2] = fmaf(b, Y[2], a * Y[0]);
+        Ko[3] = fmaf(b, Y[3], a * Y[1]);
     }
     // Jf(y) Y in float-float, a = -2 mu y0 y1 - 1, b = mu (1 - y0^2); rc = (mu, -2 mu)
     __device__ __forceinline__ void jf_times_ff(const ff* y, const ff* Y, ff* Ko, const ff* rc) const {
@@ -494,14 +508,38 @@ struct VdpRhs {
     }
 };
 
+// Whether a right-hand side provides the reduced-precision Jacobian products
+// (jf_times_f32, jf_times_ff, ff_params) that the FP32 and float-float RK4
+// chains use: true only where the type says so.
+template <class Rhs, class = void>
+struct has_reduced_jacobian { static constexpr bool value = false; };
+template <class Rhs>
+struct has_reduced_jacobian<Rhs, std::void_t<decltype(Rhs::kReducedJacobian)>> {
+    static constexpr bool value = Rhs::kReducedJacobian;
+};
+
 template <class Rhs>
 struct RK4Map {
     static constexpr int D = Rhs::D, JN = D * D, P = Rhs::P;
     Rhs rhs;
     double h;
+    // constants of the reduced-precision Jacobian chains (see below): h, h/2,
+    // h/6 and the right-hand side's two, as float-float (the FP32 chain uses
+    // the high parts); set here for the FP32 scan, from the host's split for
+    // the float-float one (init_ff)
+    ff h_ff, hh_ff, h6_ff, rc_ff[2];
     __host__ __device__ void init(const double* p, double hh) {
         rhs.init(p);
         h = hh;
+        if constexpr (has_reduced_jacobian<Rhs>::value) {
+            double rc[2];
+            Rhs::ff_params(p, rc);
+            h_ff = ff_const(hh);
+            hh_ff = ff_const(0.5 * hh);
+            h6_ff = ff_const(hh * (1.0 / 6.0));
+            rc_ff[0] = ff_const(rc[0]);
+            rc_ff[1] = ff_const(rc[1]);
+        }
     }
     // r = xc - phi(xp), jv = dphi/dx(xp) (dense, row-major)
     __device__ __forceinline__ void eval(const double* xp, const double* xc, double* res, double* jv) const {
@@ -542,13 +580,64 @@ struct RK4Map {
         for (int i = 0; i < D * D; ++i) J[i] = jv[i];
     }
 
+    // ---- FP32 delta-form scan (PITN_PREC_MIXED_FP32; right-hand sides with
+    // ff_params and jf_times_f32) ----
+    // The FP64 residual as in eval; S = J - I = (h/6)(K1 + 2 K2 + 2 K3 + K4)
+    // (the delta form needs no subtraction here) by the stage chain rule in
+    // FP32 from the FP64 stage states rounded on the integer pipes.
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res,
+                                               float* sv) const {
+        double k[D], ksum[D], y[D];
+        float yf[D], Y[D * D], K[D * D], Ks[D * D], rc[2];
+        const double a[4] = {0.0, 0.5, 0.5, 1.0};
+        const double w[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        rc[0] = rc_ff[0].hi;
+        rc[1] = rc_ff[1].hi;
+        rhs.f(xp, k);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            ksum[i] = w[0] * k[i];
+            yf[i] = d2f_int(xp[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) Y[i] = (i % (D + 1) == 0) ? 1.f : 0.f;
+        rhs.jf_times_f32(yf, Y, K, rc);   // K_1 = Jf(x)
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) Ks[i] = K[i];
+#pragma unroll
+        for (int s = 1; s < 4; ++s) {
+            const double ha = h * a[s];
+            const float hs = (s == 3) ? h_ff.hi : hh_ff.hi;
+#pragma unroll
+            for (int i = 0; i < D; ++i) y[i] = fma(ha, k[i], xp[i]);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) Y[i] = (i % (D + 1) == 0) ? fmaf(hs, K[i], 1.f) : hs * K[i];
+            rhs.f(y, k);
+#pragma unroll
+            for (int i = 0; i < D; ++i) {
+                ksum[i] = fma(w[s], k[i], ksum[i]);
+                yf[i] = d2f_int(y[i]);
+            }
+            rhs.jf_times_f32(yf, Y, K, rc);
+#pragma unroll
+            for (int i = 0; i < D * D; ++i) Ks[i] = (s == 3) ? Ks[i] + K[i] : fmaf(2.f, K[i], Ks[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < D; ++i) res[i] = xc[i] - (xp[i] + h * ksum[i]);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) sv[i] = h6_ff.hi * Ks[i];
+    }
+    __device__ __forceinline__ void sfull(const float* sv, float* S) const {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) S[i] = sv[i];
+    }
+
     // ---- float-float scan (PITN_PREC_FP64_FF; right-hand sides with
     // ff_params and jf_times_ff) ----
     // The residual is the FP64 one above, operation for operation; the
     // stage chain rule of the Jacobian runs in float-float from the FP64
     // stage states.  Constants split on the host: (h, h/2, h/6) and the
     // right-hand side's two.
-    ff h_ff, hh_ff, h6_ff, rc_ff[2];
     static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
         double rc[2];
         Rhs::ff_params(p, rc);

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-SINGLE = ["vdp", "vdp_mixed", "vdp_rk4", "robertson", "osc", "lorenz", "lorenz_mixed", "fkpp", "fkpp_mixed"]
+SINGLE = ["vdp", "vdp_mixed", "vdp_ff", "vdp_rk4", "vdp_rk4_ff", "vdp_rk4_mixed", "robertson", "osc", "lorenz", "lorenz_mixed", "fkpp", "fkpp_mixed"]
 
 
 @pytest.mark.parametrize("name", SINGLE + ["batch", "batch_small", "adjoint"])
@@ -103,3 +103,38 @@ def test_reference_arm_batch_line(monkeypatch):
     assert 0 < line["ms_per_step"] < 1e3
     assert line["config"]["projected_ms_per_solve"] == pytest.approx(float(bt.N.sum()) / 2.0e6 * 1e3)
     assert line["cpu_baseline"]["cores"] == 4 and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_clock_sampler_window():
+    """The clock record is that of the samples stamped inside the timed
+    region; with none there (a timed region shorter than the sampling
+    interval), that of the warm-up and the timed region, marked so."""
+    import datetime
+
+    class FakeSmi:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    now = datetime.datetime.now()
+
+    def line(dt, mhz, cap="Not Active"):
+        ts = (now + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.00, 0x0, Not Active, Not Active, Not Active, {cap}"
+
+    cs = bench.ClockSampler("0")
+    cs.proc = FakeSmi()
+    cs.lines = [line(-1.0, 1500), line(-0.5, 1980, "Active"), "garbage"]
+    cs.t_timed = now - datetime.timedelta(seconds=0.2)
+    r = cs.stop()
+    assert r["samples"] == 2 and r["sm_mhz"] == 1740 and r["reasons"] == ["sw_power_cap"]
+    assert r["window"].startswith("warm-up")
+
+    cs = bench.ClockSampler("0")
+    cs.proc = FakeSmi()
+    cs.lines = [line(-1.0, 1500, "Active"), line(-0.1, 2070), line(-0.05, 2060), line(5.0, 100)]
+    cs.t_timed = now - datetime.timedelta(seconds=0.2)
+    r = cs.stop()
+    assert r == {"sm_mhz": 2065, "sm_max_mhz": 2070, "reasons": [], "samples": 2, "window": "timed region"}

@@ -64,3 +64,53 @@ def test_bench_size_vdp_mixed(pk):
     assert not nf and res <= 1e-8 * (1 + 1e-6)
     seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N)
     assert float(np.abs(g - seq).max() / np.abs(seq).max()) <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# The RK4 map (eq. 2.3) with the FP32 delta-form scan: S = J - I from the
+# stage chain rule in FP32, the residual the FP64 one.  Sec. 4.1's van der
+# Pol from the ones guess on ragged sizes and at the bench size: the FP64
+# tolerance reached, the oracle's residual re-check passed, the root within
+# 1e-6 of the sequential FP64 RK4 trajectory.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [1, 7, 1000, 4099, 10007])
+def test_mixed_rk4_within_1e6(pk, N):
+    wl = W.vdp_paper(h=1e-3, t_end=N * 1e-3)
+    assert wl.N == N
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, N, 1e-11, 60, guess=np.ones((N, wl.d)),
+                          method=pk.PITN_STEP_RK4, precision=pk.PITN_PREC_MIXED_FP32, history=True)
+    assert info["status"] == O.OK and info["final_res"] <= 1e-11
+    g = traj.cpu().numpy()
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, g, method=O.RK4)
+    assert not nf and res <= 1e-11 * (1 + 1e-6)
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, N, method=O.RK4)
+    assert float(np.abs(g - seq).max() / np.abs(seq).max()) <= 1e-6
+
+
+def test_mixed_rk4_rejects_other_systems(pk):
+    from paper_2511_01465_gb300 import pitn as P
+    wl = W.lorenz(N=100)
+    with pytest.raises(P.PitnError):
+        pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 5, method=P.PITN_STEP_RK4,
+                 precision=P.PITN_PREC_MIXED_FP32)
+
+
+def test_bench_size_vdp_rk4_mixed(pk):
+    """The RK4 bench workload (h = 1e-5, N = 1e6, guess ones) with the FP32
+    scan.  At the bench's tol 1e-8: converged, its residual re-checked by the
+    oracle.  That tolerance still leaves an iterate ~5e-6 (relative) from the
+    sequential trajectory after 1e6 steps, the FP64 solve's as well (its last
+    residual 6.6e-10, the FP32 solve's 7.1e-9, both after 7 updates), so the
+    distance to the sequential FP64 RK4 trajectory is checked at tol 1e-11:
+    within 1e-9 (both solves ~5e-12 there)."""
+    wl = W.vdp_paper(h=1e-5)
+    seq = O.sequential(wl.system, wl.params, wl.x0, wl.h, wl.N, method=O.RK4)
+    for tol, bar in ((1e-8, None), (1e-11, 1e-9)):
+        traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, tol, 50, guess=np.ones((wl.N, wl.d)),
+                              method=pk.PITN_STEP_RK4, precision=pk.PITN_PREC_MIXED_FP32)
+        assert info["status"] == O.OK and info["final_res"] <= tol
+        g = traj.cpu().numpy()
+        _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, g, method=O.RK4)
+        assert not nf and res <= tol * (1 + 1e-6)
+        if bar is not None:
+            assert float(np.abs(g - seq).max() / np.abs(seq).max()) <= bar
