@@ -4,7 +4,7 @@ One step = one complete Newton solve (every residual evaluation, scan and
 update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|lorenz|lorenz_mixed|lorenz_ff|osc|
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|vdp_rk4_ff|vdp_rk4_mixed|lorenz|lorenz_mixed|lorenz_ff|osc|
                                                       robertson|fkpp|fkpp_mixed|fkpp_tf32|batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
