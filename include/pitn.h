@@ -194,8 +194,12 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
  *   traj_out   [sum N][d]: IVP b occupies rows offsets[b] .. offsets[b+1]-1
  *   offsets_out [B+1]: exclusive prefix sum of N (int64)
  *   iters_out, status_out [B] (int32); res_out [B] (nullable) final norms
- *   opt        guard_B, stream and tile_elems are honoured; precision must be
- *              FP64; guess and res_history must be NULL.
+ *   opt        guard_B, stream and tile_elems are honoured; method must be
+ *              explicit Euler; guess and res_history must be NULL.
+ *              precision PITN_PREC_FP64, or PITN_PREC_MIXED_FP32 /
+ *              PITN_PREC_FP64_FF (the scans of pitn_solve_ex, on the per-IVP
+ *              path only: tile_elems must then be 0, and a pinned segmented
+ *              shape returns PITN_EUNSUPPORTED).
  * Returns PITN_OK when every IVP converged, PITN_NOT_CONVERGED when one did
  * not (see status_out), or a negative error code.
  */
@@ -256,6 +260,16 @@ int pitn_release_workspace(void);
 /* Number of kernel launches the library issued since the process started
  * (all devices, all entry points). */
 int64_t pitn_launch_count(void);
+
+/* Work of the most recent pitn_solve_batch in this process (instrumentation
+ * for throughput figures): the steps whose residual and Jacobian were
+ * evaluated and folded, and the steps whose Newton step was replayed,
+ * summed over its IVPs and passes.  The per-IVP path counts them in its
+ * kernel (a guard's fill region costs one evaluation per thread, and a
+ * thread's replay ends at its first cut); the segmented path evaluates
+ * every step of a running IVP in each pass.  Both 0 before the first batch
+ * solve.  Returns PITN_EINVAL for a NULL pointer. */
+int pitn_batch_work(int64_t* evaluated, int64_t* replayed);
 
 /*
  * Allocation-free solve for the small-state systems (PITN_LORENZ63, PITN_VDP,
@@ -395,11 +409,14 @@ int pitn_debug_inject(int what, int64_t value);
  * Different shapes associate the scan differently, so results may differ in
  * the last bits.  Keys: "small:<system>:<d>:<floor log2 N>:<guarded 0/1>"
  * plus ":rk4", ":be" or ":tr" for the RK4, backward Euler and trapezoidal
- * maps and ":f32" for PITN_PREC_MIXED_FP32 (e.g. "small:2:2:22:1"), and
- * "batch:<system>:<d>:<floor log2 B>:<guarded>".
- * pitn_tune_get reads one entry; pitn_tune_set pins one (a, b > 0; a shape
- * that does not fit the device makes the solve return PITN_EUNSUPPORTED),
- * so that a deployment can fix its launch shapes without tuning. */
+ * maps and ":f32" / ":ff" for PITN_PREC_MIXED_FP32 / PITN_PREC_FP64_FF
+ * (e.g. "small:2:2:22:1"), and "batch:<system>:<d>:<floor log2 of the total
+ * steps>:<guarded>", with the same ":f32" / ":ff".
+ * pitn_tune_get reads one entry; pitn_tune_set pins one (a: threads per
+ * CTA, a multiple of 32 up to 1024; b > 0, or b = 0 in a batch key for the
+ * per-IVP path; else PITN_EINVAL.  A shape that does not fit the device
+ * makes the solve return PITN_EUNSUPPORTED or PITN_ECUDA), so that a
+ * deployment can fix its launch shapes without tuning. */
 int pitn_tune_enable(int on);
 int pitn_tune_clear(void);
 int pitn_tune_get(const char* key, int* a, int* b);

@@ -63,8 +63,10 @@ def solve(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, precision=P.P
 
 
 def solve_batch(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, device="cuda", stream=None,
-                tile_elems=0):
-    """Solves B IVPs in one segmented launch sequence.
+                tile_elems=0, precision=0):
+    """Solves B IVPs in one segmented launch sequence (precision
+    PITN_PREC_MIXED_FP32 / PITN_PREC_FP64_FF: the reduced-precision scans,
+    on the per-IVP path).
 
     Returns (traj [sum N][d], offsets [B+1], iters [B], status [B], res [B]).
     """
@@ -80,7 +82,8 @@ def solve_batch(system, params, x0, h, N, tol, max_iter, *, guard_B=0.0, device=
     iters = torch.empty(B, dtype=torch.int32, device=device)
     status = torch.empty(B, dtype=torch.int32, device=device)
     res = torch.empty(B, dtype=torch.float64, device=device)
-    opt = P.make_options(guard_B=guard_B, stream=_stream_ptr(stream, device), tile_elems=tile_elems)
+    opt = P.make_options(guard_B=guard_B, stream=_stream_ptr(stream, device), tile_elems=tile_elems,
+                         precision=precision)
     rc = P.pitn_solve_batch(system, B, p_t, x0_t, h_t, N_t, d, tol, max_iter, traj, offsets, iters,
                             status, res, opt)
     P.check(rc, "pitn_solve_batch")

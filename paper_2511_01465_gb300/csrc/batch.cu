@@ -23,12 +23,15 @@
 // Each IVP keeps its own current buffer and guard fill, so frozen IVPs are
 // never copied.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
+#include "newton_small.cuh"   // the reduced-precision scan policies (scan_policy.cuh)
 #include "solver.h"
 #include "systems.cuh"
 
@@ -61,6 +64,7 @@ struct BatchArgs {
     IvpState* st;           // [B]
     unsigned* running;      // [0] IVPs still running after the iteration, [1] iterations run,
                             // [2..3] next IVP of the per-IVP queue (64-bit)
+    unsigned long long* work;  // [2] per-IVP path: steps evaluated (residual, Jacobian, fold), steps replayed
     long long B, M, chunk;
     double tol;
     unsigned long long cap_bits;
@@ -552,6 +556,25 @@ __device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D
     b_compose<D>(eP, ec, s_w[warp], s_w[warp] + D * D, tP, tc);
 }
 
+// Work weight of a regular step against a fill step in the per-IVP path's
+// partition of an IVP's steps over the CTA's threads.  Past the iteration's
+// new cut a fill step costs nothing (its replay has stopped, and the fold
+// powers one element), before it only its replay.
+constexpr long long kBatchFillWeight = 4;
+
+// Adds a thread's step counts of the per-IVP path to the solve's totals.
+__device__ __forceinline__ void b_flush_work(const BatchArgs& a, unsigned long long ev, unsigned long long rep) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, off);
+        rep += __shfl_xor_sync(0xffffffffu, rep, off);
+    }
+    if ((threadIdx.x & 31) == 0 && a.work) {
+        atomicAdd(a.work, ev);
+        atomicAdd(a.work + 1, rep);
+    }
+}
+
 // One CTA solves whole IVPs, taken from a queue in the host's order (longest
 // first): the Newton loop of each IVP runs with CTA-level scans only, so no
 // IVP waits on another and nothing synchronises the grid.  Per iteration:
@@ -567,6 +590,7 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
     __shared__ long long s_b;
     __shared__ unsigned long long s_res, s_q;
     const int lane = threadIdx.x & 31;
+    unsigned long long n_ev = 0ull, n_rep = 0ull;   // steps evaluated / replayed by this thread
     for (;;) {
         if (threadIdx.x == 0) {
             const unsigned long long i = atomicAdd(queue, 1ull);
@@ -581,8 +605,7 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
         const double* x0 = a.x0 + b * D;
         double* Xb[2] = {a.X0 + base * D, a.X1 + base * D};
         double* scr = a.scratch + base * W;
-        const long long C = (n + blockDim.x - 1) / blockDim.x;
-        const long long k0 = min(n, (long long)threadIdx.x * C), k1 = min(n, k0 + C);
+        const long long T = blockDim.x;
         int cur = 0, it = 0, status = PITN_NOT_CONVERGED;
         long long q = 0, last_cut = n;
         double final_res = 0.0;
@@ -599,16 +622,32 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
             const double* Xc = Xb[cur];
             double* Xn = Xb[cur ^ 1];
             if (threadIdx.x == 0) { s_res = 0ull; s_q = 0ull; }
+            // Steps from sfill on lie in the guard's fill region (every state
+            // x_{q-1}; at the constant guess every state x0): all their
+            // elements are the same element, folded by binary powering.  The
+            // steps are dealt out to the threads by their work weight
+            // (kBatchFillWeight), each thread a contiguous range.
+            const long long sfill = (q < n) ? (q > 1 ? q : 1LL) : n;
+            long long k0, k1;
+            {
+                constexpr long long kw = kBatchFillWeight;
+                const long long wreg = kw * sfill, wtot = wreg + (n - sfill);
+                const long long per = (wtot + T - 1) / T;
+                const long long w0 = (long long)threadIdx.x * per, w1 = w0 + per;
+                k0 = min(n, (w0 <= wreg) ? (w0 + kw - 1) / kw : sfill + (w0 - wreg));
+                k1 = min(n, (w1 <= wreg) ? (w1 + kw - 1) / kw : sfill + (w1 - wreg));
+            }
+            const long long kreg = min(k1, max(k0, sfill));   // regular steps: [k0, kreg)
             // residuals, Jacobians and the thread fold
             double P[D * D], c[D];
             b_identity<D>(P);
 #pragma unroll
             for (int i = 0; i < D; ++i) c[i] = 0.0;
             unsigned long long mres = 0ull;
-            if (k0 < k1) {
+            if (k0 < kreg) {
                 double xp[D];
                 state(Xc, k0 - 1, xp);
-                for (long long k = k0; k < k1; ++k) {
+                for (long long k = k0; k < kreg; ++k) {
                     double x[D], r[D], jv[JN];
                     state(Xc, k, x);
                     sys.eval(xp, x, r, jv);
@@ -638,6 +677,29 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
                     for (int i = 0; i < D; ++i) xp[i] = x[i];
                 }
             }
+            n_ev += (unsigned long long)(kreg - k0) + (kreg < k1 ? 1ull : 0ull);
+            double xf[D], rf[D], jvf[JN];
+            if (kreg < k1) {   // the fill element (J(x_f), -r_f), raised to the power k1 - kreg
+                double EP[D * D], Ec[D], RP[D * D], Rc[D];
+                state(Xc, q - 1, xf);
+                sys.eval(xf, xf, rf, jvf);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const unsigned long long bits = abs_bits(rf[i]);
+                    mres = bits > mres ? bits : mres;
+                    Ec[i] = -rf[i];
+                    Rc[i] = 0.0;
+                }
+                sys.jfull(jvf, EP);
+                b_identity<D>(RP);
+                for (long long e = k1 - kreg;;) {
+                    if (e & 1) b_compose<D>(EP, Ec, RP, Rc, RP, Rc);
+                    e >>= 1;
+                    if (!e) break;
+                    b_compose<D>(EP, Ec, EP, Ec, EP, Ec);
+                }
+                b_compose<D>(RP, Rc, P, c, P, c);
+            }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const unsigned long long o = __shfl_xor_sync(0xffffffffu, mres, off);
@@ -653,20 +715,17 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
             if (final_res <= a.tol) { status = PITN_OK; break; }
             if (it >= a.max_iter) { status = PITN_NOT_CONVERGED; break; }
             // replay of the Newton step from the thread's incoming vector (the
-            // element of step 0 has matrix 0, so the prefix's vector is it)
+            // element of step 0 has matrix 0, so the prefix's vector is it).  A
+            // thread stops at its first cut: every later state of its range
+            // lies beyond the iteration's cut and is never read again.
             unsigned long long my_q = 0ull;
             if (k0 < k1) {
                 double z[D];
 #pragma unroll
                 for (int i = 0; i < D; ++i) z[i] = tc[i];
                 bool found = false;
-                for (long long k = k0; k < k1; ++k) {
-                    double jv[JN], r[D], x[D];
-#pragma unroll
-                    for (int i = 0; i < JN; ++i) jv[i] = scr[k * W + i];
-#pragma unroll
-                    for (int i = 0; i < D; ++i) r[i] = scr[k * W + JN + i];
-                    state(Xc, k, x);
+                auto step = [&](long long k, const double* jv, const double* r, const double* x) {
+                    ++n_rep;
                     if (k == 0) {
 #pragma unroll
                         for (int i = 0; i < D; ++i) z[i] = -r[i];
@@ -683,11 +742,21 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
                         const unsigned long long bits = abs_bits(z[i]);
                         zb = bits > zb ? bits : zb;
                     }
-                    if (!found && zb > a.cap_bits) {
+                    if (zb > a.cap_bits) {
                         found = true;
                         my_q = ~(unsigned long long)k;
                     }
+                };
+                for (long long k = k0; k < kreg && !found; ++k) {
+                    double jv[JN], r[D], x[D];
+#pragma unroll
+                    for (int i = 0; i < JN; ++i) jv[i] = scr[k * W + i];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) r[i] = scr[k * W + JN + i];
+                    state(Xc, k, x);
+                    step(k, jv, r, x);
                 }
+                for (long long k = kreg; k < k1 && !found; ++k) step(k, jvf, rf, xf);
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -718,6 +787,208 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
         }
         __syncthreads();   // s_b is overwritten by the next pick
     }
+    b_flush_work(a, n_ev, n_rep);
+}
+
+// The per-IVP solve with a reduced-precision scan (an inexact Newton step):
+// the same Newton loop, with the residual, the stopping test and the update
+// in FP64 and the elements, folds, CTA scan and replay in the scan policy's
+// arithmetic (scan_policy.cuh: ScanF32, the FP32 delta form; ScanFF,
+// float-float).  The scratch holds the policy's values (at most 8 bytes
+// each, in the FP64 path's slots).
+template <class Sys, class Pol>
+__global__ void __launch_bounds__(256) batch_ivp_mixed_kernel(BatchArgs a, const long long* __restrict__ order,
+                                                              unsigned long long* __restrict__ queue) {
+    using T = typename Pol::T;
+    constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
+    static_assert(sizeof(T) <= sizeof(double), "scratch slots are 8 bytes");
+    __shared__ T s_wex[kMaxWarps][E];
+    __shared__ T s_tot[E];
+    __shared__ long long s_b;
+    __shared__ unsigned long long s_res, s_q;
+    const int lane = threadIdx.x & 31;
+    const float capf = (float)fmin(__longlong_as_double((long long)a.cap_bits), (double)FLT_MAX);
+    unsigned long long n_ev = 0ull, n_rep = 0ull;   // steps evaluated / replayed by this thread
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long i = atomicAdd(queue, 1ull);
+            s_b = (i < (unsigned long long)a.B) ? order[i] : -1;
+        }
+        __syncthreads();
+        const long long b = s_b;
+        if (b < 0) break;
+        const long long base = a.off[b], n = a.off[b + 1] - base;
+        Sys sys;
+        sys.init(a.params + b * Sys::P, a.h[b]);
+        Pol::setup_ivp(sys, a.params + b * Sys::P, a.h[b]);
+        const double* x0 = a.x0 + b * D;
+        double* Xb[2] = {a.X0 + base * D, a.X1 + base * D};
+        T* scr = reinterpret_cast<T*>(a.scratch + base * W);
+        const long long Tn = blockDim.x;
+        int cur = 0, it = 0, status = PITN_NOT_CONVERGED;
+        long long q = 0, last_cut = n;
+        double final_res = 0.0;
+        auto state = [&](const double* X, long long j, double* o) {
+            const double* src;
+            if (j < 0) src = x0;
+            else if (j < q) src = X + j * D;
+            else if (q > 0) src = X + (q - 1) * D;
+            else src = x0;
+#pragma unroll
+            for (int i = 0; i < D; ++i) o[i] = src[i];
+        };
+        for (;; ++it) {
+            const double* Xc = Xb[cur];
+            double* Xn = Xb[cur ^ 1];
+            if (threadIdx.x == 0) { s_res = 0ull; s_q = 0ull; }
+            // regular steps [0, sfill) and the fill region, weighted as in
+            // batch_ivp_kernel
+            const long long sfill = (q < n) ? (q > 1 ? q : 1LL) : n;
+            long long k0, k1;
+            {
+                constexpr long long kw = kBatchFillWeight;
+                const long long wreg = kw * sfill, wtot = wreg + (n - sfill);
+                const long long per = (wtot + Tn - 1) / Tn;
+                const long long w0 = (long long)threadIdx.x * per, w1 = w0 + per;
+                k0 = min(n, (w0 <= wreg) ? (w0 + kw - 1) / kw : sfill + (w0 - wreg));
+                k1 = min(n, (w1 <= wreg) ? (w1 + kw - 1) / kw : sfill + (w1 - wreg));
+            }
+            const long long kreg = min(k1, max(k0, sfill));
+            T Q[D * D], c[D];
+            Pol::template ident<D>(Q, c);
+            unsigned long long mres = 0ull;
+            if (k0 < kreg) {
+                double xp[D];
+                state(Xc, k0 - 1, xp);
+                for (long long k = k0; k < kreg; ++k) {
+                    double x[D], r[D];
+                    T sv[JN], rf[D];
+                    state(Xc, k, x);
+                    Pol::eval(sys, xp, x, r, sv);
+#pragma unroll
+                    for (int i = 0; i < JN; ++i) scr[k * W + i] = sv[i];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        rf[i] = Pol::from_double(r[i]);
+                        scr[k * W + JN + i] = rf[i];
+                        const unsigned long long bits = abs_bits(r[i]);
+                        mres = bits > mres ? bits : mres;
+                    }
+                    if (k == 0) Pol::template head<D>(rf, Q, c);   // a_0 = (0, -r_0), eq. 3.4
+                    else Pol::leaf(sys, sv, rf, Q, c);
+#pragma unroll
+                    for (int i = 0; i < D; ++i) xp[i] = x[i];
+                }
+            }
+            n_ev += (unsigned long long)(kreg - k0) + (kreg < k1 ? 1ull : 0ull);
+            double xf[D];
+            T svf[JN], rff[D];
+            if (kreg < k1) {   // the fill element, raised to the power k1 - kreg
+                double rf64[D];
+                T EQ[D * D], Ec[D], RQ[D * D], Rc[D];
+                state(Xc, q - 1, xf);
+                Pol::eval(sys, xf, xf, rf64, svf);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const unsigned long long bits = abs_bits(rf64[i]);
+                    mres = bits > mres ? bits : mres;
+                    rff[i] = Pol::from_double(rf64[i]);
+                }
+                Pol::elem(sys, svf, rff, EQ, Ec);
+                Pol::template ident<D>(RQ, Rc);
+                for (long long e = k1 - kreg;;) {
+                    if (e & 1) Pol::template compose<D>(EQ, Ec, RQ, Rc, RQ, Rc);
+                    e >>= 1;
+                    if (!e) break;
+                    Pol::template compose<D>(EQ, Ec, EQ, Ec, EQ, Ec);
+                }
+                Pol::template compose<D>(RQ, Rc, Q, c, Q, c);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, mres, off);
+                mres = o > mres ? o : mres;
+            }
+            T eQ[D * D], ec[D];
+            pol_block_scan<Pol, D>(Q, c, eQ, ec, s_wex, s_tot);   // (its barriers order s_res's reset)
+            if (lane == 0 && mres) atomicMax(&s_res, mres);
+            __syncthreads();
+            const unsigned long long rb = s_res;
+            final_res = __longlong_as_double((long long)rb);
+            if (rb >= kInf) { status = PITN_NONFINITE; break; }
+            if (final_res <= a.tol) { status = PITN_OK; break; }
+            if (it >= a.max_iter) { status = PITN_NOT_CONVERGED; break; }
+            // replay from the thread's incoming vector, FP64 update; a thread
+            // stops at its first cut
+            unsigned long long my_q = 0ull;
+            if (k0 < k1) {
+                T z[D], zw[D], zero[D];
+#pragma unroll
+                for (int i = 0; i < D; ++i) zero[i] = Pol::zero();
+                Pol::template apply<D>(s_wex[threadIdx.x >> 5], s_wex[threadIdx.x >> 5] + D * D, zero, zw);
+                Pol::template apply<D>(eQ, ec, zw, z);
+                bool found = false;
+                auto step = [&](long long k, const T* sv, const T* rf, const double* x) {
+                    ++n_rep;
+                    if (k == 0) {
+#pragma unroll
+                        for (int i = 0; i < D; ++i) z[i] = Pol::neg(rf[i]);
+                    } else {
+                        Pol::replay(sys, sv, rf, z);
+                    }
+                    bool bad = false;
+#pragma unroll
+                    for (int i = 0; i < D; ++i) {
+                        Xn[k * D + i] = Pol::add_to(x[i], z[i]);
+                        bad |= !Pol::within(z[i], capf);
+                    }
+                    if (bad) {
+                        found = true;
+                        my_q = ~(unsigned long long)k;
+                    }
+                };
+                for (long long k = k0; k < kreg && !found; ++k) {
+                    T sv[JN], rf[D];
+                    double x[D];
+#pragma unroll
+                    for (int i = 0; i < JN; ++i) sv[i] = scr[k * W + i];
+#pragma unroll
+                    for (int i = 0; i < D; ++i) rf[i] = scr[k * W + JN + i];
+                    state(Xc, k, x);
+                    step(k, sv, rf, x);
+                }
+                for (long long k = kreg; k < k1 && !found; ++k) step(k, svf, rff, xf);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, my_q, off);
+                my_q = o > my_q ? o : my_q;
+            }
+            if (lane == 0 && my_q) atomicMax(&s_q, my_q);
+            __syncthreads();
+            const unsigned long long qe = s_q;
+            const long long cut = qe ? (long long)(~qe) : n;
+            __syncthreads();   // s_res / s_q are reset at the top of the next iteration
+            if (!a.guarded && cut < n) { status = PITN_NONFINITE; break; }
+            q = a.guarded ? cut : n;
+            cur ^= 1;
+            last_cut = cut;
+        }
+        if (threadIdx.x == 0) {
+            IvpState s = a.st[b];
+            s.cur = cur;
+            s.q = q;
+            s.iters = it;
+            s.status = status;
+            s.final_res = final_res;
+            s.guard_index = last_cut;
+            s.active = 0;
+            s.stepping = 0;
+            a.st[b] = s;
+        }
+        __syncthreads();   // s_b is overwritten by the next pick
+    }
+    b_flush_work(a, n_ev, n_rep);
 }
 
 __global__ void batch_init_kernel(BatchArgs a) {
@@ -776,9 +1047,18 @@ __global__ void batch_loop_kernel(BatchArgs a, cudaGraphConditionalHandle h) {
 // The per-IVP path: a persistent grid of CTAs takes IVPs from the queue
 // (longest first) and solves each one whole.  `iterations` reports the
 // launch count of the Newton loop (one).
-template <class Sys>
+// Pol: void for the FP64 solve, else the reduced-precision scan policy.
+template <class Sys, class Pol = void>
 int batch_run_ivp(BatchArgs& a, int block, cudaStream_t st, const long long* order, double* out,
                   int* iters_out, int* status_out, double* res_out, long long* off_out, int* iterations) {
+    using Kern = void (*)(BatchArgs, const long long*, unsigned long long*);
+    Kern kern;
+    if constexpr (std::is_void<Pol>::value) {
+        kern = batch_ivp_kernel<Sys>;
+    } else {
+        if (block > kMaxWarps * 32) return PITN_EUNSUPPORTED;   // the policy's CTA scan
+        kern = batch_ivp_mixed_kernel<Sys, Pol>;
+    }
     const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);
     batch_init_kernel<<<eg, 256, 0, st>>>(a);
     count_launch(1);
@@ -786,12 +1066,12 @@ int batch_run_ivp(BatchArgs& a, int block, cudaStream_t st, const long long* ord
     unsigned long long* queue = reinterpret_cast<unsigned long long*>(a.running + 2);
     if (cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st) != cudaSuccess) return PITN_ECUDA;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ivp_kernel<Sys>, block, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, 0) != cudaSuccess)
         return PITN_ECUDA;
     if (per_sm < 1) return PITN_EUNSUPPORTED;
     const long long grid = std::min<long long>((long long)per_sm * props().multiProcessorCount, a.B);
     auto tok = timed_begin("batch", st);
-    batch_ivp_kernel<Sys><<<(unsigned)grid, block, 0, st>>>(a, order, queue);
+    kern<<<(unsigned)grid, block, 0, st>>>(a, order, queue);
     timed_end(tok, st);
     count_launch(1);
     if (cudaGetLastError() != cudaSuccess) return PITN_ECUDA;
@@ -876,6 +1156,16 @@ int batch_run(BatchArgs& a, int block, long long grid, cudaStream_t st, unsigned
 
 using namespace pitn_host;
 
+// step counts of the last batch solve in this process (pitn_batch_work)
+static std::atomic<int64_t> g_batch_work[2];
+
+extern "C" int pitn_batch_work(int64_t* evaluated, int64_t* replayed) {
+    if (!evaluated || !replayed) return PITN_EINVAL;
+    *evaluated = g_batch_work[0].load();
+    *replayed = g_batch_work[1].load();
+    return PITN_OK;
+}
+
 extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, const double* x0,
                                 const double* h, const int64_t* N, int d, double tol, int max_iter,
                                 double* traj_out, int64_t* offsets_out, int32_t* iters_out,
@@ -888,9 +1178,12 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     if (B < 1 || !params || !x0 || !h || !N || !traj_out || !offsets_out || !iters_out || !status_out)
         return PITN_EINVAL;
     if (!std::isfinite(tol) || !(tol >= 0.0) || max_iter < 0 || max_iter > kMaxIter) return PITN_EINVAL;
-    if (o.precision != PITN_PREC_FP64 || o.guess || o.res_history || std::isnan(o.guard_B) ||
-        o.method != PITN_STEP_EULER)
+    if ((o.precision != PITN_PREC_FP64 && o.precision != PITN_PREC_MIXED_FP32 &&
+         o.precision != PITN_PREC_FP64_FF) ||
+        o.guess || o.res_history || std::isnan(o.guard_B) || o.method != PITN_STEP_EULER)
         return PITN_EINVAL;
+    // the reduced-precision scans run on the per-IVP path only
+    const bool reduced = o.precision != PITN_PREC_FP64;
     if (o.tile_elems < 0) return PITN_EINVAL;
     if (any_foreign({params, x0, h, N, traj_out, offsets_out, iters_out, status_out, res_out}))
         return PITN_EINVAL;
@@ -922,14 +1215,20 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     long long chunk = o.tile_elems > 0 ? o.tile_elems : 32;
     const bool guarded_b = o.guard_B > 0.0 && std::isfinite(o.guard_B);
     char tkey[96];
-    std::snprintf(tkey, sizeof(tkey), "batch:%d:%d:%d:%d", system_id, d, tune_bucket(M), guarded_b ? 1 : 0);
+    std::snprintf(tkey, sizeof(tkey), "batch:%d:%d:%d:%d%s", system_id, d, tune_bucket(M), guarded_b ? 1 : 0,
+                  o.precision == PITN_PREC_MIXED_FP32 ? ":f32" : o.precision == PITN_PREC_FP64_FF ? ":ff" : "");
     int tb = 0, tc = 0;
     bool tune_now = false;
+    if (reduced && o.tile_elems > 0) return PITN_EINVAL;   // no segmented path to tile
     if (o.tile_elems <= 0 && tune_lookup(tkey, &tb, &tc)) {
         block = tb;
         chunk = tc;
+        if (reduced && chunk != 0) return PITN_EUNSUPPORTED;
     } else if (o.tile_elems <= 0 && tune_enabled()) {
         tune_now = true;
+    } else if (reduced) {
+        block = 128;
+        chunk = 0;
     } else if (o.tile_elems <= 0) {
         // untuned default: the per-IVP path when no IVP is longer than one
         // CTA's share of the steps (about four 128-thread CTAs per SM), so
@@ -962,7 +1261,7 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
                  o_st = take(sizeof(IvpState) * B), o_run = take(16),
                  o_it = take(sizeof(int) * B), o_stat = take(sizeof(int) * B),
                  o_res = take(sizeof(double) * B), o_offo = take(sizeof(long long) * (B + 1)),
-                 o_ord = take(sizeof(long long) * B),
+                 o_ord = take(sizeof(long long) * B), o_work = take(16),
                  o_out = out_dev ? 0 : take(sizeof(double) * (size_t)M * d);
     char* small = (char*)workspace(off, kSlotStage);
     double* X1 = (double*)workspace(sizeof(double) * (size_t)M * d, kSlotX1);
@@ -1002,6 +1301,7 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     a.texcl = (double*)(aux2 + ((aggB + 255) & ~(size_t)255));
     a.st = (IvpState*)(small + o_st);
     a.running = (unsigned*)(small + o_run);
+    a.work = (unsigned long long*)(small + o_work);
     a.B = B;
     a.M = M;
     a.chunk = chunk;
@@ -1022,6 +1322,27 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     const long long* ord_d = (const long long*)(small + o_ord);
     // a shape with chunk 0 is the per-IVP path with `blk` threads per CTA
     auto run_shape = [&](int blk, long long ch, int* iters_run) -> int {
+        if (reduced) {
+            if (ch != 0) return PITN_EUNSUPPORTED;
+            const bool f32 = o.precision == PITN_PREC_MIXED_FP32;
+            switch (system_id) {
+            case PITN_LORENZ63:
+                return f32 ? batch_run_ivp<Lorenz63, ScanF32>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                              iters_run)
+                           : batch_run_ivp<Lorenz63, ScanFF>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                             iters_run);
+            case PITN_VDP:
+                return f32 ? batch_run_ivp<VanDerPol, ScanF32>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                               iters_run)
+                           : batch_run_ivp<VanDerPol, ScanFF>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                              iters_run);
+            default:
+                return f32 ? batch_run_ivp<LinearOsc, ScanF32>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                               iters_run)
+                           : batch_run_ivp<LinearOsc, ScanFF>(a, blk, st, ord_d, a.X0, it_d, stat_d, res_d, offo_d,
+                                                              iters_run);
+            }
+        }
         if (ch == 0) {
             switch (system_id) {
             case PITN_LORENZ63:
@@ -1080,8 +1401,30 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
         tune_store(tkey, block, (int)chunk);
     }
     int its_final = 0;
+    if (cudaMemsetAsync(a.work, 0, 16, st) != cudaSuccess) return PITN_ECUDA;   // counts of this solve only
     int rc = run_shape(block, chunk, &its_final);
     if (rc != PITN_OK) return rc;
+    {
+        // step counts of the solve (pitn_batch_work): counted by the per-IVP
+        // kernels; the segmented path evaluates every step of an IVP in each
+        // of its passes
+        unsigned long long wk[2] = {0ull, 0ull};
+        if (chunk == 0) {
+            if (cudaMemcpyAsync(wk, a.work, sizeof(wk), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                return PITN_ECUDA;
+        } else {
+            std::vector<int> hi((size_t)B);
+            if (cudaMemcpy(hi.data(), it_d, sizeof(int) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return PITN_ECUDA;
+            for (int64_t b = 0; b < B; ++b) {
+                wk[0] += (unsigned long long)hN[b] * (unsigned long long)(hi[b] + 1);
+                wk[1] += (unsigned long long)hN[b] * (unsigned long long)hi[b];
+            }
+        }
+        g_batch_work[0].store((int64_t)wk[0]);
+        g_batch_work[1].store((int64_t)wk[1]);
+    }
     // host copies of the outputs given as host memory
     auto get = [&](void* dst, const void* src, size_t bytes) {
         return dst == src || cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost) == cudaSuccess;

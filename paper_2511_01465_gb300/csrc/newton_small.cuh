@@ -882,7 +882,7 @@ struct SmallKernel {
 template <class Sys, int VAR = kVarPlain>
 static SmallKernel small_kernel_of() {
     SmallKernel k{&launch_small<Sys, VAR>, &max_blocks_per_sm<Sys, VAR>, Sys::JN + Sys::D, nullptr};
-    if constexpr (VAR == kVarFusedFF || VAR == kVarMixedFF) k.consts = &Sys::host_ff_consts;
+    if constexpr (VAR == kVarFusedFF || VAR == kVarMixedFF) k.consts = &Sys::ff_consts;
     return k;
 }
 

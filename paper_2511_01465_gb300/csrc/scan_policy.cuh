@@ -39,6 +39,9 @@ struct ScanF32 {
     }
     template <class Sys>
     static __device__ __forceinline__ void setup(Sys&, const SmallArgs&) {}
+    // one IVP of a batch: the FP32 constants come with Sys::init
+    template <class Sys>
+    static __device__ __forceinline__ void setup_ivp(Sys&, const double*, double) {}
     template <class Sys>
     static __device__ __forceinline__ void eval(const Sys& sys, const double* xp, const double* xc, double* r,
                                                 T* sv) {
@@ -150,6 +153,14 @@ struct ScanFF {
     // constants from the host (see SmallArgs::fc, dc)
     template <class Sys>
     static __device__ __forceinline__ void setup(Sys& sys, const SmallArgs& a) { sys.init_ff(a.fc, a.dc); }
+    // one IVP of a batch: its constants split here, from its own parameters
+    template <class Sys>
+    static __device__ __forceinline__ void setup_ivp(Sys& sys, const double* p, double h) {
+        float fc[16];
+        double dc[4];
+        Sys::ff_consts(p, h, fc, dc);
+        sys.init_ff(fc, dc);
+    }
     template <class Sys>
     static __device__ __forceinline__ void eval(const Sys& sys, const double* xp, const double* xc, double* r,
                                                 T* jv) {

@@ -109,10 +109,11 @@ struct Lorenz63 {
         J[3] = jv[0]; J[4] = j11;   J[5] = -jv[1];
         J[6] = jv[2]; J[7] = jv[1]; J[8] = j22;
     }
-    // float-float scan: constants split on the host, fc = (h, h rho, 1 - h sigma,
-    // h sigma, 1 - h, 1 - h beta) as hi/lo pairs
+    // float-float scan: constants split once per solve (for one IVP on the
+    // host, for each IVP of a batch on the device), fc = (h, h rho,
+    // 1 - h sigma, h sigma, 1 - h, 1 - h beta) as hi/lo pairs
     ff h_ff, hr_ff, j00_ff, j01_ff, j11_ff, j22_ff;
-    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+    __host__ __device__ static void ff_consts(const double* p, double hh, float* fc, double* dc) {
         const double c[6] = {hh, hh * p[1], 1.0 - hh * p[0], hh * p[0], 1.0 - hh, 1.0 - hh * p[2]};
         for (int i = 0; i < 6; ++i) {
             const ff v = ff_const(c[i]);
@@ -200,9 +201,9 @@ struct VanDerPol {
         h_f = (float)h; hmu_f = (float)hmu; m2hmu_f = (float)m2hmu;
         h_ff = ff_const(h); hmu_ff = ff_const(hmu); m2hmu_ff = ff_const(m2hmu);
     }
-    // float-float constants, split on the host: fc = (h, h mu, -2 h mu) as
-    // hi/lo pairs, dc = (h mu, -2 h mu)
-    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+    // float-float constants, split once per solve: fc = (h, h mu, -2 h mu)
+    // as hi/lo pairs, dc = (h mu, -2 h mu)
+    __host__ __device__ static void ff_consts(const double* p, double hh, float* fc, double* dc) {
         const double c[3] = {hh, hh * p[0], -2.0 * hh * p[0]};
         for (int i = 0; i < 3; ++i) {
             const ff v = ff_const(c[i]);
@@ -332,9 +333,9 @@ struct LinearOsc {
         h_ff = ff_const(h); j10_ff = ff_const(j10); j11_ff = ff_const(j11);
         ww = w * w; zw2 = 2.0 * z * w;
     }
-    // float-float constants, split on the host: fc = (h, j10, j11) as hi/lo
+    // float-float constants, split once per solve: fc = (h, j10, j11) as hi/lo
     // pairs, dc = (w^2, 2 z w)
-    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+    __host__ __device__ static void ff_consts(const double* p, double hh, float* fc, double* dc) {
         const double c[3] = {hh, -hh * p[0] * p[0], 1.0 - 2.0 * hh * p[1] * p[0]};
         for (int i = 0; i < 3; ++i) {
             const ff v = ff_const(c[i]);
@@ -636,9 +637,9 @@ struct RK4Map {
     // ff_params and jf_times_ff) ----
     // The residual is the FP64 one above, operation for operation; the
     // stage chain rule of the Jacobian runs in float-float from the FP64
-    // stage states.  Constants split on the host: (h, h/2, h/6) and the
+    // stage states.  Constants split once per solve: (h, h/2, h/6) and the
     // right-hand side's two.
-    static void host_ff_consts(const double* p, double hh, float* fc, double* dc) {
+    __host__ __device__ static void ff_consts(const double* p, double hh, float* fc, double* dc) {
         double rc[2];
         Rhs::ff_params(p, rc);
         const double c[5] = {hh, 0.5 * hh, hh / 6.0, rc[0], rc[1]};

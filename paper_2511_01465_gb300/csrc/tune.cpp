@@ -104,7 +104,10 @@ int pitn_tune_get(const char* key, int* a, int* b) {
 }
 
 int pitn_tune_set(const char* key, int a, int b) {
-    if (!key || !key[0] || a <= 0 || b <= 0 || std::strlen(key) >= 128) return PITN_EINVAL;
+    if (!key || !key[0] || std::strlen(key) >= 128) return PITN_EINVAL;
+    // threads per CTA: whole warps; b = 0 only in a batch key (the per-IVP path)
+    const bool batch = std::strncmp(key, "batch:", 6) == 0;
+    if (a < 32 || a > 1024 || a % 32 != 0 || b < 0 || (b == 0 && !batch)) return PITN_EINVAL;
     pitn_host::tune_store(key, a, b);
     return PITN_OK;
 }

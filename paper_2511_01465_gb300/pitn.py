@@ -81,6 +81,8 @@ def lib():
         L.pitn_release_workspace.restype = c_int
         L.pitn_launch_count.argtypes = []
         L.pitn_launch_count.restype = i64
+        L.pitn_batch_work.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.pitn_batch_work.restype = c_int
         L.pitn_probe_fma_rate.argtypes = [c_int, ctypes.POINTER(d)]
         L.pitn_probe_fma_rate.restype = c_int
         L.pitn_debug_inject.argtypes = [c_int, i64]
@@ -237,6 +239,13 @@ def pitn_release_workspace():
 
 def pitn_launch_count():
     return lib().pitn_launch_count()
+
+
+def pitn_batch_work():
+    """(steps evaluated, steps replayed) of the most recent batch solve."""
+    ev, rep = ctypes.c_int64(0), ctypes.c_int64(0)
+    check(lib().pitn_batch_work(ctypes.byref(ev), ctypes.byref(rep)), "pitn_batch_work")
+    return int(ev.value), int(rep.value)
 
 
 def pitn_tune_enable(on=True):

@@ -9,7 +9,8 @@ scan), vdp_rk4 (RK4 van der Pol on [0, 10], h = 10 / N, from the ones
 guess, or from the root with --from-root), robertson (backward Euler from
 the zero guess, h = 500 / N), fkpp,
 fkpp_mixed, fkpp_tf32 (d = 128; BF16 / TF32 tensor-core composes),
-batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]), adjoint
+batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]; --precision
+2 / 3 for the FP32 / float-float scans), adjoint
 (Van der Pol batch forward + backward).  Sizes default to the small cases
 used for full captures; prints the outcome of the last repetition.
 """
@@ -76,7 +77,8 @@ def main():
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter, precision=prec)[1]
         elif a.workload == "batch":
             bt = W.lorenz_batch(B=a.B, n_min=a.nmin, n_max=a.nmax)
-            r = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, a.tol, a.max_iter, guard_B=a.guard)
+            r = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, a.tol, a.max_iter, guard_B=a.guard,
+                                precision=a.precision)
             out = {"mean_iters": float(r[2].float().mean()), "converged": int((r[3] == 0).sum())}
         elif a.workload == "adjoint":
             bt = W.vdp_adjoint_batch(B=a.B, N=a.N)

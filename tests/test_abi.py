@@ -115,10 +115,12 @@ def test_tune_set_pins_a_shape(tmp_path, lib):
     cache = tmp_path / "tune.txt"
     code = ("from paper_2511_01465_gb300 import pitn as P; "
             "print(P.pitn_tune_set('small:7:3:22:0:be', 256, 1), P.pitn_tune_get('small:7:3:22:0:be'), "
-            "P.pitn_tune_set('x', 0, 1), P.pitn_tune_set('', 1, 1))")
+            "P.pitn_tune_set('x', 0, 1), P.pitn_tune_set('', 1, 1), P.pitn_tune_set('small:1:3:13:1', 100, 1), "
+            "P.pitn_tune_set('small:1:3:13:1', 128, 0), P.pitn_tune_set('batch:1:3:13:1', 128, 0), "
+            "P.pitn_tune_get('batch:1:3:13:1'))")
     env = dict(os.environ, PITN_TUNE_CACHE=str(cache))
     out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
                          timeout=120)
     assert out.returncode == 0, out.stderr
-    assert out.stdout.strip() == "0 (256, 1) -1 -1"
-    assert cache.read_text().split() == ["small:7:3:22:0:be", "256", "1"]
+    assert out.stdout.strip() == "0 (256, 1) -1 -1 -1 -1 0 (128, 0)"
+    assert sorted(cache.read_text().splitlines()) == ["batch:1:3:13:1 128 0", "small:7:3:22:0:be 256 1"]

@@ -32,9 +32,10 @@ def relerr(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def run_batch(pk, bt, tol, max_iter, guard_B, tile_elems=0):
+def run_batch(pk, bt, tol, max_iter, guard_B, tile_elems=0, precision=0):
     traj, offs, iters, status, res = pk.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, tol,
-                                                    max_iter, guard_B=guard_B, tile_elems=tile_elems)
+                                                    max_iter, guard_B=guard_B, tile_elems=tile_elems,
+                                                    precision=precision)
     return (traj.cpu().numpy(), offs.cpu().numpy(), iters.cpu().numpy(), status.cpu().numpy(),
             res.cpu().numpy())
 
@@ -190,3 +191,84 @@ def test_default_shape_takes_per_ivp_path(pk):
     out = run_batch(pk, bt, 1e-10, 60, 0.0)
     assert pk.pitn_launch_count() - l0 == 3
     compare(bt, out, 1e-10, 60, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# The reduced-precision scans on the per-IVP path (an inexact Newton step;
+# residual, stopping test and update in FP64): every IVP the FP64 oracle
+# solves is solved, its FP64 residual re-checked by the oracle, its iterate
+# within the path's bar (FP32 scan 1e-6, float-float 1e-10) of the oracle's
+# at the same count, else of the sequential root beyond the oracle's own
+# distance from it; the float-float solve's plain-Newton counts equal the
+# oracle's.
+# ---------------------------------------------------------------------------
+def reduced_case(kind):
+    if kind == "vdp_plain":
+        rng = np.random.default_rng(5)
+        B = 24
+        bt = W.Batch("vdp", W.VDP, rng.uniform(0.5, 2.0, (B, 1)), rng.uniform(-2, 2, (B, 2)),
+                     np.full(B, 1e-3), rng.integers(1, 3000, B).astype(np.int64))
+        bt.N[:4] = [1, 2, 3, 257]
+        return bt, 60, 0.0
+    if kind == "osc_plain":
+        rng = np.random.default_rng(8)
+        B = 16
+        bt = W.Batch("osc", W.LINEAR_OSC, np.column_stack([rng.uniform(0.5, 2.0, B), rng.uniform(0.0, 0.3, B)]),
+                     rng.uniform(-2, 2, (B, 2)), np.full(B, 1e-3), rng.integers(1, 5000, B).astype(np.int64))
+        return bt, 10, 0.0
+    return W.lorenz_batch(B=40, seed=3, n_min=1, n_max=3000), 400, 100.0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "ff"])
+@pytest.mark.parametrize("kind", ["vdp_plain", "osc_plain", "lorenz_guard"])
+def test_reduced_precision_batch(pk, precision, kind):
+    from paper_2511_01465_gb300 import pitn as P
+    prec = P.PITN_PREC_MIXED_FP32 if precision == "fp32" else P.PITN_PREC_FP64_FF
+    bar = 1e-6 if precision == "fp32" else 1e-10
+    tol = 1e-11
+    bt, it, gb = reduced_case(kind)
+    traj, offs, iters, status, res = run_batch(pk, bt, tol, it, gb, precision=prec)
+    assert offs[0] == 0 and np.array_equal(np.diff(offs), bt.N)
+    solved = 0
+    for b in range(bt.B):
+        o = O.newton(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b], tol, it, guard_B=gb)
+        if o["status"] != O.OK:
+            continue
+        solved += 1
+        g = traj[offs[b]:offs[b + 1]]
+        assert status[b] == O.OK and res[b] <= tol, (b, status[b], res[b])
+        _, r, nf = O.residual(bt.system, bt.params[b], bt.x0[b], bt.h[b], g)
+        assert not nf and r <= tol * (1 + 1e-6), (b, r)
+        if iters[b] == o["iters"]:
+            assert relerr(g, o["traj"]) <= bar, (b, relerr(g, o["traj"]))
+        else:
+            # another count: the iterate stops elsewhere within the tolerance;
+            # against the sequential root, allowing the FP64 iterate's own
+            # distance from it at this tolerance
+            seq = O.sequential(bt.system, bt.params[b], bt.x0[b], bt.h[b], bt.N[b])
+            assert relerr(g, seq) <= bar + relerr(o["traj"], seq), (b, relerr(g, seq))
+        if precision == "ff" and gb <= 0:
+            assert iters[b] == o["iters"], (b, iters[b], o["iters"])
+    assert solved >= bt.B // 2
+
+
+def test_reduced_precision_batch_paths(pk):
+    """The reduced-precision scans exist on the per-IVP path only: a tiled
+    (segmented) request is an argument error, a pinned segmented shape is
+    unsupported, a pinned per-IVP shape runs."""
+    from paper_2511_01465_gb300 import pitn as P
+    bt = W.lorenz_batch(B=8, seed=1, n_min=10, n_max=200)
+    with pytest.raises(P.PitnError):
+        run_batch(pk, bt, 1e-10, 50, 100.0, tile_elems=16, precision=P.PITN_PREC_MIXED_FP32)
+    M = int(bt.N.sum())
+    key = f"batch:{bt.system}:{bt.d}:{M.bit_length() - 1}:1:f32"
+    P.pitn_tune_clear()
+    try:
+        P.pitn_tune_set(key, 256, 16)
+        with pytest.raises(P.PitnError):
+            run_batch(pk, bt, 1e-10, 50, 100.0, precision=P.PITN_PREC_MIXED_FP32)
+        P.pitn_tune_set(key, 64, 0)
+        out = run_batch(pk, bt, 1e-10, 50, 100.0, precision=P.PITN_PREC_MIXED_FP32)
+        assert (out[3] == O.OK).all()
+    finally:
+        P.pitn_tune_clear()
