@@ -603,7 +603,8 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
         Sys sys;
         sys.init(a.params + b * Sys::P, a.h[b]);
         const double* x0 = a.x0 + b * D;
-        double* Xb[2] = {a.X0 + base * D, a.X1 + base * D};
+        double* const XA = a.X0 + base * D;
+        double* const XB = a.X1 + base * D;
         double* scr = a.scratch + base * W;
         const long long T = blockDim.x;
         int cur = 0, it = 0, status = PITN_NOT_CONVERGED;
@@ -619,8 +620,8 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
             for (int i = 0; i < D; ++i) o[i] = src[i];
         };
         for (;; ++it) {
-            const double* Xc = Xb[cur];
-            double* Xn = Xb[cur ^ 1];
+            const double* Xc = cur ? XB : XA;
+            double* Xn = cur ? XA : XB;
             if (threadIdx.x == 0) { s_res = 0ull; s_q = 0ull; }
             // Steps from sfill on lie in the guard's fill region (every state
             // x_{q-1}; at the constant guess every state x0): all their
@@ -797,11 +798,12 @@ __global__ void __launch_bounds__(512) batch_ivp_kernel(BatchArgs a, const long 
 // float-float).  The scratch holds the policy's values (at most 8 bytes
 // each, in the FP64 path's slots).
 template <class Sys, class Pol>
-__global__ void __launch_bounds__(256) batch_ivp_mixed_kernel(BatchArgs a, const long long* __restrict__ order,
+__global__ void __launch_bounds__(Pol::kBatchThreads, Pol::kBatchMinBlocks) batch_ivp_mixed_kernel(BatchArgs a, const long long* __restrict__ order,
                                                               unsigned long long* __restrict__ queue) {
     using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D, W = JN + D;
     static_assert(sizeof(T) <= sizeof(double), "scratch slots are 8 bytes");
+    static_assert(Pol::kBatchThreads <= kMaxWarps * 32, "the policy's CTA scan holds kMaxWarps warps");
     __shared__ T s_wex[kMaxWarps][E];
     __shared__ T s_tot[E];
     __shared__ long long s_b;
@@ -822,7 +824,8 @@ __global__ void __launch_bounds__(256) batch_ivp_mixed_kernel(BatchArgs a, const
         sys.init(a.params + b * Sys::P, a.h[b]);
         Pol::setup_ivp(sys, a.params + b * Sys::P, a.h[b]);
         const double* x0 = a.x0 + b * D;
-        double* Xb[2] = {a.X0 + base * D, a.X1 + base * D};
+        double* const XA = a.X0 + base * D;
+        double* const XB = a.X1 + base * D;
         T* scr = reinterpret_cast<T*>(a.scratch + base * W);
         const long long Tn = blockDim.x;
         int cur = 0, it = 0, status = PITN_NOT_CONVERGED;
@@ -838,8 +841,8 @@ __global__ void __launch_bounds__(256) batch_ivp_mixed_kernel(BatchArgs a, const
             for (int i = 0; i < D; ++i) o[i] = src[i];
         };
         for (;; ++it) {
-            const double* Xc = Xb[cur];
-            double* Xn = Xb[cur ^ 1];
+            const double* Xc = cur ? XB : XA;
+            double* Xn = cur ? XA : XB;
             if (threadIdx.x == 0) { s_res = 0ull; s_q = 0ull; }
             // regular steps [0, sfill) and the fill region, weighted as in
             // batch_ivp_kernel
@@ -1056,7 +1059,7 @@ int batch_run_ivp(BatchArgs& a, int block, cudaStream_t st, const long long* ord
     if constexpr (std::is_void<Pol>::value) {
         kern = batch_ivp_kernel<Sys>;
     } else {
-        if (block > kMaxWarps * 32) return PITN_EUNSUPPORTED;   // the policy's CTA scan
+        if (block > Pol::kBatchThreads) return PITN_EUNSUPPORTED;   // the kernel's launch bound
         kern = batch_ivp_mixed_kernel<Sys, Pol>;
     }
     const int eg = (int)std::min<long long>((a.B + 255) / 256, 1024);

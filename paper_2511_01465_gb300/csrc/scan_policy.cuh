@@ -21,6 +21,8 @@ struct ScanF32 {
     template <class Sys>
     static constexpr int min_blocks() { return 0; }
     static constexpr bool kRollScans = false;
+    // per-IVP batch kernel: threads per CTA at most, CTAs per SM at least
+    static constexpr int kBatchThreads = 256, kBatchMinBlocks = 0;   // (0: the compiler's own choice)
     template <int D>
     static __device__ __forceinline__ void ident(T* Q, T* c) { dz_zero<D>(Q, c); }
     template <int D>
@@ -98,6 +100,9 @@ struct ScanFF {
     // within the instruction caches (unrolled, the d = 3 kernel's warps
     // waited on instruction fetch more than on anything else).
     static constexpr bool kRollScans = true;
+    // per-IVP batch kernel: 128-thread CTAs, three per SM (at most 170
+    // registers: the d = 3 kernel's 194 left two per SM)
+    static constexpr int kBatchThreads = 128, kBatchMinBlocks = 3;
     template <int D>
     static __device__ __forceinline__ void ident(T* P, T* c) {
 #pragma unroll
