@@ -79,7 +79,9 @@ def main():
             bt = W.lorenz_batch(B=a.B, n_min=a.nmin, n_max=a.nmax)
             r = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, a.tol, a.max_iter, guard_B=a.guard,
                                 precision=a.precision)
-            out = {"mean_iters": float(r[2].float().mean()), "converged": int((r[3] == 0).sum())}
+            from .pitn import pitn_batch_work
+            out = {"mean_iters": float(r[2].float().mean()), "converged": int((r[3] == 0).sum()),
+                   "steps_evaluated_replayed": pitn_batch_work()}
         elif a.workload == "adjoint":
             bt = W.vdp_adjoint_batch(B=a.B, N=a.N)
             traj, offs, it, st, res = api.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, 1e-12,
