@@ -43,9 +43,17 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28941035264 + 24169681408, "bb76b2b48a7d82ec"),        # 147 passes
-    "vdp_ff": (25447224576 + 27272660480, "bb76b2b48a7d82ec"),     # 151 passes (fused float-float kernel)
-    "vdp_mixed": (13103398656 + 15208973056, "bb76b2b48a7d82ec"),  # 137 passes (fused FP32-scan kernel)
+    "vdp": (28936933632 + 24168118528, "e4c3f760f8e9fb97"),  # 147 passes, newton_small_kernel<VanDerPol>
+    "vdp_ff": (25449432832 + 27272645376, "e4c3f760f8e9fb97"),  # 151 passes, newton_fused_mixed_kernel<VanDerPol, ScanFF>
+    "vdp_mixed": (13103136000 + 15207755520, "e4c3f760f8e9fb97"),  # 137 passes, newton_fused_mixed_kernel<VanDerPol, ScanF32>
+    "lorenz": (142080 + 47104, "e4c3f760f8e9fb97"),  # 64 passes, newton_small_kernel<Lorenz63>
+    "lorenz_ff": (270592 + 36096, "e4c3f760f8e9fb97"),  # 62 passes, newton_small_mixed_kernel<Lorenz63, ScanFF>
+    "lorenz_mixed": (99584 + 20224, "e4c3f760f8e9fb97"),  # 52 passes, newton_small_mixed_kernel<Lorenz63, ScanF32>
+    "vdp_rk4": (30531072 + 347592448, "e4c3f760f8e9fb97"),  # 8 passes, newton_fused_kernel<RK4Map<VdpRhs>>
+    "vdp_rk4_ff": (41264384 + 336654336, "e4c3f760f8e9fb97"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanFF>
+    "vdp_rk4_mixed": (16181248 + 20568576, "e4c3f760f8e9fb97"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanF32>
+    "robertson": (13366389248 + 13725486336, "e4c3f760f8e9fb97"),  # 22 passes, newton_fused_kernel<BackwardEulerMap<RobertsonRhs>>
+    "osc": (102368512 + 197437952, "e4c3f760f8e9fb97"),  # 2 passes, newton_small_kernel<LinearOsc>
 }
 
 
