@@ -264,11 +264,10 @@ int64_t pitn_launch_count(void);
 /* Work of the most recent pitn_solve_batch in this process (instrumentation
  * for throughput figures): the steps whose residual and Jacobian were
  * evaluated and folded, and the steps whose Newton step was replayed,
- * summed over its IVPs and passes.  The per-IVP path counts them in its
- * kernel (a guard's fill region costs one evaluation per thread, and a
- * thread's replay ends at its first cut); the segmented path evaluates
- * every step of a running IVP in each pass.  Both 0 before the first batch
- * solve.  Returns PITN_EINVAL for a NULL pointer. */
+ * summed over its IVPs and passes, as the kernels count them (on both
+ * paths a thread's share of a guard's fill region costs one evaluation, and
+ * a thread's replay of an IVP ends at its first cut).  Both 0 before the
+ * first batch solve.  Returns PITN_EINVAL for a NULL pointer. */
 int pitn_batch_work(int64_t* evaluated, int64_t* replayed);
 
 /*

@@ -169,6 +169,20 @@ __device__ __forceinline__ bool cta_has_work(const BatchArgs& a, long long kf, l
     return s_any != 0;
 }
 
+// Adds a thread's step counts (evaluated, replayed) to the solve's totals;
+// every thread of the warp calls it.
+__device__ __forceinline__ void b_flush_work(const BatchArgs& a, unsigned long long ev, unsigned long long rep) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ev += __shfl_xor_sync(0xffffffffu, ev, off);
+        rep += __shfl_xor_sync(0xffffffffu, rep, off);
+    }
+    if ((threadIdx.x & 31) == 0 && a.work) {
+        atomicAdd(a.work, ev);
+        atomicAdd(a.work + 1, rep);
+    }
+}
+
 // ---- A ----------------------------------------------------------------------
 template <class Sys>
 __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
@@ -195,7 +209,7 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
 #pragma unroll
     for (int j = 0; j < D; ++j) c[j] = 0.0;
     long long b = -1, base = 0, next = 0;
-    unsigned long long mres = 0ull;
+    unsigned long long mres = 0ull, n_ev = 0ull;
     IvpState s{};
     Sys sys;
     double xp[D];
@@ -213,9 +227,43 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
         }
         if (!s.active) continue;  // frozen IVP: identity element
         const long long j = k - base;
+        {
+            // steps from the guard's fill start on all hold x_{q-1} (x0 at the
+            // constant guess): this chunk's share of them is one element,
+            // raised to its count by binary powering; their scratch rows are
+            // not written (the replay evaluates the element itself)
+            const long long nb = next - base;
+            const long long sf = (s.q < nb) ? (s.q > 1 ? s.q : 1LL) : nb;
+            if (j >= sf) {
+                const long long kend = min(k1, next);
+                double xf[D], rf[D], jvf[JN], EP[D * D], Ec[D], RP[D * D], Rc[D];
+                b_state<D>(a, s, b, base, s.q - 1, xf);
+                sys.eval(xf, xf, rf, jvf);
+#pragma unroll
+                for (int i = 0; i < D; ++i) {
+                    const unsigned long long bits = abs_bits(rf[i]);
+                    mres = bits > mres ? bits : mres;
+                    Ec[i] = -rf[i];
+                    Rc[i] = 0.0;
+                }
+                ++n_ev;
+                sys.jfull(jvf, EP);
+                b_identity<D>(RP);
+                for (long long e = kend - k;;) {
+                    if (e & 1) b_compose<D>(EP, Ec, RP, Rc, RP, Rc);
+                    e >>= 1;
+                    if (!e) break;
+                    b_compose<D>(EP, Ec, EP, Ec, EP, Ec);
+                }
+                b_compose<D>(RP, Rc, P, c, P, c);
+                k = kend - 1;   // the IVP's last step in this chunk
+                continue;
+            }
+        }
         double x[D], r[D], jv[JN];
         b_state<D>(a, s, b, base, j, x);
         sys.eval(xp, x, r, jv);
+        ++n_ev;
 #pragma unroll
         for (int i = 0; i < JN; ++i) a.scratch[k * W + i] = jv[i];
 #pragma unroll
@@ -338,6 +386,7 @@ __global__ void __launch_bounds__(256) batch_fold_kernel(BatchArgs a) {
 #pragma unroll
     for (int i = 0; i < D; ++i) te[D * D + i] = tc[i];
     if (threadIdx.x < E) a.agg[(size_t)blockIdx.x * E + threadIdx.x] = s_tot[threadIdx.x];
+    b_flush_work(a, n_ev, 0ull);
 }
 
 // ---- D ----------------------------------------------------------------------
@@ -392,9 +441,9 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
         for (int i = 0; i < D; ++i) s_zin[i] = z[i];
     }
     __syncthreads();
-    if (k0 >= k1) return;
+    unsigned long long n_rep = 0ull;
     double z[D];
-    {
+    if (k0 < k1) {
         const double* te = a.texcl + (size_t)gt * E;
         double tP[D * D], tc[D], zi[D];
 #pragma unroll
@@ -403,10 +452,11 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
         for (int i = 0; i < D; ++i) { tc[i] = te[D * D + i]; zi[i] = s_zin[i]; }
         b_apply<D>(tP, tc, zi, z);
     }
-    long long b = -1, base = 0, next = 0;
+    long long b = -1, base = 0, next = 0, sf = 0;
     IvpState s{};
     Sys sys;
-    bool found = false;
+    bool found = false, have_fill = false;
+    double xf[D], rf[D], jvf[JN];   // the IVP's fill element (its scratch rows are not written)
     for (long long k = k0; k < k1; ++k) {
         if (k >= next || b < 0) {
             b = (b < 0) ? seg_of(a.off, a.B, k) : b + 1;
@@ -416,15 +466,34 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
             s = a.st[b];
             sys.init(a.params + b * Sys::P, a.h[b]);
             found = false;
+            have_fill = false;
+            const long long nb = next - base;
+            sf = (s.q < nb) ? (s.q > 1 ? s.q : 1LL) : nb;
         }
         if (!s.stepping) continue;
+        if (found) {   // past this thread's first cut: never read again
+            k = next - 1;
+            continue;
+        }
         const long long j = k - base;
         double jv[JN], r[D], x[D];
+        if (j < sf) {
 #pragma unroll
-        for (int i = 0; i < JN; ++i) jv[i] = a.scratch[k * W + i];
+            for (int i = 0; i < JN; ++i) jv[i] = a.scratch[k * W + i];
 #pragma unroll
-        for (int i = 0; i < D; ++i) r[i] = a.scratch[k * W + JN + i];
-        b_state<D>(a, s, b, base, j, x);
+            for (int i = 0; i < D; ++i) r[i] = a.scratch[k * W + JN + i];
+            b_state<D>(a, s, b, base, j, x);
+        } else {
+            if (!have_fill) {
+                b_state<D>(a, s, b, base, s.q - 1, xf);
+                sys.eval(xf, xf, rf, jvf);
+                have_fill = true;
+            }
+#pragma unroll
+            for (int i = 0; i < JN; ++i) jv[i] = jvf[i];
+#pragma unroll
+            for (int i = 0; i < D; ++i) { r[i] = rf[i]; x[i] = xf[i]; }
+        }
         if (j == 0) {
 #pragma unroll
             for (int i = 0; i < D; ++i) z[i] = -r[i];
@@ -442,11 +511,13 @@ __global__ void __launch_bounds__(256) batch_replay_kernel(BatchArgs a) {
             const unsigned long long bits = abs_bits(z[i]);
             zb = bits > zb ? bits : zb;
         }
+        ++n_rep;
         if (!found && zb > a.cap_bits) {
             found = true;
             atomicMax(&a.st[b].qenc, ~(unsigned long long)j);
         }
     }
+    b_flush_work(a, 0ull, n_rep);   // (threads without steps took no pass through the loop)
 }
 
 // ---- E ----------------------------------------------------------------------
@@ -562,18 +633,6 @@ __device__ __forceinline__ void b_cta_scan(double* P, double* c, double (*s_w)[D
 // powers one element), before it only its replay.
 constexpr long long kBatchFillWeight = 4;
 
-// Adds a thread's step counts of the per-IVP path to the solve's totals.
-__device__ __forceinline__ void b_flush_work(const BatchArgs& a, unsigned long long ev, unsigned long long rep) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        ev += __shfl_xor_sync(0xffffffffu, ev, off);
-        rep += __shfl_xor_sync(0xffffffffu, rep, off);
-    }
-    if ((threadIdx.x & 31) == 0 && a.work) {
-        atomicAdd(a.work, ev);
-        atomicAdd(a.work + 1, rep);
-    }
-}
 
 // One CTA solves whole IVPs, taken from a queue in the host's order (longest
 // first): the Newton loop of each IVP runs with CTA-level scans only, so no
@@ -1408,23 +1467,11 @@ extern "C" int pitn_solve_batch(int system_id, int64_t B, const double* params, 
     int rc = run_shape(block, chunk, &its_final);
     if (rc != PITN_OK) return rc;
     {
-        // step counts of the solve (pitn_batch_work): counted by the per-IVP
-        // kernels; the segmented path evaluates every step of an IVP in each
-        // of its passes
+        // step counts of the solve (pitn_batch_work), counted by the kernels
         unsigned long long wk[2] = {0ull, 0ull};
-        if (chunk == 0) {
-            if (cudaMemcpyAsync(wk, a.work, sizeof(wk), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess)
-                return PITN_ECUDA;
-        } else {
-            std::vector<int> hi((size_t)B);
-            if (cudaMemcpy(hi.data(), it_d, sizeof(int) * B, cudaMemcpyDeviceToHost) != cudaSuccess)
-                return PITN_ECUDA;
-            for (int64_t b = 0; b < B; ++b) {
-                wk[0] += (unsigned long long)hN[b] * (unsigned long long)(hi[b] + 1);
-                wk[1] += (unsigned long long)hN[b] * (unsigned long long)hi[b];
-            }
-        }
+        if (cudaMemcpyAsync(wk, a.work, sizeof(wk), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return PITN_ECUDA;
         g_batch_work[0].store((int64_t)wk[0]);
         g_batch_work[1].store((int64_t)wk[1]);
     }
