@@ -272,3 +272,19 @@ def test_reduced_precision_batch_paths(pk):
         assert (out[3] == O.OK).all()
     finally:
         P.pitn_tune_clear()
+
+
+@pytest.mark.parametrize("tile_elems", [0, 16])
+def test_batch_work_counts(pk, tile_elems):
+    """pitn_batch_work: the kernels' own counts of the steps they evaluated
+    and replayed.  At most every step of an IVP in each of its passes
+    (residual passes = updates + 1, replays = updates), fewer when the guard
+    leaves a fill region, and at least one evaluation per pass."""
+    from paper_2511_01465_gb300 import pitn as P
+    bt = W.lorenz_batch(B=40, seed=3, n_min=1, n_max=3000)
+    out = run_batch(pk, bt, 1e-10, 50, 100.0, tile_elems=tile_elems)
+    iters = out[2].astype(np.int64)
+    ev, rep = P.pitn_batch_work()
+    assert 0 < ev <= int((bt.N * (iters + 1)).sum())
+    assert 0 <= rep <= int((bt.N * iters).sum())
+    assert ev >= int((iters + 1).sum())
