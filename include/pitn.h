@@ -101,9 +101,11 @@ enum {
                                   stopping test and update in FP64.  An
                                   inexact Newton step */
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC) with explicit
-                                  Euler, and VDP with RK4 (not in the paper; the
+                                  Euler, VDP with RK4 (not in the paper; the
                                   stage chain rule of S in FP32 from the FP64
-                                  stage states): the scan's elements in FP32
+                                  stage states), and backward Euler (ROBERTSON,
+                                  DAHLQUIST, VDP, LOGISTIC; S = M^-1 - I from
+                                  the FP64 inverse): the scan's elements in FP32
                                   delta form (I + S, c); an inexact Newton step */
     PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63) with explicit
                                   Euler, and VDP with RK4 (not in the paper): the

@@ -8,14 +8,28 @@
 // whose eval(x_{n-1}, x_n) yields the scan element of step n; for backward
 // Euler that element is (M_n^{-1}, -M_n^{-1} h_n) with M_n = I - h Jf(x_n)
 // (eqs. 3.16-3.19), built by BackwardEulerMap in systems.cuh; TrapezoidMap
-// builds the trapezoidal rule's.  The FP32
-// delta form and the batched and adjoint entry points are explicit-only.
+// builds the trapezoidal rule's.  Backward Euler also runs with the FP32
+// delta-form scan (the fused reduced-precision kernel, newton_fused_mixed.cuh);
+// the batched and adjoint entry points are explicit-only.
 #include "newton_small.cuh"
 
 namespace pitn_host {
 
-int select_implicit_kernel(int system_id, int method, pitn::SmallKernel* K) {
+int select_implicit_kernel(int system_id, int method, int precision, pitn::SmallKernel* K) {
     using namespace pitn;
+    if (precision == PITN_PREC_MIXED_FP32) {
+        // backward Euler with the FP32 delta-form scan: the residual and the
+        // inverse of I - h Jf stay FP64, the folds, scans and replay FP32
+        if (method != PITN_STEP_BACKWARD_EULER) return PITN_EUNSUPPORTED;
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>, kVarFusedMixed>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (precision != PITN_PREC_FP64) return PITN_EUNSUPPORTED;
     if (method == PITN_STEP_BACKWARD_EULER) {
         switch (system_id) {
         case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>, kVarFused>(); return PITN_OK;

@@ -81,6 +81,8 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
         *K = small_kernel_of<RK4Map<VdpRhs>, kVarFusedMixed>();
         return PITN_OK;
     }
+    if (precision == PITN_PREC_MIXED_FP32 && method == PITN_STEP_BACKWARD_EULER)
+        return select_implicit_kernel(system_id, method, precision, K);
     if (precision == PITN_PREC_MIXED_FP32) {
         // the d = 2 FP32-scan solves run fused: their FP64 work (residual,
         // update) is light enough that one pass per iteration beats two (van
@@ -114,7 +116,7 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
         default: break;
         }
     }
-    return select_implicit_kernel(system_id, method, K);
+    return select_implicit_kernel(system_id, method, precision, K);
 }
 
 // One solve with an explicit launch shape: `block` threads per CTA, at most

@@ -891,5 +891,5 @@ static SmallKernel small_kernel_of() {
 namespace pitn_host {
 // Instantiations for the backward Euler map and for the stiff test systems
 // (newton_implicit.cu); PITN_EUNSUPPORTED for combinations not built.
-int select_implicit_kernel(int system_id, int method, pitn::SmallKernel* K);
+int select_implicit_kernel(int system_id, int method, int precision, pitn::SmallKernel* K);
 }  // namespace pitn_host

@@ -875,6 +875,19 @@ struct BackwardEulerMap : RK4Map<Rhs> {
         small_inverse<D>(M, jv);
         this->jvec(jv, hn, res);
     }
+    // FP32 delta-form scan (PITN_PREC_MIXED_FP32): the FP64 residual and
+    // inverse of eval; the element's S = M_n^{-1} - I formed in FP64 and
+    // rounded to FP32 on the integer pipes (dense, row-major)
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res, float* sv) const {
+        double Mi[D * D];
+        eval(xp, xc, res, Mi);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) sv[i] = d2f_int((i % (D + 1) == 0) ? Mi[i] - 1.0 : Mi[i]);
+    }
+    __device__ __forceinline__ void sfull(const float* sv, float* S) const {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) S[i] = sv[i];
+    }
 };
 
 

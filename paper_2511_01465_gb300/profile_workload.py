@@ -7,7 +7,7 @@
 Workloads: vdp, lorenz, osc (single IVP; --precision 2 for the FP32 delta
 scan), vdp_rk4 (RK4 van der Pol on [0, 10], h = 10 / N, from the ones
 guess, or from the root with --from-root), robertson (backward Euler from
-the zero guess, h = 500 / N), fkpp,
+the zero guess, h = 500 / N; --precision 2 for the FP32 scan), fkpp,
 fkpp_mixed, fkpp_tf32 (d = 128; BF16 / TF32 tensor-core composes),
 batch (Lorenz batch, --B IVPs of lengths in [--nmin, --nmax]; --precision
 2 / 3 for the FP32 / float-float scans), adjoint
@@ -69,7 +69,8 @@ def main():
         elif a.workload == "robertson":
             wl = W.robertson(h=500.0 / a.N)
             out = api.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, a.tol, a.max_iter,
-                            guess=np.zeros((wl.N, wl.d)), method=PITN_STEP_BACKWARD_EULER)[1]
+                            guess=np.zeros((wl.N, wl.d)), method=PITN_STEP_BACKWARD_EULER,
+                            precision=a.precision)[1]
         elif a.workload in ("fkpp", "fkpp_mixed", "fkpp_tf32"):
             wl = W.fkpp(N=a.N)
             prec = {"fkpp": PITN_PREC_FP64, "fkpp_mixed": PITN_PREC_MIXED_BF16,

@@ -135,9 +135,12 @@ def test_implicit_unsupported_combinations(pk):
     from paper_2511_01465_gb300 import pitn as P
     with pytest.raises(P.PitnError):   # no backward Euler instantiation for Lorenz-63
         pk.solve(1, [10, 28, 8 / 3], [1, 1, 1], 1e-3, 100, 1e-10, 5, method=pk.PITN_STEP_BACKWARD_EULER)
-    with pytest.raises(P.PitnError):   # the FP32 delta form is explicit-only
+    with pytest.raises(P.PitnError):   # the FP32 delta form: explicit maps and backward Euler only
         pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
-                 method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)
+                 method=pk.PITN_STEP_TRAPEZOID, precision=pk.PITN_PREC_MIXED_FP32)
+    with pytest.raises(P.PitnError):   # no float-float scan for the implicit rules
+        pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
+                 method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_FP64_FF)
 
 
 def test_bench_size_robertson(pk):
@@ -166,3 +169,42 @@ def test_implicit_singular_step_matrix(pk, rule):
     m, lam = ((pk.PITN_STEP_BACKWARD_EULER, 2.0) if rule == "backward_euler" else (pk.PITN_STEP_TRAPEZOID, 4.0))
     traj, info = pk.solve(O.DAHLQUIST, [lam], [1.0], 0.5, 20, 1e-12, 10, guess=np.zeros((20, 1)), method=m)
     assert info["status"] == pk.PITN_NONFINITE and info["iters"] == 0
+
+
+# ---------------------------------------------------------------------------
+# Backward Euler with the FP32 delta-form scan (an inexact Newton step): the
+# residual M_n^{-1} h_n, the inverse and the update stay FP64, the element's
+# S = M_n^{-1} - I is rounded to FP32.  It must reach the same FP64 residual
+# tolerance, pass the oracle's residual test, and stay within 1e-6 (against
+# the largest state) of the FP64 oracle's root; its Newton count is reported,
+# not required to match.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_backward_euler_fp32_scan(pk, case):
+    _, sys, p, x0, h, N, gv, B = case
+    d = len(x0)
+    guess = None if gv is None else np.full((N, d), gv)
+    traj, info = pk.solve(sys, p, x0, h, N, 1e-12, 150, guard_B=B, guess=guess, history=True,
+                          method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)
+    o = O.newton(sys, p, x0, h, N, 1e-12, 150, guard_B=B, guess=guess, method=O.BACKWARD_EULER)
+    assert o["status"] == O.OK
+    assert info["status"] == pk.PITN_OK and info["final_res"] <= 1e-12
+    t = traj.cpu().numpy()
+    _, res, nf = O.residual(sys, p, x0, h, t, method=O.BACKWARD_EULER)
+    assert not nf and res <= 1e-12 * (1 + 1e-6)
+    assert np.abs(t - o["traj"]).max() <= 1e-6 * np.abs(o["traj"]).max()
+
+
+def test_bench_size_robertson_fp32_scan(pk):
+    """The implicit bench workload (backward Euler, h = 1e-4, N = 5e6, zero
+    guess, tol 1e-8) with the FP32 scan: converged, its returned trajectory
+    passing the oracle's implicit residual test, the linear invariant
+    y1 + y2 + y3 = 1 of the exact root kept to the residual's level."""
+    wl = W.robertson(h=1e-4)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, 1e-8, 60, guess=np.zeros((wl.N, wl.d)),
+                          history=True, method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)
+    assert info["status"] == pk.PITN_OK and info["final_res"] <= 1e-8
+    t = traj.cpu().numpy()
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, t, method=O.BACKWARD_EULER)
+    assert not nf and res <= 1e-8 * (1 + 1e-6)
+    assert np.abs(t.sum(axis=1) - 1.0).max() <= 1e-6
