@@ -5,7 +5,7 @@ update until ||h||_inf <= tol) of the selected workload, inputs resident on
 the device.  Prints ONE JSON line (rank 0).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload vdp|vdp_mixed|vdp_ff|vdp_rk4|vdp_rk4_ff|vdp_rk4_mixed|lorenz|lorenz_mixed|lorenz_ff|osc|
-                                                      robertson|robertson_mixed|fkpp|fkpp_mixed|fkpp_tf32|batch|batch_small|adjoint]
+                                                      robertson|robertson_mixed|robertson_ff|fkpp|fkpp_mixed|fkpp_tf32|batch|batch_small|adjoint]
     python bench.py --impl reference ...     # the CPU oracle, timed on the host cores
 
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica of
@@ -146,7 +146,11 @@ REDUCED_FP64 = {"vdp_mixed": (9.0, 13.0), "vdp_ff": (11.0, 15.0), "lorenz_mixed"
                 # (one division counted as 1 flop), M^-1 h_n, S's diagonal and the
                 # update: 104 flops from the source; 74.8 FP64 instructions per step
                 # and pass as counted by ncu (DFMA + DMUL + DADD thread instructions)
-                "robertson_mixed": (74.8, 104.0)}
+                "robertson_mixed": (74.8, 104.0),
+                # the same FP64 work with the float-float update instead of S's
+                # diagonal and the FP32 update: 69.8 FP64 instructions per step and
+                # pass as counted by ncu
+                "robertson_ff": (69.8, 104.0)}
 # Fisher-KPP (d padded to 128): per step, fold of the dense column block
 # (4 flops per entry in the working precision) + FP64 residual/diagonal and
 # vector fold; per compose 2*128^3.
@@ -211,6 +215,12 @@ def workload(name):
                     desc="robertson k=(0.04,3e7,1e4) y0=(1,0,0) on [0,500], backward Euler h=1e-4 N=5e6, "
                          "plain Newton from the zero guess (Sec. 4.2), preconditioned residual; scan in FP32 "
                          "delta form (inexact Newton), FP64 residual, inverse and update")
+    if name == "robertson_ff":
+        return dict(kind="single", wl=W.robertson(h=1e-4), tol=1e-8, max_iter=60, guard_B=0.0, method=2,
+                    precision=3, guess=0.0,
+                    desc="robertson k=(0.04,3e7,1e4) y0=(1,0,0) on [0,500], backward Euler h=1e-4 N=5e6, "
+                         "plain Newton from the zero guess (Sec. 4.2), preconditioned residual; scan in "
+                         "double-FP32 (float-float), FP64 residual, inverse and update")
     if name == "fkpp":
         return dict(kind="single", wl=W.fkpp(), tol=1e-8, max_iter=50, guard_B=0.0, precision=0,
                     desc="fisher_kpp MOL d=128 D=1e-3 h=5e-5 N=2^15, plain Newton, FP64 scan")
@@ -1029,6 +1039,7 @@ def oracle_passes(name, fallback):
            "fkpp": "fkpp_d128_2^15_plain_tol1e-8_it50", "fkpp_mixed": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "fkpp_tf32": "fkpp_d128_2^15_plain_tol1e-8_it50",
            "robertson": "robertson_5e6_be_zeros_tol1e-8_it60", "robertson_mixed": "robertson_5e6_be_zeros_tol1e-8_it60",
+           "robertson_ff": "robertson_5e6_be_zeros_tol1e-8_it60",
            "vdp_rk4": "vdp_rk4_1e6_ones_tol1e-8_it50",
            "vdp_rk4_ff": "vdp_rk4_1e6_ones_tol1e-8_it50", "vdp_rk4_mixed": "vdp_rk4_1e6_ones_tol1e-8_it50"}
     p = os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")
@@ -1060,7 +1071,7 @@ def cpu_baseline(spec, full_passes, sample_iters):
 
 # Newton iterations of the oracle timed per baseline sample (bounded CPU time)
 SAMPLE_ITERS = {"vdp": 6, "osc": 1, "lorenz": 62, "fkpp": 3, "fkpp_mixed": 3, "fkpp_tf32": 3, "vdp_mixed": 6, "vdp_ff": 6, "lorenz_ff": 62,
-                "lorenz_mixed": 62, "robertson": 9, "robertson_mixed": 9, "vdp_rk4": 7, "vdp_rk4_ff": 7,
+                "lorenz_mixed": 62, "robertson": 9, "robertson_mixed": 9, "robertson_ff": 9, "vdp_rk4": 7, "vdp_rk4_ff": 7,
                 "vdp_rk4_mixed": 7}
 
 

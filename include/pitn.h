@@ -108,7 +108,9 @@ enum {
                                   the FP64 inverse): the scan's elements in FP32
                                   delta form (I + S, c); an inexact Newton step */
     PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63) with explicit
-                                  Euler, and VDP with RK4 (not in the paper): the
+                                  Euler, VDP with RK4, and backward Euler
+                                  (ROBERTSON, DAHLQUIST, VDP, LOGISTIC; the FP64
+                                  inverse split into pairs) (not in the paper): the
                                   scan (Jacobians -- for RK4 the stage chain rule --,
                                   folds, carries, replay) in double-FP32 "float-float"
                                   arithmetic, ~2^-47 relative, on the FP32 pipe;

@@ -370,7 +370,10 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
     if (o.precision == PITN_PREC_FP64_FF &&
         !(((system_id == PITN_VDP || system_id == PITN_LINEAR_OSC || system_id == PITN_LORENZ63) &&
            o.method == PITN_STEP_EULER) ||
-          (system_id == PITN_VDP && o.method == PITN_STEP_RK4)))
+          (system_id == PITN_VDP && o.method == PITN_STEP_RK4) ||
+          ((system_id == PITN_ROBERTSON || system_id == PITN_DAHLQUIST || system_id == PITN_VDP ||
+            system_id == PITN_LOGISTIC) &&
+           o.method == PITN_STEP_BACKWARD_EULER)))
         return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_FP32 &&

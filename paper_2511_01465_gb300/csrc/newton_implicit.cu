@@ -9,7 +9,8 @@
 // Euler that element is (M_n^{-1}, -M_n^{-1} h_n) with M_n = I - h Jf(x_n)
 // (eqs. 3.16-3.19), built by BackwardEulerMap in systems.cuh; TrapezoidMap
 // builds the trapezoidal rule's.  Backward Euler also runs with the FP32
-// delta-form scan (the fused reduced-precision kernel, newton_fused_mixed.cuh);
+// delta-form and the float-float scans (the fused reduced-precision kernel,
+// newton_fused_mixed.cuh);
 // the batched and adjoint entry points are explicit-only.
 #include "newton_small.cuh"
 
@@ -26,6 +27,19 @@ int select_implicit_kernel(int system_id, int method, int precision, pitn::Small
         case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>, kVarFusedMixed>(); return PITN_OK;
         case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>, kVarFusedMixed>(); return PITN_OK;
         case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>, kVarFusedMixed>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (precision == PITN_PREC_FP64_FF) {
+        // backward Euler with the float-float scan: the residual, the inverse
+        // and the update in FP64, the dense folds, scans and replay in pairs
+        // of floats
+        if (method != PITN_STEP_BACKWARD_EULER) return PITN_EUNSUPPORTED;
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<BackwardEulerMap<DahlquistRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<BackwardEulerMap<RobertsonRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<BackwardEulerMap<VdpRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<BackwardEulerMap<LogisticRhs>, kVarFusedFF>(); return PITN_OK;
         default: return PITN_EUNSUPPORTED;
         }
     }

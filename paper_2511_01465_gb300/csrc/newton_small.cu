@@ -57,6 +57,8 @@ void small_default_config(int d, long long N, int* block, int* C) {
 // stiff test systems live in newton_implicit.cu.
 int select_small_kernel(int system_id, int method, int precision, pitn::SmallKernel* K) {
     using namespace pitn;
+    if (precision == PITN_PREC_FP64_FF && method == PITN_STEP_BACKWARD_EULER)
+        return select_implicit_kernel(system_id, method, precision, K);
     if (precision == PITN_PREC_FP64_FF) {
         // the float-float scan runs fused, like the FP32 one: its FP64 work
         // is the residual and the update

@@ -888,6 +888,18 @@ struct BackwardEulerMap : RK4Map<Rhs> {
 #pragma unroll
         for (int i = 0; i < D * D; ++i) S[i] = sv[i];
     }
+    // float-float scan (PITN_PREC_FP64_FF): the FP64 residual and inverse of
+    // eval, the element M_n^{-1} split into float-float pairs on the integer
+    // pipes; the dense fold, replay and element of RK4Map's float-float
+    // helpers.  No constants enter the float-float arithmetic.
+    __host__ __device__ static void ff_consts(const double*, double, float*, double*) {}
+    __device__ __forceinline__ void init_ff(const float*, const double*) {}
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        double Mi[D * D];
+        eval(xp, xc, res, Mi);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) jv[i] = ff_from_double(Mi[i]);
+    }
 };
 
 

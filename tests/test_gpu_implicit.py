@@ -138,9 +138,9 @@ def test_implicit_unsupported_combinations(pk):
     with pytest.raises(P.PitnError):   # the FP32 delta form: explicit maps and backward Euler only
         pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
                  method=pk.PITN_STEP_TRAPEZOID, precision=pk.PITN_PREC_MIXED_FP32)
-    with pytest.raises(P.PitnError):   # no float-float scan for the implicit rules
+    with pytest.raises(P.PitnError):   # the float-float scan: no trapezoidal rule
         pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
-                 method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_FP64_FF)
+                 method=pk.PITN_STEP_TRAPEZOID, precision=pk.PITN_PREC_FP64_FF)
 
 
 def test_bench_size_robertson(pk):
@@ -208,3 +208,48 @@ def test_bench_size_robertson_fp32_scan(pk):
     _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, t, method=O.BACKWARD_EULER)
     assert not nf and res <= 1e-8 * (1 + 1e-6)
     assert np.abs(t.sum(axis=1) - 1.0).max() <= 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Backward Euler with the float-float scan: the FP64 residual and inverse, the
+# dense folds, scans and replay in pairs of floats (~2^-47).  It must meet
+# the FP64 path's bars: plain Newton counts and residual traces equal to the
+# oracle's, the root within 1e-9 of the oracle's per component scale, the
+# oracle's residual test passed.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_backward_euler_ff_scan(pk, case):
+    _, sys, p, x0, h, N, gv, B = case
+    d = len(x0)
+    guess = None if gv is None else np.full((N, d), gv)
+    traj, info = pk.solve(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, history=True,
+                          method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_FP64_FF)
+    o = O.newton(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, method=O.BACKWARD_EULER)
+    assert o["status"] == O.OK
+    assert info["status"] == pk.PITN_OK
+    if B == 0.0:
+        assert info["iters"] == o["iters"]
+        np.testing.assert_allclose(info["res_history"][:-1], o["res_hist"][:-1], rtol=1e-6, atol=1e-15)
+    t = traj.cpu().numpy()
+    scale = np.abs(o["traj"]).max(axis=0)
+    assert (np.abs(t - o["traj"]) <= 1e-9 * scale + 1e-15).all()
+    _, res, nf = O.residual(sys, p, x0, h, t, method=O.BACKWARD_EULER)
+    assert not nf and res <= 1e-12 * (1 + 1e-6)
+
+
+def test_bench_size_robertson_ff_scan(pk):
+    """The implicit bench workload with the float-float scan: the oracle's
+    stored count and status, its residual history, the residual test and
+    the conservation of y1 + y2 + y3 as for the FP64 solve."""
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_full_size.json")) as f:
+        gold = json.load(f)["robertson_5e6_be_zeros_tol1e-8_it60"]
+    wl = W.robertson(h=1e-4)
+    traj, info = pk.solve(wl.system, wl.params, wl.x0, wl.h, wl.N, gold["tol"], gold["max_iter"],
+                          guess=np.zeros((wl.N, wl.d)), history=True, method=pk.PITN_STEP_BACKWARD_EULER,
+                          precision=pk.PITN_PREC_FP64_FF)
+    assert (info["iters"], info["status"]) == (gold["iters"], gold["status"])
+    np.testing.assert_allclose(info["res_history"][:-1], gold["res_history"][:-1], rtol=1e-6, atol=1e-15)
+    t = traj.cpu().numpy()
+    _, res, nf = O.residual(wl.system, wl.params, wl.x0, wl.h, t, method=O.BACKWARD_EULER)
+    assert not nf and res <= gold["tol"]
+    np.testing.assert_allclose(t.sum(axis=1), 1.0, atol=1e-9)
