@@ -103,14 +103,16 @@ enum {
     PITN_PREC_MIXED_FP32 = 2,  /* d <= 3 (LORENZ63, VDP, LINEAR_OSC) with explicit
                                   Euler, VDP with RK4 (not in the paper; the
                                   stage chain rule of S in FP32 from the FP64
-                                  stage states), and backward Euler (ROBERTSON,
-                                  DAHLQUIST, VDP, LOGISTIC; S = M^-1 - I from
-                                  the FP64 inverse): the scan's elements in FP32
+                                  stage states), and the implicit rules (backward
+                                  Euler, trapezoidal; ROBERTSON, DAHLQUIST, VDP,
+                                  LOGISTIC; S = J - I from the FP64 element):
+                                  the scan's elements in FP32
                                   delta form (I + S, c); an inexact Newton step */
     PITN_PREC_FP64_FF = 3,     /* d <= 3 (VDP, LINEAR_OSC, LORENZ63) with explicit
-                                  Euler, VDP with RK4, and backward Euler
-                                  (ROBERTSON, DAHLQUIST, VDP, LOGISTIC; the FP64
-                                  inverse split into pairs) (not in the paper): the
+                                  Euler, VDP with RK4, and the implicit rules
+                                  (backward Euler, trapezoidal; ROBERTSON,
+                                  DAHLQUIST, VDP, LOGISTIC; the FP64 element
+                                  split into pairs) (not in the paper): the
                                   scan (Jacobians -- for RK4 the stage chain rule --,
                                   folds, carries, replay) in double-FP32 "float-float"
                                   arithmetic, ~2^-47 relative, on the FP32 pipe;

@@ -373,7 +373,7 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
           (system_id == PITN_VDP && o.method == PITN_STEP_RK4) ||
           ((system_id == PITN_ROBERTSON || system_id == PITN_DAHLQUIST || system_id == PITN_VDP ||
             system_id == PITN_LOGISTIC) &&
-           o.method == PITN_STEP_BACKWARD_EULER)))
+           (o.method == PITN_STEP_BACKWARD_EULER || o.method == PITN_STEP_TRAPEZOID))))
         return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_BF16 && system_id != PITN_FKPP) return PITN_EINVAL;
     if (o.precision == PITN_PREC_MIXED_FP32 &&
@@ -382,7 +382,7 @@ int pitn_solve_ex(int system_id, const double* params, const double* x0, double 
           (system_id == PITN_VDP && o.method == PITN_STEP_RK4) ||
           ((system_id == PITN_ROBERTSON || system_id == PITN_DAHLQUIST || system_id == PITN_VDP ||
             system_id == PITN_LOGISTIC) &&
-           o.method == PITN_STEP_BACKWARD_EULER)))
+           (o.method == PITN_STEP_BACKWARD_EULER || o.method == PITN_STEP_TRAPEZOID))))
         return PITN_EINVAL;
     if (o.tile_elems < 0) return PITN_EINVAL;
     if (o.method < PITN_STEP_EULER || o.method > PITN_STEP_TRAPEZOID) return PITN_EINVAL;

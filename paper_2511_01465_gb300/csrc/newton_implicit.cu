@@ -8,7 +8,7 @@
 // whose eval(x_{n-1}, x_n) yields the scan element of step n; for backward
 // Euler that element is (M_n^{-1}, -M_n^{-1} h_n) with M_n = I - h Jf(x_n)
 // (eqs. 3.16-3.19), built by BackwardEulerMap in systems.cuh; TrapezoidMap
-// builds the trapezoidal rule's.  Backward Euler also runs with the FP32
+// builds the trapezoidal rule's.  Both rules also run with the FP32
 // delta-form and the float-float scans (the fused reduced-precision kernel,
 // newton_fused_mixed.cuh);
 // the batched and adjoint entry points are explicit-only.
@@ -18,6 +18,24 @@ namespace pitn_host {
 
 int select_implicit_kernel(int system_id, int method, int precision, pitn::SmallKernel* K) {
     using namespace pitn;
+    if (precision == PITN_PREC_MIXED_FP32 && method == PITN_STEP_TRAPEZOID) {
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<TrapezoidMap<DahlquistRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<TrapezoidMap<RobertsonRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<TrapezoidMap<VdpRhs>, kVarFusedMixed>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<TrapezoidMap<LogisticRhs>, kVarFusedMixed>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
+    if (precision == PITN_PREC_FP64_FF && method == PITN_STEP_TRAPEZOID) {
+        switch (system_id) {
+        case PITN_DAHLQUIST: *K = small_kernel_of<TrapezoidMap<DahlquistRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_ROBERTSON: *K = small_kernel_of<TrapezoidMap<RobertsonRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_VDP: *K = small_kernel_of<TrapezoidMap<VdpRhs>, kVarFusedFF>(); return PITN_OK;
+        case PITN_LOGISTIC: *K = small_kernel_of<TrapezoidMap<LogisticRhs>, kVarFusedFF>(); return PITN_OK;
+        default: return PITN_EUNSUPPORTED;
+        }
+    }
     if (precision == PITN_PREC_MIXED_FP32) {
         // backward Euler with the FP32 delta-form scan: the residual and the
         // inverse of I - h Jf stay FP64, the folds, scans and replay FP32

@@ -57,7 +57,7 @@ void small_default_config(int d, long long N, int* block, int* C) {
 // stiff test systems live in newton_implicit.cu.
 int select_small_kernel(int system_id, int method, int precision, pitn::SmallKernel* K) {
     using namespace pitn;
-    if (precision == PITN_PREC_FP64_FF && method == PITN_STEP_BACKWARD_EULER)
+    if (precision == PITN_PREC_FP64_FF && (method == PITN_STEP_BACKWARD_EULER || method == PITN_STEP_TRAPEZOID))
         return select_implicit_kernel(system_id, method, precision, K);
     if (precision == PITN_PREC_FP64_FF) {
         // the float-float scan runs fused, like the FP32 one: its FP64 work
@@ -83,7 +83,7 @@ int select_small_kernel(int system_id, int method, int precision, pitn::SmallKer
         *K = small_kernel_of<RK4Map<VdpRhs>, kVarFusedMixed>();
         return PITN_OK;
     }
-    if (precision == PITN_PREC_MIXED_FP32 && method == PITN_STEP_BACKWARD_EULER)
+    if (precision == PITN_PREC_MIXED_FP32 && (method == PITN_STEP_BACKWARD_EULER || method == PITN_STEP_TRAPEZOID))
         return select_implicit_kernel(system_id, method, precision, K);
     if (precision == PITN_PREC_MIXED_FP32) {
         // the d = 2 FP32-scan solves run fused: their FP64 work (residual,

@@ -929,6 +929,27 @@ struct TrapezoidMap : RK4Map<Rhs> {
         this->jmul(Mi, Jp, jv);
         this->jvec(Mi, hn, res);
     }
+    // the reduced-precision scans, as for backward Euler: the FP64 residual and
+    // element of eval; S = J - I rounded to FP32, or J split into float-float
+    // pairs, on the integer pipes
+    __device__ __forceinline__ void eval_mixed(const double* xp, const double* xc, double* res, float* sv) const {
+        double J[D * D];
+        eval(xp, xc, res, J);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) sv[i] = d2f_int((i % (D + 1) == 0) ? J[i] - 1.0 : J[i]);
+    }
+    __device__ __forceinline__ void sfull(const float* sv, float* S) const {
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) S[i] = sv[i];
+    }
+    __host__ __device__ static void ff_consts(const double*, double, float*, double*) {}
+    __device__ __forceinline__ void init_ff(const float*, const double*) {}
+    __device__ __forceinline__ void eval_ff(const double* xp, const double* xc, double* res, ff* jv) const {
+        double J[D * D];
+        eval(xp, xc, res, J);
+#pragma unroll
+        for (int i = 0; i < D * D; ++i) jv[i] = ff_from_double(J[i]);
+    }
 };
 
 }  // namespace pitn

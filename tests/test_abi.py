@@ -86,12 +86,12 @@ def test_argument_errors_are_detected_on_the_host(lib):
     opt = P.make_options(method=P.PITN_STEP_BACKWARD_EULER)
     rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
     assert rc == P.PITN_EUNSUPPORTED                                                     # not instantiated
-    opt = P.make_options(method=P.PITN_STEP_TRAPEZOID, precision=P.PITN_PREC_MIXED_FP32)
-    rc, _ = P.pitn_solve_ex(P.PITN_ROBERTSON, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
-    assert rc == E                                                                       # FP32 form: no trapezoid
+    opt = P.make_options(method=P.PITN_STEP_BACKWARD_EULER, precision=P.PITN_PREC_MIXED_FP32)
+    rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+    assert rc == E                                                                       # FP32 form: no implicit Lorenz
     opt = P.make_options(method=P.PITN_STEP_TRAPEZOID, precision=P.PITN_PREC_FP64_FF)
-    rc, _ = P.pitn_solve_ex(P.PITN_ROBERTSON, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
-    assert rc == E                                                                       # float-float: no trapezoid
+    rc, _ = P.pitn_solve_ex(P.PITN_LORENZ63, p, x0, 1e-3, 10, 3, 1e-10, 5, out, opt)
+    assert rc == E                                                                       # float-float: no implicit Lorenz
     assert not out.any()  # nothing written on an argument error
 
 

@@ -135,12 +135,10 @@ def test_implicit_unsupported_combinations(pk):
     from paper_2511_01465_gb300 import pitn as P
     with pytest.raises(P.PitnError):   # no backward Euler instantiation for Lorenz-63
         pk.solve(1, [10, 28, 8 / 3], [1, 1, 1], 1e-3, 100, 1e-10, 5, method=pk.PITN_STEP_BACKWARD_EULER)
-    with pytest.raises(P.PitnError):   # the FP32 delta form: explicit maps and backward Euler only
-        pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
-                 method=pk.PITN_STEP_TRAPEZOID, precision=pk.PITN_PREC_MIXED_FP32)
-    with pytest.raises(P.PitnError):   # the float-float scan: no trapezoidal rule
-        pk.solve(O.ROBERTSON, [0.04, 3e7, 1e4], [1, 0, 0], 0.1, 100, 1e-10, 5,
-                 method=pk.PITN_STEP_TRAPEZOID, precision=pk.PITN_PREC_FP64_FF)
+    for prec in (pk.PITN_PREC_MIXED_FP32, pk.PITN_PREC_FP64_FF):   # no implicit Lorenz-63, any precision
+        with pytest.raises(P.PitnError):
+            pk.solve(1, [10, 28, 8 / 3], [1, 1, 1], 1e-3, 100, 1e-10, 5, method=pk.PITN_STEP_BACKWARD_EULER,
+                     precision=prec)
 
 
 def test_bench_size_robertson(pk):
@@ -172,25 +170,31 @@ def test_implicit_singular_step_matrix(pk, rule):
 
 
 # ---------------------------------------------------------------------------
-# Backward Euler with the FP32 delta-form scan (an inexact Newton step): the
-# residual M_n^{-1} h_n, the inverse and the update stay FP64, the element's
-# S = M_n^{-1} - I is rounded to FP32.  It must reach the same FP64 residual
+# The implicit rules with the FP32 delta-form scan (an inexact Newton step):
+# the residual M_n^{-1} h_n, the element and the update stay FP64, the
+# element's S = J_n - I is rounded to FP32.  It must reach the same FP64 residual
 # tolerance, pass the oracle's residual test, and stay within 1e-6 (against
 # the largest state) of the FP64 oracle's root; its Newton count is reported,
 # not required to match.
 # ---------------------------------------------------------------------------
+RULES = {"backward_euler": ("PITN_STEP_BACKWARD_EULER", O.BACKWARD_EULER),
+         "trapezoid": ("PITN_STEP_TRAPEZOID", O.TRAPEZOID)}
+
+
+@pytest.mark.parametrize("rule", list(RULES))
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_backward_euler_fp32_scan(pk, case):
+def test_implicit_fp32_scan(pk, case, rule):
     _, sys, p, x0, h, N, gv, B = case
     d = len(x0)
     guess = None if gv is None else np.full((N, d), gv)
+    m_gpu, m_or = getattr(pk, RULES[rule][0]), RULES[rule][1]
     traj, info = pk.solve(sys, p, x0, h, N, 1e-12, 150, guard_B=B, guess=guess, history=True,
-                          method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_MIXED_FP32)
-    o = O.newton(sys, p, x0, h, N, 1e-12, 150, guard_B=B, guess=guess, method=O.BACKWARD_EULER)
+                          method=m_gpu, precision=pk.PITN_PREC_MIXED_FP32)
+    o = O.newton(sys, p, x0, h, N, 1e-12, 150, guard_B=B, guess=guess, method=m_or)
     assert o["status"] == O.OK
     assert info["status"] == pk.PITN_OK and info["final_res"] <= 1e-12
     t = traj.cpu().numpy()
-    _, res, nf = O.residual(sys, p, x0, h, t, method=O.BACKWARD_EULER)
+    _, res, nf = O.residual(sys, p, x0, h, t, method=m_or)
     assert not nf and res <= 1e-12 * (1 + 1e-6)
     assert np.abs(t - o["traj"]).max() <= 1e-6 * np.abs(o["traj"]).max()
 
@@ -211,20 +215,22 @@ def test_bench_size_robertson_fp32_scan(pk):
 
 
 # ---------------------------------------------------------------------------
-# Backward Euler with the float-float scan: the FP64 residual and inverse, the
-# dense folds, scans and replay in pairs of floats (~2^-47).  It must meet
+# The implicit rules with the float-float scan: the FP64 residual and element,
+# the dense folds, scans and replay in pairs of floats (~2^-47).  It must meet
 # the FP64 path's bars: plain Newton counts and residual traces equal to the
 # oracle's, the root within 1e-9 of the oracle's per component scale, the
 # oracle's residual test passed.
 # ---------------------------------------------------------------------------
+@pytest.mark.parametrize("rule", list(RULES))
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_backward_euler_ff_scan(pk, case):
+def test_implicit_ff_scan(pk, case, rule):
     _, sys, p, x0, h, N, gv, B = case
     d = len(x0)
     guess = None if gv is None else np.full((N, d), gv)
+    m_gpu, m_or = getattr(pk, RULES[rule][0]), RULES[rule][1]
     traj, info = pk.solve(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, history=True,
-                          method=pk.PITN_STEP_BACKWARD_EULER, precision=pk.PITN_PREC_FP64_FF)
-    o = O.newton(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, method=O.BACKWARD_EULER)
+                          method=m_gpu, precision=pk.PITN_PREC_FP64_FF)
+    o = O.newton(sys, p, x0, h, N, 1e-12, 80, guard_B=B, guess=guess, method=m_or)
     assert o["status"] == O.OK
     assert info["status"] == pk.PITN_OK
     if B == 0.0:
@@ -233,7 +239,7 @@ def test_backward_euler_ff_scan(pk, case):
     t = traj.cpu().numpy()
     scale = np.abs(o["traj"]).max(axis=0)
     assert (np.abs(t - o["traj"]) <= 1e-9 * scale + 1e-15).all()
-    _, res, nf = O.residual(sys, p, x0, h, t, method=O.BACKWARD_EULER)
+    _, res, nf = O.residual(sys, p, x0, h, t, method=m_or)
     assert not nf and res <= 1e-12 * (1 + 1e-6)
 
 
