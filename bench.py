@@ -43,19 +43,19 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28938381824 + 24168879360, "26345b3b15534885"),  # 147 passes, newton_small_kernel<VanDerPol>
-    "vdp_ff": (25448123904 + 27271746816, "26345b3b15534885"),  # 151 passes, newton_fused_mixed_kernel<VanDerPol, ScanFF>
-    "vdp_mixed": (13102116608 + 15207670784, "26345b3b15534885"),  # 137 passes, newton_fused_mixed_kernel<VanDerPol, ScanF32>
-    "lorenz": (141824 + 37376, "26345b3b15534885"),  # 64 passes, newton_small_kernel<Lorenz63>
-    "lorenz_ff": (224256 + 34560, "26345b3b15534885"),  # 62 passes, newton_small_mixed_kernel<Lorenz63, ScanFF>
-    "lorenz_mixed": (99840 + 18688, "26345b3b15534885"),  # 52 passes, newton_small_mixed_kernel<Lorenz63, ScanF32>
-    "vdp_rk4": (30540544 + 347680512, "26345b3b15534885"),  # 8 passes, newton_fused_kernel<RK4Map<VdpRhs>>
-    "vdp_rk4_ff": (41506560 + 336632832, "26345b3b15534885"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanFF>
-    "vdp_rk4_mixed": (16178688 + 20551168, "26345b3b15534885"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanF32>
-    "robertson": (13364797440 + 13725581312, "26345b3b15534885"),  # 22 passes, newton_fused_kernel<BackwardEulerMap<RobertsonRhs>>
-    "robertson_mixed": (8639868160 + 8673182208, "26345b3b15534885"),  # 23 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanF32>
-    "robertson_ff": (13365919488 + 13700761856, "26345b3b15534885"),  # 22 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanFF>
-    "osc": (102260480 + 197060864, "26345b3b15534885"),  # 2 passes, newton_small_kernel<LinearOsc>
+    "vdp": (28930136832 + 24170678016, "1a14bf8cd41a6fe0"),  # 147 passes, newton_small_kernel<VanDerPol>
+    "vdp_ff": (25473852672 + 27281544704, "1a14bf8cd41a6fe0"),  # 151 passes, newton_fused_mixed_kernel<VanDerPol, ScanFF>
+    "vdp_mixed": (13103372800 + 15205731328, "1a14bf8cd41a6fe0"),  # 137 passes, newton_fused_mixed_kernel<VanDerPol, ScanF32>
+    "lorenz": (142336 + 41216, "1a14bf8cd41a6fe0"),  # 64 passes, newton_small_kernel<Lorenz63>
+    "lorenz_ff": (224256 + 34048, "1a14bf8cd41a6fe0"),  # 62 passes, newton_small_mixed_kernel<Lorenz63, ScanFF>
+    "lorenz_mixed": (98816 + 28672, "1a14bf8cd41a6fe0"),  # 52 passes, newton_small_mixed_kernel<Lorenz63, ScanF32>
+    "vdp_rk4": (31002368 + 345276672, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_kernel<RK4Map<VdpRhs>>
+    "vdp_rk4_ff": (44308224 + 338988544, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanFF>
+    "vdp_rk4_mixed": (16180480 + 20772352, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanF32>
+    "robertson": (13364683264 + 13725557504, "1a14bf8cd41a6fe0"),  # 22 passes, newton_fused_kernel<BackwardEulerMap<RobertsonRhs>>
+    "robertson_mixed": (8638968576 + 8672771328, "1a14bf8cd41a6fe0"),  # 23 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanF32>
+    "robertson_ff": (13364671744 + 13701077504, "1a14bf8cd41a6fe0"),  # 22 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanFF>
+    "osc": (102216192 + 197429248, "1a14bf8cd41a6fe0"),  # 2 passes, newton_small_kernel<LinearOsc>
 }
 
 
