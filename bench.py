@@ -652,9 +652,47 @@ def run_ours_adjoint(args, rank, world, local_rank, spec):
                 "note": "FP64 flops of the forward solve's steps evaluated and replayed (counted by "
                         "the kernels), per step counted from the kernel source; peak = measured DFMA "
                         "rate x 2"}
+    mixed = None
+    if world == 1 and not args.no_companions:
+        # the same step with the forward solve's scan in FP32 or float-float (the
+        # adjoint stays FP64); the gradients against the FP64 step's
+        gp_ref, gx_ref = gp.clone(), gx0.clone()
+        mixed = {}
+        for key, prec in (("fp32_scan", P.PITN_PREC_MIXED_FP32), ("float_float_scan", P.PITN_PREC_FP64_FF)):
+            mo = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=prec)
+
+            def step_m():
+                P.check(P.pitn_solve_batch(bt.system, bt.B, params, x0, h, N, d, spec["tol"], spec["max_iter"],
+                                           traj, offs, iters, status, res, mo), "pitn_solve_batch")
+                gNm = (2.0 * (traj[offs[1:] - 1] - target)).contiguous()
+                P.check(P.pitn_backward(bt.system, bt.B, params, x0, h, N, d, traj, None, gNm, 1024, gx0, gp,
+                                        opt), "pitn_backward")
+
+            P.pitn_tune_enable(not args.no_tune)
+            for _ in range(args.warmup):
+                step_m()
+            P.pitn_tune_enable(False)
+            mt = []
+            for _ in range(args.steps):
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step_m()
+                e1.record(stream)
+                e1.synchronize()
+                mt.append(e0.elapsed_time(e1))
+            ok_m = status.cpu().numpy() == P.PITN_OK
+            ms_m = float(sum(mt)) / len(mt)
+            v_m = float(bt.N[ok_m].sum()) / (ms_m / 1e3)
+            rel = lambda a, b: float((a - b).abs().max() / b.abs().max())
+            mixed[key] = {"value": v_m, "unit": UNIT, "ms_per_step": ms_m,
+                          "vs_fp64": v_m / value if value > 0 else None, "converged_ivps": int(ok_m.sum()),
+                          "grad_params_rel_diff": rel(gp, gp_ref), "grad_x0_rel_diff": rel(gx0, gx_ref)}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "mixed": mixed,
             "config": {"workload": spec["desc"], "B": bt.B, "sum_N": M, "d": d, "tol": spec["tol"],
                        "converged_ivps": int(ok.sum()), "mean_newton_updates": float(it_h.mean()),
                        "forward_ms_per_step": fwd_ms / nk, "launch_shape": shape,

@@ -115,3 +115,32 @@ def test_autograd_function(pk):
                            grad_xN=2.0 * (tr[e - 1] - [1.0, 0.0]))
         assert rel(x0.grad[b].cpu().numpy(), ox) <= 1e-10
         assert rel(params.grad[b].cpu().numpy(), op) <= 1e-10
+
+
+@pytest.mark.parametrize("precision,bar", [(3, 1e-10), (2, 1e-6)], ids=["float_float", "fp32"])
+def test_gradients_through_reduced_precision_forward(pk, precision, bar):
+    """The differentiation workload with its forward batch solved by the
+    float-float or the FP32 scan (the adjoint itself FP64) at tol 1e-12: every
+    IVP converges, and the gradients match the oracle adjoint on the returned
+    trajectories to 1e-10 (the adjoint is exact on any trajectory) and the
+    FP64-forward gradients to the scan's bar."""
+    bt = W.vdp_adjoint_batch()
+    dev = "cuda"
+    grads = []
+    for prec in (0, precision):
+        traj, offs, iters, status, res = pk.solve_batch(bt.system, bt.params, bt.x0, bt.h, bt.N, 1e-12, 200,
+                                                        guard_B=100.0, precision=prec)
+        assert (status.cpu().numpy() == 0).all()
+        last = offs[1:] - 1
+        target = torch.tensor([1.0, 0.0], dtype=torch.float64, device=dev)
+        gN = (2.0 * (traj[last] - target)).contiguous()
+        gx0, gp = pk.backward(bt.system, bt.params, bt.x0, bt.h, bt.N, traj, grad_xN=gN, ckpt_every=1024)
+        grads.append((gx0.cpu().numpy(), gp.cpu().numpy(), traj.cpu().numpy(), offs.cpu().numpy()))
+    (gx_ref, gp_ref, _, _), (gx, gp, tr, offs) = grads
+    for b in (0, 17, 101, 255):
+        s, e = offs[b], offs[b + 1]
+        ox, op = O.adjoint(bt.system, bt.params[b], bt.x0[b], bt.h[b], tr[s:e],
+                           grad_xN=2.0 * (tr[e - 1] - [1.0, 0.0]))
+        assert rel(gx[b], ox) <= 1e-10 and rel(gp[b], op) <= 1e-10, b
+    assert np.abs(gp - gp_ref).max() <= bar * np.abs(gp_ref).max()
+    assert np.abs(gx - gx_ref).max() <= bar * np.abs(gx_ref).max()
