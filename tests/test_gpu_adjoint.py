@@ -96,14 +96,16 @@ def test_differentiation_workload_vs_fd(pk):
         assert np.abs(gx0[b] - fd_x).max() <= 1e-5 * scale, (b, gx0[b], fd_x)
 
 
-def test_autograd_function(pk):
+@pytest.mark.parametrize("precision", [0, 2, 3], ids=["fp64", "fp32_scan", "float_float_scan"])
+def test_autograd_function(pk, precision):
     from paper_2511_01465_gb300.autograd import odesolve
     bt = W.vdp_adjoint_batch(B=8, N=3000)
     dev = "cuda"
     params = torch.tensor(bt.params, device=dev, requires_grad=True)
     x0 = torch.tensor(bt.x0, device=dev, requires_grad=True)
     traj, offs, status = odesolve(bt.system, params, x0, torch.tensor(bt.h), torch.tensor(bt.N),
-                                  tol=1e-12, max_iter=100)
+                                  tol=1e-12, max_iter=100, precision=precision)
+    assert (status.cpu().numpy() == 0).all()
     last = offs[1:] - 1
     loss = ((traj[last] - torch.tensor([1.0, 0.0], dtype=torch.float64, device=dev)) ** 2).sum()
     loss.backward()
