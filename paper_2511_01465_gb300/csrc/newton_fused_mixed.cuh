@@ -10,10 +10,22 @@
 
 namespace pitn {
 
+// A request to bring the line holding p into L1 (prefetch.global.L1).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+// steps ahead at which a chain's state row is prefetched: one 128-byte line
+// of d = 2 rows
+constexpr long long kStatePrefetch = 8;
+
 template <class Sys, class Pol>
 __global__ void __launch_bounds__(256, Pol::template min_blocks<Sys>()) newton_fused_mixed_kernel(SmallArgs a) {
     using T = typename Pol::T;
     constexpr int D = Sys::D, JN = Sys::JN, E = D * D + D;
+    // L1 prefetch in the step loop: the FP32 scan with compact elements (van
+    // der Pol FP32 scan 16.1 -> 15.3 ms); slower with float-float (27.1 ->
+    // 28.0 ms) and with the dense RK4 elements, which keep it off
+    constexpr bool kPrefetch = Pol::kPrefetchL1 && JN <= D;
     Sys sys;
     sys.init(a.params, a.h);
     Pol::setup(sys, a);
@@ -236,6 +248,15 @@ __global__ void __launch_bounds__(256, Pol::template min_blocks<Sys>()) newton_f
         auto step = [&](int ch, long long k, long long s, T* z, double* prev, T* NQ,
                         T* nc, long long& cut, unsigned long long& res) {
             T sv[JN], r[D];
+            // the next step's scratch lines and the state row a line ahead are
+            // requested into L1 now (no registers held; nothing waits on them)
+            if constexpr (kPrefetch) {
+                if (k + 1 < sfill && k + 1 < k1) {   // (within this thread's scratch slots)
+#pragma unroll
+                    for (int j = 0; j < JN + D; ++j) prefetch_l1(scr + sidx(k + 1, j));
+                }
+                if (k + kStatePrefetch < q) prefetch_l1(Xc + (k + kStatePrefetch) * D);
+            }
             if (k < sfill) {
 #pragma unroll
                 for (int j = 0; j < JN; ++j) sv[j] = scr[sidx(k, j)];

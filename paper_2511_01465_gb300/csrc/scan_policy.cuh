@@ -23,6 +23,8 @@ struct ScanF32 {
     static constexpr bool kRollScans = false;
     // per-IVP batch kernel: threads per CTA at most, CTAs per SM at least
     static constexpr int kBatchThreads = 256, kBatchMinBlocks = 0;   // (0: the compiler's own choice)
+    // fused pass: L1 prefetch of the next step's scratch and state lines
+    static constexpr bool kPrefetchL1 = true;
     template <int D>
     static __device__ __forceinline__ void ident(T* Q, T* c) { dz_zero<D>(Q, c); }
     template <int D>
@@ -103,6 +105,7 @@ struct ScanFF {
     // per-IVP batch kernel: 128-thread CTAs, three per SM (at most 170
     // registers: the d = 3 kernel's 194 left two per SM)
     static constexpr int kBatchThreads = 128, kBatchMinBlocks = 3;
+    static constexpr bool kPrefetchL1 = false;
     template <int D>
     static __device__ __forceinline__ void ident(T* P, T* c) {
 #pragma unroll
