@@ -43,19 +43,19 @@ SMALL_SRC = ["newton_small.cuh", "newton_small.cu", "newton_small_mixed.cuh", "n
              "common.cuh"]
 TRAFFIC = {
     # workload: (bytes per launch of the timed solve, kernel-source hash)
-    "vdp": (28930136832 + 24170678016, "1a14bf8cd41a6fe0"),  # 147 passes, newton_small_kernel<VanDerPol>
-    "vdp_ff": (25473852672 + 27281544704, "1a14bf8cd41a6fe0"),  # 151 passes, newton_fused_mixed_kernel<VanDerPol, ScanFF>
-    "vdp_mixed": (13103372800 + 15205731328, "1a14bf8cd41a6fe0"),  # 137 passes, newton_fused_mixed_kernel<VanDerPol, ScanF32>
-    "lorenz": (142336 + 41216, "1a14bf8cd41a6fe0"),  # 64 passes, newton_small_kernel<Lorenz63>
-    "lorenz_ff": (224256 + 34048, "1a14bf8cd41a6fe0"),  # 62 passes, newton_small_mixed_kernel<Lorenz63, ScanFF>
-    "lorenz_mixed": (98816 + 28672, "1a14bf8cd41a6fe0"),  # 52 passes, newton_small_mixed_kernel<Lorenz63, ScanF32>
-    "vdp_rk4": (31002368 + 345276672, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_kernel<RK4Map<VdpRhs>>
-    "vdp_rk4_ff": (44308224 + 338988544, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanFF>
-    "vdp_rk4_mixed": (16180480 + 20772352, "1a14bf8cd41a6fe0"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanF32>
-    "robertson": (13364683264 + 13725557504, "1a14bf8cd41a6fe0"),  # 22 passes, newton_fused_kernel<BackwardEulerMap<RobertsonRhs>>
-    "robertson_mixed": (8638968576 + 8672771328, "1a14bf8cd41a6fe0"),  # 23 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanF32>
-    "robertson_ff": (13364671744 + 13701077504, "1a14bf8cd41a6fe0"),  # 22 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanFF>
-    "osc": (102216192 + 197429248, "1a14bf8cd41a6fe0"),  # 2 passes, newton_small_kernel<LinearOsc>
+    "vdp": (28936841472 + 24172120576, "66a389d6a17f759c"),  # 147 passes, newton_small_kernel<VanDerPol>
+    "vdp_ff": (25473908736 + 27281655552, "66a389d6a17f759c"),  # 151 passes, newton_fused_mixed_kernel<VanDerPol, ScanFF>
+    "vdp_mixed": (18092340736 + 15309869824, "66a389d6a17f759c"),  # 137 passes, newton_fused_mixed_kernel<VanDerPol, ScanF32>
+    "lorenz": (158208 + 45312, "66a389d6a17f759c"),  # 64 passes, newton_small_kernel<Lorenz63>
+    "lorenz_ff": (224512 + 34304, "66a389d6a17f759c"),  # 62 passes, newton_small_mixed_kernel<Lorenz63, ScanFF>
+    "lorenz_mixed": (99840 + 25088, "66a389d6a17f759c"),  # 52 passes, newton_small_mixed_kernel<Lorenz63, ScanF32>
+    "vdp_rk4": (31176192 + 345217536, "66a389d6a17f759c"),  # 8 passes, newton_fused_kernel<RK4Map<VdpRhs>>
+    "vdp_rk4_ff": (44198144 + 338967808, "66a389d6a17f759c"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanFF>
+    "vdp_rk4_mixed": (16180480 + 20744192, "66a389d6a17f759c"),  # 8 passes, newton_fused_mixed_kernel<RK4Map<VdpRhs>, ScanF32>
+    "robertson": (13365496320 + 13725852672, "66a389d6a17f759c"),  # 22 passes, newton_fused_kernel<BackwardEulerMap<RobertsonRhs>>
+    "robertson_mixed": (8638719488 + 8672999168, "66a389d6a17f759c"),  # 23 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanF32>
+    "robertson_ff": (13365422592 + 13701216512, "66a389d6a17f759c"),  # 22 passes, newton_fused_mixed_kernel<BackwardEulerMap<RobertsonRhs>, ScanFF>
+    "osc": (102232576 + 197507840, "66a389d6a17f759c"),  # 2 passes, newton_small_kernel<LinearOsc>
 }
 
 
