@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
-SINGLE = ["vdp", "vdp_mixed", "vdp_ff", "vdp_rk4", "vdp_rk4_ff", "vdp_rk4_mixed", "robertson", "osc", "lorenz", "lorenz_mixed", "fkpp", "fkpp_mixed"]
+SINGLE = ["vdp", "vdp_mixed", "vdp_ff", "vdp_rk4", "vdp_rk4_ff", "vdp_rk4_mixed", "robertson", "robertson_mixed",
+          "robertson_ff", "osc", "lorenz", "lorenz_mixed", "lorenz_ff", "fkpp", "fkpp_mixed", "fkpp_tf32"]
 
 
 @pytest.mark.parametrize("name", SINGLE + ["batch", "batch_small", "adjoint"])
@@ -138,3 +139,20 @@ def test_clock_sampler_window():
     cs.t_timed = now - datetime.timedelta(seconds=0.2)
     r = cs.stop()
     assert r == {"sm_mhz": 2065, "sm_max_mhz": 2070, "reasons": [], "samples": 2, "window": "timed region"}
+
+
+
+@pytest.mark.parametrize("name", [n for n in SINGLE if not n.startswith("fkpp")])
+def test_small_state_roofline_counts(name):
+    """Every small-state workload has its per-step FP64 work (SMALL_FLOPS for
+    the FP64 kernels, REDUCED_FP64 for the reduced-precision scans) and, while
+    the kernel sources are unchanged, its captured DRAM traffic."""
+    spec = bench.workload(name)
+    if spec.get("precision", 0) in (2, 3):
+        ops, flops = bench.REDUCED_FP64[name]
+        assert 0 < ops <= flops
+    else:
+        p1, p3 = bench.SMALL_FLOPS[name]
+        assert p1 > 0 and p3 > 0
+    t = bench.TRAFFIC.get(name)
+    assert t is not None and t[0] > 0
