@@ -828,16 +828,25 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "kernel_ms_per_step": {k: v[0] / nk for k, v in ktimes.items()}}
-    if args.workload == "vdp" and not args.no_companions and world == 1:
-        # the metric's comparison: reduced-precision scans and batching against
-        # the plain FP64 solver, same tolerance, timed after the FP64 line (on
-        # one GPU: with several, the replicas' line carries no comparison)
+    if args.workload in TWINS and not args.no_companions and world == 1:
+        # the metric's comparison: reduced-precision scans (and, on the default
+        # line, batching) against the plain FP64 solver, same tolerance, timed
+        # after the FP64 line (on one GPU: with several, the replicas' line
+        # carries no comparison)
+        f32, ffw = TWINS[args.workload]
         line["mixed"] = {
-            "fp32_scan": companion_single(args, "vdp_mixed", dev, stream, flush, value, traj),
-            "float_float_scan": companion_single(args, "vdp_ff", dev, stream, flush, value, traj),
+            "fp32_scan": companion_single(args, f32, dev, stream, flush, value, traj),
+            "float_float_scan": companion_single(args, ffw, dev, stream, flush, value, traj),
         }
-        line["batched"] = companion_batched(args, dev, stream)
+        if args.workload == "vdp":
+            line["batched"] = companion_batched(args, dev, stream)
     return line
+
+
+# FP64 workloads and their FP32-scan and float-float twins (same problem,
+# tolerance and iteration limit)
+TWINS = {"vdp": ("vdp_mixed", "vdp_ff"), "lorenz": ("lorenz_mixed", "lorenz_ff"),
+         "vdp_rk4": ("vdp_rk4_mixed", "vdp_rk4_ff"), "robertson": ("robertson_mixed", "robertson_ff")}
 
 
 def companion_single(args, name, dev, stream, flush, ref_value, ref_traj):
@@ -851,7 +860,11 @@ def companion_single(args, name, dev, stream, flush, ref_value, ref_traj):
     params = torch.tensor(wl.params, dtype=torch.float64, device=dev)
     x0 = torch.tensor(wl.x0, dtype=torch.float64, device=dev)
     traj = torch.empty((wl.N, wl.d), dtype=torch.float64, device=dev)
-    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=spec["precision"])
+    guess = None
+    if "guess" in spec:  # constant initial guess, copied into the trajectory by every solve
+        guess = torch.full((wl.N, wl.d), spec["guess"], dtype=torch.float64, device=dev)
+    opt = P.make_options(guard_B=spec["guard_B"], stream=stream.cuda_stream, precision=spec["precision"],
+                         guess=guess, method=spec.get("method", 0))
 
     def solve_once():
         rc, res = P.pitn_solve_ex(wl.system, params, x0, wl.h, wl.N, wl.d, spec["tol"], spec["max_iter"],

@@ -156,3 +156,17 @@ def test_small_state_roofline_counts(name):
         assert p1 > 0 and p3 > 0
     t = bench.TRAFFIC.get(name)
     assert t is not None and t[0] > 0
+
+
+@pytest.mark.parametrize("name", sorted(bench.TWINS))
+def test_reduced_precision_twins_match(name):
+    """The comparison lines of an FP64 workload solve the same problem to the
+    same tolerance and limits, only with the FP32 / float-float scans."""
+    base = bench.workload(name)
+    for twin, prec in zip(bench.TWINS[name], (2, 3)):
+        t = bench.workload(twin)
+        assert t["precision"] == prec and base.get("precision", 0) == 0
+        for k in ("tol", "max_iter", "guard_B"):
+            assert t[k] == base[k]
+        assert t.get("method", 0) == base.get("method", 0) and t.get("guess") == base.get("guess")
+        assert (t["wl"].system, t["wl"].N, t["wl"].h) == (base["wl"].system, base["wl"].N, base["wl"].h)
