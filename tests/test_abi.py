@@ -127,3 +127,46 @@ def test_tune_set_pins_a_shape(tmp_path, lib):
     assert out.returncode == 0, out.stderr
     assert out.stdout.strip() == "0 (256, 1) -1 -1 -1 -1 0 (128, 0)"
     assert sorted(cache.read_text().splitlines()) == ["batch:1:3:13:1 128 0", "small:7:3:22:0:be 256 1"]
+
+
+def test_precision_support_matrix(lib):
+    """The reduced-precision scans are accepted exactly where include/pitn.h
+    documents them (FP32 delta form and float-float: Lorenz-63, van der Pol,
+    oscillator with explicit Euler; van der Pol with RK4; Robertson,
+    Dahlquist, van der Pol, logistic with backward Euler or the trapezoidal
+    rule; BF16 / TF32 only for Fisher-KPP) and refused on the host
+    (PITN_EINVAL, nothing written) everywhere else."""
+    from paper_2511_01465_gb300 import pitn as P
+    dims = {P.PITN_LORENZ63: 3, P.PITN_VDP: 2, P.PITN_LINEAR_OSC: 2, P.PITN_LOGISTIC: 1,
+            P.PITN_DAHLQUIST: 1, P.PITN_ROBERTSON: 3}
+    implicit = (P.PITN_STEP_BACKWARD_EULER, P.PITN_STEP_TRAPEZOID)
+
+    def reduced_ok(sys, m):
+        return ((sys in (P.PITN_LORENZ63, P.PITN_VDP, P.PITN_LINEAR_OSC) and m == P.PITN_STEP_EULER)
+                or (sys == P.PITN_VDP and m == P.PITN_STEP_RK4)
+                or (sys in (P.PITN_ROBERTSON, P.PITN_DAHLQUIST, P.PITN_VDP, P.PITN_LOGISTIC) and m in implicit))
+
+    # (an accepted request goes on to device work, which without a GPU fails
+    # slowly: one accepted request per step map and reduced precision is run)
+    accepted_run = set()
+    for sys, d in dims.items():
+        p = np.full(P.pitn_num_params(sys), 0.5)
+        x0 = np.full(d, 0.5)
+        for m in (P.PITN_STEP_EULER, P.PITN_STEP_RK4, P.PITN_STEP_BACKWARD_EULER, P.PITN_STEP_TRAPEZOID):
+            for prec in (P.PITN_PREC_MIXED_BF16, P.PITN_PREC_MIXED_FP32, P.PITN_PREC_FP64_FF,
+                         P.PITN_PREC_MIXED_TF32):
+                if prec in (P.PITN_PREC_MIXED_BF16, P.PITN_PREC_MIXED_TF32):
+                    valid = False
+                else:
+                    valid = reduced_ok(sys, m)
+                if valid and (m, prec) in accepted_run:
+                    continue
+                out = np.full((10, d), 7.0)
+                opt = P.make_options(method=m, precision=prec)
+                rc, _ = P.pitn_solve_ex(sys, p, x0, 1e-3, 10, d, 1e-10, 5, out, opt)
+                if valid:
+                    accepted_run.add((m, prec))
+                    assert rc != P.PITN_EINVAL, (sys, m, prec, rc)
+                else:
+                    assert rc == P.PITN_EINVAL and (out == 7.0).all(), (sys, m, prec, rc)
+    assert len(accepted_run) == 8
