@@ -170,3 +170,15 @@ def test_precision_support_matrix(lib):
                 else:
                     assert rc == P.PITN_EINVAL and (out == 7.0).all(), (sys, m, prec, rc)
     assert len(accepted_run) == 8
+
+
+def test_batch_work_before_any_batch_solve(lib):
+    """pitn_batch_work reports zeros until a batch solve has run in the
+    process, and refuses NULL pointers."""
+    import subprocess
+    import sys
+    code = ("import ctypes; from paper_2511_01465_gb300 import pitn as P; "
+            "print(P.pitn_batch_work(), P.lib().pitn_batch_work(None, None))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "(0, 0) -1"
